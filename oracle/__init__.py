@@ -1,0 +1,278 @@
+"""CPU oracle for the half-precision staggered-grid wave scheme -- TEST INFRASTRUCTURE.
+
+This package is the reference that the CUDA path is checked against. It is a
+plain, slow restatement of Gao & Harms, "Half precision wave simulation"
+(arXiv 2310.00236): the fourth-order staggered leapfrog scheme of Section 3
+(Eq. 1 acoustic, Eq. 2 elastic in Appendix A) with every operation rounded to
+a chosen format, and the plain (Algorithm 1) or compensated (Algorithm 2,
+Code 1 / Code 2) solution update.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it. It shares no code with the CUDA path and never
+imports the product package.
+
+Parity status of each function is stated in its docstring; functions without a
+pin that is independent of this file say "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wave_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+FP64, FP32, FP16, BF16 = 0, 1, 2, 3
+BC_PERIODIC, BC_RIGID = 0, 1
+FORMAT_NAMES = {"fp64": FP64, "fp32": FP32, "fp16": FP16, "bf16": BF16}
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (gcc, no contraction, no fast-math, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-fopenmp", _SRC, "-o", _LIB + ".tmp", "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        dp = C.POINTER(C.c_double)
+        i64 = C.c_int64
+        L.orc_round.restype = C.c_double
+        L.orc_round.argtypes = [C.c_double, C.c_int]
+        L.orc_round_array.argtypes = [i64, dp, C.c_int, dp]
+        L.orc_op_array.argtypes = [i64, C.c_int, dp, dp, C.c_int, dp]
+        L.orc_sum_op_array.argtypes = [i64, C.c_int, dp, dp, C.c_int, dp, dp]
+        L.orc_stencil_c2.restype = C.c_double
+        L.orc_stencil_c2.argtypes = [C.c_int]
+        L.orc_acoustic_apply_walls.argtypes = [C.c_void_p, dp, dp, dp, dp]
+        L.orc_acoustic_run.restype = C.c_int
+        L.orc_acoustic_run.argtypes = ([C.c_void_p] + [dp] * 8 + [dp] * 4 +
+                                       [i64, i64, i64, i64, dp, C.c_int32, i64,
+                                        C.POINTER(C.c_int64), dp, dp])
+        L.orc_acoustic_coefficients.restype = C.c_int
+        L.orc_acoustic_coefficients.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double,
+                                                dp, dp, dp, dp, dp, dp, dp]
+        L.orc_scale_pressure.argtypes = [i64, dp, C.c_double, C.c_int, dp]
+        L.orc_scale_velocity.argtypes = [i64, dp, C.c_double, C.c_double, C.c_int, dp]
+        L.orc_scale_source.argtypes = [i64, dp, C.c_double, C.c_double, C.c_double, C.c_int,
+                                       C.c_int, dp]
+        L.orc_energy_factor.restype = C.c_double
+        L.orc_energy_factor.argtypes = [C.c_double] * 4 + [C.c_int]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# Formats and arithmetic (Section 2, Table 1)
+# --------------------------------------------------------------------------
+
+def round_to(x, fmt: int) -> np.ndarray:
+    """Round binary64 values to the nearest value of `fmt`, ties to even.
+
+    Pinned against numpy's binary16 / binary32 conversions and torch's
+    bfloat16 conversion, and against the Table 1 constants.
+    """
+    x = _f64(x)
+    out = np.empty_like(x)
+    lib().orc_round_array(x.size, _dp(x), fmt, _dp(out))
+    return out
+
+
+def op(name: str, a, b, fmt: int) -> np.ndarray:
+    """Correctly rounded a+b, a-b or a*b in `fmt` (Section 2's IEEE model).
+
+    Pinned against numpy float16/float32 and torch bfloat16 arithmetic.
+    """
+    a, b = np.broadcast_arrays(_f64(a), _f64(b))
+    a, b = _f64(a), _f64(b)
+    out = np.empty_like(a)
+    lib().orc_op_array(a.size, {"add": 0, "sub": 1, "mul": 2}[name], _dp(a), _dp(b), fmt, _dp(out))
+    return out
+
+
+def compensated_sum(variant: int, a, b, fmt: int):
+    """sum_3op (Code 1) or sum_6op (Code 2) of Section 4, element-wise.
+
+    Pinned by the error-free-transformation identity a + b = s + t checked in
+    exact (binary64) arithmetic, for sum_3op when |a| >= |b|.
+    """
+    a, b = np.broadcast_arrays(_f64(a), _f64(b))
+    a, b = _f64(a), _f64(b)
+    s = np.empty_like(a)
+    t = np.empty_like(a)
+    lib().orc_sum_op_array(a.size, variant, _dp(a), _dp(b), fmt, _dp(s), _dp(t))
+    return s, t
+
+
+def stencil_c2(fmt: int) -> float:
+    """The 1/24 stencil weight rounded to `fmt` (Section 3)."""
+    return lib().orc_stencil_c2(fmt)
+
+
+# --------------------------------------------------------------------------
+# Acoustic solver (Eq. 1, Algorithms 1 and 2)
+# --------------------------------------------------------------------------
+
+class AcousticCfg(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("bc", C.c_int32 * 3), ("n", C.c_int64 * 3),
+                ("store_fmt", C.c_int32), ("arith_fmt", C.c_int32),
+                ("stencil_fmt", C.c_int32), ("comp", C.c_int32)]
+
+
+def acoustic_cfg(shape, bc, store_fmt, comp, arith_fmt=None, stencil_fmt=None) -> AcousticCfg:
+    """shape: cells per axis, ordered (x, y[, z]); bc: one code per axis."""
+    nd = len(shape)
+    cfg = AcousticCfg()
+    cfg.ndim = nd
+    for ax in range(3):
+        cfg.n[ax] = shape[ax] if ax < nd else 1
+        cfg.bc[ax] = bc[ax] if ax < nd else BC_PERIODIC
+    cfg.store_fmt = store_fmt
+    cfg.arith_fmt = store_fmt if arith_fmt is None else arith_fmt
+    cfg.stencil_fmt = cfg.arith_fmt if stencil_fmt is None else stencil_fmt
+    cfg.comp = comp
+    return cfg
+
+
+class AcousticState:
+    """Fields stored as numpy float64 arrays shaped (z, y, x) (or (y, x) in 2D),
+    x fastest, each value representable in the storage format."""
+
+    def __init__(self, cfg: AcousticCfg):
+        self.cfg = cfg
+        nd = cfg.ndim
+        self.shape = tuple(int(cfg.n[a]) for a in range(nd))[::-1]
+        z = lambda: np.zeros(self.shape, np.float64)
+        self.p, self.tp = z(), z()
+        self.v = [z() for _ in range(3)]
+        self.tv = [z() for _ in range(3)]
+        self.a = [np.zeros(self.shape) for _ in range(3)]
+        self.b = np.zeros(self.shape)
+        self.step = 0
+        self.src_index = -1
+        self.src = None
+
+    def copy(self):
+        s = AcousticState(self.cfg)
+        s.p, s.tp = self.p.copy(), self.tp.copy()
+        s.v = [x.copy() for x in self.v]
+        s.tv = [x.copy() for x in self.tv]
+        s.a = [x.copy() for x in self.a]
+        s.b = self.b.copy()
+        s.step, s.src_index, s.src = self.step, self.src_index, self.src
+        return s
+
+    def apply_walls(self):
+        lib().orc_acoustic_apply_walls(C.byref(self.cfg), _dp(self.p), _dp(self.v[0]),
+                                       _dp(self.v[1]), _dp(self.v[2]))
+
+    def run(self, nsteps: int, rec_field: int = 0, rec_index=None, energy: bool = False):
+        """Advance `nsteps` steps; returns (traces [nsteps, nrec] or None,
+        scaled energies [nsteps] or None)."""
+        nrec = 0 if rec_index is None else len(rec_index)
+        traces = np.zeros((nsteps, nrec)) if nrec else None
+        en = np.zeros(nsteps) if energy else None
+        ri = None
+        if nrec:
+            ri_arr = np.ascontiguousarray(rec_index, dtype=np.int64)
+            ri = ri_arr.ctypes.data_as(C.POINTER(C.c_int64))
+        src = None if self.src is None else _f64(self.src)
+        rc = lib().orc_acoustic_run(
+            C.byref(self.cfg), _dp(self.p), _dp(self.tp), _dp(self.v[0]), _dp(self.tv[0]),
+            _dp(self.v[1]), _dp(self.tv[1]), _dp(self.v[2]), _dp(self.tv[2]),
+            _dp(self.a[0]), _dp(self.a[1]), _dp(self.a[2]), _dp(self.b),
+            nsteps, self.step, self.src_index, 0 if src is None else src.size, _dp(src),
+            rec_field, nrec, ri, _dp(traces), _dp(en))
+        if rc != 0:
+            raise MemoryError("oracle run failed")
+        self.step += nsteps
+        return traces, en
+
+
+def acoustic_coefficients(cfg: AcousticCfg, h: float, dt: float, P0: float, rho, c):
+    """Per-point multipliers a_x, a_y, a_z (at v points) and b (at p nodes).
+
+    Returns (a list, b, Z0, ok). Pinned through the uniform case (a = b = CFL,
+    exactly) and the exact energy conservation that uses these values.
+    """
+    rho, c = _f64(rho), _f64(c)
+    shape = rho.shape
+    a = [np.zeros(shape) for _ in range(3)]
+    b = np.zeros(shape)
+    z0 = C.c_double(0.0)
+    bad = lib().orc_acoustic_coefficients(C.byref(cfg), h, dt, P0, _dp(rho), _dp(c), _dp(a[0]),
+                                          _dp(a[1]), _dp(a[2]), _dp(b), C.byref(z0))
+    return a, b, z0.value, bad == 0
+
+
+def scale_pressure(p, P0, fmt):
+    """p^ = RN(p / P0). parity unpinned beyond the rounding pins."""
+    p = _f64(p)
+    out = np.empty_like(p)
+    lib().orc_scale_pressure(p.size, _dp(p), P0, fmt, _dp(out))
+    return out
+
+
+def scale_velocity(v, Z0, P0, fmt):
+    """v^ = RN(v * Z0 / P0). parity unpinned beyond the rounding pins."""
+    v = _f64(v)
+    out = np.empty_like(v)
+    lib().orc_scale_velocity(v.size, _dp(v), Z0, P0, fmt, _dp(out))
+    return out
+
+
+def scale_source(w, Z0, P0, h, ndim, fmt):
+    """Scaled point-source values s^ = RN(w Z0 / (P0 h^(d-1)))."""
+    w = _f64(w)
+    out = np.empty_like(w)
+    lib().orc_scale_source(w.size, _dp(w), Z0, P0, h, ndim, fmt, _dp(out))
+    return out
+
+
+def energy_factor(h, dt, P0, Z0, ndim) -> float:
+    return lib().orc_energy_factor(h, dt, P0, Z0, ndim)
+
+
+def acoustic_setup(shape, bc, h, dt, rho, c, store_fmt, comp, P0=1.0, arith_fmt=None,
+                   stencil_fmt=None, p0=None, v0=None):
+    """Build a ready-to-run AcousticState from physical inputs: coefficients
+    (rounded once), scaled and rounded initial fields, walls applied."""
+    cfg = acoustic_cfg(shape, bc, store_fmt, comp, arith_fmt, stencil_fmt)
+    st = AcousticState(cfg)
+    a, b, Z0, ok = acoustic_coefficients(cfg, h, dt, P0, rho, c)
+    if not ok:
+        raise ValueError("coefficient outside the storage format's normal range")
+    st.a, st.b, st.Z0, st.P0, st.h, st.dt = a, b, Z0, P0, h, dt
+    if p0 is not None:
+        st.p = scale_pressure(p0, P0, store_fmt).reshape(st.shape)
+    if v0 is not None:
+        for ax, vv in enumerate(v0):
+            if vv is not None:
+                st.v[ax] = scale_velocity(vv, Z0, P0, store_fmt).reshape(st.shape)
+    st.apply_walls()
+    return st

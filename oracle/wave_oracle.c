@@ -1,0 +1,444 @@
+/*
+ * wave_oracle.c -- TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.
+ *
+ * A plain, slow CPU restatement of the method of Gao & Harms, "Half precision
+ * wave simulation" (arXiv 2310.00236): the staggered-grid, fourth-order,
+ * leapfrog discretisation of the first-order acoustic system (Eq. 1) and of the
+ * 2D isotropic elastic velocity-stress system (Eq. 2, Appendix A), with every
+ * arithmetic operation rounded to a chosen IEEE format and the solution update
+ * done either as a plain sum (Algorithm 1) or as a compensated sum
+ * (Algorithm 2, with the 3-operation or 6-operation error-free sum of Code 1 /
+ * Code 2 in Section 4).
+ *
+ * Only the test-suite, the smoke check and the benchmark's CPU-baseline leg
+ * load this library. It shares no code with the CUDA path.
+ *
+ * Representation: every field, compensation and coefficient value is held in a
+ * C double that is exactly representable in the field's storage format. Every
+ * operation "x op y" in a format F is evaluated as RN_F(x op y) where the
+ * inner op is the host's IEEE binary64 operation and RN_F is the
+ * round-to-nearest-even conversion below. For binary16 operands the binary64
+ * sum, difference and product are exact, so this is a single rounding. For
+ * bfloat16 and binary32 operands binary64 has at least 2p+2 bits, so rounding
+ * twice gives the same result as rounding once (the classical double-rounding
+ * condition for +, -, *; Section 2 of the paper states the correctly-rounded
+ * IEEE model that this reproduces).
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared -fopenmp
+ * (no -ffast-math: the rounding and the order of every operation matter).
+ */
+#include <math.h>
+#include <float.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Formats (Table 1 of Section 2; bfloat16 added).                          */
+/* ------------------------------------------------------------------------ */
+
+enum { ORC_FP64 = 0, ORC_FP32 = 1, ORC_FP16 = 2, ORC_BF16 = 3 };
+
+typedef struct {
+    int precision;  /* significand bits including the hidden bit */
+    int emin;       /* exponent of the smallest normal number */
+    double maxv;    /* largest finite value */
+} orc_format;
+
+static const orc_format FORMATS[4] = {
+    {53, -1022, DBL_MAX},
+    {24, -126, FLT_MAX},
+    {11, -14, 65504.0},
+    {8, -126, 3.38953138925153547590470800371487866880e38}, /* (2 - 2^-7) * 2^127 */
+};
+
+/* Round x to the nearest value of format fmt, ties to even (IEEE 754
+ * roundTiesToEven), with gradual underflow and overflow to infinity.
+ * Scaling by a power of two is exact, and nearbyint() rounds to the nearest
+ * integer with ties to even in the default rounding mode. */
+double orc_round(double x, int fmt)
+{
+    if (fmt == ORC_FP64 || x == 0.0 || !isfinite(x)) return x;
+    const orc_format *f = &FORMATS[fmt];
+    double ax = fabs(x);
+    int e = ilogb(ax);                       /* floor(log2 |x|) */
+    if (e < f->emin) e = f->emin;            /* subnormal range: fixed quantum */
+    double quantum = ldexp(1.0, e - (f->precision - 1));
+    double r = nearbyint(ax / quantum) * quantum;
+    if (r > f->maxv) r = INFINITY;
+    return copysign(r, x);
+}
+
+void orc_round_array(int64_t n, const double *x, int fmt, double *out)
+{
+    for (int64_t i = 0; i < n; i++) out[i] = orc_round(x[i], fmt);
+}
+
+/* Element-wise rounded operations, exposed for the arithmetic pins. */
+void orc_op_array(int64_t n, int op, const double *a, const double *b, int fmt, double *out)
+{
+    for (int64_t i = 0; i < n; i++) {
+        double r;
+        switch (op) {
+        case 0: r = a[i] + b[i]; break;
+        case 1: r = a[i] - b[i]; break;
+        default: r = a[i] * b[i]; break;
+        }
+        out[i] = orc_round(r, fmt);
+    }
+}
+
+static inline double add_f(double a, double b, int f) { return orc_round(a + b, f); }
+static inline double sub_f(double a, double b, int f) { return orc_round(a - b, f); }
+static inline double mul_f(double a, double b, int f) { return orc_round(a * b, f); }
+
+/* Compensated sums of Section 4.
+ * sum_3op (Code 1): s = a + b; z = s - a; t = b - z.  Error free when |a| >= |b|.
+ * sum_6op (Code 2): s = a + b; pa = s - b; pb = s - pa; da = a - pa; db = b - pb;
+ *                   t = da + db.  Error free for any order of magnitudes. */
+static void sum_3op(double a, double b, int f, double *s, double *t)
+{
+    double s_ = add_f(a, b, f);
+    double z = sub_f(s_, a, f);
+    *t = sub_f(b, z, f);
+    *s = s_;
+}
+
+static void sum_6op(double a, double b, int f, double *s, double *t)
+{
+    double s_ = add_f(a, b, f);
+    double pa = sub_f(s_, b, f);
+    double pb = sub_f(s_, pa, f);
+    double da = sub_f(a, pa, f);
+    double db = sub_f(b, pb, f);
+    *t = add_f(da, db, f);
+    *s = s_;
+}
+
+void orc_sum_op_array(int64_t n, int variant, const double *a, const double *b, int fmt,
+                      double *s, double *t)
+{
+    for (int64_t i = 0; i < n; i++) {
+        if (variant == 3) sum_3op(a[i], b[i], fmt, &s[i], &t[i]);
+        else sum_6op(a[i], b[i], fmt, &s[i], &t[i]);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Grid, boundaries and the stencil (Section 3, Fig. 1 reading).            */
+/* ------------------------------------------------------------------------ */
+
+enum { ORC_BC_PERIODIC = 0, ORC_BC_RIGID = 1 };
+
+/* Along one axis with N cells, a field lives either on the nodes m = 0..N-1
+ * (node N is the wall or, periodically, node 0) or at the half points
+ * m + 1/2, m = 0..N-1. Reading index m outside 0..N-1:
+ *   periodic: wrap around the domain (Section 3);
+ *   rigid (p = 0 on the walls at nodes 0 and N): node fields are odd about
+ *     the walls, half-point fields are even about them.
+ * Returns the sign (+1, -1, or 0 for the wall node N itself) and the index. */
+static int map_axis(int64_t m, int64_t N, int bc, int node, int64_t *out)
+{
+    if (m >= 0 && m < N) { *out = m; return 1; }
+    if (bc == ORC_BC_PERIODIC) { *out = ((m % N) + N) % N; return 1; }
+    if (node) {
+        if (m < 0) { *out = -m; return -1; }
+        if (m == N) { *out = 0; return 0; }
+        *out = 2 * N - m; return -1;
+    }
+    if (m < 0) { *out = -1 - m; return 1; }
+    *out = 2 * N - 1 - m; return 1;
+}
+
+typedef struct {
+    int32_t ndim;
+    int32_t bc[3];
+    int64_t n[3];
+    int32_t store_fmt;
+    int32_t arith_fmt;
+    int32_t stencil_fmt;
+    int32_t comp;
+} orc_acoustic_cfg;
+
+static inline int64_t lin(const int64_t n[3], int64_t i, int64_t j, int64_t k)
+{
+    return i + n[0] * (j + n[1] * k);
+}
+
+/* Value of field f at the point whose coordinate along axis ax is replaced by m. */
+static double read_axis(const double *f, const int64_t n[3], const int32_t bc[3], int ax,
+                        int node, int64_t i, int64_t j, int64_t k, int64_t m)
+{
+    int64_t idx[3] = {i, j, k}, mm;
+    int sign = map_axis(m, n[ax], bc[ax], node, &mm);
+    if (sign == 0) return 0.0;
+    idx[ax] = mm;
+    double v = f[lin(n, idx[0], idx[1], idx[2])];
+    return sign > 0 ? v : -v;
+}
+
+/* Fourth-order staggered difference, coefficients [1/24, -9/8, 9/8, -1/24]
+ * (Section 3), evaluated as D = C1*(f[+1/2] - f[-1/2]) - C2*(f[+3/2] - f[-3/2])
+ * with C1 = 9/8 and C2 = 1/24 rounded to the stencil format. The value is the
+ * undivided difference (the 1/h factor lives in the coefficient). */
+static double stencil(double fm3, double fm1, double fp1, double fp3, int f)
+{
+    const double c1 = 9.0 / 8.0;
+    const double c2 = orc_round(1.0 / 24.0, f);
+    double t1 = sub_f(fp1, fm1, f);
+    double t2 = sub_f(fp3, fm3, f);
+    return sub_f(mul_f(c1, t1, f), mul_f(c2, t2, f), f);
+}
+
+double orc_stencil_c2(int fmt) { return orc_round(1.0 / 24.0, fmt); }
+
+/* Solution update V += inc of Algorithm 1 (comp = 0) or the compensated update
+ * of Algorithm 2 (comp = 3 or 6). The carried compensation T is added to the
+ * scaled increment before the error-free sum, R = T + inc; sum(V, R) -> (V, T).
+ * When the arithmetic format is wider than the storage format (half storage
+ * with binary32 registers), the sum is formed in the arithmetic format and
+ * the lost part is the difference between that sum and its stored rounding. */
+static void update(double *V, double *T, double inc, int comp, int af, int sf)
+{
+    if (comp == 0) {
+        *V = orc_round(add_f(*V, inc, af), sf);
+        return;
+    }
+    double R = add_f(*T, inc, af);
+    if (af == sf) {
+        double s, t;
+        if (comp == 3) sum_3op(*V, R, af, &s, &t);
+        else sum_6op(*V, R, af, &s, &t);
+        *V = s;
+        *T = t;
+    } else {
+        double s = add_f(*V, R, af);
+        double vs = orc_round(s, sf);
+        *T = orc_round(sub_f(s, vs, af), sf);
+        *V = vs;
+    }
+}
+
+/* Neumaier-compensated binary64 accumulation, for energies. */
+typedef struct { double s, c; } acc_t;
+static inline void acc_add(acc_t *a, double x)
+{
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+    else a->c += (x - t) + a->s;
+    a->s = t;
+}
+static inline double acc_val(const acc_t *a) { return a->s + a->c; }
+
+/* ------------------------------------------------------------------------ */
+/* Acoustic leapfrog (Eq. 1, Algorithms 1 and 2; 3D by adding vz and d/dz). */
+/* ------------------------------------------------------------------------ */
+
+/* Set the values that the rigid walls hold at zero: p on every wall node
+ * plane, and each velocity component on the wall planes of the axes it is
+ * not staggered along. */
+void orc_acoustic_apply_walls(const orc_acoustic_cfg *cfg, double *p, double *vx, double *vy,
+                              double *vz)
+{
+    const int64_t *n = cfg->n;
+    double *v[3] = {vx, vy, vz};
+    for (int64_t k = 0; k < n[2]; k++)
+        for (int64_t j = 0; j < n[1]; j++)
+            for (int64_t i = 0; i < n[0]; i++) {
+                int64_t idx[3] = {i, j, k};
+                int64_t q = lin(n, i, j, k);
+                int on_wall[3];
+                for (int ax = 0; ax < 3; ax++)
+                    on_wall[ax] = ax < cfg->ndim && cfg->bc[ax] == ORC_BC_RIGID && idx[ax] == 0;
+                if (on_wall[0] || on_wall[1] || on_wall[2]) p[q] = 0.0;
+                for (int c = 0; c < cfg->ndim; c++) {
+                    if (!v[c]) continue;
+                    for (int ax = 0; ax < cfg->ndim; ax++)
+                        if (ax != c && on_wall[ax]) v[c][q] = 0.0;
+                }
+            }
+}
+
+/* Advance nsteps leapfrog steps. State on entry: p^n, v^{n-1/2} and their
+ * compensations; on exit p^{n+nsteps}, v^{n+nsteps-1/2}.
+ * Per step (Algorithm 1/2 order): all velocity components from p^n, then p
+ * from the new velocities. The pressure right-hand side is
+ * R = Dx(vx) + Dy(vy) [+ Dz(vz)] [+ source], summed left to right.
+ * Energy (scaled units) after step n: E^{n+1/2} = sum v^2/a + sum p^n p^{n+1}/b
+ * over all stored points, with the rounded coefficients the scheme uses.
+ * src: scaled source values (already rounded to the arithmetic format) for
+ * global steps 0..src_nt-1, added at p point src_index; NULL for none.
+ * Receivers sample field rec_field (0 p, 1 vx, 2 vy, 3 vz) after each step. */
+int orc_acoustic_run(const orc_acoustic_cfg *cfg, double *p, double *tp, double *vx, double *tvx,
+                     double *vy, double *tvy, double *vz, double *tvz, const double *ax_c,
+                     const double *ay_c, const double *az_c, const double *b_c, int64_t nsteps,
+                     int64_t step0, int64_t src_index, int64_t src_nt, const double *src,
+                     int32_t rec_field, int64_t nrec, const int64_t *rec_index, double *traces,
+                     double *energy)
+{
+    const int64_t *n = cfg->n;
+    const int nd = cfg->ndim;
+    const int sf = cfg->store_fmt, af = cfg->arith_fmt, stf = cfg->stencil_fmt;
+    const int comp = cfg->comp;
+    double *v[3] = {vx, vy, vz}, *tv[3] = {tvx, tvy, tvz};
+    const double *a[3] = {ax_c, ay_c, az_c};
+    const int64_t npts = n[0] * n[1] * n[2];
+    double *rowacc = (double *)calloc((size_t)(n[1] * n[2]) * 2, sizeof(double));
+    if (!rowacc) return -1;
+
+    for (int64_t s = 0; s < nsteps; s++) {
+        const int64_t gstep = step0 + s;
+        /* velocity half step: v^{n+1/2} = v^{n-1/2} + a * D(p^n) */
+#pragma omp parallel for schedule(static)
+        for (int64_t jk = 0; jk < n[1] * n[2]; jk++) {
+            const int64_t j = jk % n[1], k = jk / n[1];
+            for (int64_t i = 0; i < n[0]; i++) {
+                const int64_t q = lin(n, i, j, k);
+                const int64_t idx[3] = {i, j, k};
+                for (int c = 0; c < nd; c++) {
+                    /* v_c sits at m + 1/2 along axis c; p at nodes m-1, m, m+1, m+2 */
+                    const int64_t m = idx[c];
+                    double fm3 = read_axis(p, n, cfg->bc, c, 1, i, j, k, m - 1);
+                    double fm1 = read_axis(p, n, cfg->bc, c, 1, i, j, k, m);
+                    double fp1 = read_axis(p, n, cfg->bc, c, 1, i, j, k, m + 1);
+                    double fp3 = read_axis(p, n, cfg->bc, c, 1, i, j, k, m + 2);
+                    double D = stencil(fm3, fm1, fp1, fp3, stf);
+                    double inc = orc_round(mul_f(a[c][q], D, stf), af);
+                    update(&v[c][q], &tv[c][q], inc, comp, af, sf);
+                }
+            }
+        }
+        /* pressure half step: p^{n+1} = p^n + b * (div v^{n+1/2} + s) */
+#pragma omp parallel for schedule(static)
+        for (int64_t jk = 0; jk < n[1] * n[2]; jk++) {
+            const int64_t j = jk % n[1], k = jk / n[1];
+            acc_t ep = {0.0, 0.0}, ev = {0.0, 0.0};
+            for (int64_t i = 0; i < n[0]; i++) {
+                const int64_t q = lin(n, i, j, k);
+                const int64_t idx[3] = {i, j, k};
+                double R = 0.0;
+                for (int c = 0; c < nd; c++) {
+                    /* p sits on node m along axis c; v_c at m-2, m-1, m, m+1 (+1/2) */
+                    const int64_t m = idx[c];
+                    double fm3 = read_axis(v[c], n, cfg->bc, c, 0, i, j, k, m - 2);
+                    double fm1 = read_axis(v[c], n, cfg->bc, c, 0, i, j, k, m - 1);
+                    double fp1 = read_axis(v[c], n, cfg->bc, c, 0, i, j, k, m);
+                    double fp3 = read_axis(v[c], n, cfg->bc, c, 0, i, j, k, m + 1);
+                    double D = stencil(fm3, fm1, fp1, fp3, stf);
+                    R = (c == 0) ? D : add_f(R, D, stf);
+                }
+                if (src && q == src_index && gstep < src_nt) R = add_f(R, src[gstep], stf);
+                double inc = orc_round(mul_f(b_c[q], R, stf), af);
+                const double p_old = p[q];
+                update(&p[q], &tp[q], inc, comp, af, sf);
+                if (energy) {
+                    acc_add(&ep, p_old * p[q] / b_c[q]);
+                    for (int c = 0; c < nd; c++) acc_add(&ev, v[c][q] * v[c][q] / a[c][q]);
+                }
+            }
+            rowacc[2 * jk] = acc_val(&ev);
+            rowacc[2 * jk + 1] = acc_val(&ep);
+        }
+        if (energy) {
+            acc_t e = {0.0, 0.0};
+            for (int64_t jk = 0; jk < n[1] * n[2]; jk++) {
+                acc_add(&e, rowacc[2 * jk]);
+                acc_add(&e, rowacc[2 * jk + 1]);
+            }
+            energy[s] = acc_val(&e);
+        }
+        if (traces && nrec > 0) {
+            const double *f = rec_field == 0 ? p : v[rec_field - 1];
+            for (int64_t r = 0; r < nrec; r++) {
+                int64_t q = rec_index[r];
+                traces[s * nrec + r] = (q >= 0 && q < npts) ? f[q] : 0.0;
+            }
+        }
+    }
+    free(rowacc);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Coefficient preparation and scaling (Section 5 "Range"; units chosen so  */
+/* that coefficients and fields stay inside the half-precision range).      */
+/* ------------------------------------------------------------------------ */
+
+/* Z0 = rho0 * c0 with rho0 = max rho, c0 = max c; field scales: p^ = p / P0,
+ * v^ = v * Z0 / P0. Per-point multipliers, computed in binary64 in exactly
+ * this order and rounded once to the storage format:
+ *   b   = (((dt * rho) * c) * c) / (Z0 * h)          at p nodes
+ *   a_c = ((dt * Z0) / h) / rho_c                     at v_c points
+ *   rho_c = (rho[m] + rho[m+1]) * 0.5 along axis c, where the neighbour m+1
+ *           wraps (periodic) or is clamped to m (rigid) at the last cell.
+ * Returns 0, or 1 if some coefficient is not a positive normal number of the
+ * storage format. */
+int orc_acoustic_coefficients(const orc_acoustic_cfg *cfg, double h, double dt, double P0,
+                              const double *rho, const double *c, double *ax_c, double *ay_c,
+                              double *az_c, double *b_c, double *Z0_out)
+{
+    const int64_t *n = cfg->n;
+    const int64_t npts = n[0] * n[1] * n[2];
+    const int sf = cfg->store_fmt;
+    double rho0 = 0.0, c0 = 0.0;
+    (void)P0;
+    for (int64_t q = 0; q < npts; q++) {
+        if (rho[q] > rho0) rho0 = rho[q];
+        if (c[q] > c0) c0 = c[q];
+    }
+    const double Z0 = rho0 * c0;
+    *Z0_out = Z0;
+    double *a[3] = {ax_c, ay_c, az_c};
+    int bad = 0;
+    const double tiny = ldexp(1.0, FORMATS[sf].emin);
+    for (int64_t k = 0; k < n[2]; k++)
+        for (int64_t j = 0; j < n[1]; j++)
+            for (int64_t i = 0; i < n[0]; i++) {
+                const int64_t q = lin(n, i, j, k);
+                const int64_t idx[3] = {i, j, k};
+                double bq = orc_round((((dt * rho[q]) * c[q]) * c[q]) / (Z0 * h), sf);
+                b_c[q] = bq;
+                if (!(bq >= tiny && isfinite(bq))) bad = 1;
+                for (int ax = 0; ax < cfg->ndim; ax++) {
+                    int64_t nb[3] = {i, j, k};
+                    int64_t m = idx[ax] + 1;
+                    if (m >= n[ax]) m = (cfg->bc[ax] == ORC_BC_PERIODIC) ? 0 : idx[ax];
+                    nb[ax] = m;
+                    double rho_c = (rho[q] + rho[lin(n, nb[0], nb[1], nb[2])]) * 0.5;
+                    double aq = orc_round(((dt * Z0) / h) / rho_c, sf);
+                    a[ax][q] = aq;
+                    if (!(aq >= tiny && isfinite(aq))) bad = 1;
+                }
+            }
+    return bad;
+}
+
+/* p^ = RN(p / P0) */
+void orc_scale_pressure(int64_t n, const double *in, double P0, int fmt, double *out)
+{
+    for (int64_t i = 0; i < n; i++) out[i] = orc_round(in[i] / P0, fmt);
+}
+
+/* v^ = RN((v * Z0) / P0) */
+void orc_scale_velocity(int64_t n, const double *in, double Z0, double P0, int fmt, double *out)
+{
+    for (int64_t i = 0; i < n; i++) out[i] = orc_round((in[i] * Z0) / P0, fmt);
+}
+
+/* A point source of strength w(t) on the pressure equation, as a discrete
+ * delta w / h^d, enters R (undivided-difference units) as
+ * s^ = RN(w * (Z0 / (P0 * h^(d-1)))), with h^(d-1) = h (2D) or h * h (3D). */
+void orc_scale_source(int64_t nt, const double *w, double Z0, double P0, double h, int ndim,
+                      int fmt, double *out)
+{
+    const double hd1 = (ndim == 2) ? h : h * h;
+    const double scale = Z0 / (P0 * hd1);
+    for (int64_t i = 0; i < nt; i++) out[i] = orc_round(w[i] * scale, fmt);
+}
+
+/* Physical energy from the scaled one: E = 0.5 * h^(d-1) * P0^2 * dt / Z0 * E^ */
+double orc_energy_factor(double h, double dt, double P0, double Z0, int ndim)
+{
+    const double hd1 = (ndim == 2) ? h : h * h;
+    return 0.5 * hd1 * P0 * P0 * dt / Z0;
+}

@@ -1,0 +1,115 @@
+"""Seeded synthetic inputs for the wave workloads.
+
+This module only draws and shapes input data (materials, initial fields,
+source wavelets). It holds none of the scheme's arithmetic, so both the CUDA
+path and the CPU oracle can be fed from it without sharing any of the method.
+
+Array convention: numpy float64, shaped (z, y, x) in 3D and (y, x) in 2D,
+x fastest. Along each axis with N cells and spacing h, p nodes sit at m*h for
+m = 0..N-1 (the node at N*h is the far wall, or node 0 again when periodic).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def node_coords(n: int, h: float) -> np.ndarray:
+    return np.arange(n, dtype=np.float64) * h
+
+
+def gaussian(shape, h: float, sigma: float, center=None, peak: float = 1.0) -> np.ndarray:
+    """Gaussian bump exp(-|x - xc|^2 / (2 sigma^2)) sampled on p nodes.
+
+    shape: cells per axis in (x, y[, z]) order; the result is reversed to
+    (z, y, x). The default centre is the domain centre, node N/2 on each axis.
+    """
+    nd = len(shape)
+    if center is None:
+        center = [0.5 * shape[a] * h for a in range(nd)]
+    grids = np.meshgrid(*[node_coords(shape[a], h) - center[a] for a in range(nd)],
+                        indexing="ij")
+    r2 = np.zeros(grids[0].shape)
+    for g in grids:
+        r2 += g * g
+    return np.ascontiguousarray((peak * np.exp(-r2 / (2.0 * sigma * sigma))).transpose())
+
+
+def smooth_random_field(shape, seed: int, sigma_cells: float, lo: float, hi: float,
+                        dtype=np.float64) -> np.ndarray:
+    """Gaussian-filtered white noise (periodic FFT filter), affinely rescaled
+    to [lo, hi]. shape in (x, y[, z]) order; result (z, y, x).
+
+    The noise is numpy's PCG64 standard normal with the given seed, drawn in
+    (z, y, x) order.
+    """
+    rshape = tuple(shape[::-1])
+    rng = np.random.default_rng(seed)
+    noise = rng.standard_normal(rshape, dtype=np.float32 if dtype == np.float32 else np.float64)
+    spec = np.fft.rfftn(noise)
+    del noise
+    kernel = None
+    for ax, n in enumerate(rshape):
+        if ax == len(rshape) - 1:
+            k = np.fft.rfftfreq(n)
+        else:
+            k = np.fft.fftfreq(n)
+        g = np.exp(-2.0 * (np.pi * sigma_cells * k) ** 2)
+        shp = [1] * len(rshape)
+        shp[ax] = g.size
+        g = g.reshape(shp)
+        kernel = g if kernel is None else kernel * g
+    spec *= kernel
+    field = np.fft.irfftn(spec, s=rshape, axes=tuple(range(len(rshape))))
+    del spec
+    fmin, fmax = float(field.min()), float(field.max())
+    field = lo + (field - fmin) * ((hi - lo) / (fmax - fmin))
+    return np.ascontiguousarray(field.astype(np.float64))
+
+
+def ricker(t: np.ndarray, f: float, t0: float) -> np.ndarray:
+    """Ricker wavelet (1 - 2 pi^2 f^2 tau^2) exp(-pi^2 f^2 tau^2), tau = t - t0."""
+    tau = np.asarray(t, dtype=np.float64) - t0
+    a = (np.pi * f * tau) ** 2
+    return (1.0 - 2.0 * a) * np.exp(-a)
+
+
+def ricker_table(nt: int, dt: float, f: float, t0: float | None = None,
+                 half_step: bool = True, cutoff: float | None = None) -> np.ndarray:
+    """Wavelet samples for steps 0..nt-1 at t = (n + 1/2) dt (pressure
+    sources) or t = n dt; t0 defaults to 1.2 / f. Samples after `cutoff`
+    seconds are zero."""
+    if t0 is None:
+        t0 = 1.2 / f
+    t = (np.arange(nt, dtype=np.float64) + (0.5 if half_step else 0.0)) * dt
+    w = ricker(t, f, t0)
+    if cutoff is not None:
+        w[t > cutoff] = 0.0
+    return w
+
+
+# ---------------------------------------------------------------------------
+# Workload recipes (sizes and value distributions of the benchmark configs)
+# ---------------------------------------------------------------------------
+
+def acoustic_2d_gaussian(n: int = 256, steps: int = 2000, cfl: float = 0.5, sigma: float = 0.05):
+    """2D acoustic, n x n cells on [0,1]^2, h = 1/n, rho = c = 1, p = 0 walls,
+    centred Gaussian initial pressure, v = 0, dt = cfl * h."""
+    h = 1.0 / n
+    return dict(ndim=2, shape=(n, n), h=h, dt=cfl * h, steps=steps,
+                rho=np.ones((n, n)), c=np.ones((n, n)),
+                p0=gaussian((n, n), h, sigma), P0=1.0)
+
+
+def acoustic_3d_random(n: int = 512, steps: int = 1000, cfl: float = 0.4, h: float = 10.0,
+                       seed: int = 0, sigma_cells: float = 16.0, vmin: float = 1500.0,
+                       vmax: float = 4500.0, rho: float = 1000.0, ic_sigma_cells: float = 6.0,
+                       smooth_dtype=np.float32):
+    """3D acoustic, n^3 cells, spacing h metres, density rho, smooth random
+    velocity in [vmin, vmax] (seeded Gaussian-filtered noise), p = 0 walls,
+    Gaussian initial pressure of width ic_sigma_cells * h and peak 1 Pa,
+    dt = cfl * h / vmax."""
+    shape = (n, n, n)
+    c = smooth_random_field(shape, seed, sigma_cells, vmin, vmax, dtype=smooth_dtype)
+    return dict(ndim=3, shape=shape, h=h, dt=cfl * h / vmax, steps=steps,
+                rho=np.full(c.shape, rho), c=c,
+                p0=gaussian(shape, h, ic_sigma_cells * h), P0=1.0)

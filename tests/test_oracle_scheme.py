@@ -1,0 +1,171 @@
+"""Pins for the oracle's time stepping (Section 3, Algorithms 1 and 2).
+
+* Exact discrete energy conservation of the FP64 scheme (Section 3 states the
+  discrete system conserves energy; the energy used is the leapfrog form
+  E^{n+1/2} = sum v^2/a + sum p^n p^{n+1}/b with the scheme's own coefficients).
+* Second-order convergence in time to an analytic standing mode.
+* Exact mirror / transpose symmetry in every precision for a centred Gaussian.
+* Special cases: zero stays zero; constant pressure with periodic walls stays.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2310_00236_gb300 import inputs
+
+
+def _drift(E):
+    return float(np.max(np.abs(E - E[0])) / abs(E[0]))
+
+
+def test_energy_conserved_fp64_2d_gaussian_2000_steps(oracle_lib):
+    """256^2 cells, rho = c = 1, p = 0 walls, CFL 0.5, 2000 steps."""
+    w = inputs.acoustic_2d_gaussian(256, 2000)
+    st = O.acoustic_setup(w["shape"], (O.BC_RIGID,) * 2, w["h"], w["dt"], w["rho"], w["c"],
+                          O.FP64, 0, p0=w["p0"])
+    _, E = st.run(w["steps"], energy=True)
+    assert _drift(E) <= 1e-12
+    assert E[0] > 0
+
+
+def test_energy_conserved_fp64_variable_media(oracle_lib):
+    """Variable density and speed, mixed boundaries, 2D and 3D."""
+    rng = np.random.default_rng(7)
+    for shape, bc in (((48, 40), (O.BC_RIGID, O.BC_PERIODIC)),
+                      ((20, 18, 16), (O.BC_PERIODIC, O.BC_RIGID, O.BC_RIGID))):
+        nd = len(shape)
+        h = 5.0
+        c = inputs.smooth_random_field(shape, 3, 3.0, 1500.0, 4500.0)
+        rho = inputs.smooth_random_field(shape, 4, 3.0, 1000.0, 2500.0)
+        dt = 0.45 * h / 4500.0 / np.sqrt(nd / 2.0)
+        p0 = inputs.gaussian(shape, h, 3 * h) + 0.1 * rng.standard_normal(c.shape)
+        v0 = [0.01 * rng.standard_normal(c.shape) for _ in range(nd)]
+        st = O.acoustic_setup(shape, bc, h, dt, rho, c, O.FP64, 0, P0=1.0, p0=p0, v0=v0)
+        _, E = st.run(300, energy=True)
+        assert _drift(E) <= 1e-12, (shape, _drift(E))
+
+
+def test_energy_formula_recomputed_outside_the_oracle(oracle_lib):
+    """The oracle's energy equals sum v^2/a + sum p^n p^{n+1}/b recomputed here
+    with numpy from the stepped states, and weighting with coefficients that are
+    not the ones the scheme rounded (here fp16-rounded vs exact) shows drift, so
+    the conservation pin depends on the weights being the scheme's own."""
+    n = 64
+    h = 1.0 / n
+    dt = 0.37 * h
+    c = inputs.smooth_random_field((n, n), 5, 4.0, 0.6, 1.0)
+    st = O.acoustic_setup((n, n), (O.BC_RIGID,) * 2, h, dt, np.ones((n, n)), c, O.FP64, 0,
+                          p0=inputs.gaussian((n, n), h, 0.1))
+    b_exact = dt * c * c / (1.0 * h)      # Z0 = 1 here
+    st16 = [O.round_to(x, O.FP16) for x in (st.a[0], st.a[1], st.b)]
+    st.a[0], st.a[1], st.b = st16
+    E_orc, E_ext, E_wrong = [], [], []
+    for _ in range(300):
+        p_old = st.p.copy()
+        _, E = st.run(1, energy=True)
+        E_orc.append(E[0])
+        kin = np.sum(st.v[0] ** 2 / st.a[0]) + np.sum(st.v[1] ** 2 / st.a[1])
+        E_ext.append(kin + np.sum(p_old * st.p / st.b))
+        E_wrong.append(kin + np.sum(p_old * st.p / b_exact))
+    E_orc, E_ext, E_wrong = map(np.array, (E_orc, E_ext, E_wrong))
+    np.testing.assert_allclose(E_orc, E_ext, rtol=1e-13)
+    assert _drift(E_orc) <= 1e-12
+    assert _drift(E_wrong) > 1e-7
+
+
+def _standing_mode(N, cfl, T, k=1, l=2):
+    """p = cos(w t) sin(k pi x) sin(l pi y) on [0,1]^2, p = 0 walls, rho = c = 1.
+    With rho dv/dt = grad p (Eq. 1 sign convention), v = sin(w t)/w grad(sin sin)."""
+    h = 1.0 / N
+    dt = cfl * h
+    nsteps = int(round(T / dt))
+    w = np.pi * np.hypot(k, l)
+    x = np.arange(N) * h
+    xh = x + 0.5 * h
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    p0 = np.sin(k * np.pi * X) * np.sin(l * np.pi * Y)
+    t_half = -0.5 * dt
+    Xh, Yn = np.meshgrid(xh, x, indexing="xy")
+    vx = np.sin(w * t_half) / w * k * np.pi * np.cos(k * np.pi * Xh) * np.sin(l * np.pi * Yn)
+    Xn, Yh = np.meshgrid(x, xh, indexing="xy")
+    vy = np.sin(w * t_half) / w * l * np.pi * np.sin(k * np.pi * Xn) * np.cos(l * np.pi * Yh)
+    st = O.acoustic_setup((N, N), (O.BC_RIGID,) * 2, h, dt, np.ones((N, N)), np.ones((N, N)),
+                          O.FP64, 0, p0=p0, v0=[vx, vy])
+    st.run(nsteps)
+    exact = np.cos(w * nsteps * dt) * p0
+    return np.max(np.abs(st.p - exact))
+
+
+def test_second_order_convergence_standing_mode(oracle_lib):
+    Ns = [32, 64, 128]
+    errs = [_standing_mode(N, 0.5, 0.5) for N in Ns]
+    slopes = np.diff(np.log(errs)) / np.diff(np.log([1.0 / N for N in Ns]))
+    assert np.all(np.abs(slopes - 2.0) < 0.1), (errs, slopes)
+
+
+def test_fourth_order_in_space_at_small_cfl(oracle_lib):
+    """At a tiny time step the spatial 4th-order error dominates."""
+    Ns = [16, 32]
+    errs = [_standing_mode(N, 0.02, 0.25, k=2, l=3) for N in Ns]
+    slope = np.log(errs[0] / errs[1]) / np.log(2.0)
+    assert 3.6 < slope < 4.4, (errs, slope)
+
+
+VARIANTS = [(O.FP16, 0, None), (O.FP16, 3, None), (O.FP16, 6, None), (O.BF16, 3, None),
+            (O.FP32, 0, None), (O.FP16, 3, O.FP32), (O.FP16, 0, O.FP32), (O.BF16, 3, O.FP32)]
+
+
+@pytest.mark.parametrize("fmt,comp,arith", VARIANTS)
+def test_centred_gaussian_symmetries_exact(oracle_lib, fmt, comp, arith):
+    N = 32
+    w = inputs.acoustic_2d_gaussian(N, 60, cfl=0.45, sigma=0.1)
+    st = O.acoustic_setup(w["shape"], (O.BC_RIGID,) * 2, w["h"], w["dt"], w["rho"], w["c"],
+                          fmt, comp, arith_fmt=arith, p0=w["p0"])
+    st.run(60)
+    p, vx, vy = st.p, st.v[0], st.v[1]
+    assert np.any(p != 0)
+    # transpose symmetry
+    assert np.array_equal(p, p.T)
+    assert np.array_equal(vx, vy.T)
+    assert np.array_equal(st.tp, st.tp.T)
+    # mirror about the centre node N/2: p[i] = p[N - i], vx[i] = -vx[N - 1 - i]
+    idx = np.arange(1, N)
+    assert np.array_equal(p[:, idx], p[:, N - idx])
+    assert np.array_equal(vx[:, :], -vx[:, ::-1])
+    assert np.array_equal(st.tv[0][:, :], -st.tv[0][:, ::-1])
+
+
+@pytest.mark.parametrize("fmt,comp,arith", VARIANTS)
+def test_zero_state_stays_zero(oracle_lib, fmt, comp, arith):
+    shape = (12, 10)
+    st = O.acoustic_setup(shape, (O.BC_RIGID, O.BC_PERIODIC), 0.1, 0.02,
+                          np.ones((10, 12)), np.ones((10, 12)), fmt, comp, arith_fmt=arith)
+    st.run(20)
+    for f in [st.p, st.tp, *st.v, *st.tv]:
+        assert not np.any(f)
+
+
+@pytest.mark.parametrize("fmt,comp,arith", VARIANTS)
+def test_constant_pressure_periodic_stays(oracle_lib, fmt, comp, arith):
+    shape = (12, 10, 8)
+    ones = np.ones((8, 10, 12))
+    st = O.acoustic_setup(shape, (O.BC_PERIODIC,) * 3, 0.1, 0.02, ones, ones, fmt, comp,
+                          arith_fmt=arith, p0=0.71 * ones)
+    p_init = st.p.copy()
+    st.run(15)
+    assert np.array_equal(st.p, p_init)
+    for f in [st.tp, *st.v, *st.tv]:
+        assert not np.any(f)
+
+
+def test_fp64_equals_fp32_to_roundoff(oracle_lib):
+    """FP32 tracks FP64 closely on a short run (Section 3: fp32 is adequate)."""
+    w = inputs.acoustic_2d_gaussian(64, 200)
+    r = {}
+    for fmt in (O.FP64, O.FP32):
+        st = O.acoustic_setup(w["shape"], (O.BC_RIGID,) * 2, w["h"], w["dt"], w["rho"], w["c"],
+                              fmt, 0, p0=w["p0"])
+        st.run(200)
+        r[fmt] = st.p
+    err = np.linalg.norm(r[O.FP32] - r[O.FP64]) / np.linalg.norm(r[O.FP64])
+    assert 0 < err < 1e-5
