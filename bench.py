@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark: grid-point updates per second of the half-precision compensated
+staggered-grid acoustic leapfrog on the 3D workload (512^3 cells, smooth random
+velocity 1500-4500 m/s, rho = 1000, p = 0 walls, Gaussian initial pressure,
+CFL 0.4), FP16 + sum_3op, with the FP32 path run beside it at the same size.
+
+One "step" is one full leapfrog step: velocity half step, pressure half step
+(with the discrete-energy accumulation of the last step of every call).
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun every rank runs its own replica (weak scaling, no exchange).
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpoint-updates/s & %HBM roofline, FP16+Kahan vs FP32 at matched energy drift"
+UNIT = "Gpoint-updates/s"
+
+# Algorithmic bytes per grid point of each kernel (each array read once and
+# written once per launch). Acoustic 3D, uniform a (constant density), per-point b.
+#   velocity half step : read p + v(3) [+ t_v(3)], write v(3) [+ t_v(3)]
+#   pressure half step : read v(3) + p [+ t_p] + b, write p [+ t_p]
+BYTES = {
+    ("fp16", True): {"kv": 2 + 6 + 6 + 6 + 6, "kp": 6 + 2 + 2 + 2 + 2 + 2},
+    ("fp16", False): {"kv": 2 + 6 + 6, "kp": 6 + 2 + 2 + 2},
+    ("fp32", False): {"kv": 4 + 12 + 12, "kp": 12 + 4 + 4 + 4},
+    ("fp32", True): {"kv": 4 + 12 + 12 + 12 + 12, "kp": 12 + 4 + 4 + 4 + 4 + 4},
+}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# -------------------------------------------------------------- workload
+def workload(n: int):
+    from paper_2310_00236_gb300 import inputs
+    return inputs.acoustic_3d_random(n=n)
+
+
+def run_variant(W, w, prec_name, comp, steps, warmup, timing=True):
+    """Create a context, warm up, time `steps` steps with CUDA events on the
+    library's stream. Returns dict of measurements."""
+    import torch
+    code = W.PRECISIONS[prec_name]
+    stream = torch.cuda.current_stream()
+    ctx = W.wave_create(w["shape"], w["h"], w["rho"], w["c"], w["dt"], code, comp,
+                        bc=[W.WAVE_BC_RIGID] * 6, field_scale=w["P0"], stream=stream.cuda_stream)
+    try:
+        W.wave_set_initial(ctx, W.WAVE_F_P, w["p0"])
+        W.wave_step(ctx, warmup)
+        W.wave_sync(ctx)
+        e0 = W.wave_energy(ctx)
+        if timing:
+            W.wave_set_timing(ctx, True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        W.wave_step(ctx, steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        e1 = W.wave_energy(ctx)
+        kt = {}
+        if timing:
+            for kind, name in ((0, "kv"), (1, "kp")):
+                nl, kms = W.wave_get_timing(ctx, kind)
+                kt[name] = (nl, kms)
+            W.wave_set_timing(ctx, False)
+    finally:
+        W.wave_destroy(ctx)
+    return {"ms": ms, "e0": e0, "e1": e1, "kt": kt}
+
+
+def run_e2e(W, w, prec_name, comp, steps):
+    """Same workload through the public API with host buffers: host initial
+    pressure in, K steps, host pressure field and energy out."""
+    import torch
+    code = W.PRECISIONS[prec_name]
+    stream = torch.cuda.current_stream()
+    ctx = W.wave_create(w["shape"], w["h"], w["rho"], w["c"], w["dt"], code, comp,
+                        bc=[W.WAVE_BC_RIGID] * 6, field_scale=w["P0"], stream=stream.cuda_stream)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        W.wave_set_initial(ctx, W.WAVE_F_P, w["p0"])
+        W.wave_step(ctx, steps)
+        p = W.wave_get_field(ctx, W.WAVE_F_P)
+        e = W.wave_energy(ctx)
+        t1 = time.perf_counter()
+    finally:
+        W.wave_destroy(ctx)
+    eb = 2 if prec_name != "fp32" else 4
+    npts = int(np.prod(w["shape"]))
+    return {"s": t1 - t0, "h2d": npts * eb, "d2h": npts * eb + 8, "energy": e,
+            "finite": bool(np.isfinite(p).all())}
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_sample(target_s: float = 12.0, n: int = 64):
+    """The CPU oracle (fp16 + sum_3op emulation, OpenMP on all host cores) on a
+    bounded sample of the workload: an n^3 grid of the same recipe. Runs
+    batches of steps until target_s seconds have elapsed."""
+    import oracle as O
+    from paper_2310_00236_gb300 import inputs
+    w = inputs.acoustic_3d_random(n=n, sigma_cells=16.0 * n / 512, ic_sigma_cells=6.0 * n / 512,
+                                  smooth_dtype=np.float64)
+    st = O.acoustic_setup(w["shape"], (1, 1, 1), w["h"], w["dt"], w["rho"], w["c"], O.FP16, 3,
+                          p0=w["p0"])
+    st.run(2)
+    steps, t0 = 0, time.perf_counter()
+    batch = 4
+    while time.perf_counter() - t0 < target_s:
+        st.run(batch)
+        steps += batch
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n ** 3 * steps / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n}^3 grid of the same recipe, fp16+sum_3op emulation, {steps} steps, "
+                      f"{dt:.1f} s"}
+
+
+# ------------------------------------------------------------------ main
+def dist_setup(backend):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def main_reference(args):
+    ws, rank, _ = dist_setup("gloo")
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2310_00236_gb300 import inputs
+    n = 64
+    w = inputs.acoustic_3d_random(n=n, sigma_cells=16.0 * n / 512, ic_sigma_cells=6.0 * n / 512,
+                                  smooth_dtype=np.float64)
+    st = O.acoustic_setup(w["shape"], (1, 1, 1), w["h"], w["dt"], w["rho"], w["c"], O.FP16, 3,
+                          p0=w["p0"])
+    st.run(args.warmup)
+    t0 = time.perf_counter()
+    st.run(args.steps)
+    dt = time.perf_counter() - t0
+    value = n ** 3 * args.steps / dt / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
+            "data": "synthetic",
+            "config": {"workload": "3d_acoustic_random_velocity_rigid_gaussian",
+                       "n": 512, "sample_n": n, "precision": "fp16", "compensation": "sum_3op"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n}^3 grid of the 512^3 recipe per step, "
+                                       f"fp16+sum_3op emulation"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return main_reference(args)
+
+    import torch
+    ws, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    from paper_2310_00236_gb300 import build as B
+    from paper_2310_00236_gb300 import wave as W
+    if not os.path.exists(B.LIB):
+        raise SystemExit("libwave.so missing: run __graft_entry__.build() first")
+    W.lib()
+
+    w = workload(args.n)
+    npts = int(np.prod(w["shape"]))
+    peak, peak_kind = load_peaks()
+
+    barrier(ws)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid).replace("GPU-", "")
+    except Exception:
+        gpu_id = str(local)
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    r16 = run_variant(W, w, "fp16", 3, args.steps, args.warmup)
+    clocks = sampler.stop()
+    t_max = max_over_ranks(r16["ms"], ws, device="cuda")
+    value = npts * args.steps * ws / (t_max * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (largest share of device time)
+    kt = r16["kt"]
+    dom = max(kt, key=lambda k: kt[k][1])
+    nl, kms = kt[dom]
+    bpp = BYTES[("fp16", True)][dom]
+    achieved = bpp * npts / (kms / nl * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": {"kv": "velocity half step", "kp": "pressure half step"}[dom],
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_kind": peak_kind, "traffic": None,
+            "bytes_per_point": bpp, "ms_per_launch": kms / nl,
+            "shares": {k: kt[k][1] / sum(v[1] for v in kt.values()) for k in kt}}
+    drift16 = abs(r16["e1"] - r16["e0"]) / abs(r16["e0"])
+
+    compare = None
+    if not args.no_compare:
+        r32 = run_variant(W, w, "fp32", 0, args.steps, args.warmup)
+        t32 = max_over_ranks(r32["ms"], ws, device="cuda")
+        compare = {"fp32": {"value": npts * args.steps * ws / (t32 * 1e-3) / 1e9,
+                            "ms_per_step": t32 / args.steps,
+                            "energy_drift": abs(r32["e1"] - r32["e0"]) / abs(r32["e0"])},
+                   "fp16_sum3op": {"value": value, "energy_drift": drift16}}
+
+    e2e = None
+    if not args.no_e2e:
+        r = run_e2e(W, w, "fp16", 3, args.steps)
+        t = max_over_ranks(r["s"], ws, device="cuda")
+        e2e = {"value": npts * args.steps * ws / t / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": r["h2d"] / args.steps, "d2h_bytes_per_step": r["d2h"] / args.steps,
+               "seconds": t}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = oracle_sample()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+                "config": {"workload": "3d_acoustic_random_velocity_rigid_gaussian",
+                           "n": args.n, "cells": npts, "h_m": w["h"], "cfl": 0.4,
+                           "precision": "fp16", "compensation": "sum_3op",
+                           "l2": "working set 2.4 GB > L2 (no flush needed)"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": sum(v[0] for v in kt.values()), "compare": compare,
+                "energy_drift": drift16}
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

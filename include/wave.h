@@ -1,0 +1,277 @@
+/*
+ * wave.h -- C ABI of the GB300 half-precision staggered-grid wave library.
+ *
+ * The library advances the first-order acoustic system (Eq. 1 of Gao & Harms,
+ * "Half precision wave simulation", arXiv 2310.00236; extended to 3D by adding
+ * v_z and d/dz) and the 2D isotropic elastic velocity-stress system (Eq. 2,
+ * Appendix A) with the fourth-order staggered stencil [1/24, -9/8, 9/8, -1/24]
+ * of Section 3 and the staggered leapfrog in time, storing every field in a
+ * chosen format and doing every solution update either as a plain sum
+ * (Algorithm 1) or as a compensated sum (Algorithm 2 with sum_3op / sum_6op,
+ * Code 1 / Code 2 of Section 4).
+ *
+ * Conventions for every entry point:
+ *  - Nothing is thrown across the ABI; every call returns a wave_status and,
+ *    on failure, wave_last_error() describes it (thread-local string).
+ *  - Host arrays passed in are owned by the caller and copied before return.
+ *  - Grid arrays are x fastest: value (i, j, k) sits at i + n[0]*(j + n[1]*k).
+ *  - Work is queued on the CUDA stream given to wave_create. wave_step returns
+ *    before the GPU finishes; CUDA errors it causes surface at the next call
+ *    that synchronises (wave_energy, wave_get_*, wave_sync) as WAVE_ECUDA.
+ *  - After any error other than WAVE_EINVAL, WAVE_ERANGE on input data, or
+ *    WAVE_ENOTIMPL, the context is poisoned: later calls on it return
+ *    WAVE_ESTATE until it is destroyed.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *
+ * Grid layout (the reading of Fig. 1, whose image is not available): along
+ * an axis with N cells of spacing h, pressure (and the normal stresses) sit
+ * on the nodes m*h, m = 0..N-1; the velocity component along that axis sits
+ * at (m + 1/2)*h. Every field is stored as an N-point array per axis with the
+ * same (i, j, k) indexing. Boundaries per axis:
+ *  - WAVE_BC_PERIODIC: the stencil wraps around the domain (Section 3).
+ *  - WAVE_BC_RIGID (acoustic): p = 0 on walls at node 0 and node N. The
+ *    scheme reads p as odd and the normal velocity as even about each wall,
+ *    which is the periodic scheme on the doubled domain, so the discrete
+ *    energy stays exactly conserved. Node 0 is stored and held at 0, node N
+ *    is not stored.
+ * Elastic boundaries are described at wave_create.
+ */
+#ifndef WAVE_H
+#define WAVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wave_ctx wave_ctx;
+
+typedef enum {
+    WAVE_OK = 0,
+    WAVE_EINVAL = 1,    /* bad argument; context unchanged */
+    WAVE_ENOMEM = 2,    /* device or host allocation failed */
+    WAVE_ERANGE = 3,    /* coefficient or input value outside the storage format's normal range */
+    WAVE_ECUDA = 4,     /* a CUDA call failed (message has the CUDA error) */
+    WAVE_ETIMEOUT = 5,  /* a bounded device wait expired */
+    WAVE_ESTATE = 6,    /* context poisoned by an earlier error */
+    WAVE_ENOTIMPL = 7   /* valid request this build does not implement */
+} wave_status;
+
+typedef enum { WAVE_ACOUSTIC = 0, WAVE_ELASTIC = 1 } wave_physics;
+
+/* Storage format of fields, compensations and coefficients, and the format
+ * the arithmetic is done in.
+ *   WAVE_FP32, WAVE_FP16, WAVE_BF16: store and compute in that format; every
+ *     +, -, * is one correctly rounded operation of the format (Section 2).
+ *   WAVE_FP16_F32ARITH, WAVE_BF16_F32ARITH: store in half / bfloat16, compute
+ *     in binary32 registers; with compensation the update forms s = V + (T +
+ *     inc) in binary32 and stores V' = RN(s), T' = RN(s - V') (not in the paper).
+ *   WAVE_FP64 is accepted only by the CPU oracle; wave_create returns
+ *     WAVE_ENOTIMPL for it. */
+typedef enum {
+    WAVE_FP64 = 0,
+    WAVE_FP32 = 1,
+    WAVE_FP16 = 2,
+    WAVE_BF16 = 3,
+    WAVE_FP16_F32ARITH = 4,
+    WAVE_BF16_F32ARITH = 5
+} wave_precision;
+
+/* Solution update: plain V += inc (Algorithm 1), or the compensated update of
+ * Algorithm 2 with the carried term added after the coefficient multiply:
+ * R = T + inc; (V, T) = sum(V, R) with sum_3op (Code 1) or sum_6op (Code 2).
+ * For the *_F32ARITH precisions WAVE_COMP_3OP and WAVE_COMP_6OP both select
+ * the binary32 compensated form described above. */
+typedef enum { WAVE_COMP_NONE = 0, WAVE_COMP_3OP = 3, WAVE_COMP_6OP = 6 } wave_comp;
+
+typedef enum { WAVE_BC_PERIODIC = 0, WAVE_BC_RIGID = 1, WAVE_BC_FREE = 2 } wave_bc;
+
+typedef enum {
+    WAVE_F_P = 0, WAVE_F_VX = 1, WAVE_F_VY = 2, WAVE_F_VZ = 3,
+    WAVE_F_SXX = 4, WAVE_F_SYY = 5, WAVE_F_SXY = 6
+} wave_field;
+
+typedef struct {
+    int32_t ndim;   /* 2 or 3 (elastic: 2) */
+    int64_t n[3];   /* cells per axis, x first; n[2] ignored in 2D. Each >= 8. */
+} wave_grid;
+
+typedef struct {
+    wave_physics kind;
+    const double *rho;  /* density, host, one value per p node (x fastest) */
+    const double *vp;   /* sound speed (acoustic) or P-wave speed (elastic), host */
+    const double *vs;   /* S-wave speed (elastic), host; NULL for acoustic */
+    int32_t bc[6];      /* per face: x-lo, x-hi, y-lo, y-hi, z-lo, z-hi.
+                           Acoustic: each axis uses one code on both faces. */
+} wave_materials;
+
+typedef struct {
+    double field_scale;  /* P0 > 0: stored p^ = p / P0 and v^ = v * Z0 / P0
+                            (Z0 = max(rho) * max(vp)); default 1.0 */
+    int32_t kernel;      /* 0: automatic choice; 1: generic kernels only */
+    int32_t reserved[7];
+} wave_options;
+
+/* Optional device allocator for the context's memory (for instance a caching
+ * allocator of the host application). alloc returns NULL on failure. Process
+ * wide; passing NULLs restores cudaMallocAsync / cudaFreeAsync on the
+ * context's stream. */
+typedef void *(*wave_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*wave_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+wave_status wave_set_allocator(wave_alloc_fn alloc, wave_free_fn free_fn, void *user);
+
+/*
+ * wave_create -- Section 3 (problem statement), Section 5 "Range" (units).
+ * Builds a context: validates the arguments, nondimensionalises the materials
+ * into per-point multipliers, rounds each once to the storage format, checks
+ * their range, and allocates the device state (all fields zero).
+ *   grid      cells per axis (>= 8 each)
+ *   spacing   h per axis in metres; all used axes must be equal (else EINVAL)
+ *   mat       host material arrays (copied) and boundary codes
+ *   dt        time step in seconds (> 0). Stability needs
+ *             max(vp) * dt / h <= 1 / (sqrt(ndim) * (9/8 + 1/24)).
+ *   prec, compensated   see the enums above
+ *   opt       NULL for defaults
+ *   cuda_stream  cudaStream_t to queue work on (NULL = legacy default stream)
+ *   out       receives the context
+ * Acoustic multipliers (binary64 in exactly this order, then one rounding):
+ *   Z0 = max(rho) * max(vp)
+ *   b   = (((dt * rho) * vp) * vp) / (Z0 * h)          at p nodes
+ *   a_c = ((dt * Z0) / h) / rho_c                      at v_c points
+ *   rho_c = (rho[m] + rho[m+1]) * 0.5 along axis c; at the last cell the
+ *   neighbour wraps (periodic) or is the cell itself (rigid).
+ * Elastic multipliers (WAVE_ELASTIC, 2D; mu = rho vs^2, lambda = rho vp^2 - 2 mu):
+ *   Z0 = max(rho) * max(vp);  bx = ((dt * Z0) / h) / rho_x, by likewise
+ *   (rho_x, rho_y as rho_c above); at sigma_xx/yy nodes
+ *   l2m = ((dt * (lambda + 2 mu)) / Z0) / h, lam = ((dt * lambda) / Z0) / h;
+ *   at sigma_xy points mu_xy = ((dt * mu_q) / Z0) / h with mu_q the
+ *   harmonic mean 4 / (1/mu + 1/mu + 1/mu + 1/mu) of the four surrounding
+ *   nodes (0 where any of them is 0).
+ * Elastic boundaries: x faces PERIODIC (both) or RIGID; y-lo FREE or RIGID;
+ * y-hi RIGID. RIGID is a frictionless rigid wall (normal velocity and shear
+ * stress odd, the other fields even about the wall); FREE is a traction-free
+ * surface in the zero-stress-outside form, whose wall sits half a cell above
+ * node row 0.
+ * Errors: EINVAL (bad grid, spacing, dt, enum, NULL pointer, unsupported BC),
+ * ERANGE (a multiplier is not a positive normal number of the storage format,
+ * or a material value is not positive and finite), ENOTIMPL (WAVE_FP64),
+ * ENOMEM, ECUDA.
+ */
+wave_status wave_create(const wave_grid *grid, const double spacing[3],
+                        const wave_materials *mat, double dt, wave_precision prec,
+                        wave_comp compensated, const wave_options *opt, void *cuda_stream,
+                        wave_ctx **out);
+
+/* wave_set_initial -- initial state (Section 3: the paper starts at rest; the
+ * benchmark configurations start from a Gaussian pressure). host_values holds
+ * one physical value per grid point (x fastest). Stored values are
+ * RN(p / P0) for pressure and stresses, RN((v * Z0) / P0) for velocities,
+ * rounded once to the storage format. Values a rigid wall holds at zero are
+ * set to zero. The field's compensation is reset to zero. Acoustic p is
+ * p^0; velocities are v^{-1/2}. Synchronous with respect to host_values.
+ * Errors: EINVAL (field not in this physics, NULL), ERANGE (non-finite input
+ * or a value that overflows the storage format). */
+wave_status wave_set_initial(wave_ctx *ctx, wave_field field, const double *host_values);
+
+/* wave_set_source -- point source (Section 3: a Ricker wavelet on p at one
+ * point; Appendix A: a vertical force on v_y). wavelet[s] is the physical
+ * source amplitude at global step s, for s < nt; later steps have none. It is
+ * stored as s^ = RN(w * (Z0 / (P0 * h^(d-1)))) in the arithmetic format and
+ * added to the right-hand side before the coefficient multiply (Algorithm 1,
+ * the source line of the pressure loop); for the elastic v_y source the
+ * scale is 1 / (P0 * h^(d-1)) * (Z0 / Z0) = 1 / (P0 * h) and it is added to
+ * the v_y right-hand side. idx is the grid point (i, j, k).
+ * Acoustic: field must be WAVE_F_P. Elastic: WAVE_F_VY. */
+wave_status wave_set_source(wave_ctx *ctx, wave_field field, const int64_t idx[3],
+                            const double *wavelet, int64_t nt);
+
+/* wave_set_receivers -- receiver time histories (Section 3: traces recorded
+ * at a receiver point). After every step s (counted from this call), the
+ * stored value of `field` at each of the nrec points idx[3*r..3*r+2] is
+ * written, converted exactly to binary32 and still in scaled units, to
+ * device_traces[s * nrec + r] for s < capacity_steps. device_traces is caller
+ * owned device memory of capacity_steps * nrec floats. nrec = 0 disables. */
+wave_status wave_set_receivers(wave_ctx *ctx, wave_field field, const int64_t *idx,
+                               int64_t nrec, float *device_traces, int64_t capacity_steps);
+
+/* wave_step -- advance n >= 0 leapfrog steps (Algorithm 1 / 2 per step:
+ * velocities from p^n, then p^{n+1} from the new velocities; elastic:
+ * velocities from the stresses, then the stresses). Asynchronous. The last
+ * step of each call also accumulates the discrete energy (wave_energy). */
+wave_status wave_step(wave_ctx *ctx, int64_t n);
+
+/* wave_set_energy_trace -- record the energy of every step into caller owned
+ * device memory: device_energy[s] (binary64, physical units) for steps s
+ * counted from this call, s < capacity. capacity = 0 disables. */
+wave_status wave_set_energy_trace(wave_ctx *ctx, double *device_energy, int64_t capacity);
+
+/* wave_energy -- discrete energy after the most recent step (Section 3 states
+ * the discrete system conserves an energy; its formula is the leapfrog form):
+ *   acoustic  E = 0.5 h^(d-1) P0^2 dt / Z0 * ( sum v^2 / a + sum p^n p^{n+1} / b )
+ *   elastic   E = 0.5 h P0^2 dt / Z0 * ( sum v^2 / b_v + sum sigma^n . C^-1 sigma^{n+1} )
+ * with the stored (rounded) values and multipliers; compensations are not
+ * included. Products are formed in binary32 (exact for half and bfloat16
+ * operands), divided once, summed with compensation per thread and in binary64
+ * across threads. Synchronises the stream. ESTATE if no step has run yet. */
+wave_status wave_energy(wave_ctx *ctx, double *E);
+
+/* wave_get_field -- physical values of a field (inverse of the scaling of
+ * wave_set_initial, in binary64), one per grid point. Synchronises. */
+wave_status wave_get_field(wave_ctx *ctx, wave_field field, double *host_out);
+
+/* wave_get_raw -- the stored bits of a field (compensation = 0) or of its
+ * compensation (compensation = 1): n[0]*n[1]*n[2] elements of the storage
+ * format (2 bytes for half / bfloat16, 4 for binary32), x fastest, no pitch.
+ * Synchronises. */
+wave_status wave_get_raw(wave_ctx *ctx, wave_field field, int32_t compensation, void *host_out);
+
+/* wave_set_raw -- inverse of wave_get_raw (no scaling, no wall masking). */
+wave_status wave_set_raw(wave_ctx *ctx, wave_field field, int32_t compensation,
+                         const void *host_in);
+
+/* wave_get_coefficient -- the rounded multipliers as binary64, one per grid
+ * point: which = 0 b (acoustic p) / l2m (elastic), 1..3 a_x..a_z (acoustic) /
+ * 1 bx, 2 by, 4 lam, 5 mu_xy (elastic). Also returns Z0 when Z0 != NULL. */
+wave_status wave_get_coefficient(wave_ctx *ctx, int32_t which, double *host_out, double *Z0);
+
+/* wave_get_state / wave_set_state -- checkpoint and resume: every field, its
+ * compensation, the step counter. *size is in/out (bytes); blob = NULL
+ * queries the size. The blob is only meaningful for a context created with
+ * the same arguments. Synchronises. */
+wave_status wave_get_state(wave_ctx *ctx, void *blob, size_t *size);
+wave_status wave_set_state(wave_ctx *ctx, const void *blob, size_t size);
+
+/* wave_sync -- wait for the queued work and report its errors. */
+wave_status wave_sync(wave_ctx *ctx);
+
+/* wave_steps_done -- global step counter. */
+wave_status wave_steps_done(wave_ctx *ctx, int64_t *steps);
+
+/* wave_set_timing / wave_get_timing -- per-kernel device time. While timing
+ * is enabled, wave_step brackets every kernel launch with CUDA events recorded
+ * on the context's stream. wave_get_timing synchronises and returns, for one
+ * kernel kind, the launches and their summed device time (milliseconds) since
+ * timing was last enabled. Kinds: 0 velocity half step, 1 pressure (or stress)
+ * half step including source and energy, 2 receiver sampling. Enabling resets
+ * the totals. Not part of the method; a measurement aid. */
+wave_status wave_set_timing(wave_ctx *ctx, int32_t enable);
+wave_status wave_get_timing(wave_ctx *ctx, int32_t kind, int64_t *launches, double *ms);
+
+/* wave_adjoint_step -- adjoint time stepping for the gradient with respect to
+ * the velocity model. Not in the paper; not implemented in this build:
+ * returns WAVE_ENOTIMPL. */
+wave_status wave_adjoint_step(wave_ctx *ctx, int64_t n, const float *residual_traces);
+
+void wave_destroy(wave_ctx *ctx);
+const char *wave_last_error(void);
+
+/* Build description: "sm_103a ..." plus the compile options that matter for
+ * bit-exactness (-fmad=false). */
+const char *wave_build_info(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WAVE_H */

@@ -1,0 +1,912 @@
+// wave_abi.cu -- the C ABI of include/wave.h: argument checking, coefficient
+// preparation (binary64, rounded once), device state, step launches, I/O.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "../../include/wave.h"
+#include "acoustic_common.cuh"
+#include "wave_kernels.h"
+
+using namespace wave;
+
+// ------------------------------------------------------------------ errors
+static thread_local char g_err[512] = "";
+
+static wave_status fail(wave_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+extern "C" const char *wave_last_error(void) { return g_err; }
+
+extern "C" const char *wave_build_info(void) {
+    return "libwave: sm_103a, -fmad=false, explicit .rn half/bfloat16/binary32 arithmetic";
+}
+
+// ------------------------------------------------------------- allocation
+static wave_alloc_fn g_alloc = nullptr;
+static wave_free_fn g_free = nullptr;
+static void *g_alloc_user = nullptr;
+
+extern "C" wave_status wave_set_allocator(wave_alloc_fn alloc, wave_free_fn free_fn, void *user) {
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(WAVE_EINVAL, "wave_set_allocator: give both functions or neither");
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_alloc_user = user;
+    return WAVE_OK;
+}
+
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    wave_free_fn free_fn = nullptr;  // allocator that owns it (nullptr: cudaFreeAsync)
+    void *user = nullptr;
+};
+
+// ------------------------------------------------------------ host rounding
+// Round a binary64 value to a binary format with `mant` fraction bits and
+// `expb` exponent bits, to nearest with ties to even, with gradual underflow
+// and overflow to infinity. Works on the integer fields of the binary64.
+static uint16_t round_bits16(double x, int mant, int expb) {
+    uint64_t u;
+    memcpy(&u, &x, 8);
+    const uint32_t sign = (u >> 63) ? (1u << (mant + expb)) : 0u;
+    const uint32_t ex = (uint32_t)((u >> 52) & 0x7FF);
+    const uint64_t fr = u & ((1ull << 52) - 1);
+    const int bias = (1 << (expb - 1)) - 1;
+    const uint32_t inf = ((1u << expb) - 1) << mant;
+    if (ex == 0x7FF) return (uint16_t)(sign | inf | (fr ? (1u << (mant - 1)) : 0u));
+    if (ex == 0) return (uint16_t)sign;
+    const int e = (int)ex - 1023;
+    const uint64_t m = fr | (1ull << 52);
+    const int emin = 1 - bias;
+    const int shift = 52 - mant + (e < emin ? emin - e : 0);
+    if (shift > 53) return (uint16_t)sign;
+    uint64_t q = m >> shift;
+    const uint64_t rem = m & ((1ull << shift) - 1);
+    const uint64_t halfway = 1ull << (shift - 1);
+    if (rem > halfway || (rem == halfway && (q & 1))) q++;
+    uint32_t bits = (e < emin) ? (uint32_t)q
+                               : ((uint32_t)(e + bias) << mant) + (uint32_t)q - (1u << mant);
+    if (bits >= inf) bits = inf;
+    return (uint16_t)(sign | bits);
+}
+
+static double half_to_double(uint16_t h) {
+    const int s = h >> 15, e = (h >> 10) & 0x1F, m = h & 0x3FF;
+    double v;
+    if (e == 0) v = ldexp((double)m, -24);
+    else if (e == 31) v = m ? NAN : INFINITY;
+    else v = ldexp((double)(m + 1024), e - 25);
+    return s ? -v : v;
+}
+
+static double bf16_to_double(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+// Storage-format helpers keyed by precision.
+static int elem_bytes(int prec) { return prec == PREC_FP32 ? 4 : 2; }
+static bool is_bf16_storage(int prec) { return prec == PREC_BF16 || prec == PREC_BF16_F32ARITH; }
+static bool arith_is_f32(int prec) {
+    return prec == PREC_FP32 || prec == PREC_FP16_F32ARITH || prec == PREC_BF16_F32ARITH;
+}
+
+// value -> storage bits (uint16 or float bits) ; returns false if not finite
+static inline void store_value(int prec, double x, void *dst, int64_t i) {
+    if (prec == PREC_FP32) {
+        static_cast<float *>(dst)[i] = (float)x;
+    } else if (is_bf16_storage(prec)) {
+        static_cast<uint16_t *>(dst)[i] = round_bits16(x, 7, 8);
+    } else {
+        static_cast<uint16_t *>(dst)[i] = round_bits16(x, 10, 5);
+    }
+}
+
+static inline double load_value(int prec, const void *src, int64_t i) {
+    if (prec == PREC_FP32) return (double)static_cast<const float *>(src)[i];
+    if (is_bf16_storage(prec)) return bf16_to_double(static_cast<const uint16_t *>(src)[i]);
+    return half_to_double(static_cast<const uint16_t *>(src)[i]);
+}
+
+// Smallest positive normal number of the storage format.
+static double min_normal(int prec) {
+    return (prec == PREC_FP16 || prec == PREC_FP16_F32ARITH) ? ldexp(1.0, -14) : ldexp(1.0, -126);
+}
+
+// Parallel loop over [0, n) on the host.
+template <class F>
+static void parallel_for(int64_t n, F f) {
+    unsigned nt = std::thread::hardware_concurrency();
+    if (nt == 0) nt = 1;
+    if (nt > 32) nt = 32;
+    if (n < (int64_t)1 << 20 || nt == 1) {
+        f((int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    int64_t chunk = (n + nt - 1) / nt;
+    for (unsigned t = 0; t < nt; t++) {
+        int64_t lo = t * chunk, hi = std::min(n, lo + chunk);
+        if (lo >= hi) break;
+        th.emplace_back([=]() { f(lo, hi); });
+    }
+    for (auto &x : th) x.join();
+}
+
+// ---------------------------------------------------------------- context
+struct wave_ctx {
+    int kind = WAVE_ACOUSTIC;
+    int ndim = 2;
+    int64_t n[3] = {1, 1, 1};
+    int64_t pitch = 0, plane = 0, total = 0;  // elements
+    int bc[6] = {0, 0, 0, 0, 0, 0};
+    int prec = PREC_FP16, comp = 0;
+    int kernel_choice = 0;
+    double h = 0, dt = 0, P0 = 1.0, Z0 = 1.0;
+    cudaStream_t stream = nullptr;
+    bool poisoned = false;
+    int64_t step = 0;
+    bool have_energy = false;
+
+    // fields and compensations; acoustic: 0 p, 1 vx, 2 vy, 3 vz
+    // elastic: 1 vx, 2 vy, 4 sxx, 5 syy, 6 sxy
+    DevBuf f[7], t[7];
+    // coefficients (per-point arrays when not uniform)
+    DevBuf coef[6];
+    uint32_t coef_uni[6] = {0, 0, 0, 0, 0, 0};
+    bool coef_is_uniform[6] = {false, false, false, false, false, false};
+    std::vector<double> coef_host[6];
+
+    DevBuf e_part, e_misc;   // e_misc: [double e_last][unsigned counter]
+    unsigned e_blocks = 0;
+    double *e_trace = nullptr;
+    int64_t e_trace_cap = 0, e_trace_pos = 0;
+
+    DevBuf src_table;
+    int64_t src_q = -1, src_nt = 0;
+    int src_field = -1;
+
+    // per-kernel timing (measurement aid)
+    bool timing = false;
+    struct TimedLaunch { int kind; cudaEvent_t a, b; };
+    std::vector<TimedLaunch> pending;
+    std::vector<cudaEvent_t> event_pool;
+    int64_t t_launches[3] = {0, 0, 0};
+    double t_ms[3] = {0, 0, 0};
+
+    DevBuf rec_q;
+    int64_t nrec = 0;
+    int rec_field = 0;
+    float *rec_traces = nullptr;
+    int64_t rec_cap = 0, rec_pos = 0;
+};
+
+static bool field_valid(const wave_ctx *c, int field) {
+    if (c->kind == WAVE_ACOUSTIC) return field >= 0 && field <= (c->ndim == 3 ? 3 : 2);
+    return field == WAVE_F_VX || field == WAVE_F_VY || field == WAVE_F_SXX ||
+           field == WAVE_F_SYY || field == WAVE_F_SXY;
+}
+
+static wave_status dev_alloc(wave_ctx *c, DevBuf &b, size_t bytes) {
+    b.bytes = bytes;
+    if (bytes == 0) return WAVE_OK;
+    if (g_alloc) {
+        b.ptr = g_alloc(bytes, (void *)c->stream, g_alloc_user);
+        b.free_fn = g_free;
+        b.user = g_alloc_user;
+        if (!b.ptr) return fail(WAVE_ENOMEM, "allocator returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMallocAsync(&b.ptr, bytes, c->stream);
+        if (e != cudaSuccess) {
+            b.ptr = nullptr;
+            cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? WAVE_ENOMEM : WAVE_ECUDA,
+                        "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+        }
+    }
+    cudaError_t e = cudaMemsetAsync(b.ptr, 0, bytes, c->stream);
+    if (e != cudaSuccess) return fail(WAVE_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    return WAVE_OK;
+}
+
+static void dev_free(wave_ctx *c, DevBuf &b) {
+    if (!b.ptr) return;
+    if (b.free_fn) b.free_fn(b.ptr, b.bytes, (void *)c->stream, b.user);
+    else cudaFreeAsync(b.ptr, c->stream);
+    b.ptr = nullptr;
+    b.bytes = 0;
+}
+
+static wave_status cuda_check(wave_ctx *c, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return WAVE_OK;
+    c->poisoned = true;
+    return fail(WAVE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CHECK_CTX(c)                                                                  \
+    do {                                                                              \
+        if (!(c)) return fail(WAVE_EINVAL, "%s: NULL context", __func__);             \
+        if ((c)->poisoned) return fail(WAVE_ESTATE, "%s: context poisoned", __func__); \
+    } while (0)
+
+// Copy a packed host array (n[0]*n[1]*n[2] elements) into a pitched field.
+static wave_status upload_packed(wave_ctx *c, void *dev, const void *host) {
+    const size_t eb = elem_bytes(c->prec);
+    cudaError_t e = cudaMemcpy2DAsync(dev, c->pitch * eb, host, c->n[0] * eb, c->n[0] * eb,
+                                      c->n[1] * c->n[2], cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_check(c, e, "upload");
+}
+
+static wave_status download_packed(wave_ctx *c, const void *dev, void *host) {
+    const size_t eb = elem_bytes(c->prec);
+    cudaError_t e = cudaMemcpy2DAsync(host, c->n[0] * eb, dev, c->pitch * eb, c->n[0] * eb,
+                                      c->n[1] * c->n[2], cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_check(c, e, "download");
+}
+
+// ------------------------------------------------------- acoustic creation
+static wave_status acoustic_coefficients(wave_ctx *c, const wave_materials *mat) {
+    const int64_t npts = c->n[0] * c->n[1] * c->n[2];
+    double rho0 = 0.0, c0 = 0.0;
+    for (int64_t q = 0; q < npts; q++) {
+        if (!(mat->rho[q] > 0.0) || !isfinite(mat->rho[q]) || !(mat->vp[q] > 0.0) ||
+            !isfinite(mat->vp[q]))
+            return fail(WAVE_ERANGE, "material value at point %lld is not positive and finite",
+                        (long long)q);
+        if (mat->rho[q] > rho0) rho0 = mat->rho[q];
+        if (mat->vp[q] > c0) c0 = mat->vp[q];
+    }
+    const double Z0 = rho0 * c0;
+    c->Z0 = Z0;
+    const double h = c->h, dt = c->dt;
+    const double tiny = min_normal(c->prec);
+    for (int w = 0; w < 4; w++) c->coef_host[w].assign(npts, 0.0);
+    std::vector<double> &b = c->coef_host[0];
+    const int64_t nx = c->n[0], ny = c->n[1];
+    const int64_t str[3] = {1, nx, nx * ny};
+    bool bad = false;
+    int64_t bad_q = -1;
+    for (int64_t q = 0; q < npts; q++) {
+        const int64_t idx[3] = {q % nx, (q / nx) % ny, q / (nx * ny)};
+        double v = (((dt * mat->rho[q]) * mat->vp[q]) * mat->vp[q]) / (Z0 * h);
+        double r;
+        {
+            uint16_t tmp16;
+            float tmp32;
+            if (c->prec == PREC_FP32) { tmp32 = (float)v; r = tmp32; }
+            else { store_value(c->prec, v, &tmp16, 0); r = load_value(c->prec, &tmp16, 0); }
+        }
+        b[q] = r;
+        if (!(r >= tiny) || !isfinite(r)) { bad = true; bad_q = q; }
+        for (int ax = 0; ax < c->ndim; ax++) {
+            int64_t m = idx[ax] + 1;
+            if (m >= c->n[ax]) m = (c->bc[2 * ax] == WAVE_BC_PERIODIC) ? 0 : idx[ax];
+            const int64_t nb = q + (m - idx[ax]) * str[ax];
+            const double rho_c = (mat->rho[q] + mat->rho[nb]) * 0.5;
+            double av = ((dt * Z0) / h) / rho_c;
+            double ar;
+            uint16_t tmp16;
+            float tmp32;
+            if (c->prec == PREC_FP32) { tmp32 = (float)av; ar = tmp32; }
+            else { store_value(c->prec, av, &tmp16, 0); ar = load_value(c->prec, &tmp16, 0); }
+            c->coef_host[1 + ax][q] = ar;
+            if (!(ar >= tiny) || !isfinite(ar)) { bad = true; bad_q = q; }
+        }
+    }
+    if (bad)
+        return fail(WAVE_ERANGE,
+                    "multiplier at point %lld is not a positive normal number of the storage "
+                    "format (rescale units or change dt)", (long long)bad_q);
+    return WAVE_OK;
+}
+
+// Upload coefficient w (0 b, 1..3 a_x..a_z) as a uniform value or an array.
+static wave_status upload_coef(wave_ctx *c, int w) {
+    const std::vector<double> &v = c->coef_host[w];
+    const int64_t npts = (int64_t)v.size();
+    bool uni = true;
+    for (int64_t q = 1; q < npts && uni; q++) uni = (v[q] == v[0]);
+    c->coef_is_uniform[w] = uni;
+    if (uni) {
+        if (c->prec == PREC_FP32) {
+            float f = (float)v[0];
+            memcpy(&c->coef_uni[w], &f, 4);
+        } else {
+            uint16_t hb;
+            store_value(c->prec, v[0], &hb, 0);
+            c->coef_uni[w] = hb;
+        }
+        return WAVE_OK;
+    }
+    const size_t eb = elem_bytes(c->prec);
+    wave_status st = dev_alloc(c, c->coef[w], c->total * eb);
+    if (st) return st;
+    std::vector<unsigned char> tmp(npts * eb);
+    for (int64_t q = 0; q < npts; q++) store_value(c->prec, v[q], tmp.data(), q);
+    return upload_packed(c, c->coef[w].ptr, tmp.data());
+}
+
+static void fill_acoustic_params(wave_ctx *c, AcParams &prm) {
+    memset(&prm, 0, sizeof prm);
+    for (int ax = 0; ax < 3; ax++) {
+        prm.n[ax] = (int)c->n[ax];
+        prm.bc[ax] = ax < c->ndim ? (c->bc[2 * ax] == WAVE_BC_PERIODIC ? BC_PERIODIC : BC_RIGID)
+                                  : BC_PERIODIC;
+    }
+    prm.sy = c->pitch;
+    prm.sz = c->plane;
+    prm.p = c->f[0].ptr;
+    prm.tp = c->t[0].ptr;
+    for (int ax = 0; ax < 3; ax++) {
+        prm.v[ax] = c->f[1 + ax].ptr;
+        prm.tv[ax] = c->t[1 + ax].ptr;
+        prm.a[ax] = c->coef_is_uniform[1 + ax] ? nullptr : c->coef[1 + ax].ptr;
+        prm.a_uni[ax] = c->coef_uni[1 + ax];
+    }
+    prm.b = c->coef_is_uniform[0] ? nullptr : c->coef[0].ptr;
+    prm.b_uni = c->coef_uni[0];
+    prm.src_q = c->src_field == WAVE_F_P ? c->src_q : -1;
+    prm.src = c->src_table.ptr;
+    prm.src_nt = c->src_nt;
+    prm.e_part = static_cast<double *>(c->e_part.ptr);
+    prm.e_count = reinterpret_cast<unsigned *>(static_cast<char *>(c->e_misc.ptr) + 8);
+    prm.e_out = static_cast<double *>(c->e_misc.ptr);
+    const double hd1 = c->ndim == 2 ? c->h : c->h * c->h;
+    prm.e_factor = 0.5 * hd1 * c->P0 * c->P0 * c->dt / c->Z0;
+}
+
+static cudaEvent_t take_event(wave_ctx *c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Record an event on the context stream when timing is on; returns it (or null).
+static cudaEvent_t mark(wave_ctx *c) {
+    if (!c->timing) return nullptr;
+    cudaEvent_t e = take_event(c);
+    cudaEventRecord(e, c->stream);
+    return e;
+}
+
+static void timed(wave_ctx *c, int kind, cudaEvent_t a, cudaEvent_t b) {
+    if (a && b) c->pending.push_back({kind, a, b});
+}
+
+// Sum the elapsed times of finished launch pairs (stream must be synchronised).
+static void collect_timing(wave_ctx *c) {
+    std::vector<cudaEvent_t> seen;
+    for (auto &t : c->pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t.a, t.b);
+        c->t_launches[t.kind]++;
+        c->t_ms[t.kind] += ms;
+        seen.push_back(t.a);
+        seen.push_back(t.b);
+    }
+    c->pending.clear();
+    std::sort(seen.begin(), seen.end());
+    seen.erase(std::unique(seen.begin(), seen.end()), seen.end());
+    for (auto e : seen) c->event_pool.push_back(e);
+}
+
+static void destroy_ctx(wave_ctx *c) {
+    if (!c) return;
+    for (auto &b : c->f) dev_free(c, b);
+    for (auto &b : c->t) dev_free(c, b);
+    for (auto &b : c->coef) dev_free(c, b);
+    dev_free(c, c->e_part);
+    dev_free(c, c->e_misc);
+    dev_free(c, c->src_table);
+    dev_free(c, c->rec_q);
+    cudaStreamSynchronize(c->stream);
+    collect_timing(c);
+    for (auto e : c->event_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+extern "C" void wave_destroy(wave_ctx *c) { destroy_ctx(c); }
+
+extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3],
+                                   const wave_materials *mat, double dt, wave_precision prec,
+                                   wave_comp compensated, const wave_options *opt,
+                                   void *cuda_stream, wave_ctx **out) {
+    if (!grid || !spacing || !mat || !out) return fail(WAVE_EINVAL, "wave_create: NULL argument");
+    *out = nullptr;
+    if (grid->ndim != 2 && grid->ndim != 3) return fail(WAVE_EINVAL, "ndim must be 2 or 3");
+    if (mat->kind != WAVE_ACOUSTIC && mat->kind != WAVE_ELASTIC)
+        return fail(WAVE_EINVAL, "unknown physics %d", (int)mat->kind);
+    if (mat->kind == WAVE_ELASTIC)
+        return fail(WAVE_ENOTIMPL, "elastic physics is not built yet");
+    for (int ax = 0; ax < grid->ndim; ax++) {
+        if (grid->n[ax] < 8) return fail(WAVE_EINVAL, "n[%d] = %lld < 8", ax, (long long)grid->n[ax]);
+        if (grid->n[ax] > (1 << 20)) return fail(WAVE_EINVAL, "n[%d] too large", ax);
+        if (!(spacing[ax] > 0.0) || !isfinite(spacing[ax]))
+            return fail(WAVE_EINVAL, "spacing[%d] must be positive", ax);
+        if (spacing[ax] != spacing[0]) return fail(WAVE_EINVAL, "spacing must be isotropic");
+    }
+    if (!(dt > 0.0) || !isfinite(dt)) return fail(WAVE_EINVAL, "dt must be positive and finite");
+    if (prec == WAVE_FP64) return fail(WAVE_ENOTIMPL, "WAVE_FP64 runs only in the CPU oracle");
+    if (prec < WAVE_FP32 || prec > WAVE_BF16_F32ARITH) return fail(WAVE_EINVAL, "bad precision");
+    if (compensated != WAVE_COMP_NONE && compensated != WAVE_COMP_3OP &&
+        compensated != WAVE_COMP_6OP)
+        return fail(WAVE_EINVAL, "bad compensation %d", (int)compensated);
+    if (!mat->rho || !mat->vp) return fail(WAVE_EINVAL, "material arrays are NULL");
+    if (mat->kind == WAVE_ELASTIC && !mat->vs) return fail(WAVE_EINVAL, "elastic needs vs");
+    double P0 = 1.0;
+    int kchoice = 0;
+    if (opt) {
+        if (opt->field_scale != 0.0) P0 = opt->field_scale;
+        kchoice = opt->kernel;
+    }
+    if (!(P0 > 0.0) || !isfinite(P0)) return fail(WAVE_EINVAL, "field_scale must be positive");
+    const int64_t npts = grid->n[0] * grid->n[1] * (grid->ndim == 3 ? grid->n[2] : 1);
+    if (npts > ((int64_t)1 << 31) - 1) return fail(WAVE_EINVAL, "grid too large (>= 2^31 points)");
+
+    wave_ctx *c = new (std::nothrow) wave_ctx();
+    if (!c) return fail(WAVE_ENOMEM, "host allocation failed");
+    c->kind = mat->kind;
+    c->ndim = grid->ndim;
+    for (int ax = 0; ax < 3; ax++) c->n[ax] = ax < grid->ndim ? grid->n[ax] : 1;
+    for (int fc = 0; fc < 6; fc++) c->bc[fc] = mat->bc[fc];
+    c->prec = prec;
+    c->comp = compensated;
+    c->kernel_choice = kchoice;
+    c->h = spacing[0];
+    c->dt = dt;
+    c->P0 = P0;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    // pitch: x extent rounded up to 16 elements (>= 32 bytes, 16-byte aligned rows)
+    c->pitch = (c->n[0] + 15) / 16 * 16;
+    c->plane = c->pitch * c->n[1];
+    c->total = c->plane * c->n[2];
+
+    wave_status st;
+    if (c->kind == WAVE_ACOUSTIC) {
+        for (int ax = 0; ax < 3; ax++) {
+            if (ax >= c->ndim) continue;
+            int lo = c->bc[2 * ax], hi = c->bc[2 * ax + 1];
+            if (lo != hi || (lo != WAVE_BC_PERIODIC && lo != WAVE_BC_RIGID)) {
+                delete c;
+                return fail(WAVE_EINVAL, "acoustic axis %d: faces must both be PERIODIC or RIGID",
+                            ax);
+            }
+        }
+        st = acoustic_coefficients(c, mat);
+        if (st) { delete c; return st; }
+        const size_t eb = elem_bytes(prec);
+        int nf = 1 + c->ndim;
+        for (int fi = 0; fi < nf && !st; fi++) {
+            st = dev_alloc(c, c->f[fi], c->total * eb);
+            if (!st && compensated) st = dev_alloc(c, c->t[fi], c->total * eb);
+        }
+        for (int w = 0; w < 1 + c->ndim && !st; w++) st = upload_coef(c, w);
+        AcParams prm;
+        fill_acoustic_params(c, prm);
+        c->e_blocks = acoustic_generic_blocks(prm, c->ndim);
+    }
+    if (!st) st = dev_alloc(c, c->e_part, sizeof(double) * (size_t)std::max(1u, c->e_blocks));
+    if (!st) st = dev_alloc(c, c->e_misc, 16);
+    if (!st) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) st = fail(WAVE_ECUDA, "wave_create: %s", cudaGetErrorString(e));
+    }
+    if (st) {
+        destroy_ctx(c);
+        return st;
+    }
+    *out = c;
+    return WAVE_OK;
+}
+
+// --------------------------------------------------------------- field I/O
+static bool on_rigid_wall_zeroed(const wave_ctx *c, int field, const int64_t idx[3]) {
+    // acoustic: p is zero on every rigid wall node plane; v_c on the wall
+    // planes of the rigid axes other than c
+    for (int ax = 0; ax < c->ndim; ax++) {
+        if (c->bc[2 * ax] != WAVE_BC_RIGID || idx[ax] != 0) continue;
+        if (field == WAVE_F_P) return true;
+        if (field - 1 != ax) return true;
+    }
+    return false;
+}
+
+extern "C" wave_status wave_set_initial(wave_ctx *c, wave_field field, const double *host) {
+    CHECK_CTX(c);
+    if (!host) return fail(WAVE_EINVAL, "wave_set_initial: NULL values");
+    if (!field_valid(c, field)) return fail(WAVE_EINVAL, "field %d not in this physics", field);
+    const int64_t npts = c->n[0] * c->n[1] * c->n[2];
+    const size_t eb = elem_bytes(c->prec);
+    std::vector<unsigned char> tmp;
+    try { tmp.resize(npts * eb); } catch (...) { return fail(WAVE_ENOMEM, "host buffer"); }
+    const bool is_vel = (field == WAVE_F_VX || field == WAVE_F_VY || field == WAVE_F_VZ);
+    const double P0 = c->P0, Z0 = c->Z0;
+    const int prec = c->prec;
+    const int64_t nx = c->n[0], ny = c->n[1];
+    std::vector<int64_t> badv(1, -1);
+    int64_t *bad = badv.data();
+    unsigned char *dst = tmp.data();
+    const wave_ctx *cc = c;
+    parallel_for(npts, [=](int64_t lo, int64_t hi) {
+        for (int64_t q = lo; q < hi; q++) {
+            double x = host[q];
+            double s = is_vel ? (x * Z0) / P0 : x / P0;
+            if (!isfinite(x)) { *bad = q; s = 0.0; }
+            if (cc->kind == WAVE_ACOUSTIC) {
+                const int64_t idx[3] = {q % nx, (q / nx) % ny, q / (nx * ny)};
+                if (on_rigid_wall_zeroed(cc, field, idx)) s = 0.0;
+            }
+            store_value(prec, s, dst, q);
+            if (!isfinite(load_value(prec, dst, q))) *bad = q;
+        }
+    });
+    if (*bad >= 0)
+        return fail(WAVE_ERANGE, "initial value at point %lld is not finite in the storage format",
+                    (long long)*bad);
+    wave_status st = upload_packed(c, c->f[field].ptr, tmp.data());
+    if (st) return st;
+    if (c->t[field].ptr) {
+        cudaError_t e = cudaMemsetAsync(c->t[field].ptr, 0, c->t[field].bytes, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        return cuda_check(c, e, "reset compensation");
+    }
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_get_raw(wave_ctx *c, wave_field field, int32_t compensation,
+                                    void *host) {
+    CHECK_CTX(c);
+    if (!host) return fail(WAVE_EINVAL, "wave_get_raw: NULL output");
+    if (!field_valid(c, field)) return fail(WAVE_EINVAL, "field %d not in this physics", field);
+    const int64_t npts = c->n[0] * c->n[1] * c->n[2];
+    if (compensation && !c->t[field].ptr) {
+        memset(host, 0, npts * elem_bytes(c->prec));
+        return WAVE_OK;
+    }
+    return download_packed(c, compensation ? c->t[field].ptr : c->f[field].ptr, host);
+}
+
+extern "C" wave_status wave_set_raw(wave_ctx *c, wave_field field, int32_t compensation,
+                                    const void *host) {
+    CHECK_CTX(c);
+    if (!host) return fail(WAVE_EINVAL, "wave_set_raw: NULL input");
+    if (!field_valid(c, field)) return fail(WAVE_EINVAL, "field %d not in this physics", field);
+    if (compensation && !c->t[field].ptr)
+        return fail(WAVE_EINVAL, "context has no compensation arrays");
+    return upload_packed(c, compensation ? c->t[field].ptr : c->f[field].ptr, host);
+}
+
+extern "C" wave_status wave_get_field(wave_ctx *c, wave_field field, double *host) {
+    CHECK_CTX(c);
+    if (!host) return fail(WAVE_EINVAL, "wave_get_field: NULL output");
+    if (!field_valid(c, field)) return fail(WAVE_EINVAL, "field %d not in this physics", field);
+    const int64_t npts = c->n[0] * c->n[1] * c->n[2];
+    std::vector<unsigned char> tmp(npts * elem_bytes(c->prec));
+    wave_status st = download_packed(c, c->f[field].ptr, tmp.data());
+    if (st) return st;
+    const bool is_vel = (field == WAVE_F_VX || field == WAVE_F_VY || field == WAVE_F_VZ);
+    const double P0 = c->P0, Z0 = c->Z0;
+    const int prec = c->prec;
+    const unsigned char *src = tmp.data();
+    parallel_for(npts, [=](int64_t lo, int64_t hi) {
+        for (int64_t q = lo; q < hi; q++) {
+            double s = load_value(prec, src, q);
+            host[q] = is_vel ? (s * P0) / Z0 : s * P0;
+        }
+    });
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_get_coefficient(wave_ctx *c, int32_t which, double *host, double *Z0) {
+    CHECK_CTX(c);
+    if (Z0) *Z0 = c->Z0;
+    if (!host) return WAVE_OK;
+    const std::vector<double> *v = nullptr;
+    if (c->kind == WAVE_ACOUSTIC) {
+        if (which < 0 || which > c->ndim) return fail(WAVE_EINVAL, "bad coefficient index");
+        v = &c->coef_host[which];
+    } else {
+        return fail(WAVE_EINVAL, "bad coefficient index");
+    }
+    memcpy(host, v->data(), v->size() * sizeof(double));
+    return WAVE_OK;
+}
+
+// ----------------------------------------------------------------- source
+extern "C" wave_status wave_set_source(wave_ctx *c, wave_field field, const int64_t idx[3],
+                                       const double *wavelet, int64_t nt) {
+    CHECK_CTX(c);
+    if (nt < 0 || (nt > 0 && (!wavelet || !idx))) return fail(WAVE_EINVAL, "bad source arguments");
+    if (c->kind == WAVE_ACOUSTIC && field != WAVE_F_P)
+        return fail(WAVE_EINVAL, "acoustic sources act on p");
+    if (c->kind == WAVE_ELASTIC && field != WAVE_F_VY)
+        return fail(WAVE_EINVAL, "elastic sources act on v_y");
+    dev_free(c, c->src_table);
+    c->src_q = -1;
+    c->src_nt = 0;
+    c->src_field = -1;
+    if (nt == 0) return WAVE_OK;
+    for (int ax = 0; ax < c->ndim; ax++)
+        if (idx[ax] < 0 || idx[ax] >= c->n[ax]) return fail(WAVE_EINVAL, "source outside grid");
+    const double hd1 = c->ndim == 2 ? c->h : c->h * c->h;
+    const double scale = c->kind == WAVE_ACOUSTIC ? c->Z0 / (c->P0 * hd1) : 1.0 / (c->P0 * hd1);
+    const bool f32 = arith_is_f32(c->prec);
+    std::vector<unsigned char> tab(nt * (f32 ? 4 : 2));
+    for (int64_t s = 0; s < nt; s++) {
+        if (!isfinite(wavelet[s])) return fail(WAVE_ERANGE, "wavelet sample %lld", (long long)s);
+        double v = wavelet[s] * scale;
+        if (f32) {
+            float x = (float)v;
+            memcpy(&tab[4 * s], &x, 4);
+        } else {
+            uint16_t hb = is_bf16_storage(c->prec) ? round_bits16(v, 7, 8) : round_bits16(v, 10, 5);
+            memcpy(&tab[2 * s], &hb, 2);
+        }
+    }
+    wave_status st = dev_alloc(c, c->src_table, tab.size());
+    if (st) return st;
+    cudaError_t e = cudaMemcpyAsync(c->src_table.ptr, tab.data(), tab.size(),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "source upload");
+    c->src_q = idx[0] + c->pitch * idx[1] + (c->ndim == 3 ? c->plane * idx[2] : 0);
+    c->src_nt = nt;
+    c->src_field = field;
+    return WAVE_OK;
+}
+
+// -------------------------------------------------------------- receivers
+extern "C" wave_status wave_set_receivers(wave_ctx *c, wave_field field, const int64_t *idx,
+                                          int64_t nrec, float *traces, int64_t cap) {
+    CHECK_CTX(c);
+    dev_free(c, c->rec_q);
+    c->nrec = 0;
+    c->rec_traces = nullptr;
+    if (nrec == 0) return WAVE_OK;
+    if (nrec < 0 || nrec > 65536 || !idx || !traces || cap < 0)
+        return fail(WAVE_EINVAL, "bad receiver arguments");
+    if (!field_valid(c, field)) return fail(WAVE_EINVAL, "field %d not in this physics", field);
+    std::vector<int64_t> q(nrec);
+    for (int64_t r = 0; r < nrec; r++) {
+        for (int ax = 0; ax < c->ndim; ax++)
+            if (idx[3 * r + ax] < 0 || idx[3 * r + ax] >= c->n[ax])
+                return fail(WAVE_EINVAL, "receiver %lld outside grid", (long long)r);
+        q[r] = idx[3 * r] + c->pitch * idx[3 * r + 1] +
+               (c->ndim == 3 ? c->plane * idx[3 * r + 2] : 0);
+    }
+    wave_status st = dev_alloc(c, c->rec_q, nrec * sizeof(int64_t));
+    if (st) return st;
+    cudaError_t e = cudaMemcpyAsync(c->rec_q.ptr, q.data(), nrec * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "receiver upload");
+    c->nrec = nrec;
+    c->rec_field = field;
+    c->rec_traces = traces;
+    c->rec_cap = cap;
+    c->rec_pos = 0;
+    return WAVE_OK;
+}
+
+namespace wave {
+__global__ void receivers_kernel(const void *field, int eb, int is_bf16, const int64_t *q, int nrec,
+                                 float *out) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrec) return;
+    float v;
+    if (eb == 4) v = static_cast<const float *>(field)[q[r]];
+    else if (is_bf16) v = BF16::to_f32(static_cast<const uint16_t *>(field)[q[r]]);
+    else v = F16::to_f32(static_cast<const uint16_t *>(field)[q[r]]);
+    out[r] = v;
+}
+
+cudaError_t sample_receivers(const void *field, int eb, int is_bf16, const int64_t *q, int nrec,
+                             float *traces, cudaStream_t st) {
+    receivers_kernel<<<(nrec + 127) / 128, 128, 0, st>>>(field, eb, is_bf16, q, nrec, traces);
+    return cudaGetLastError();
+}
+}  // namespace wave
+
+// ------------------------------------------------------------------ energy
+extern "C" wave_status wave_set_energy_trace(wave_ctx *c, double *dev, int64_t cap) {
+    CHECK_CTX(c);
+    if (cap < 0 || (cap > 0 && !dev)) return fail(WAVE_EINVAL, "bad energy trace");
+    c->e_trace = cap ? dev : nullptr;
+    c->e_trace_cap = cap;
+    c->e_trace_pos = 0;
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_energy(wave_ctx *c, double *E) {
+    CHECK_CTX(c);
+    if (!E) return fail(WAVE_EINVAL, "wave_energy: NULL output");
+    if (!c->have_energy) return fail(WAVE_ESTATE, "no step has run yet");
+    double e = 0.0;
+    cudaError_t err = cudaMemcpyAsync(&e, c->e_misc.ptr, sizeof(double), cudaMemcpyDeviceToHost,
+                                      c->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+    if (err != cudaSuccess) return cuda_check(c, err, "wave_energy");
+    *E = e;
+    return WAVE_OK;
+}
+
+// -------------------------------------------------------------------- step
+static wave_status acoustic_steps(wave_ctx *c, int64_t n) {
+    AcParams prm;
+    fill_acoustic_params(c, prm);
+    const size_t eb = elem_bytes(c->prec);
+    for (int64_t s = 0; s < n; s++) {
+        prm.step = c->step;
+        const bool trace = c->e_trace && c->e_trace_pos < c->e_trace_cap;
+        prm.energy = (s == n - 1) || trace;
+        prm.e_out = static_cast<double *>(c->e_misc.ptr);
+        cudaEvent_t m0 = mark(c);
+        cudaError_t e = acoustic_generic_half_step(prm, c->ndim, c->prec, c->comp, 0, c->stream);
+        cudaEvent_t m1 = mark(c);
+        timed(c, 0, m0, m1);
+        if (e == cudaSuccess)
+            e = acoustic_generic_half_step(prm, c->ndim, c->prec, c->comp, 1, c->stream);
+        cudaEvent_t m2 = mark(c);
+        timed(c, 1, m1, m2);
+        if (e == cudaSuccess && trace)
+            e = cudaMemcpyAsync(c->e_trace + c->e_trace_pos, c->e_misc.ptr, sizeof(double),
+                                cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess && c->nrec && c->rec_pos < c->rec_cap)
+            e = sample_receivers(c->f[c->rec_field].ptr, (int)eb, is_bf16_storage(c->prec),
+                                 static_cast<const int64_t *>(c->rec_q.ptr), (int)c->nrec,
+                                 c->rec_traces + c->rec_pos * c->nrec, c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "wave_step launch");
+        if (trace) c->e_trace_pos++;
+        if (c->nrec && c->rec_pos < c->rec_cap) c->rec_pos++;
+        c->step++;
+    }
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_step(wave_ctx *c, int64_t n) {
+    CHECK_CTX(c);
+    if (n < 0) return fail(WAVE_EINVAL, "negative step count");
+    if (n == 0) return WAVE_OK;
+    wave_status st;
+    if (c->kind == WAVE_ACOUSTIC) {
+        st = acoustic_steps(c, n);
+    } else {
+        st = fail(WAVE_ENOTIMPL, "elastic physics is not built yet");
+    }
+    if (!st) c->have_energy = true;
+    return st;
+}
+
+extern "C" wave_status wave_sync(wave_ctx *c) {
+    CHECK_CTX(c);
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "wave_sync");
+}
+
+extern "C" wave_status wave_steps_done(wave_ctx *c, int64_t *steps) {
+    CHECK_CTX(c);
+    if (!steps) return fail(WAVE_EINVAL, "NULL output");
+    *steps = c->step;
+    return WAVE_OK;
+}
+
+// ------------------------------------------------------- checkpoint/resume
+struct StateHeader {
+    uint64_t magic;
+    int64_t step;
+    int64_t n[3];
+    int32_t prec, comp, kind, nfields;
+};
+static const uint64_t kMagic = 0x31564157454C4657ull;
+
+static int state_fields(const wave_ctx *c, int *list) {
+    int k = 0;
+    if (c->kind == WAVE_ACOUSTIC) {
+        for (int f = 0; f <= c->ndim; f++) list[k++] = f;
+    } else {
+        const int ef[5] = {WAVE_F_VX, WAVE_F_VY, WAVE_F_SXX, WAVE_F_SYY, WAVE_F_SXY};
+        for (int f : ef) list[k++] = f;
+    }
+    return k;
+}
+
+extern "C" wave_status wave_get_state(wave_ctx *c, void *blob, size_t *size) {
+    CHECK_CTX(c);
+    if (!size) return fail(WAVE_EINVAL, "NULL size");
+    int list[7];
+    const int nf = state_fields(c, list);
+    const size_t arr = (size_t)(c->n[0] * c->n[1] * c->n[2]) * elem_bytes(c->prec);
+    const size_t need = sizeof(StateHeader) + 2 * nf * arr;
+    if (!blob) { *size = need; return WAVE_OK; }
+    if (*size < need) return fail(WAVE_EINVAL, "state buffer too small (%zu < %zu)", *size, need);
+    StateHeader hd{kMagic, c->step, {c->n[0], c->n[1], c->n[2]}, c->prec, c->comp, c->kind, nf};
+    memcpy(blob, &hd, sizeof hd);
+    unsigned char *p = static_cast<unsigned char *>(blob) + sizeof hd;
+    for (int i = 0; i < nf; i++) {
+        for (int comp = 0; comp < 2; comp++) {
+            wave_status st = wave_get_raw(c, (wave_field)list[i], comp, p);
+            if (st) return st;
+            p += arr;
+        }
+    }
+    *size = need;
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_set_state(wave_ctx *c, const void *blob, size_t size) {
+    CHECK_CTX(c);
+    if (!blob || size < sizeof(StateHeader)) return fail(WAVE_EINVAL, "bad state blob");
+    StateHeader hd;
+    memcpy(&hd, blob, sizeof hd);
+    int list[7];
+    const int nf = state_fields(c, list);
+    const size_t arr = (size_t)(c->n[0] * c->n[1] * c->n[2]) * elem_bytes(c->prec);
+    if (hd.magic != kMagic || hd.n[0] != c->n[0] || hd.n[1] != c->n[1] || hd.n[2] != c->n[2] ||
+        hd.prec != c->prec || hd.comp != c->comp || hd.kind != c->kind || hd.nfields != nf ||
+        size < sizeof hd + 2 * nf * arr)
+        return fail(WAVE_EINVAL, "state blob does not match this context");
+    const unsigned char *p = static_cast<const unsigned char *>(blob) + sizeof hd;
+    for (int i = 0; i < nf; i++) {
+        wave_status st = wave_set_raw(c, (wave_field)list[i], 0, p);
+        if (st) return st;
+        p += arr;
+        if (c->t[list[i]].ptr) {
+            st = wave_set_raw(c, (wave_field)list[i], 1, p);
+            if (st) return st;
+        }
+        p += arr;
+    }
+    c->step = hd.step;
+    c->have_energy = false;
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_set_timing(wave_ctx *c, int32_t enable) {
+    CHECK_CTX(c);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "wave_set_timing");
+    collect_timing(c);
+    for (int k = 0; k < 3; k++) { c->t_launches[k] = 0; c->t_ms[k] = 0.0; }
+    c->timing = enable != 0;
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_get_timing(wave_ctx *c, int32_t kind, int64_t *launches, double *ms) {
+    CHECK_CTX(c);
+    if (kind < 0 || kind > 2 || !launches || !ms) return fail(WAVE_EINVAL, "bad timing query");
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "wave_get_timing");
+    collect_timing(c);
+    *launches = c->t_launches[kind];
+    *ms = c->t_ms[kind];
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_adjoint_step(wave_ctx *c, int64_t n, const float *residual) {
+    CHECK_CTX(c);
+    (void)n;
+    (void)residual;
+    return fail(WAVE_ENOTIMPL, "adjoint time stepping is not implemented in this build");
+}

@@ -1,0 +1,25 @@
+// wave_kernels.h -- internal interface between the C ABI and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wave {
+
+// Same values as wave_precision in include/wave.h.
+enum { PREC_FP64 = 0, PREC_FP32 = 1, PREC_FP16 = 2, PREC_BF16 = 3,
+       PREC_FP16_F32ARITH = 4, PREC_BF16_F32ARITH = 5 };
+
+struct AcParams;
+
+// One acoustic half step with the one-thread-per-point kernels:
+// half_step 0 = velocities, 1 = pressure (with source and optional energy).
+cudaError_t acoustic_generic_half_step(const AcParams &prm, int ndim, int prec, int comp,
+                                       int half_step, cudaStream_t st);
+// Number of blocks the generic pressure kernel launches (energy partials).
+unsigned acoustic_generic_blocks(const AcParams &prm, int ndim);
+
+// Receiver sampling: traces[r] = float(field[q[r]]) for r < nrec.
+cudaError_t sample_receivers(const void *field, int elem_bytes, int is_bf16, const int64_t *q,
+                             int nrec, float *traces, cudaStream_t st);
+
+}  // namespace wave

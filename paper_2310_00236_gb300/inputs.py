@@ -26,12 +26,13 @@ def gaussian(shape, h: float, sigma: float, center=None, peak: float = 1.0) -> n
     nd = len(shape)
     if center is None:
         center = [0.5 * shape[a] * h for a in range(nd)]
-    grids = np.meshgrid(*[node_coords(shape[a], h) - center[a] for a in range(nd)],
-                        indexing="ij")
-    r2 = np.zeros(grids[0].shape)
-    for g in grids:
-        r2 += g * g
-    return np.ascontiguousarray((peak * np.exp(-r2 / (2.0 * sigma * sigma))).transpose())
+    # separable: the product of one 1D Gaussian per axis, outermost axis first
+    out = np.full((), peak, dtype=np.float64)
+    for a in reversed(range(nd)):
+        x = node_coords(shape[a], h) - center[a]
+        g = np.exp(-(x * x) / (2.0 * sigma * sigma))
+        out = np.multiply.outer(out, g)
+    return np.ascontiguousarray(out)
 
 
 def smooth_random_field(shape, seed: int, sigma_cells: float, lo: float, hi: float,
@@ -42,10 +43,17 @@ def smooth_random_field(shape, seed: int, sigma_cells: float, lo: float, hi: flo
     The noise is numpy's PCG64 standard normal with the given seed, drawn in
     (z, y, x) order.
     """
+    try:
+        import scipy.fft as sfft
+        rfftn = lambda a: sfft.rfftn(a, workers=-1)
+        irfftn = lambda a, s: sfft.irfftn(a, s=s, workers=-1)
+    except ImportError:
+        rfftn = np.fft.rfftn
+        irfftn = lambda a, s: np.fft.irfftn(a, s=s, axes=tuple(range(len(s))))
     rshape = tuple(shape[::-1])
     rng = np.random.default_rng(seed)
     noise = rng.standard_normal(rshape, dtype=np.float32 if dtype == np.float32 else np.float64)
-    spec = np.fft.rfftn(noise)
+    spec = rfftn(noise)
     del noise
     kernel = None
     for ax, n in enumerate(rshape):
@@ -58,8 +66,8 @@ def smooth_random_field(shape, seed: int, sigma_cells: float, lo: float, hi: flo
         shp[ax] = g.size
         g = g.reshape(shp)
         kernel = g if kernel is None else kernel * g
-    spec *= kernel
-    field = np.fft.irfftn(spec, s=rshape, axes=tuple(range(len(rshape))))
+    spec *= kernel.astype(spec.real.dtype)
+    field = irfftn(spec, rshape)
     del spec
     fmin, fmax = float(field.min()), float(field.max())
     field = lo + (field - fmin) * ((hi - lo) / (fmax - fmin))

@@ -1,0 +1,325 @@
+"""Thin ctypes binding of the C ABI in include/wave.h (same names).
+
+Only argument marshalling lives here: every step of the computation runs in
+libwave.so's CUDA kernels. torch supplies the CUDA stream (and, optionally,
+device memory through the caching allocator). Loading fails loudly if the
+library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwave.so")
+
+WAVE_OK, WAVE_EINVAL, WAVE_ENOMEM, WAVE_ERANGE, WAVE_ECUDA, WAVE_ETIMEOUT, WAVE_ESTATE, \
+    WAVE_ENOTIMPL = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ERANGE", "ECUDA", "ETIMEOUT", "ESTATE", "ENOTIMPL"]
+WAVE_ACOUSTIC, WAVE_ELASTIC = 0, 1
+WAVE_FP64, WAVE_FP32, WAVE_FP16, WAVE_BF16, WAVE_FP16_F32ARITH, WAVE_BF16_F32ARITH = range(6)
+WAVE_COMP_NONE, WAVE_COMP_3OP, WAVE_COMP_6OP = 0, 3, 6
+WAVE_BC_PERIODIC, WAVE_BC_RIGID, WAVE_BC_FREE = 0, 1, 2
+WAVE_F_P, WAVE_F_VX, WAVE_F_VY, WAVE_F_VZ, WAVE_F_SXX, WAVE_F_SYY, WAVE_F_SXY = range(7)
+
+PRECISIONS = {"fp32": WAVE_FP32, "fp16": WAVE_FP16, "bf16": WAVE_BF16,
+              "fp16_f32arith": WAVE_FP16_F32ARITH, "bf16_f32arith": WAVE_BF16_F32ARITH,
+              "fp64": WAVE_FP64}
+
+# Every symbol include/wave.h declares.
+EXPORTS = ["wave_set_allocator", "wave_create", "wave_set_initial", "wave_set_source",
+           "wave_set_receivers", "wave_step", "wave_set_energy_trace", "wave_energy",
+           "wave_get_field", "wave_get_raw", "wave_set_raw", "wave_get_coefficient",
+           "wave_get_state", "wave_set_state", "wave_sync", "wave_steps_done",
+           "wave_adjoint_step", "wave_destroy", "wave_last_error", "wave_build_info",
+           "wave_set_timing", "wave_get_timing"]
+
+
+class WaveError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class wave_grid(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("n", C.c_int64 * 3)]
+
+
+class wave_materials(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("rho", C.POINTER(C.c_double)),
+                ("vp", C.POINTER(C.c_double)), ("vs", C.POINTER(C.c_double)),
+                ("bc", C.c_int32 * 6)]
+
+
+class wave_options(C.Structure):
+    _fields_ = [("field_scale", C.c_double), ("kernel", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libwave.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libwave.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double)
+    sig = {
+        "wave_set_allocator": [ALLOC_FN, FREE_FN, vp],
+        "wave_create": [C.POINTER(wave_grid), dp, C.POINTER(wave_materials), C.c_double, C.c_int,
+                        C.c_int, C.POINTER(wave_options), vp, C.POINTER(vp)],
+        "wave_set_initial": [vp, C.c_int, dp],
+        "wave_set_source": [vp, C.c_int, C.POINTER(C.c_int64), dp, i64],
+        "wave_set_receivers": [vp, C.c_int, C.POINTER(C.c_int64), i64, vp, i64],
+        "wave_step": [vp, i64],
+        "wave_set_energy_trace": [vp, vp, i64],
+        "wave_energy": [vp, dp],
+        "wave_get_field": [vp, C.c_int, dp],
+        "wave_get_raw": [vp, C.c_int, i32, vp],
+        "wave_set_raw": [vp, C.c_int, i32, vp],
+        "wave_get_coefficient": [vp, i32, dp, dp],
+        "wave_get_state": [vp, vp, C.POINTER(C.c_size_t)],
+        "wave_set_state": [vp, vp, C.c_size_t],
+        "wave_sync": [vp],
+        "wave_steps_done": [vp, C.POINTER(C.c_int64)],
+        "wave_adjoint_step": [vp, i64, vp],
+        "wave_set_timing": [vp, i32],
+        "wave_get_timing": [vp, i32, C.POINTER(C.c_int64), dp],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.wave_destroy.argtypes = [vp]
+    L.wave_destroy.restype = None
+    L.wave_last_error.restype = C.c_char_p
+    L.wave_build_info.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def wave_last_error() -> str:
+    return lib().wave_last_error().decode()
+
+
+def wave_build_info() -> str:
+    return lib().wave_build_info().decode()
+
+
+def _check(st: int):
+    if st != WAVE_OK:
+        raise WaveError(st, wave_last_error())
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Context:
+    """Handle returned by wave_create: the opaque pointer plus the grid shape."""
+
+    def __init__(self, ptr, ndim, n, prec, kind):
+        self.ptr = ptr
+        self.ndim = ndim
+        self.n = tuple(n)
+        self.prec = prec
+        self.kind = kind
+
+    @property
+    def shape(self):
+        """numpy shape of one field: (z, y, x) or (y, x)."""
+        return tuple(self.n[: self.ndim][::-1])
+
+    @property
+    def npts(self):
+        return int(np.prod(self.n[: self.ndim]))
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return stream
+    import torch
+    if torch.cuda.is_available():
+        return torch.cuda.current_stream().cuda_stream
+    return None
+
+
+def wave_create(n, spacing, rho, vp, dt, precision, comp, vs=None, bc=(WAVE_BC_RIGID,) * 6,
+                kind=WAVE_ACOUSTIC, field_scale=1.0, kernel=0, stream=None) -> Context:
+    """n: cells per axis (x, y[, z]); rho, vp, vs: arrays shaped like a field."""
+    ndim = len(n)
+    g = wave_grid()
+    g.ndim = ndim
+    for ax in range(3):
+        g.n[ax] = n[ax] if ax < ndim else 1
+    sp = (C.c_double * 3)(*([float(spacing)] * 3 if np.isscalar(spacing) else list(spacing) + [0.0] * (3 - len(spacing))))
+    rho_a, rho_p = _f64(rho)
+    vp_a, vp_p = _f64(vp)
+    m = wave_materials()
+    m.kind = kind
+    m.rho = rho_p
+    m.vp = vp_p
+    keep = [rho_a, vp_a]
+    if vs is not None:
+        vs_a, vs_p = _f64(vs)
+        m.vs = vs_p
+        keep.append(vs_a)
+    for i in range(6):
+        m.bc[i] = bc[i] if i < len(bc) else WAVE_BC_PERIODIC
+    o = wave_options()
+    o.field_scale = field_scale
+    o.kernel = kernel
+    out = C.c_void_p()
+    _check(lib().wave_create(C.byref(g), sp, C.byref(m), float(dt), int(precision), int(comp),
+                             C.byref(o), _stream_handle(stream), C.byref(out)))
+    return Context(out, ndim, [g.n[0], g.n[1], g.n[2]], precision, kind)
+
+
+def wave_destroy(ctx: Context):
+    if ctx.ptr:
+        lib().wave_destroy(ctx.ptr)
+        ctx.ptr = None
+
+
+def wave_set_initial(ctx: Context, field: int, values):
+    a, p = _f64(values)
+    assert a.size == ctx.npts
+    _check(lib().wave_set_initial(ctx.ptr, field, p))
+
+
+def wave_set_source(ctx: Context, field: int, idx, wavelet):
+    ix = (C.c_int64 * 3)(*(list(idx) + [0] * (3 - len(idx))))
+    w, wp = _f64(wavelet)
+    _check(lib().wave_set_source(ctx.ptr, field, ix, wp, w.size))
+
+
+def wave_set_receivers(ctx: Context, field: int, idx, traces=None, capacity_steps=0):
+    """idx: sequence of (i, j[, k]); traces: device tensor of capacity_steps*nrec floats."""
+    idx = np.asarray(idx, dtype=np.int64).reshape(len(idx), -1) if len(idx) else np.zeros((0, 3), np.int64)
+    full = np.zeros((idx.shape[0], 3), np.int64)
+    full[:, : idx.shape[1]] = idx
+    full = np.ascontiguousarray(full)
+    ptr = None if traces is None else C.c_void_p(traces.data_ptr())
+    _check(lib().wave_set_receivers(ctx.ptr, field, full.ctypes.data_as(C.POINTER(C.c_int64)),
+                                    full.shape[0], ptr, capacity_steps))
+
+
+def wave_step(ctx: Context, n: int):
+    _check(lib().wave_step(ctx.ptr, int(n)))
+
+
+def wave_set_energy_trace(ctx: Context, device_energy=None, capacity=0):
+    ptr = None if device_energy is None else C.c_void_p(device_energy.data_ptr())
+    _check(lib().wave_set_energy_trace(ctx.ptr, ptr, capacity))
+
+
+def wave_energy(ctx: Context) -> float:
+    e = C.c_double()
+    _check(lib().wave_energy(ctx.ptr, C.byref(e)))
+    return e.value
+
+
+def wave_get_field(ctx: Context, field: int) -> np.ndarray:
+    out = np.empty(ctx.shape, np.float64)
+    _check(lib().wave_get_field(ctx.ptr, field, out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+def _raw_dtype(prec):
+    return np.float32 if prec == WAVE_FP32 else np.uint16
+
+
+def wave_get_raw(ctx: Context, field: int, compensation: int = 0) -> np.ndarray:
+    out = np.empty(ctx.shape, _raw_dtype(ctx.prec))
+    _check(lib().wave_get_raw(ctx.ptr, field, compensation, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def wave_set_raw(ctx: Context, field: int, compensation: int, values):
+    a = np.ascontiguousarray(values, dtype=_raw_dtype(ctx.prec))
+    _check(lib().wave_set_raw(ctx.ptr, field, compensation, a.ctypes.data_as(C.c_void_p)))
+
+
+def wave_get_coefficient(ctx: Context, which: int):
+    out = np.empty(ctx.shape, np.float64)
+    z0 = C.c_double()
+    _check(lib().wave_get_coefficient(ctx.ptr, which, out.ctypes.data_as(C.POINTER(C.c_double)),
+                                      C.byref(z0)))
+    return out, z0.value
+
+
+def wave_get_state(ctx: Context) -> bytes:
+    size = C.c_size_t(0)
+    _check(lib().wave_get_state(ctx.ptr, None, C.byref(size)))
+    buf = C.create_string_buffer(size.value)
+    _check(lib().wave_get_state(ctx.ptr, buf, C.byref(size)))
+    return buf.raw[: size.value]
+
+
+def wave_set_state(ctx: Context, blob: bytes):
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(lib().wave_set_state(ctx.ptr, buf, len(blob)))
+
+
+def wave_sync(ctx: Context):
+    _check(lib().wave_sync(ctx.ptr))
+
+
+def wave_steps_done(ctx: Context) -> int:
+    s = C.c_int64()
+    _check(lib().wave_steps_done(ctx.ptr, C.byref(s)))
+    return s.value
+
+
+def wave_adjoint_step(ctx: Context, n: int, residual=None):
+    ptr = None if residual is None else C.c_void_p(residual.data_ptr())
+    _check(lib().wave_adjoint_step(ctx.ptr, int(n), ptr))
+
+
+def wave_set_timing(ctx: Context, enable: bool):
+    _check(lib().wave_set_timing(ctx.ptr, 1 if enable else 0))
+
+
+def wave_get_timing(ctx: Context, kind: int):
+    """(launches, total milliseconds) for kernel kind 0 velocity, 1 pressure, 2 receivers."""
+    n = C.c_int64()
+    ms = C.c_double()
+    _check(lib().wave_get_timing(ctx.ptr, kind, C.byref(n), C.byref(ms)))
+    return n.value, ms.value
+
+
+# ---------------------------------------------------------------- allocator
+_alloc_cbs = None
+
+
+def use_torch_allocator(device: int = 0):
+    """Route the library's device allocations through torch's caching allocator."""
+    import torch
+    global _alloc_cbs
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream or 0)
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    _alloc_cbs = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _check(lib().wave_set_allocator(_alloc_cbs[0], _alloc_cbs[1], None))
+
+
+def use_default_allocator():
+    global _alloc_cbs
+    _check(lib().wave_set_allocator(ALLOC_FN(), FREE_FN(), None))
+    _alloc_cbs = None

@@ -1,0 +1,88 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and
+loads, it exports exactly the functions include/wave.h declares, and argument
+errors are reported as status codes before any CUDA call is made."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2310_00236_gb300 import build as B
+from paper_2310_00236_gb300 import wave as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return W.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "wave.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return set(re.findall(r"\b(wave_[a-z_]+)\s*\(", src)) - {"wave_alloc_fn", "wave_free_fn"}
+
+
+def test_exports_match_header(lib):
+    declared = _declared()
+    assert declared == set(W.EXPORTS)
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (wave_[a-z_]+)$", out, flags=re.M))
+    assert declared <= exported
+    for name in declared:
+        assert hasattr(lib, name)
+
+
+def test_build_info(lib):
+    assert "sm_103a" in W.wave_build_info()
+
+
+def _ones(n=(16, 16)):
+    return np.ones(n[::-1])
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(n=(4, 16)), W.WAVE_EINVAL),                      # too small
+    (dict(precision=W.WAVE_FP64), W.WAVE_ENOTIMPL),        # oracle only
+    (dict(precision=17), W.WAVE_EINVAL),
+    (dict(comp=4), W.WAVE_EINVAL),
+    (dict(dt=-1.0), W.WAVE_EINVAL),
+    (dict(dt=float("nan")), W.WAVE_EINVAL),
+    (dict(spacing=(0.1, 0.2)), W.WAVE_EINVAL),             # anisotropic
+    (dict(bc=(1, 0, 1, 1, 0, 0)), W.WAVE_EINVAL),          # mixed faces on one axis
+    (dict(bc=(2, 2, 1, 1, 0, 0)), W.WAVE_EINVAL),          # free surface is elastic only
+    (dict(field_scale=-1.0), W.WAVE_EINVAL),
+    (dict(rho_scale=0.0), W.WAVE_ERANGE),                   # non-positive material
+    (dict(kind=W.WAVE_ELASTIC, vs=True), W.WAVE_ENOTIMPL),
+])
+def test_create_argument_errors(lib, kw, status):
+    n = kw.pop("n", (16, 16))
+    args = dict(precision=W.WAVE_FP16, comp=3, dt=0.01, spacing=0.1, bc=(1,) * 6,
+                field_scale=1.0, kind=W.WAVE_ACOUSTIC)
+    rho_scale = kw.pop("rho_scale", 1.0)
+    want_vs = kw.pop("vs", False)
+    args.update(kw)
+    with pytest.raises(W.WaveError) as e:
+        W.wave_create(n, args["spacing"], _ones(n) * rho_scale, _ones(n), args["dt"],
+                      args["precision"], args["comp"], bc=args["bc"], kind=args["kind"],
+                      field_scale=args["field_scale"], vs=_ones(n) * 0.5 if want_vs else None)
+    assert e.value.status == status, str(e.value)
+    assert W.wave_last_error()
+
+
+def test_null_context_is_einval(lib):
+    import ctypes as C
+    assert lib.wave_step(None, 1) == W.WAVE_EINVAL
+    assert lib.wave_sync(None) == W.WAVE_EINVAL
+    e = C.c_double()
+    assert lib.wave_energy(None, C.byref(e)) == W.WAVE_EINVAL
+    lib.wave_destroy(None)   # no-op
+
+
+def test_allocator_pair_required(lib):
+    with pytest.raises(W.WaveError):
+        W._check(lib.wave_set_allocator(W.ALLOC_FN(lambda n, s, u: None), W.FREE_FN(), None))
+    W.use_default_allocator()
