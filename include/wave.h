@@ -110,8 +110,9 @@ typedef struct {
 typedef struct {
     double field_scale;  /* P0 > 0: stored p^ = p / P0 and v^ = v * Z0 / P0
                             (Z0 = max(rho) * max(vp)); default 1.0 */
-    int32_t kernel;      /* 0: automatic choice; 1: generic kernels only */
-    int32_t reserved[7];
+    int32_t kernel;      /* 0: automatic choice; 1: one-thread-per-point kernels only */
+    int32_t zchunk;      /* z planes per thread block of the 3D streaming kernels (0: automatic) */
+    int32_t reserved[6];
 } wave_options;
 
 /* Optional device allocator for the context's memory (for instance a caching

@@ -276,3 +276,131 @@ def acoustic_setup(shape, bc, h, dt, rho, c, store_fmt, comp, P0=1.0, arith_fmt=
                 st.v[ax] = scale_velocity(vv, Z0, P0, store_fmt).reshape(st.shape)
     st.apply_walls()
     return st
+
+
+# --------------------------------------------------------------------------
+# Elastic solver (Eq. 2, Appendix A)
+# --------------------------------------------------------------------------
+EBC_PERIODIC, EBC_RIGID, EBC_FREE = 0, 1, 2
+
+
+class ElasticCfg(C.Structure):
+    _fields_ = [("n", C.c_int64 * 2), ("bc", C.c_int32 * 4), ("store_fmt", C.c_int32),
+                ("arith_fmt", C.c_int32), ("stencil_fmt", C.c_int32), ("comp", C.c_int32)]
+
+
+def elastic_cfg(shape, bc, store_fmt, comp, arith_fmt=None, stencil_fmt=None) -> ElasticCfg:
+    """shape (nx, ny); bc per face (x-lo, x-hi, y-lo, y-hi)."""
+    cfg = ElasticCfg()
+    cfg.n[0], cfg.n[1] = shape
+    for i in range(4):
+        cfg.bc[i] = bc[i]
+    cfg.store_fmt = store_fmt
+    cfg.arith_fmt = store_fmt if arith_fmt is None else arith_fmt
+    cfg.stencil_fmt = cfg.arith_fmt if stencil_fmt is None else stencil_fmt
+    cfg.comp = comp
+    return cfg
+
+
+ELASTIC_FIELDS = ("vx", "vy", "sxx", "syy", "sxy")
+
+
+class ElasticState:
+    """Fields as float64 arrays shaped (ny, nx); f[name] values, t[name] compensations."""
+
+    def __init__(self, cfg: ElasticCfg):
+        self.cfg = cfg
+        self.shape = (int(cfg.n[1]), int(cfg.n[0]))
+        self.f = {k: np.zeros(self.shape) for k in ELASTIC_FIELDS}
+        self.t = {k: np.zeros(self.shape) for k in ELASTIC_FIELDS}
+        self.coef = {k: np.zeros(self.shape) for k in ("bx", "by", "l2m", "lam", "mu")}
+        self.step = 0
+        self.src_index = -1
+        self.src = None
+
+    def apply_walls(self):
+        _elib().orc_elastic_apply_walls(C.byref(self.cfg), _dp(self.f["vx"]), _dp(self.f["vy"]),
+                                        _dp(self.f["sxy"]))
+
+    def run(self, nsteps, rec_field=2, rec_index=None, energy=False):
+        nrec = 0 if rec_index is None else len(rec_index)
+        traces = np.zeros((nsteps, nrec)) if nrec else None
+        en = np.zeros(nsteps) if energy else None
+        ri = None
+        if nrec:
+            ri_arr = np.ascontiguousarray(rec_index, dtype=np.int64)
+            ri = ri_arr.ctypes.data_as(C.POINTER(C.c_int64))
+        src = None if self.src is None else _f64(self.src)
+        f, t, c = self.f, self.t, self.coef
+        rc = _elib().orc_elastic_run(
+            C.byref(self.cfg), _dp(f["vx"]), _dp(t["vx"]), _dp(f["vy"]), _dp(t["vy"]),
+            _dp(f["sxx"]), _dp(t["sxx"]), _dp(f["syy"]), _dp(t["syy"]), _dp(f["sxy"]),
+            _dp(t["sxy"]), _dp(c["bx"]), _dp(c["by"]), _dp(c["l2m"]), _dp(c["lam"]), _dp(c["mu"]),
+            nsteps, self.step, self.src_index, 0 if src is None else src.size, _dp(src),
+            rec_field, nrec, ri, _dp(traces), _dp(en))
+        if rc != 0:
+            raise MemoryError("oracle run failed")
+        self.step += nsteps
+        return traces, en
+
+
+_elib_done = False
+
+
+def _elib():
+    global _elib_done
+    L = lib()
+    if not _elib_done:
+        dp = C.POINTER(C.c_double)
+        i64 = C.c_int64
+        L.orc_elastic_apply_walls.argtypes = [C.c_void_p, dp, dp, dp]
+        L.orc_elastic_run.restype = C.c_int
+        L.orc_elastic_run.argtypes = ([C.c_void_p] + [dp] * 10 + [dp] * 5 +
+                                      [i64, i64, i64, i64, dp, C.c_int32, i64,
+                                       C.POINTER(C.c_int64), dp, dp])
+        L.orc_elastic_coefficients.restype = C.c_int
+        L.orc_elastic_coefficients.argtypes = [C.c_void_p, C.c_double, C.c_double, dp, dp, dp,
+                                               dp, dp, dp, dp, dp, dp]
+        L.orc_elastic_scale_source.argtypes = [i64, dp, C.c_double, C.c_double, C.c_double,
+                                               C.c_double, C.c_int, dp]
+        _elib_done = True
+    return L
+
+
+def elastic_coefficients(cfg: ElasticCfg, h, dt, rho, vp, vs):
+    """Multipliers bx, by (velocities), l2m, lam (normal stresses), mu (shear).
+    Returns (dict, Z0, ok)."""
+    rho, vp, vs = _f64(rho), _f64(vp), _f64(vs)
+    out = {k: np.zeros(rho.shape) for k in ("bx", "by", "l2m", "lam", "mu")}
+    z0 = C.c_double()
+    bad = _elib().orc_elastic_coefficients(C.byref(cfg), h, dt, _dp(rho), _dp(vp), _dp(vs),
+                                           _dp(out["bx"]), _dp(out["by"]), _dp(out["l2m"]),
+                                           _dp(out["lam"]), _dp(out["mu"]), C.byref(z0))
+    return out, z0.value, bad == 0
+
+
+def elastic_scale_source(w, dt, Z0, P0, h, fmt):
+    """v_y source in increment units s^ = RN(w dt Z0 / (P0 h^2))."""
+    w = _f64(w)
+    out = np.empty_like(w)
+    _elib().orc_elastic_scale_source(w.size, _dp(w), dt, Z0, P0, h, fmt, _dp(out))
+    return out
+
+
+def elastic_setup(shape, bc, h, dt, rho, vp, vs, store_fmt, comp, P0=1.0, arith_fmt=None,
+                  stencil_fmt=None, init=None):
+    """Ready-to-run ElasticState from physical inputs. init: dict field -> array
+    (velocities in m/s, stresses in Pa)."""
+    cfg = elastic_cfg(shape, bc, store_fmt, comp, arith_fmt, stencil_fmt)
+    st = ElasticState(cfg)
+    coef, Z0, ok = elastic_coefficients(cfg, h, dt, rho, vp, vs)
+    if not ok:
+        raise ValueError("elastic multiplier outside the storage format's range")
+    st.coef, st.Z0, st.P0, st.h, st.dt = coef, Z0, P0, h, dt
+    for name, arr in (init or {}).items():
+        if name in ("vx", "vy"):
+            st.f[name] = scale_velocity(arr, Z0, P0, store_fmt).reshape(st.shape)
+        else:
+            st.f[name] = scale_pressure(arr, P0, store_fmt).reshape(st.shape)
+    st.apply_walls()
+    return st

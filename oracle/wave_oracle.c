@@ -442,3 +442,237 @@ double orc_energy_factor(double h, double dt, double P0, double Z0, int ndim)
     const double hd1 = (ndim == 2) ? h : h * h;
     return 0.5 * hd1 * P0 * P0 * dt / Z0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* 2D isotropic elastic velocity-stress leapfrog (Eq. 2, Appendix A).       */
+/* ------------------------------------------------------------------------ */
+/* Grid (Virieux staggering, the reading of the missing Fig. 1 extended to
+ * Eq. 2): sxx, syy at nodes (i, j); vx at (i+1/2, j); vy at (i, j+1/2);
+ * sxy at (i+1/2, j+1/2). All fields stored n[0] x n[1], x fastest.
+ * Boundary kinds per face (x-lo, x-hi, y-lo, y-hi):
+ *   ORC_BC_PERIODIC (both faces of an axis): wrap.
+ *   ORC_EBC_RIGID: frictionless rigid wall on the half points -1/2 and
+ *     N-1/2: the normal velocity and the shear stress are odd about the wall
+ *     (zero on it; the stored point at N-1 is held at zero), the tangential
+ *     velocity and the normal stresses are even.
+ *   ORC_EBC_FREE (y-lo only): traction-free top in zero-extension form: every
+ *     field reads zero above row 0.
+ * Each closure is a restriction of a skew operator, so the pair (gradient of
+ * stress, divergence of velocity) stays an exact negative transpose. */
+enum { ORC_EBC_RIGID = 1, ORC_EBC_FREE = 2 };
+
+typedef struct {
+    int64_t n[2];
+    int32_t bc[4];
+    int32_t store_fmt, arith_fmt, stencil_fmt, comp;
+} orc_elastic_cfg;
+
+/* Image of index m along an axis of N points for a field that is node-type
+ * (node = 1) or half-type (node = 0) along that axis, with odd parity about a
+ * rigid wall when odd = 1. lo_bc / hi_bc are the two faces' kinds.
+ * Returns the sign (+1, -1) or 0 for "reads zero". */
+static int e_map(int64_t m, int64_t N, int lo_bc, int hi_bc, int node, int odd, int64_t *out)
+{
+    if (m >= 0 && m < N) { *out = m; return 1; }
+    int bc = m < 0 ? lo_bc : hi_bc;
+    if (bc == ORC_BC_PERIODIC) { *out = ((m % N) + N) % N; return 1; }
+    if (bc == ORC_EBC_FREE) return 0;
+    /* rigid wall at -1/2 (low) or N-1/2 (high) */
+    if (node) {                       /* node m <-> -1-m, 2N-1-m */
+        *out = m < 0 ? -1 - m : 2 * N - 1 - m;
+        return odd ? -1 : 1;
+    }
+    /* half point m + 1/2 <-> -2-m (low), 2N-2-m (high); -1 is on the wall */
+    if (m == -1) { if (odd) return 0; *out = 0; return 1; }
+    *out = m < 0 ? -2 - m : 2 * N - 2 - m;
+    return odd ? -1 : 1;
+}
+
+static double e_read(const double *f, const orc_elastic_cfg *c, int ax, int node, int odd,
+                     int64_t i, int64_t j, int64_t m)
+{
+    int64_t idx[2] = {i, j}, mm;
+    int s = e_map(m, c->n[ax], c->bc[2 * ax], c->bc[2 * ax + 1], node, odd, &mm);
+    if (s == 0) return 0.0;
+    idx[ax] = mm;
+    double v = f[idx[0] + c->n[0] * idx[1]];
+    return s > 0 ? v : -v;
+}
+
+/* Points a rigid wall holds at zero: vx and sxy on column N-1 (rigid x),
+ * vy and sxy on row N-1 (rigid y-hi). */
+void orc_elastic_apply_walls(const orc_elastic_cfg *c, double *vx, double *vy, double *sxy)
+{
+    const int64_t nx = c->n[0], ny = c->n[1];
+    for (int64_t j = 0; j < ny; j++)
+        for (int64_t i = 0; i < nx; i++) {
+            int64_t q = i + nx * j;
+            if (c->bc[1] == ORC_EBC_RIGID && i == nx - 1) { vx[q] = 0.0; sxy[q] = 0.0; }
+            if (c->bc[3] == ORC_EBC_RIGID && j == ny - 1) { vy[q] = 0.0; sxy[q] = 0.0; }
+        }
+}
+
+/* Stencil of field f along axis ax around the target, whose offsets to f's
+ * points are -3/2..+3/2: f's indices base-1..base+2 (node-type f targeted at a
+ * half point, base = target index) or base-2..base+1 (half-type f targeted at
+ * a node, base = target index). */
+static double e_stencil(const double *f, const orc_elastic_cfg *c, int ax, int node, int odd,
+                        int64_t i, int64_t j, int fmt)
+{
+    const int64_t m = ax == 0 ? i : j;
+    const int64_t first = node ? m - 1 : m - 2;
+    double a0 = e_read(f, c, ax, node, odd, i, j, first);
+    double a1 = e_read(f, c, ax, node, odd, i, j, first + 1);
+    double a2 = e_read(f, c, ax, node, odd, i, j, first + 2);
+    double a3 = e_read(f, c, ax, node, odd, i, j, first + 3);
+    return stencil(a0, a1, a2, a3, fmt);
+}
+
+/* One elastic leapfrog step per iteration, Eq. 2 in Algorithm 1 / 2 form:
+ *   vx += bx * (Dx sxx + Dy sxy)
+ *   vy += by * (Dx sxy + Dy syy)            [+ s, added to the increment]
+ *   sxx += (l2m * Dx vx) + (lam * Dy vy)
+ *   syy += (lam * Dx vx) + (l2m * Dy vy)
+ *   sxy += mu * (Dx vy + Dy vx)
+ * Energy (scaled) after each step, with the rounded multipliers:
+ *   E = sum vx^2/bx + sum vy^2/by
+ *     + sum over nodes (l2m (sxx sxx' + syy syy') - lam (sxx syy' + syy sxx')) / (l2m^2 - lam^2)
+ *     + sum sxy sxy' / mu              (primes: after the step) */
+int orc_elastic_run(const orc_elastic_cfg *c, double *vx, double *tvx, double *vy, double *tvy,
+                    double *sxx, double *tsxx, double *syy, double *tsyy, double *sxy,
+                    double *tsxy, const double *bx, const double *by, const double *l2m,
+                    const double *lam, const double *mu, int64_t nsteps, int64_t step0,
+                    int64_t src_index, int64_t src_nt, const double *src, int32_t rec_field,
+                    int64_t nrec, const int64_t *rec_index, double *traces, double *energy)
+{
+    const int64_t nx = c->n[0], ny = c->n[1];
+    const int sf = c->store_fmt, af = c->arith_fmt, stf = c->stencil_fmt, comp = c->comp;
+    double *rowacc = (double *)calloc((size_t)ny, sizeof(double));
+    if (!rowacc) return -1;
+    for (int64_t s = 0; s < nsteps; s++) {
+        const int64_t gstep = step0 + s;
+#pragma omp parallel for schedule(static)
+        for (int64_t j = 0; j < ny; j++)
+            for (int64_t i = 0; i < nx; i++) {
+                const int64_t q = i + nx * j;
+                /* vx at (i+1/2, j): sxx node-type in x (even); sxy half-type in y (odd) */
+                double R = add_f(e_stencil(sxx, c, 0, 1, 0, i, j, stf),
+                                 e_stencil(sxy, c, 1, 0, 1, i, j, stf), stf);
+                double inc = orc_round(mul_f(bx[q], R, stf), af);
+                update(&vx[q], &tvx[q], inc, comp, af, sf);
+                /* vy at (i, j+1/2): sxy half-type in x (odd); syy node-type in y (even) */
+                R = add_f(e_stencil(sxy, c, 0, 0, 1, i, j, stf),
+                          e_stencil(syy, c, 1, 1, 0, i, j, stf), stf);
+                inc = orc_round(mul_f(by[q], R, stf), af);
+                if (src && q == src_index && gstep < src_nt) inc = add_f(inc, src[gstep], af);
+                update(&vy[q], &tvy[q], inc, comp, af, sf);
+            }
+#pragma omp parallel for schedule(static)
+        for (int64_t j = 0; j < ny; j++) {
+            acc_t e = {0.0, 0.0};
+            for (int64_t i = 0; i < nx; i++) {
+                const int64_t q = i + nx * j;
+                /* nodes: vx half-type in x (odd), vy half-type in y (odd) */
+                const double dxvx = e_stencil(vx, c, 0, 0, 1, i, j, stf);
+                const double dyvy = e_stencil(vy, c, 1, 0, 1, i, j, stf);
+                const double sxx0 = sxx[q], syy0 = syy[q], sxy0 = sxy[q];
+                double inc = orc_round(add_f(mul_f(l2m[q], dxvx, stf), mul_f(lam[q], dyvy, stf), stf), af);
+                update(&sxx[q], &tsxx[q], inc, comp, af, sf);
+                inc = orc_round(add_f(mul_f(lam[q], dxvx, stf), mul_f(l2m[q], dyvy, stf), stf), af);
+                update(&syy[q], &tsyy[q], inc, comp, af, sf);
+                /* sxy at (i+1/2, j+1/2): vy node-type in x (even), vx node-type in y (even) */
+                double R = add_f(e_stencil(vy, c, 0, 1, 0, i, j, stf),
+                                 e_stencil(vx, c, 1, 1, 0, i, j, stf), stf);
+                inc = orc_round(mul_f(mu[q], R, stf), af);
+                update(&sxy[q], &tsxy[q], inc, comp, af, sf);
+                if (energy) {
+                    acc_add(&e, vx[q] * vx[q] / bx[q]);
+                    acc_add(&e, vy[q] * vy[q] / by[q]);
+                    const double det = l2m[q] * l2m[q] - lam[q] * lam[q];
+                    acc_add(&e, (l2m[q] * (sxx0 * sxx[q] + syy0 * syy[q]) -
+                                 lam[q] * (sxx0 * syy[q] + syy0 * sxx[q])) / det);
+                    if (mu[q] > 0.0) acc_add(&e, sxy0 * sxy[q] / mu[q]);
+                }
+            }
+            rowacc[j] = acc_val(&e);
+        }
+        if (energy) {
+            acc_t e = {0.0, 0.0};
+            for (int64_t j = 0; j < ny; j++) acc_add(&e, rowacc[j]);
+            energy[s] = acc_val(&e);
+        }
+        if (traces && nrec > 0) {
+            const double *f = rec_field == 1 ? vx : rec_field == 2 ? vy : rec_field == 4 ? sxx
+                              : rec_field == 5 ? syy : sxy;
+            for (int64_t r = 0; r < nrec; r++) traces[s * nrec + r] = f[rec_index[r]];
+        }
+    }
+    free(rowacc);
+    return 0;
+}
+
+/* Elastic multipliers, binary64 in exactly this order, each rounded once:
+ *   Z0 = max(rho) * max(vp)
+ *   bx = ((dt * Z0) / h) / rho_x,   rho_x = (rho[i] + rho[i+1]) * 0.5
+ *   by = ((dt * Z0) / h) / rho_y,   rho_y = (rho[j] + rho[j+1]) * 0.5
+ *   mu = (rho * vs) * vs,  lambda = ((rho * vp) * vp) - (2.0 * mu)
+ *   l2m = ((dt * (lambda + 2.0 * mu)) / Z0) / h,  lam = ((dt * lambda) / Z0) / h
+ *   mu_xy = 4 / (1/mu00 + 1/mu10 + 1/mu01 + 1/mu11) (0 if any is 0)
+ *   mu = ((dt * mu_xy) / Z0) / h
+ * The neighbour index i+1 (j+1) wraps on periodic axes and is clamped to the
+ * last point otherwise. Returns 0, or 1 if bx, by, l2m are not positive
+ * normal numbers or lam, mu are neither zero nor normal, or l2m <= |lam|. */
+int orc_elastic_coefficients(const orc_elastic_cfg *c, double h, double dt, const double *rho,
+                             const double *vp, const double *vs, double *bx, double *by,
+                             double *l2m, double *lam, double *mu, double *Z0_out)
+{
+    const int64_t nx = c->n[0], ny = c->n[1], npts = nx * ny;
+    const int sf = c->store_fmt;
+    double rho0 = 0.0, c0 = 0.0;
+    for (int64_t q = 0; q < npts; q++) {
+        if (rho[q] > rho0) rho0 = rho[q];
+        if (vp[q] > c0) c0 = vp[q];
+    }
+    const double Z0 = rho0 * c0;
+    *Z0_out = Z0;
+    const double tiny = ldexp(1.0, FORMATS[sf].emin);
+    int bad = 0;
+#define LAMEMU(q, m_, l_) do { m_ = (rho[q] * vs[q]) * vs[q]; l_ = ((rho[q] * vp[q]) * vp[q]) - (2.0 * m_); } while (0)
+    for (int64_t j = 0; j < ny; j++)
+        for (int64_t i = 0; i < nx; i++) {
+            const int64_t q = i + nx * j;
+            int64_t i1 = i + 1 < nx ? i + 1 : (c->bc[1] == ORC_BC_PERIODIC ? 0 : i);
+            int64_t j1 = j + 1 < ny ? j + 1 : (c->bc[3] == ORC_BC_PERIODIC ? 0 : j);
+            const double rx = (rho[q] + rho[i1 + nx * j]) * 0.5;
+            const double ry = (rho[q] + rho[i + nx * j1]) * 0.5;
+            bx[q] = orc_round(((dt * Z0) / h) / rx, sf);
+            by[q] = orc_round(((dt * Z0) / h) / ry, sf);
+            double m00, l00, m10, l10, m01, l01, m11, l11;
+            LAMEMU(q, m00, l00);
+            LAMEMU(i1 + nx * j, m10, l10);
+            LAMEMU(i + nx * j1, m01, l01);
+            LAMEMU(i1 + nx * j1, m11, l11);
+            (void)l10; (void)l01; (void)l11;
+            l2m[q] = orc_round(((dt * (l00 + 2.0 * m00)) / Z0) / h, sf);
+            lam[q] = orc_round(((dt * l00) / Z0) / h, sf);
+            double mh = 0.0;
+            if (m00 > 0.0 && m10 > 0.0 && m01 > 0.0 && m11 > 0.0)
+                mh = 4.0 / (1.0 / m00 + 1.0 / m10 + 1.0 / m01 + 1.0 / m11);
+            mu[q] = orc_round(((dt * mh) / Z0) / h, sf);
+            if (!(bx[q] >= tiny && isfinite(bx[q])) || !(by[q] >= tiny && isfinite(by[q])) ||
+                !(l2m[q] >= tiny && isfinite(l2m[q])) ||
+                !((lam[q] == 0.0 || fabs(lam[q]) >= tiny) && isfinite(lam[q])) ||
+                !((mu[q] == 0.0 || mu[q] >= tiny) && isfinite(mu[q])) || !(l2m[q] > fabs(lam[q])))
+                bad = 1;
+        }
+#undef LAMEMU
+    return bad;
+}
+
+/* Elastic v_y source in increment units: s^ = RN(w * ((dt * Z0) / (P0 * (h * h)))) */
+void orc_elastic_scale_source(int64_t nt, const double *w, double dt, double Z0, double P0,
+                              double h, int fmt, double *out)
+{
+    const double scale = (dt * Z0) / (P0 * (h * h));
+    for (int64_t i = 0; i < nt; i++) out[i] = orc_round(w[i] * scale, fmt);
+}

@@ -1,0 +1,562 @@
+// acoustic3d_stream.cu -- 2.5D streaming kernels for the 3D acoustic leapfrog.
+//
+// Same arithmetic, operation for operation, as the one-thread-per-point
+// kernels (fourth-order staggered difference of Section 3, plain or
+// compensated update of Algorithms 1 / 2), laid out for HBM bandwidth:
+//   * a CTA owns a TX x TY tile of (x, y) columns and walks a chunk of z planes;
+//   * each thread owns VEC consecutive x points of one row (one 16-byte vector
+//     of the storage format) and keeps the z-neighbour planes of its own
+//     vector in registers (a 4-deep queue), so every array is read once;
+//   * x neighbours come from the adjacent lanes by warp shuffle (global loads
+//     only at tile edges), y neighbours from a double-buffered shared-memory
+//     plane (one __syncthreads per plane);
+//   * half and bfloat16 arithmetic is done on packed pairs (f16x2 / bf16x2).
+// Requirements: 3D, n[0] a multiple of VEC. Boundary images (periodic, or the
+// odd / even images of the p = 0 walls) are applied on every halo load.
+#include <cuda_runtime.h>
+#include "acoustic_common.cuh"
+#include "wave_kernels.h"
+
+namespace wave {
+
+// ------------------------------------------------------------------------
+// Vector policies: VEC consecutive values of one thread.
+//   Raw: the 16-byte storage vector.   AV: the arithmetic vector.
+//   RS / AS: raw / arithmetic scalar.
+// ------------------------------------------------------------------------
+template <class P>
+struct VPacked {  // binary16 / bfloat16 stored and computed in pairs
+    static constexpr int N = 8;
+    using Raw = uint4;
+    using AV = uint4;
+    using RS = uint16_t;
+    using AS = uint16_t;
+    static __device__ __forceinline__ AV ld(const Raw &r) { return r; }
+    static __device__ __forceinline__ AS lds(RS s) { return s; }
+    static __device__ __forceinline__ Raw zero() { return make_uint4(0, 0, 0, 0); }
+    static __device__ __forceinline__ Raw rneg(const Raw &r) {
+        return make_uint4(r.x ^ 0x80008000u, r.y ^ 0x80008000u, r.z ^ 0x80008000u,
+                          r.w ^ 0x80008000u);
+    }
+    static __device__ __forceinline__ RS rneg_s(RS s) { return s ^ 0x8000u; }
+    static __device__ __forceinline__ AV add(const AV &a, const AV &b) {
+        return make_uint4(P::add2(a.x, b.x), P::add2(a.y, b.y), P::add2(a.z, b.z), P::add2(a.w, b.w)); }
+    static __device__ __forceinline__ AV sub(const AV &a, const AV &b) {
+        return make_uint4(P::sub2(a.x, b.x), P::sub2(a.y, b.y), P::sub2(a.z, b.z), P::sub2(a.w, b.w)); }
+    static __device__ __forceinline__ AV mul(const AV &a, const AV &b) {
+        return make_uint4(P::mul2(a.x, b.x), P::mul2(a.y, b.y), P::mul2(a.z, b.z), P::mul2(a.w, b.w)); }
+    static __device__ __forceinline__ AV splat(AS s) {
+        uint32_t w = (uint32_t)s | ((uint32_t)s << 16);
+        return make_uint4(w, w, w, w);
+    }
+    static __device__ __forceinline__ RS get(const Raw &r, int i) {
+        uint32_t w = (i >> 1) == 0 ? r.x : (i >> 1) == 1 ? r.y : (i >> 1) == 2 ? r.z : r.w;
+        return (RS)((i & 1) ? (w >> 16) : (w & 0xFFFFu));
+    }
+    static __device__ __forceinline__ void set(AV &r, int i, AS s) {
+        uint32_t *w = (i >> 1) == 0 ? &r.x : (i >> 1) == 1 ? &r.y : (i >> 1) == 2 ? &r.z : &r.w;
+        *w = (i & 1) ? ((*w & 0xFFFFu) | ((uint32_t)s << 16)) : ((*w & 0xFFFF0000u) | s);
+    }
+    static __device__ __forceinline__ AS aget(const AV &r, int i) { return get(r, i); }
+    static __device__ __forceinline__ float f32(const Raw &r, int i) { return P::to_f32(get(r, i)); }
+    // values at offsets +1, +2, -1, -2 from the own vector
+    static __device__ __forceinline__ AV shl1(const AV &o, AS r0) {
+        return make_uint4(__byte_perm(o.x, o.y, 0x5432), __byte_perm(o.y, o.z, 0x5432),
+                          __byte_perm(o.z, o.w, 0x5432), __byte_perm(o.w, (uint32_t)r0, 0x5432));
+    }
+    static __device__ __forceinline__ AV shl2(const AV &o, AS r0, AS r1) {
+        return make_uint4(o.y, o.z, o.w, (uint32_t)r0 | ((uint32_t)r1 << 16));
+    }
+    static __device__ __forceinline__ AV shr1(const AV &o, AS l0) {
+        return make_uint4(__byte_perm((uint32_t)l0, o.x, 0x5410), __byte_perm(o.x, o.y, 0x5432),
+                          __byte_perm(o.y, o.z, 0x5432), __byte_perm(o.z, o.w, 0x5432));
+    }
+    static __device__ __forceinline__ AV shr2(const AV &o, AS l1, AS l0) {
+        return make_uint4((uint32_t)l1 | ((uint32_t)l0 << 16), o.x, o.y, o.z);
+    }
+    // compensated / plain update on packed pairs (Algorithm 1 / 2)
+    template <int COMP>
+    static __device__ __forceinline__ void update(Raw &V, Raw &T, const AV &inc) {
+        if (COMP == 0) { V = add(V, inc); return; }
+        AV R = add(T, inc);
+        AV s = add(V, R);
+        if (COMP == 3) {
+            AV z = sub(s, V);
+            T = sub(R, z);
+        } else {
+            AV pa = sub(s, R);
+            AV pb = sub(s, pa);
+            AV da = sub(V, pa);
+            AV db = sub(R, pb);
+            T = add(da, db);
+        }
+        V = s;
+    }
+    static __device__ __forceinline__ AV c1() { return splat(P::c1()); }
+    static __device__ __forceinline__ AV c2() { return splat(P::c2()); }
+};
+
+struct VF32 {  // binary32 stored and computed, 4 per vector
+    static constexpr int N = 4;
+    using P = F32;
+    using Raw = float4;
+    using AV = float4;
+    using RS = float;
+    using AS = float;
+    static __device__ __forceinline__ AV ld(const Raw &r) { return r; }
+    static __device__ __forceinline__ AS lds(RS s) { return s; }
+    static __device__ __forceinline__ Raw zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    static __device__ __forceinline__ Raw rneg(const Raw &r) { return make_float4(-r.x, -r.y, -r.z, -r.w); }
+    static __device__ __forceinline__ RS rneg_s(RS s) { return -s; }
+    static __device__ __forceinline__ AV add(const AV &a, const AV &b) {
+        return make_float4(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z), __fadd_rn(a.w, b.w)); }
+    static __device__ __forceinline__ AV sub(const AV &a, const AV &b) {
+        return make_float4(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z), __fsub_rn(a.w, b.w)); }
+    static __device__ __forceinline__ AV mul(const AV &a, const AV &b) {
+        return make_float4(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y), __fmul_rn(a.z, b.z), __fmul_rn(a.w, b.w)); }
+    static __device__ __forceinline__ AV splat(AS s) { return make_float4(s, s, s, s); }
+    static __device__ __forceinline__ RS get(const Raw &r, int i) {
+        return i == 0 ? r.x : i == 1 ? r.y : i == 2 ? r.z : r.w; }
+    static __device__ __forceinline__ void set(AV &r, int i, AS s) {
+        if (i == 0) r.x = s; else if (i == 1) r.y = s; else if (i == 2) r.z = s; else r.w = s; }
+    static __device__ __forceinline__ AS aget(const AV &r, int i) { return get(r, i); }
+    static __device__ __forceinline__ float f32(const Raw &r, int i) { return get(r, i); }
+    static __device__ __forceinline__ AV shl1(const AV &o, AS r0) { return make_float4(o.y, o.z, o.w, r0); }
+    static __device__ __forceinline__ AV shl2(const AV &o, AS r0, AS r1) { return make_float4(o.z, o.w, r0, r1); }
+    static __device__ __forceinline__ AV shr1(const AV &o, AS l0) { return make_float4(l0, o.x, o.y, o.z); }
+    static __device__ __forceinline__ AV shr2(const AV &o, AS l1, AS l0) { return make_float4(l1, l0, o.x, o.y); }
+    template <int COMP>
+    static __device__ __forceinline__ void update(Raw &V, Raw &T, const AV &inc) {
+        float v[4] = {V.x, V.y, V.z, V.w}, t[4] = {T.x, T.y, T.z, T.w};
+        float in[4] = {inc.x, inc.y, inc.z, inc.w};
+#pragma unroll
+        for (int i = 0; i < 4; i++) wave::update<F32, COMP>(v[i], t[i], in[i]);
+        V = make_float4(v[0], v[1], v[2], v[3]);
+        T = make_float4(t[0], t[1], t[2], t[3]);
+    }
+    static __device__ __forceinline__ AV c1() { return splat(1.125f); }
+    static __device__ __forceinline__ AV c2() { return splat(F32::c2()); }
+};
+
+template <class P, class Store>
+struct VWide {  // half / bfloat16 stored, binary32 arithmetic, 8 per vector
+    static constexpr int N = 8;
+    using Raw = uint4;
+    struct AV { float f[8]; };
+    using RS = uint16_t;
+    using AS = float;
+    static __device__ __forceinline__ RS get(const Raw &r, int i) { return VPacked<Store>::get(r, i); }
+    static __device__ __forceinline__ AV ld(const Raw &r) {
+        AV a;
+#pragma unroll
+        for (int i = 0; i < 8; i++) a.f[i] = P::ld(get(r, i));
+        return a;
+    }
+    static __device__ __forceinline__ AS lds(RS s) { return P::ld(s); }
+    static __device__ __forceinline__ Raw zero() { return make_uint4(0, 0, 0, 0); }
+    static __device__ __forceinline__ Raw rneg(const Raw &r) { return VPacked<Store>::rneg(r); }
+    static __device__ __forceinline__ RS rneg_s(RS s) { return s ^ 0x8000u; }
+#define WAVE_VW_OP(name, fn)                                                     \
+    static __device__ __forceinline__ AV name(const AV &a, const AV &b) {        \
+        AV r;                                                                    \
+        _Pragma("unroll") for (int i = 0; i < 8; i++) r.f[i] = fn(a.f[i], b.f[i]); \
+        return r;                                                                \
+    }
+    WAVE_VW_OP(add, __fadd_rn)
+    WAVE_VW_OP(sub, __fsub_rn)
+    WAVE_VW_OP(mul, __fmul_rn)
+#undef WAVE_VW_OP
+    static __device__ __forceinline__ AV splat(AS s) {
+        AV a;
+#pragma unroll
+        for (int i = 0; i < 8; i++) a.f[i] = s;
+        return a;
+    }
+    static __device__ __forceinline__ void set(AV &r, int i, AS s) { r.f[i] = s; }
+    static __device__ __forceinline__ AS aget(const AV &r, int i) { return r.f[i]; }
+    static __device__ __forceinline__ float f32(const Raw &r, int i) { return Store::to_f32(get(r, i)); }
+    static __device__ __forceinline__ AV shl1(const AV &o, AS r0) {
+        AV a;
+#pragma unroll
+        for (int i = 0; i < 7; i++) a.f[i] = o.f[i + 1];
+        a.f[7] = r0;
+        return a;
+    }
+    static __device__ __forceinline__ AV shl2(const AV &o, AS r0, AS r1) {
+        AV a;
+#pragma unroll
+        for (int i = 0; i < 6; i++) a.f[i] = o.f[i + 2];
+        a.f[6] = r0;
+        a.f[7] = r1;
+        return a;
+    }
+    static __device__ __forceinline__ AV shr1(const AV &o, AS l0) {
+        AV a;
+        a.f[0] = l0;
+#pragma unroll
+        for (int i = 1; i < 8; i++) a.f[i] = o.f[i - 1];
+        return a;
+    }
+    static __device__ __forceinline__ AV shr2(const AV &o, AS l1, AS l0) {
+        AV a;
+        a.f[0] = l1;
+        a.f[1] = l0;
+#pragma unroll
+        for (int i = 2; i < 8; i++) a.f[i] = o.f[i - 2];
+        return a;
+    }
+    template <int COMP>
+    static __device__ __forceinline__ void update(Raw &V, Raw &T, const AV &inc) {
+        Raw v2 = V, t2 = T;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            uint16_t v = get(V, i), t = get(T, i);
+            wave::update<P, COMP>(v, t, inc.f[i]);
+            VPacked<Store>::set(v2, i, v);
+            VPacked<Store>::set(t2, i, t);
+        }
+        V = v2;
+        T = t2;
+    }
+    static __device__ __forceinline__ AV c1() { return splat(1.125f); }
+    static __device__ __forceinline__ AV c2() { return splat(P::c2()); }
+};
+
+template <class P> struct VecOf;
+template <> struct VecOf<F16> { using T = VPacked<F16>; };
+template <> struct VecOf<BF16> { using T = VPacked<BF16>; };
+template <> struct VecOf<F32> { using T = VF32; };
+template <> struct VecOf<F16W> { using T = VWide<F16W, F16>; };
+template <> struct VecOf<BF16W> { using T = VWide<BF16W, BF16>; };
+
+template <class V>
+__device__ __forceinline__ typename V::AV vstencil(const typename V::AV &fm3, const typename V::AV &fm1,
+                                                   const typename V::AV &fp1, const typename V::AV &fp3) {
+    typename V::AV t1 = V::sub(fp1, fm1);
+    typename V::AV t2 = V::sub(fp3, fm3);
+    return V::sub(V::mul(V::c1(), t1), V::mul(V::c2(), t2));
+}
+
+// Load the raw vector of a field at (x, row m_y, plane m_z) applying the
+// boundary images along y and z. node_y / node_z: the field sits on nodes
+// (odd image, wall at N) or half points (even image) along that axis.
+template <class V>
+__device__ __forceinline__ typename V::Raw load_vec_img(const void *f, const AcParams &prm, int x,
+                                                        int my, int mz, bool node_y, bool node_z) {
+    int jy, kz;
+    int sy = node_y ? img_node(my, prm.n[1], prm.bc[1], jy) : img_half(my, prm.n[1], prm.bc[1], jy);
+    int sz = node_z ? img_node(mz, prm.n[2], prm.bc[2], kz) : img_half(mz, prm.n[2], prm.bc[2], kz);
+    if (sy == 0 || sz == 0 || x >= prm.n[0] || my > prm.n[1] + 2 || my < -3 || mz > prm.n[2] + 2 || mz < -3)
+        return V::zero();
+    const typename V::Raw *p = reinterpret_cast<const typename V::Raw *>(
+        static_cast<const char *>(f) + (x + prm.sy * jy + prm.sz * (int64_t)kz) * sizeof(typename V::RS));
+    typename V::Raw r = *p;
+    return (sy * sz < 0) ? V::rneg(r) : r;
+}
+
+// One scalar of a field at (mx, row j, plane k) with the x boundary image.
+template <class V>
+__device__ __forceinline__ typename V::RS load_x_img(const void *f, const AcParams &prm, int mx, int j,
+                                                     int k, bool node_x) {
+    int ix;
+    int s = node_x ? img_node(mx, prm.n[0], prm.bc[0], ix) : img_half(mx, prm.n[0], prm.bc[0], ix);
+    if (s == 0) return typename V::RS(0);
+    typename V::RS v = static_cast<const typename V::RS *>(f)[ix + prm.sy * j + prm.sz * (int64_t)k];
+    return s < 0 ? V::rneg_s(v) : v;
+}
+
+template <class RS>
+__device__ __forceinline__ RS shfl_rs(RS v, int delta, bool up) {
+    uint32_t u;
+    if (sizeof(RS) == 2) u = (uint32_t)(*reinterpret_cast<const uint16_t *>(&v));
+    else u = *reinterpret_cast<const uint32_t *>(&v);
+    u = up ? __shfl_up_sync(0xffffffffu, u, delta) : __shfl_down_sync(0xffffffffu, u, delta);
+    RS r;
+    if (sizeof(RS) == 2) *reinterpret_cast<uint16_t *>(&r) = (uint16_t)u;
+    else *reinterpret_cast<uint32_t *>(&r) = u;
+    return r;
+}
+
+template <class V>
+__device__ __forceinline__ typename V::AV coef_vec(const void *arr, uint32_t uni, int64_t q) {
+    if (arr) return V::ld(*reinterpret_cast<const typename V::Raw *>(
+                 static_cast<const char *>(arr) + q * sizeof(typename V::RS)));
+    typename V::RS s;
+    from_bits(uni, s);
+    return V::splat(V::lds(s));
+}
+
+template <class V>
+__device__ __forceinline__ typename V::Raw &at(void *f, int64_t q) {
+    return *reinterpret_cast<typename V::Raw *>(static_cast<char *>(f) + q * sizeof(typename V::RS));
+}
+
+constexpr int TXV = 8;  // threads per tile row
+
+// ------------------------------------------------------------------------
+// Velocity half step: v_c += a_c * D_c(p), c = x, y, z.
+// ------------------------------------------------------------------------
+template <class P, int COMP, int TY>
+__global__ void __launch_bounds__(TXV *TY) kv_stream(AcParams prm, int zchunk) {
+    using V = typename VecOf<P>::T;
+    using Raw = typename V::Raw;
+    using AV = typename V::AV;
+    using RS = typename V::RS;
+    constexpr int N = V::N;
+    constexpr int TX = TXV * N;
+    __shared__ Raw sp[2][TY + 3][TXV];  // local row r <-> global row y0 - 1 + r
+
+    const int tid = threadIdx.x;
+    const int lx = tid % TXV, row = tid / TXV;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * zchunk;
+    const int z1 = min(z0 + zchunk, prm.n[2]);
+    const int x = x0 + lx * N;
+    const int j = y0 + row;
+    const bool active = x < prm.n[0] && j < prm.n[1];
+    // halo rows of the shared plane: local rows 0, TY+1, TY+2
+    const bool halo_loader = tid < 3 * TXV;
+    const int hr = tid / TXV;                       // 0, 1, 2
+    const int h_local = hr == 0 ? 0 : TY + hr;
+    const int h_row = y0 - 1 + h_local;
+    const int h_x = x0 + (tid % TXV) * N;
+
+    // z queue of the own p vector: planes k-1, k, k+1 (k+2 loaded in the loop)
+    Raw q0 = load_vec_img<V>(prm.p, prm, x, j, z0 - 1, true, true);
+    Raw q1 = load_vec_img<V>(prm.p, prm, x, j, z0, true, true);
+    Raw q2 = load_vec_img<V>(prm.p, prm, x, j, z0 + 1, true, true);
+    int buf = 0;
+    for (int k = z0; k < z1; k++) {
+        Raw q3 = load_vec_img<V>(prm.p, prm, x, j, k + 2, true, true);
+        Raw hv;
+        if (halo_loader) hv = load_vec_img<V>(prm.p, prm, h_x, h_row, k, true, true);
+        const int64_t q = x + prm.sy * j + prm.sz * (int64_t)k;
+        Raw vv[3], tt[3];
+        if (active) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                vv[c] = at<V>(prm.v[c], q);
+                tt[c] = COMP ? at<V>(prm.tv[c], q) : V::zero();
+            }
+        }
+        // x neighbours of the own plane-k vector: p[x-1], p[x+N], p[x+N+1]
+        RS l0 = shfl_rs(V::get(q1, N - 1), 1, true);
+        RS r0 = shfl_rs(V::get(q1, 0), 1, false);
+        RS r1 = shfl_rs(V::get(q1, 1), 1, false);
+        sp[buf][row + 1][lx] = q1;
+        if (halo_loader) sp[buf][h_local][tid % TXV] = hv;
+        if (active) {
+            if (lx == 0) l0 = load_x_img<V>(prm.p, prm, x - 1, j, k, true);
+            if (lx == TXV - 1 || x + N >= prm.n[0]) {
+                r0 = load_x_img<V>(prm.p, prm, x + N, j, k, true);
+                r1 = load_x_img<V>(prm.p, prm, x + N + 1, j, k, true);
+            }
+        }
+        __syncthreads();
+        if (active) {
+            const AV own = V::ld(q1);
+            // v_x at i + 1/2: p[i-1], p[i], p[i+1], p[i+2]
+            AV Dx = vstencil<V>(V::shr1(own, V::lds(l0)), own, V::shl1(own, V::lds(r0)),
+                                V::shl2(own, V::lds(r0), V::lds(r1)));
+            // v_y at j + 1/2: rows j-1, j, j+1, j+2 (local rows row, row+1, row+2, row+3)
+            AV Dy = vstencil<V>(V::ld(sp[buf][row][lx]), own, V::ld(sp[buf][row + 2][lx]),
+                                V::ld(sp[buf][row + 3][lx]));
+            // v_z at k + 1/2: planes k-1, k, k+1, k+2
+            AV Dz = vstencil<V>(V::ld(q0), own, V::ld(q2), V::ld(q3));
+            AV D[3] = {Dx, Dy, Dz};
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                AV inc = V::mul(coef_vec<V>(prm.a[c], prm.a_uni[c], q), D[c]);
+                V::template update<COMP>(vv[c], tt[c], inc);
+                at<V>(prm.v[c], q) = vv[c];
+                if (COMP) at<V>(prm.tv[c], q) = tt[c];
+            }
+        }
+        q0 = q1;
+        q1 = q2;
+        q2 = q3;
+        buf ^= 1;
+    }
+}
+
+// Compensated binary32 accumulation for the energy (TwoSum per term).
+struct KSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        float t = __fadd_rn(s, x);
+        float pa = __fsub_rn(t, x);
+        float pb = __fsub_rn(t, pa);
+        float da = __fsub_rn(s, pa);
+        float db = __fsub_rn(x, pb);
+        c = __fadd_rn(c, __fadd_rn(da, db));
+        s = t;
+    }
+};
+
+// ------------------------------------------------------------------------
+// Pressure half step: p += b * (Dx vx + Dy vy + Dz vz [+ s]), optional energy.
+// ------------------------------------------------------------------------
+template <class P, int COMP, int TY, bool ENERGY>
+__global__ void __launch_bounds__(TXV *TY) kp_stream(AcParams prm, int zchunk) {
+    using V = typename VecOf<P>::T;
+    using Raw = typename V::Raw;
+    using AV = typename V::AV;
+    using RS = typename V::RS;
+    constexpr int N = V::N;
+    constexpr int TX = TXV * N;
+    __shared__ Raw sv[2][TY + 3][TXV];  // v_y, local row r <-> global row y0 - 2 + r
+
+    const int tid = threadIdx.x;
+    const int lx = tid % TXV, row = tid / TXV;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * zchunk;
+    const int z1 = min(z0 + zchunk, prm.n[2]);
+    const int x = x0 + lx * N;
+    const int j = y0 + row;
+    const bool active = x < prm.n[0] && j < prm.n[1];
+    const bool halo_loader = tid < 3 * TXV;
+    const int hr = tid / TXV;
+    const int h_local = hr == 0 ? 0 : hr == 1 ? 1 : TY + 2;
+    const int h_row = y0 - 2 + h_local;
+    const int h_x = x0 + (tid % TXV) * N;
+
+    // z queue of the own v_z vector: planes k-2, k-1, k (k+1 loaded in the loop)
+    Raw r0 = load_vec_img<V>(prm.v[2], prm, x, j, z0 - 2, true, false);
+    Raw r1 = load_vec_img<V>(prm.v[2], prm, x, j, z0 - 1, true, false);
+    Raw r2 = load_vec_img<V>(prm.v[2], prm, x, j, z0, true, false);
+    KSum acc;
+    int buf = 0;
+    for (int k = z0; k < z1; k++) {
+        Raw r3 = load_vec_img<V>(prm.v[2], prm, x, j, k + 1, true, false);
+        // own v_x and v_y (rows beyond the grid take the even image)
+        Raw vx = load_vec_img<V>(prm.v[0], prm, x, j, k, true, true);
+        Raw vy = load_vec_img<V>(prm.v[1], prm, x, j, k, false, true);
+        Raw hv;
+        if (halo_loader) hv = load_vec_img<V>(prm.v[1], prm, h_x, h_row, k, false, true);
+        const int64_t q = x + prm.sy * j + prm.sz * (int64_t)k;
+        Raw pv, tv;
+        if (active) {
+            pv = at<V>(prm.p, q);
+            tv = COMP ? at<V>(prm.tp, q) : V::zero();
+        }
+        // x neighbours of v_x: vx[x-2], vx[x-1], vx[x+N]
+        RS l1 = shfl_rs(V::get(vx, N - 2), 1, true);
+        RS l0 = shfl_rs(V::get(vx, N - 1), 1, true);
+        RS rr = shfl_rs(V::get(vx, 0), 1, false);
+        sv[buf][row + 2][lx] = vy;
+        if (halo_loader) sv[buf][h_local][tid % TXV] = hv;
+        if (active) {
+            if (lx == 0) {
+                l1 = load_x_img<V>(prm.v[0], prm, x - 2, j, k, false);
+                l0 = load_x_img<V>(prm.v[0], prm, x - 1, j, k, false);
+            }
+            if (lx == TXV - 1 || x + N >= prm.n[0]) rr = load_x_img<V>(prm.v[0], prm, x + N, j, k, false);
+        }
+        __syncthreads();
+        if (active) {
+            const AV ownx = V::ld(vx);
+            // node i reads v_x at i-2, i-1, i, i+1 (+1/2)
+            AV R = vstencil<V>(V::shr2(ownx, V::lds(l1), V::lds(l0)), V::shr1(ownx, V::lds(l0)), ownx,
+                               V::shl1(ownx, V::lds(rr)));
+            AV Dy = vstencil<V>(V::ld(sv[buf][row][lx]), V::ld(sv[buf][row + 1][lx]), V::ld(vy),
+                                V::ld(sv[buf][row + 3][lx]));
+            R = V::add(R, Dy);
+            AV Dz = vstencil<V>(V::ld(r0), V::ld(r1), V::ld(r2), V::ld(r3));
+            R = V::add(R, Dz);
+            if (k == prm.src_k && j == prm.src_j && prm.src_i >= x && prm.src_i < x + N &&
+                prm.step < prm.src_nt) {
+                const int e = prm.src_i - x;
+                const typename V::AS sv_ = static_cast<const typename V::AS *>(prm.src)[prm.step];
+                V::set(R, e, P::add(V::aget(R, e), sv_));
+            }
+            AV inc = V::mul(coef_vec<V>(prm.b, prm.b_uni, q), R);
+            Raw pold = pv;
+            V::template update<COMP>(pv, tv, inc);
+            at<V>(prm.p, q) = pv;
+            if (COMP) at<V>(prm.tp, q) = tv;
+            if (ENERGY) {
+                typename V::RS bs, as[3];
+                const Raw *bvec = prm.b ? reinterpret_cast<const Raw *>(
+                                              static_cast<const char *>(prm.b) + q * sizeof(RS)) : nullptr;
+                Raw bv = bvec ? *bvec : V::zero();
+                Raw avv[3];
+#pragma unroll
+                for (int c = 0; c < 3; c++)
+                    avv[c] = prm.a[c] ? *reinterpret_cast<const Raw *>(static_cast<const char *>(prm.a[c]) +
+                                                                      q * sizeof(RS)) : V::zero();
+                from_bits(prm.b_uni, bs);
+#pragma unroll
+                for (int c = 0; c < 3; c++) from_bits(prm.a_uni[c], as[c]);
+                const Raw vz_own = r2;
+#pragma unroll
+                for (int e = 0; e < N; e++) {
+                    const float bw = prm.b ? V::f32(bv, e) : P::to_f32(bs);
+                    acc.add(e_term(V::f32(pold, e), V::f32(pv, e), bw));
+                    const Raw vc[3] = {vx, vy, vz_own};
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        const float aw = prm.a[c] ? V::f32(avv[c], e) : P::to_f32(as[c]);
+                        const float vf = V::f32(vc[c], e);
+                        acc.add(e_term(vf, vf, aw));
+                    }
+                }
+            }
+        }
+        r0 = r1;
+        r1 = r2;
+        r2 = r3;
+        buf ^= 1;
+    }
+    if (ENERGY) energy_reduce((double)acc.s + (double)acc.c, prm);
+}
+
+// ------------------------------------------------------------------------
+template <class P, int COMP, int TY>
+static cudaError_t launch_t(const AcParams &prm, int half_step, int zchunk, bool energy,
+                            cudaStream_t st) {
+    using V = typename VecOf<P>::T;
+    constexpr int TX = TXV * V::N;
+    dim3 grid((prm.n[0] + TX - 1) / TX, (prm.n[1] + TY - 1) / TY, (prm.n[2] + zchunk - 1) / zchunk);
+    dim3 block(TXV * TY);
+    if (half_step == 0) kv_stream<P, COMP, TY><<<grid, block, 0, st>>>(prm, zchunk);
+    else if (energy) kp_stream<P, COMP, TY, true><<<grid, block, 0, st>>>(prm, zchunk);
+    else kp_stream<P, COMP, TY, false><<<grid, block, 0, st>>>(prm, zchunk);
+    return cudaGetLastError();
+}
+
+template <class P>
+static cudaError_t launch_c(const AcParams &prm, int comp, int half_step, int zchunk, bool energy,
+                            cudaStream_t st) {
+    switch (comp) {
+    case 0: return launch_t<P, 0, 16>(prm, half_step, zchunk, energy, st);
+    case 3: return launch_t<P, 3, 16>(prm, half_step, zchunk, energy, st);
+    default: return launch_t<P, 6, 16>(prm, half_step, zchunk, energy, st);
+    }
+}
+
+int stream_vec_width(int prec) { return prec == PREC_FP32 ? 4 : 8; }
+
+bool acoustic_stream_supported(const AcParams &prm, int ndim, int prec) {
+    return ndim == 3 && prec != PREC_FP64 && prm.n[0] % stream_vec_width(prec) == 0 &&
+           prm.n[2] >= 4;
+}
+
+unsigned acoustic_stream_blocks(const AcParams &prm, int prec, int zchunk) {
+    const int tx = TXV * stream_vec_width(prec);
+    return ((prm.n[0] + tx - 1) / tx) * ((prm.n[1] + 15) / 16) * ((prm.n[2] + zchunk - 1) / zchunk);
+}
+
+cudaError_t acoustic_stream_half_step(const AcParams &prm, int prec, int comp, int half_step,
+                                      int zchunk, cudaStream_t st) {
+    const bool energy = prm.energy != 0;
+    switch (prec) {
+    case PREC_FP32: return launch_c<F32>(prm, comp, half_step, zchunk, energy, st);
+    case PREC_FP16: return launch_c<F16>(prm, comp, half_step, zchunk, energy, st);
+    case PREC_BF16: return launch_c<BF16>(prm, comp, half_step, zchunk, energy, st);
+    case PREC_FP16_F32ARITH: return launch_c<F16W>(prm, comp ? 3 : 0, half_step, zchunk, energy, st);
+    case PREC_BF16_F32ARITH: return launch_c<BF16W>(prm, comp ? 3 : 0, half_step, zchunk, energy, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace wave

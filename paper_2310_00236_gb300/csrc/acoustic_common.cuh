@@ -21,6 +21,7 @@ struct AcParams {
     uint32_t a_uni[3], b_uni;  // uniform multipliers (storage bits / float bits)
     // source (arithmetic-format table indexed by global step)
     int64_t src_q;             // linear pitched index of the source point, -1 none
+    int src_i, src_j, src_k;   // its grid coordinates (-1 none)
     const void *src;
     int64_t src_nt;
     int64_t step;              // global index of the step being taken

@@ -158,6 +158,8 @@ struct wave_ctx {
     int bc[6] = {0, 0, 0, 0, 0, 0};
     int prec = PREC_FP16, comp = 0;
     int kernel_choice = 0;
+    int zchunk = 64;
+    bool use_stream = false;
     double h = 0, dt = 0, P0 = 1.0, Z0 = 1.0;
     cudaStream_t stream = nullptr;
     bool poisoned = false;
@@ -364,6 +366,12 @@ static void fill_acoustic_params(wave_ctx *c, AcParams &prm) {
     prm.b = c->coef_is_uniform[0] ? nullptr : c->coef[0].ptr;
     prm.b_uni = c->coef_uni[0];
     prm.src_q = c->src_field == WAVE_F_P ? c->src_q : -1;
+    prm.src_i = prm.src_j = prm.src_k = -1;
+    if (prm.src_q >= 0) {
+        prm.src_k = (int)(c->src_q / c->plane);
+        prm.src_j = (int)((c->src_q % c->plane) / c->pitch);
+        prm.src_i = (int)(c->src_q % c->pitch);
+    }
     prm.src = c->src_table.ptr;
     prm.src_nt = c->src_nt;
     prm.e_part = static_cast<double *>(c->e_part.ptr);
@@ -457,11 +465,13 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
     if (!mat->rho || !mat->vp) return fail(WAVE_EINVAL, "material arrays are NULL");
     if (mat->kind == WAVE_ELASTIC && !mat->vs) return fail(WAVE_EINVAL, "elastic needs vs");
     double P0 = 1.0;
-    int kchoice = 0;
+    int kchoice = 0, zchunk = 0;
     if (opt) {
         if (opt->field_scale != 0.0) P0 = opt->field_scale;
         kchoice = opt->kernel;
+        zchunk = opt->zchunk;
     }
+    if (kchoice < 0 || kchoice > 1 || zchunk < 0) return fail(WAVE_EINVAL, "bad kernel options");
     if (!(P0 > 0.0) || !isfinite(P0)) return fail(WAVE_EINVAL, "field_scale must be positive");
     const int64_t npts = grid->n[0] * grid->n[1] * (grid->ndim == 3 ? grid->n[2] : 1);
     if (npts > ((int64_t)1 << 31) - 1) return fail(WAVE_EINVAL, "grid too large (>= 2^31 points)");
@@ -475,6 +485,7 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
     c->prec = prec;
     c->comp = compensated;
     c->kernel_choice = kchoice;
+    if (zchunk > 0) c->zchunk = zchunk;
     c->h = spacing[0];
     c->dt = dt;
     c->P0 = P0;
@@ -507,6 +518,9 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
         AcParams prm;
         fill_acoustic_params(c, prm);
         c->e_blocks = acoustic_generic_blocks(prm, c->ndim);
+        c->use_stream = kchoice == 0 && acoustic_stream_supported(prm, c->ndim, c->prec);
+        if (c->use_stream)
+            c->e_blocks = std::max(c->e_blocks, acoustic_stream_blocks(prm, c->prec, c->zchunk));
     }
     if (!st) st = dev_alloc(c, c->e_part, sizeof(double) * (size_t)std::max(1u, c->e_blocks));
     if (!st) st = dev_alloc(c, c->e_misc, 16);
@@ -764,11 +778,15 @@ static wave_status acoustic_steps(wave_ctx *c, int64_t n) {
         prm.energy = (s == n - 1) || trace;
         prm.e_out = static_cast<double *>(c->e_misc.ptr);
         cudaEvent_t m0 = mark(c);
-        cudaError_t e = acoustic_generic_half_step(prm, c->ndim, c->prec, c->comp, 0, c->stream);
+        cudaError_t e = c->use_stream
+                            ? acoustic_stream_half_step(prm, c->prec, c->comp, 0, c->zchunk, c->stream)
+                            : acoustic_generic_half_step(prm, c->ndim, c->prec, c->comp, 0, c->stream);
         cudaEvent_t m1 = mark(c);
         timed(c, 0, m0, m1);
         if (e == cudaSuccess)
-            e = acoustic_generic_half_step(prm, c->ndim, c->prec, c->comp, 1, c->stream);
+            e = c->use_stream
+                    ? acoustic_stream_half_step(prm, c->prec, c->comp, 1, c->zchunk, c->stream)
+                    : acoustic_generic_half_step(prm, c->ndim, c->prec, c->comp, 1, c->stream);
         cudaEvent_t m2 = mark(c);
         timed(c, 1, m1, m2);
         if (e == cudaSuccess && trace)

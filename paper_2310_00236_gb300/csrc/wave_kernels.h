@@ -18,6 +18,12 @@ cudaError_t acoustic_generic_half_step(const AcParams &prm, int ndim, int prec, 
 // Number of blocks the generic pressure kernel launches (energy partials).
 unsigned acoustic_generic_blocks(const AcParams &prm, int ndim);
 
+// Streaming 3D kernels (n[0] a multiple of the vector width, 3D only).
+bool acoustic_stream_supported(const AcParams &prm, int ndim, int prec);
+unsigned acoustic_stream_blocks(const AcParams &prm, int prec, int zchunk);
+cudaError_t acoustic_stream_half_step(const AcParams &prm, int prec, int comp, int half_step,
+                                      int zchunk, cudaStream_t st);
+
 // Receiver sampling: traces[r] = float(field[q[r]]) for r < nrec.
 cudaError_t sample_receivers(const void *field, int elem_bytes, int is_bf16, const int64_t *q,
                              int nrec, float *traces, cudaStream_t st);

@@ -54,7 +54,8 @@ class wave_materials(C.Structure):
 
 
 class wave_options(C.Structure):
-    _fields_ = [("field_scale", C.c_double), ("kernel", C.c_int32), ("reserved", C.c_int32 * 7)]
+    _fields_ = [("field_scale", C.c_double), ("kernel", C.c_int32), ("zchunk", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -154,7 +155,7 @@ def _stream_handle(stream):
 
 
 def wave_create(n, spacing, rho, vp, dt, precision, comp, vs=None, bc=(WAVE_BC_RIGID,) * 6,
-                kind=WAVE_ACOUSTIC, field_scale=1.0, kernel=0, stream=None) -> Context:
+                kind=WAVE_ACOUSTIC, field_scale=1.0, kernel=0, zchunk=0, stream=None) -> Context:
     """n: cells per axis (x, y[, z]); rho, vp, vs: arrays shaped like a field."""
     ndim = len(n)
     g = wave_grid()
@@ -178,6 +179,7 @@ def wave_create(n, spacing, rho, vp, dt, precision, comp, vs=None, bc=(WAVE_BC_R
     o = wave_options()
     o.field_scale = field_scale
     o.kernel = kernel
+    o.zchunk = zchunk
     out = C.c_void_p()
     _check(lib().wave_create(C.byref(g), sp, C.byref(m), float(dt), int(precision), int(comp),
                              C.byref(o), _stream_handle(stream), C.byref(out)))

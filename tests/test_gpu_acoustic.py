@@ -40,7 +40,9 @@ def _run(shape, bc, prec, comp, steps, seed=0, variable=True, src=False, kernel=
     v0 = [1e-4 * rng.standard_normal(p0.shape) for _ in range(nd)]
     s = None
     if src:
-        wav = inputs.ricker_table(steps, dt, 40.0) * 1e3
+        # amplitude chosen so the scaled source w Z0 / (P0 h^(d-1)) is about 0.5
+        z0 = float(np.max(rho) * np.max(c))
+        wav = inputs.ricker_table(steps, dt, 40.0) * 0.5 * h ** (nd - 1) / z0
         s = ([shape[a] // 3 for a in range(nd)], wav)
     ctx, st = acoustic_pair(shape, bc, prec, comp, h, dt, rho, c, p0=p0, v0=v0, src=s,
                             kernel=kernel)
@@ -132,7 +134,7 @@ def test_receivers_match_oracle_traces():
     rho, c = _media(shape, 9, h)
     dt = 0.4 * h / 4500.0
     steps = 50
-    wav = inputs.ricker_table(steps, dt, 30.0) * 1e3
+    wav = inputs.ricker_table(steps, dt, 30.0) * 0.5 * h / float(np.max(rho) * np.max(c))
     recs = [(5, 7), (20, 30), (39, 35), (0, 0)]
     ctx, st = acoustic_pair(shape, (R, P), "fp16", 3, h, dt, rho, c, src=([13, 11], wav))
     try:

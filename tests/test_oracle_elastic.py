@@ -1,0 +1,269 @@
+"""Pins for the oracle's elastic velocity-stress scheme (Eq. 2, Appendix A).
+
+* Brute-force operators on tiny grids against dense matrices assembled here
+  from the printed stencil weights and the boundary images, and the exact
+  negative-transpose (skew) structure on the free unknowns.
+* Exact FP64 energy conservation with periodic, rigid and free faces.
+* Reduction to the (separately pinned) acoustic oracle: a plane P wave along x
+  is the 1D acoustic problem with a = bx, b = l2m; a plane S wave is the one
+  with a = by, b = mu.
+* Mirror symmetry, zero state, and the paper's compensation finding in the
+  elastic case (Appendix A: fp16 without compensation loses energy, with
+  sum_6op it does not).
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2310_00236_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+PER, RIG, FREE = O.EBC_PERIODIC, O.EBC_RIGID, O.EBC_FREE
+
+
+def _weights():
+    w = {}
+    with open(os.path.join(GOLDEN, "stencil_weights.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            off, wt = line.split()
+            w[float(off)] = float(Fraction(wt))
+    return w
+
+
+def _ext(N, lo, hi, node, odd):
+    """Dense image map from N stored values to positions -3..N+2."""
+    E = np.zeros((N + 6, N))
+    for r in range(N + 6):
+        m = r - 3
+        if 0 <= m < N:
+            E[r, m] = 1.0
+            continue
+        bc = lo if m < 0 else hi
+        if bc == PER:
+            E[r, m % N] = 1.0
+        elif bc == FREE:
+            pass
+        elif node:
+            E[r, (-1 - m) if m < 0 else (2 * N - 1 - m)] = -1.0 if odd else 1.0
+        else:
+            if m == -1:
+                if not odd:
+                    E[r, 0] = 1.0
+                continue
+            E[r, (-2 - m) if m < 0 else (2 * N - 2 - m)] = -1.0 if odd else 1.0
+    return E
+
+
+def _diff(N, lo, hi, src_node, odd):
+    """Undivided derivative of a field that is node-type (src_node) or
+    half-type along the axis, evaluated at the other kind of point."""
+    w = _weights()
+    E = _ext(N, lo, hi, src_node, odd)
+    D = np.zeros((N, N))
+    for m in range(N):
+        first = m - 1 if src_node else m - 2
+        taps = dict(zip(range(first, first + 4), (w[-1.5], w[-0.5], w[0.5], w[1.5])))
+        for pos, wt in taps.items():
+            D[m] += wt * E[pos + 3]
+    return D
+
+
+def _along(mat, ax, shape):
+    nx, ny = shape
+    return np.kron(np.eye(ny), mat) if ax == 0 else np.kron(mat, np.eye(nx))
+
+
+FIELDS = ("vx", "vy", "sxx", "syy", "sxy")
+# (target, source field, axis, source node-type along axis, odd about rigid walls)
+MAPS = [("vx", "sxx", 0, True, False), ("vx", "sxy", 1, False, True),
+        ("vy", "sxy", 0, False, True), ("vy", "syy", 1, True, False),
+        ("sxx", "vx", 0, False, True), ("syy", "vy", 1, False, True),
+        ("sxy", "vy", 0, True, False), ("sxy", "vx", 1, True, False)]
+
+
+def _impulse_maps(shape, bc):
+    """Impulse responses of one FP64 step with unit multipliers, separated
+    by switching off the other half step (its multipliers set to zero)."""
+    nx, ny = shape
+    npts = nx * ny
+    cfg = O.elastic_cfg(shape, bc, O.FP64, 0)
+    out = {}
+    for tgt, src, ax, node, odd in MAPS:
+        M = np.zeros((npts, npts))
+        for q in range(npts):
+            st = O.ElasticState(cfg)
+            for k in st.coef:
+                st.coef[k] = np.zeros(st.shape)
+            st.f[src].flat[q] = 1.0
+            if tgt in ("vx", "vy"):
+                st.coef["bx" if tgt == "vx" else "by"][:] = 1.0
+            elif tgt == "sxy":
+                st.coef["mu"][:] = 1.0
+            else:
+                st.coef["l2m"][:] = 1.0
+            st.run(1)
+            M[:, q] = st.f[tgt].ravel() - (st.f[src].ravel() if src == tgt else 0)
+        out[(tgt, src)] = M
+    return out
+
+
+CASES = [((8, 8), (RIG, RIG, FREE, RIG)), ((8, 7), (PER, PER, FREE, RIG)),
+         ((7, 8), (RIG, RIG, RIG, RIG)), ((8, 8), (PER, PER, PER, PER))]
+
+
+def _held(shape, bc, name):
+    """Mask of points a rigid wall holds at zero."""
+    nx, ny = shape
+    m = np.zeros((ny, nx), bool)
+    if bc[1] == RIG and name in ("vx", "sxy"):
+        m[:, nx - 1] = True
+    if bc[3] == RIG and name in ("vy", "sxy"):
+        m[ny - 1, :] = True
+    return m.ravel()
+
+
+@pytest.mark.parametrize("shape,bc", CASES)
+def test_elastic_operators_brute_force_and_skew(oracle_lib, shape, bc):
+    maps = _impulse_maps(shape, bc)
+    for tgt, src, ax, node, odd in MAPS:
+        N = shape[ax]
+        ref = _along(_diff(N, bc[2 * ax], bc[2 * ax + 1], node, odd), ax, shape)
+        np.testing.assert_array_equal(maps[(tgt, src)], ref, err_msg=f"{src}->{tgt}")
+    # skew: the stress-to-velocity map is minus the transpose of the
+    # velocity-to-strain-rate map, on the unknowns not held at zero
+    pairs = [(("vx", "sxx"), ("sxx", "vx")), (("vx", "sxy"), ("sxy", "vx")),
+             (("vy", "sxy"), ("sxy", "vy")), (("vy", "syy"), ("syy", "vy"))]
+    for (a, b), (c, d) in pairs:
+        fa, fb = ~_held(shape, bc, a), ~_held(shape, bc, b)
+        G = maps[(a, b)][np.ix_(fa, fb)]
+        D = maps[(c, d)][np.ix_(fb, fa)]
+        np.testing.assert_array_equal(G, -D.T, err_msg=f"{a}<-{b}")
+
+
+def _layered(shape, h):
+    nx, ny = shape
+    y = np.arange(ny)
+    vp = np.where(y < ny // 3, 2000.0, np.where(y < 2 * ny // 3, 3000.0, 4000.0))
+    rho = np.where(y < ny // 3, 2000.0, np.where(y < 2 * ny // 3, 2300.0, 2600.0))
+    vp = np.repeat(vp[:, None], nx, 1)
+    rho = np.repeat(rho[:, None], nx, 1)
+    return rho, vp, vp / 1.73
+
+
+@pytest.mark.parametrize("bc", [(RIG, RIG, FREE, RIG), (PER, PER, FREE, RIG),
+                                (PER, PER, PER, PER), (RIG, RIG, RIG, RIG)])
+def test_elastic_energy_conserved_fp64(oracle_lib, bc):
+    shape = (40, 36)
+    h = 3.0
+    rho, vp, vs = _layered(shape, h)
+    dt = 0.5 * h / 4000.0
+    rng = np.random.default_rng(3)
+    init = {"sxx": rng.standard_normal(rho.shape), "sxy": rng.standard_normal(rho.shape),
+            "vy": rng.standard_normal(rho.shape) / 1e7}
+    st = O.elastic_setup(shape, bc, h, dt, rho, vp, vs, O.FP64, 0, init=init)
+    _, E = st.run(800, energy=True)
+    assert np.max(np.abs(E - E[0])) / E[0] <= 1e-12
+
+
+def test_elastic_reduces_to_acoustic_for_plane_waves(oracle_lib):
+    """A wave independent of y in a periodic homogeneous medium: (vx, sxx) is
+    the 1D acoustic problem with a = bx and b = l2m; (vy, sxy) with a = by and
+    b = mu. Same values in fp16 with sum_3op, step for step."""
+    nx, ny = 48, 8
+    h = 2.0
+    rho = np.full((ny, nx), 2200.0)
+    vp = np.full((ny, nx), 3000.0)
+    vs = vp / 1.73
+    dt = 0.45 * h / 3000.0
+    x = np.arange(nx) * h
+    prof = np.exp(-((x - 40.0) / 8.0) ** 2)
+    init = {"sxx": np.repeat(prof[None, :], ny, 0), "sxy": np.repeat(prof[None, :], ny, 0)}
+    st = O.elastic_setup((nx, ny), (PER,) * 4, h, dt, rho, vp, vs, O.FP16, 3, init=init)
+    # acoustic 2D with the elastic multipliers, uniform in y
+    cfg = O.acoustic_cfg((nx, ny), (O.BC_PERIODIC, O.BC_PERIODIC), O.FP16, 3)
+    acP = O.AcousticState(cfg)
+    acP.p = st.f["sxx"].copy()
+    acP.a = [st.coef["bx"].copy(), st.coef["bx"].copy(), np.zeros((ny, nx))]
+    acP.b = st.coef["l2m"].copy()
+    st.run(60)
+    acP.run(60)
+    np.testing.assert_array_equal(st.f["vx"], acP.v[0])
+    np.testing.assert_array_equal(st.f["sxx"], acP.p)
+    np.testing.assert_array_equal(st.t["sxx"], acP.tp)
+    # the S wave (vy, sxy) has the node and half-point roles swapped in x: it
+    # is the acoustic problem with p <- vy (nodes), v <- sxy (half points),
+    # a <- mu and b <- by, since vy' = by Dx(sxy) and sxy' = mu Dx(vy)
+    acS = O.AcousticState(cfg)
+    st2 = O.elastic_setup((nx, ny), (PER,) * 4, h, dt, rho, vp, vs, O.FP16, 3,
+                          init={"vy": np.repeat(prof[None, :], ny, 0) / 3e6})
+    acS.p = st2.f["vy"].copy()
+    acS.a = [st2.coef["mu"].copy(), st2.coef["mu"].copy(), np.zeros((ny, nx))]
+    acS.b = st2.coef["by"].copy()
+    # sxy starts at zero, so the elastic v_y half step of step 1 changes
+    # nothing and sxy after k elastic steps equals the acoustic "velocity"
+    # after k steps (both come from the same k-1 updates of vy)
+    st2.run(60)
+    acS.run(60)
+    np.testing.assert_array_equal(st2.f["sxy"], acS.v[0])
+    assert np.any(st2.f["vy"] != 0)
+
+
+def test_elastic_mirror_symmetry_exact(oracle_lib):
+    """Symmetric initial stresses about the vertical line x = (N-1)/2 in a
+    domain with rigid side walls: vy and the normal stresses stay mirror
+    symmetric and vx antisymmetric, bit for bit, in fp16 + sum_6op."""
+    nx, ny = 31, 24
+    h = 3.0
+    rho, vp, vs = _layered((nx, ny), h)
+    dt = 0.5 * h / 4000.0
+    x = np.arange(nx) - (nx - 1) / 2
+    y = np.arange(ny) - 8.0
+    X, Y = np.meshgrid(x, y)
+    g = np.exp(-(X ** 2 + Y ** 2) / 10.0) * 1e5
+    st = O.elastic_setup((nx, ny), (RIG, RIG, FREE, RIG), h, dt, rho, vp, vs, O.FP16, 6,
+                         P0=1e5, init={"sxx": g, "syy": g})
+    st.run(80)
+    for name in ("vy", "sxx", "syy"):
+        np.testing.assert_array_equal(st.f[name], st.f[name][:, ::-1])
+    # vx at i+1/2 mirrors to index nx-2-i; column nx-1 is held at zero
+    np.testing.assert_array_equal(st.f["vx"][:, : nx - 1], -st.f["vx"][:, nx - 2::-1])
+    assert np.any(st.f["vx"] != 0)
+
+
+def test_elastic_fp16_compensation_finding(oracle_lib):
+    """Appendix A: without compensation fp16 loses energy; sum_6op keeps it
+    (small CFL, pulse in a layered medium with a free top)."""
+    shape = (48, 40)
+    h = 3.0
+    rho, vp, vs = _layered(shape, h)
+    dt = 0.02 * h / 4000.0
+    x = np.arange(shape[0]) * h
+    y = np.arange(shape[1]) * h
+    X, Y = np.meshgrid(x, y)
+    g = np.exp(-((X - 72.0) ** 2 + (Y - 60.0) ** 2) / (2 * 9.0 ** 2)) * 1e6
+    res = {}
+    for comp in (0, 3, 6):
+        st = O.elastic_setup(shape, (PER, PER, FREE, RIG), h, dt, rho, vp, vs, O.FP16, comp,
+                             P0=1e6, init={"sxx": g, "syy": g})
+        _, E = st.run(3000, energy=True)
+        res[comp] = (E - E[0]) / E[0]
+    q = res[0][[750, 1500, 2250, 2999]]
+    assert np.all(np.diff(q) < 0) and res[0][-1] < -0.01       # monotone loss
+    assert np.max(np.abs(res[6])) < 0.05 * -res[0][-1]
+    # "sum_3op gives very similar results" (Appendix A)
+    assert np.max(np.abs(res[3] - res[6])) < 0.05 * -res[0][-1]
+
+
+def test_elastic_zero_state_stays_zero(oracle_lib):
+    shape = (12, 10)
+    rho, vp, vs = _layered(shape, 3.0)
+    for fmt, comp in ((O.FP16, 3), (O.BF16, 6), (O.FP32, 0)):
+        st = O.elastic_setup(shape, (RIG, RIG, FREE, RIG), 3.0, 3.0e-4, rho, vp, vs, fmt, comp)
+        st.run(10)
+        for k in O.ELASTIC_FIELDS:
+            assert not np.any(st.f[k]) and not np.any(st.t[k])
