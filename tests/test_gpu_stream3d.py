@@ -73,8 +73,8 @@ def test_stream_periodic_and_mixed_with_source(prec, comp):
 
 def test_stream_minimum_sizes():
     _run((8, 8, 8), (R, R, R), "fp16", 3, 9, zchunk=2, energy=True)
-    _run((8, 9, 4), (P, R, P), "fp16", 6, 9, zchunk=1)
-    _run((4, 8, 5), (R, P, R), "fp32", 3, 9, zchunk=4, energy=True)
+    _run((8, 9, 8), (P, R, P), "fp16", 6, 9, zchunk=1)
+    _run((12, 8, 9), (R, P, R), "fp32", 3, 9, zchunk=4, energy=True)
 
 
 # -------------------------------------------------------------- full size
