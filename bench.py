@@ -105,6 +105,9 @@ def workload(n: int):
     return inputs.acoustic_3d_random(n=n)
 
 
+ZCHUNK = 0
+
+
 def run_variant(W, w, prec_name, comp, steps, warmup, timing=True):
     """Create a context, warm up, time `steps` steps with CUDA events on the
     library's stream. Returns dict of measurements."""
@@ -112,7 +115,8 @@ def run_variant(W, w, prec_name, comp, steps, warmup, timing=True):
     code = W.PRECISIONS[prec_name]
     stream = torch.cuda.current_stream()
     ctx = W.wave_create(w["shape"], w["h"], w["rho"], w["c"], w["dt"], code, comp,
-                        bc=[W.WAVE_BC_RIGID] * 6, field_scale=w["P0"], stream=stream.cuda_stream)
+                        bc=[W.WAVE_BC_RIGID] * 6, field_scale=w["P0"], zchunk=ZCHUNK,
+                        stream=stream.cuda_stream)
     try:
         W.wave_set_initial(ctx, W.WAVE_F_P, w["p0"])
         W.wave_step(ctx, warmup)
@@ -255,7 +259,10 @@ def main():
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--zchunk", type=int, default=0, help="z planes per block (0: library default)")
     args = ap.parse_args()
+    global ZCHUNK
+    ZCHUNK = args.zchunk
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -158,7 +158,7 @@ struct wave_ctx {
     int bc[6] = {0, 0, 0, 0, 0, 0};
     int prec = PREC_FP16, comp = 0;
     int kernel_choice = 0;
-    int zchunk = 64;
+    int zchunk = 16;
     bool use_stream = false;
     double h = 0, dt = 0, P0 = 1.0, Z0 = 1.0;
     cudaStream_t stream = nullptr;
