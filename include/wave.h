@@ -265,6 +265,37 @@ wave_status wave_get_timing(wave_ctx *ctx, int32_t kind, int64_t *launches, doub
  * returns WAVE_ENOTIMPL. */
 wave_status wave_adjoint_step(wave_ctx *ctx, int64_t n, const float *residual_traces);
 
+/* wave_energy_acoustic_static -- the acoustic discrete energy (the quantity
+ * wave_energy reports) computed from device arrays the caller already owns,
+ * without allocating any device memory. The paper has no counterpart: this is
+ * an entry point for callers that cannot call cudaMalloc, such as a host
+ * framework that owns the whole device heap and hands out only views, code
+ * running while a CUDA stream is captured into a graph, or a real-time loop
+ * whose memory budget forbids allocation after start-up.
+ *   ndim, n      grid (2D or 3D), cells per axis
+ *   prec         storage format of every array below (the *_F32ARITH codes
+ *                mean half / bfloat16 storage)
+ *   p_old, p_new pressure p^n and p^{n+1}; v[c] velocities v_c^{n+1/2} (c < ndim)
+ *   a[c], b      the multipliers a_c and b, one per point
+ *                (all arrays packed, x fastest, no pitch, in device memory)
+ *   factor       multiplies the sum; 0.5 h^(d-1) P0^2 dt / Z0 gives wave_energy's units
+ *   device_out   one double in device memory, written by the GPU
+ *   cuda_stream  stream to run on (asynchronous; synchronise before reading)
+ * Its block partials live in a static device array of WAVE_ENERGY_STATIC_MAX_BLOCKS
+ * doubles (64 KiB plus a counter) that every GPU loading the library holds until
+ * the process exits; each block covers 2048 points, so grids above
+ * WAVE_ENERGY_STATIC_MAX_BLOCKS * 2048 = 16,777,216 points are rejected with
+ * WAVE_EINVAL. The first call on a device looks up the array's device address
+ * with that device current: make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (two streams,
+ * two host threads) race and return wrong sums. */
+#define WAVE_ENERGY_STATIC_MAX_BLOCKS 8192
+wave_status wave_energy_acoustic_static(int32_t ndim, const int64_t n[3], wave_precision prec,
+                                        const void *p_old, const void *p_new,
+                                        const void *const v[3], const void *const a[3],
+                                        const void *b, double factor, double *device_out,
+                                        void *cuda_stream);
+
 void wave_destroy(wave_ctx *ctx);
 const char *wave_last_error(void);
 

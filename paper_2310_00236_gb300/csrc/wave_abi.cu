@@ -30,6 +30,10 @@ static wave_status fail(wave_status st, const char *fmt, ...) {
 
 extern "C" const char *wave_last_error(void) { return g_err; }
 
+namespace wave {
+void set_last_error_text(const char *msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+}  // namespace wave
+
 extern "C" const char *wave_build_info(void) {
     return "libwave: sm_103a, -fmad=false, explicit .rn half/bfloat16/binary32 arithmetic";
 }

@@ -34,7 +34,7 @@ EXPORTS = ["wave_set_allocator", "wave_create", "wave_set_initial", "wave_set_so
            "wave_get_field", "wave_get_raw", "wave_set_raw", "wave_get_coefficient",
            "wave_get_state", "wave_set_state", "wave_sync", "wave_steps_done",
            "wave_adjoint_step", "wave_destroy", "wave_last_error", "wave_build_info",
-           "wave_set_timing", "wave_get_timing"]
+           "wave_set_timing", "wave_get_timing", "wave_energy_acoustic_static"]
 
 
 class WaveError(RuntimeError):
@@ -94,6 +94,8 @@ def lib() -> C.CDLL:
         "wave_adjoint_step": [vp, i64, vp],
         "wave_set_timing": [vp, i32],
         "wave_get_timing": [vp, i32, C.POINTER(C.c_int64), dp],
+        "wave_energy_acoustic_static": [i32, C.POINTER(C.c_int64), C.c_int, vp, vp,
+                                        C.POINTER(vp), C.POINTER(vp), vp, C.c_double, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -297,6 +299,21 @@ def wave_get_timing(ctx: Context, kind: int):
     ms = C.c_double()
     _check(lib().wave_get_timing(ctx.ptr, kind, C.byref(n), C.byref(ms)))
     return n.value, ms.value
+
+
+def wave_energy_acoustic_static(ndim, n, precision, p_old, p_new, v, a, b, factor, device_out,
+                                stream=None):
+    """The acoustic discrete energy from device tensors the caller owns, with
+    no device allocation inside the library (for callers that cannot call
+    cudaMalloc). All array arguments are torch CUDA tensors (packed, storage
+    format); device_out is a one-element float64 CUDA tensor."""
+    nn = (C.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
+    vv = (C.c_void_p * 3)(*([t.data_ptr() for t in v] + [None] * (3 - len(v))))
+    aa = (C.c_void_p * 3)(*([t.data_ptr() for t in a] + [None] * (3 - len(a))))
+    _check(lib().wave_energy_acoustic_static(
+        ndim, nn, int(precision), C.c_void_p(p_old.data_ptr()), C.c_void_p(p_new.data_ptr()),
+        vv, aa, C.c_void_p(b.data_ptr()), float(factor), C.c_void_p(device_out.data_ptr()),
+        _stream_handle(stream)))
 
 
 # ---------------------------------------------------------------- allocator
