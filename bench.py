@@ -168,6 +168,41 @@ def run_e2e(W, w, prec_name, comp, steps):
             "finite": bool(np.isfinite(p).all())}
 
 
+def run_elastic(W, steps: int, warmup: int):
+    """2D elastic three-layer workload (1024^2, free top, rigid sides, Ricker
+    15 Hz vertical force for 0.1 s), fp16 + sum_6op. L2-resident (~31 MB)."""
+    import torch
+    from paper_2310_00236_gb300 import inputs
+    w = inputs.elastic_2d_layered()
+    stream = torch.cuda.current_stream()
+    ctx = W.wave_create(w["shape"], w["h"], w["rho"], w["vp"], w["dt"], W.WAVE_FP16,
+                        W.WAVE_COMP_6OP, vs=w["vs"], bc=[1, 1, 2, 1, 0, 0], kind=W.WAVE_ELASTIC,
+                        field_scale=1e5, stream=stream.cuda_stream)
+    try:
+        # amplitude: the scaled peak increment w dt Z0 / (P0 h^2) is 0.5
+        z0 = float(w["rho"].max() * w["vp"].max())
+        amp = 0.5 * 1e5 * w["h"] ** 2 / (w["dt"] * z0)
+        W.wave_set_source(ctx, W.WAVE_F_VY, w["src_idx"], w["wavelet"] * amp)
+        # past the source window, then time
+        W.wave_step(ctx, w["src_steps"] + warmup)
+        e0 = W.wave_energy(ctx)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        W.wave_step(ctx, steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        e1 = W.wave_energy(ctx)
+    finally:
+        W.wave_destroy(ctx)
+    npts = w["shape"][0] * w["shape"][1]
+    return {"workload": "2d_elastic_1024_three_layers_free_top", "precision": "fp16",
+            "compensation": "sum_6op", "value": npts * steps / (ms * 1e-3) / 1e9, "unit": UNIT,
+            "ms_per_step": ms / steps, "energy_drift_after_source": abs(e1 - e0) / abs(e0)}
+
+
 # ------------------------------------------------------------ CPU oracle
 def oracle_sample(target_s: float = 12.0, n: int = 64):
     """The CPU oracle (fp16 + sum_3op emulation, OpenMP on all host cores) on a
@@ -315,6 +350,10 @@ def main():
                             "energy_drift": abs(r32["e1"] - r32["e0"]) / abs(r32["e0"])},
                    "fp16_sum3op": {"value": value, "energy_drift": drift16}}
 
+    elastic = None
+    if not args.no_compare:
+        elastic = run_elastic(W, min(args.steps, 4000), args.warmup)
+
     e2e = None
     if not args.no_e2e:
         r = run_e2e(W, w, "fp16", 3, args.steps)
@@ -337,6 +376,7 @@ def main():
                            "l2": "working set 2.4 GB > L2 (no flush needed)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": sum(v[0] for v in kt.values()), "compare": compare,
+                "elastic": elastic,
                 "energy_drift": drift16}
         print(json.dumps(line), flush=True)
 

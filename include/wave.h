@@ -143,18 +143,22 @@ wave_status wave_set_allocator(wave_alloc_fn alloc, wave_free_fn free_fn, void *
  *   a_c = ((dt * Z0) / h) / rho_c                      at v_c points
  *   rho_c = (rho[m] + rho[m+1]) * 0.5 along axis c; at the last cell the
  *   neighbour wraps (periodic) or is the cell itself (rigid).
- * Elastic multipliers (WAVE_ELASTIC, 2D; mu = rho vs^2, lambda = rho vp^2 - 2 mu):
- *   Z0 = max(rho) * max(vp);  bx = ((dt * Z0) / h) / rho_x, by likewise
- *   (rho_x, rho_y as rho_c above); at sigma_xx/yy nodes
- *   l2m = ((dt * (lambda + 2 mu)) / Z0) / h, lam = ((dt * lambda) / Z0) / h;
- *   at sigma_xy points mu_xy = ((dt * mu_q) / Z0) / h with mu_q the
- *   harmonic mean 4 / (1/mu + 1/mu + 1/mu + 1/mu) of the four surrounding
- *   nodes (0 where any of them is 0).
- * Elastic boundaries: x faces PERIODIC (both) or RIGID; y-lo FREE or RIGID;
- * y-hi RIGID. RIGID is a frictionless rigid wall (normal velocity and shear
- * stress odd, the other fields even about the wall); FREE is a traction-free
- * surface in the zero-stress-outside form, whose wall sits half a cell above
- * node row 0.
+ * Elastic multipliers (WAVE_ELASTIC, 2D, Eq. 2), same rules:
+ *   Z0 = max(rho) * max(vp); bx = ((dt * Z0) / h) / rho_x, by likewise, with
+ *   rho_x, rho_y two-point averages as rho_c above;
+ *   mu = (rho * vs) * vs, lambda = ((rho * vp) * vp) - (2 * mu) at each node;
+ *   l2m = ((dt * (lambda + 2 * mu)) / Z0) / h, lam = ((dt * lambda) / Z0) / h;
+ *   at the shear points mu_xy = 4 / (1/mu00 + 1/mu10 + 1/mu01 + 1/mu11), the
+ *   harmonic mean of the four surrounding nodes (0 if any is 0), and
+ *   mu = ((dt * mu_xy) / Z0) / h. Neighbours past the last point wrap
+ *   (periodic) or are clamped.
+ * Elastic boundaries: x faces PERIODIC/PERIODIC or RIGID/RIGID; y faces
+ * PERIODIC/PERIODIC or (RIGID or FREE)/RIGID. RIGID is a frictionless rigid
+ * wall on the half points -1/2 and N-1/2 (normal velocity and shear stress odd
+ * about it and zero on it, the other fields even); the stored points on the
+ * high wall are held at zero. FREE (y-lo) is a traction-free top in
+ * zero-extension form: every field reads zero above row 0. Both keep the
+ * discrete operator skew, so the energy is conserved in exact arithmetic.
  * Errors: EINVAL (bad grid, spacing, dt, enum, NULL pointer, unsupported BC),
  * ERANGE (a multiplier is not a positive normal number of the storage format,
  * or a material value is not positive and finite), ENOTIMPL (WAVE_FP64),
@@ -181,9 +185,10 @@ wave_status wave_set_initial(wave_ctx *ctx, wave_field field, const double *host
  * source amplitude at global step s, for s < nt; later steps have none. It is
  * stored as s^ = RN(w * (Z0 / (P0 * h^(d-1)))) in the arithmetic format and
  * added to the right-hand side before the coefficient multiply (Algorithm 1,
- * the source line of the pressure loop); for the elastic v_y source the
- * scale is 1 / (P0 * h^(d-1)) * (Z0 / Z0) = 1 / (P0 * h) and it is added to
- * the v_y right-hand side. idx is the grid point (i, j, k).
+ * the source line of the pressure loop). The elastic v_y force (Eq. 2 puts it
+ * outside the 1/rho factor) is stored as s^ = RN(w * ((dt * Z0) / (P0 * h^2)))
+ * and added to the v_y increment after the multiply. idx is the grid point
+ * (i, j, k).
  * Acoustic: field must be WAVE_F_P. Elastic: WAVE_F_VY. */
 wave_status wave_set_source(wave_ctx *ctx, wave_field field, const int64_t idx[3],
                             const double *wavelet, int64_t nt);
@@ -233,8 +238,8 @@ wave_status wave_set_raw(wave_ctx *ctx, wave_field field, int32_t compensation,
                          const void *host_in);
 
 /* wave_get_coefficient -- the rounded multipliers as binary64, one per grid
- * point: which = 0 b (acoustic p) / l2m (elastic), 1..3 a_x..a_z (acoustic) /
- * 1 bx, 2 by, 4 lam, 5 mu_xy (elastic). Also returns Z0 when Z0 != NULL. */
+ * point: acoustic which = 0 b, 1..3 a_x..a_z; elastic which = 0 bx, 1 by,
+ * 2 l2m, 3 lam, 4 mu. Also returns Z0 when Z0 != NULL. */
 wave_status wave_get_coefficient(wave_ctx *ctx, int32_t which, double *host_out, double *Z0);
 
 /* wave_get_state / wave_set_state -- checkpoint and resume: every field, its

@@ -78,9 +78,10 @@ __device__ __forceinline__ float e_term(float x, float y, float w) {
 }
 
 // Block sum of a double, then a deterministic last-block reduction of the
-// per-block partials in block order. Writes e_factor * total to *e_out.
+// per-block partials in block order. Writes factor * total to *e_out.
 // Must be called by every thread of the block.
-__device__ __forceinline__ void energy_reduce(double val, const AcParams &prm) {
+__device__ __forceinline__ void energy_reduce(double val, double *e_part, unsigned int *e_count,
+                                              double *e_out, double factor) {
     __shared__ double warp_sums[32];
     __shared__ bool is_last;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
@@ -93,16 +94,16 @@ __device__ __forceinline__ void energy_reduce(double val, const AcParams &prm) {
     if (tid == 0) {
         double s = 0.0;
         for (int w = 0; w < (nthreads + 31) / 32; w++) s += warp_sums[w];
-        prm.e_part[bid] = s;
+        e_part[bid] = s;
         __threadfence();
-        unsigned prev = atomicAdd(prm.e_count, 1u);
+        unsigned prev = atomicAdd(e_count, 1u);
         is_last = (prev == nblocks - 1);
     }
     __syncthreads();
     if (is_last) {
         __threadfence();
         double s = 0.0;
-        for (unsigned b = tid; b < nblocks; b += nthreads) s += __ldcg(&prm.e_part[b]);
+        for (unsigned b = tid; b < nblocks; b += nthreads) s += __ldcg(&e_part[b]);
         for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
         __syncthreads();
         if ((tid & 31) == 0) warp_sums[tid >> 5] = s;
@@ -110,10 +111,14 @@ __device__ __forceinline__ void energy_reduce(double val, const AcParams &prm) {
         if (tid == 0) {
             double tot = 0.0;
             for (int w = 0; w < (nthreads + 31) / 32; w++) tot += warp_sums[w];
-            *prm.e_out = tot * prm.e_factor;
-            *prm.e_count = 0u;
+            *e_out = tot * factor;
+            *e_count = 0u;
         }
     }
+}
+
+__device__ __forceinline__ void energy_reduce(double val, const AcParams &prm) {
+    energy_reduce(val, prm.e_part, prm.e_count, prm.e_out, prm.e_factor);
 }
 
 }  // namespace wave

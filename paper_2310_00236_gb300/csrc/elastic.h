@@ -1,0 +1,40 @@
+// elastic.h -- parameters of the 2D elastic kernels.
+//
+// Boundary kinds per face (x-lo, x-hi, y-lo, y-hi):
+//   periodic (both faces of an axis): wrap;
+//   rigid: frictionless rigid wall on the half points -1/2 and N-1/2: the
+//     normal velocity and the shear stress are odd about it (zero on it; the
+//     stored point N-1 lies on the high wall and is held at zero), the
+//     tangential velocity and the normal stresses are even;
+//   free (y-lo only): traction-free top in zero-extension form, every field
+//     reads zero above row 0.
+// Each is a restriction of a skew-adjoint operator, so the discrete energy is
+// exactly conserved in exact arithmetic.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wave {
+
+struct ElParams {
+    int n[2];
+    int bc[4];
+    int64_t sy;                 // row pitch in elements
+    void *f[5], *t[5];          // vx, vy, sxx, syy, sxy and their compensations
+    const void *c[5];           // bx, by, l2m, lam, mu (arrays) or nullptr
+    uint32_t c_uni[5];          // uniform values (storage bits)
+    int64_t src_q;              // pitched index of the v_y source, -1 none
+    const void *src;            // arithmetic-format increments per global step
+    int64_t src_nt;
+    int64_t step;
+    int energy;
+    double *e_part;
+    unsigned int *e_count;
+    double *e_out;
+    double e_factor;
+};
+
+cudaError_t elastic_half_step(const ElParams &e, int prec, int comp, int half, cudaStream_t st);
+unsigned elastic_blocks(const int n[2]);
+
+}  // namespace wave

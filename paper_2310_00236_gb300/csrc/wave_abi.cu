@@ -13,6 +13,7 @@
 
 #include "../../include/wave.h"
 #include "acoustic_common.cuh"
+#include "elastic.h"
 #include "wave_kernels.h"
 
 using namespace wave;
@@ -324,6 +325,76 @@ static wave_status acoustic_coefficients(wave_ctx *c, const wave_materials *mat)
     return WAVE_OK;
 }
 
+// Round a binary64 value once to the storage format and return it as binary64.
+static double round_store(int prec, double v) {
+    if (prec == PREC_FP32) return (double)(float)v;
+    uint16_t t;
+    store_value(prec, v, &t, 0);
+    return load_value(prec, &t, 0);
+}
+
+// Elastic multipliers (Eq. 2 scaled as in Section 5 "Range"), binary64 in this
+// order, each rounded once: Z0 = max(rho) max(vp); bx = ((dt Z0)/h)/rho_x,
+// by likewise, rho_x = (rho[i] + rho[i+1]) * 0.5; mu = (rho vs) vs,
+// lambda = ((rho vp) vp) - 2 mu; l2m = ((dt (lambda + 2 mu))/Z0)/h,
+// lam = ((dt lambda)/Z0)/h; mu_xy = 4 / (sum of 1/mu over the four nodes
+// around the shear point, 0 if any is 0), mu = ((dt mu_xy)/Z0)/h. The
+// neighbour i+1 (j+1) wraps on periodic axes and is clamped otherwise.
+static wave_status elastic_coefficients(wave_ctx *c, const wave_materials *mat) {
+    const int64_t nx = c->n[0], ny = c->n[1], npts = nx * ny;
+    double rho0 = 0.0, c0 = 0.0;
+    for (int64_t q = 0; q < npts; q++) {
+        if (!(mat->rho[q] > 0.0) || !isfinite(mat->rho[q]) || !(mat->vp[q] > 0.0) ||
+            !isfinite(mat->vp[q]) || !(mat->vs[q] >= 0.0) || !isfinite(mat->vs[q]))
+            return fail(WAVE_ERANGE, "material value at point %lld is out of range", (long long)q);
+        if (mat->rho[q] > rho0) rho0 = mat->rho[q];
+        if (mat->vp[q] > c0) c0 = mat->vp[q];
+    }
+    const double Z0 = rho0 * c0, h = c->h, dt = c->dt;
+    c->Z0 = Z0;
+    const double tiny = min_normal(c->prec);
+    for (int w = 0; w < 5; w++) c->coef_host[w].assign(npts, 0.0);
+    auto lame = [&](int64_t q, double &m, double &l) {
+        m = (mat->rho[q] * mat->vs[q]) * mat->vs[q];
+        l = ((mat->rho[q] * mat->vp[q]) * mat->vp[q]) - (2.0 * m);
+    };
+    for (int64_t j = 0; j < ny; j++)
+        for (int64_t i = 0; i < nx; i++) {
+            const int64_t q = i + nx * j;
+            const int64_t i1 = i + 1 < nx ? i + 1 : (c->bc[1] == WAVE_BC_PERIODIC ? 0 : i);
+            const int64_t j1 = j + 1 < ny ? j + 1 : (c->bc[3] == WAVE_BC_PERIODIC ? 0 : j);
+            const double rx = (mat->rho[q] + mat->rho[i1 + nx * j]) * 0.5;
+            const double ry = (mat->rho[q] + mat->rho[i + nx * j1]) * 0.5;
+            const double bx = round_store(c->prec, ((dt * Z0) / h) / rx);
+            const double by = round_store(c->prec, ((dt * Z0) / h) / ry);
+            double m00, l00, m10, l10, m01, l01, m11, l11;
+            lame(q, m00, l00);
+            lame(i1 + nx * j, m10, l10);
+            lame(i + nx * j1, m01, l01);
+            lame(i1 + nx * j1, m11, l11);
+            const double l2m = round_store(c->prec, ((dt * (l00 + 2.0 * m00)) / Z0) / h);
+            const double lam = round_store(c->prec, ((dt * l00) / Z0) / h);
+            double mh = 0.0;
+            if (m00 > 0.0 && m10 > 0.0 && m01 > 0.0 && m11 > 0.0)
+                mh = 4.0 / (1.0 / m00 + 1.0 / m10 + 1.0 / m01 + 1.0 / m11);
+            const double mu = round_store(c->prec, ((dt * mh) / Z0) / h);
+            c->coef_host[0][q] = bx;
+            c->coef_host[1][q] = by;
+            c->coef_host[2][q] = l2m;
+            c->coef_host[3][q] = lam;
+            c->coef_host[4][q] = mu;
+            const bool ok = bx >= tiny && isfinite(bx) && by >= tiny && isfinite(by) &&
+                            l2m >= tiny && isfinite(l2m) &&
+                            (lam == 0.0 || fabs(lam) >= tiny) && isfinite(lam) &&
+                            (mu == 0.0 || mu >= tiny) && isfinite(mu) && l2m > fabs(lam);
+            if (!ok)
+                return fail(WAVE_ERANGE,
+                            "elastic multiplier at point %lld outside the storage format's range "
+                            "(rescale units or change dt)", (long long)q);
+        }
+    return WAVE_OK;
+}
+
 // Upload coefficient w (0 b, 1..3 a_x..a_z) as a uniform value or an array.
 static wave_status upload_coef(wave_ctx *c, int w) {
     const std::vector<double> &v = c->coef_host[w];
@@ -451,8 +522,8 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
     if (grid->ndim != 2 && grid->ndim != 3) return fail(WAVE_EINVAL, "ndim must be 2 or 3");
     if (mat->kind != WAVE_ACOUSTIC && mat->kind != WAVE_ELASTIC)
         return fail(WAVE_EINVAL, "unknown physics %d", (int)mat->kind);
-    if (mat->kind == WAVE_ELASTIC)
-        return fail(WAVE_ENOTIMPL, "elastic physics is not built yet");
+    if (mat->kind == WAVE_ELASTIC && grid->ndim != 2)
+        return fail(WAVE_ENOTIMPL, "the elastic system is 2D (Eq. 2)");
     for (int ax = 0; ax < grid->ndim; ax++) {
         if (grid->n[ax] < 8) return fail(WAVE_EINVAL, "n[%d] = %lld < 8", ax, (long long)grid->n[ax]);
         if (grid->n[ax] > (1 << 20)) return fail(WAVE_EINVAL, "n[%d] too large", ax);
@@ -525,6 +596,28 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
         c->use_stream = kchoice == 0 && acoustic_stream_supported(prm, c->ndim, c->prec);
         if (c->use_stream)
             c->e_blocks = std::max(c->e_blocks, acoustic_stream_blocks(prm, c->prec, c->zchunk));
+    } else {
+        const int *b = c->bc;
+        const bool x_ok = (b[0] == WAVE_BC_PERIODIC && b[1] == WAVE_BC_PERIODIC) ||
+                          (b[0] == WAVE_BC_RIGID && b[1] == WAVE_BC_RIGID);
+        const bool y_ok = (b[2] == WAVE_BC_PERIODIC && b[3] == WAVE_BC_PERIODIC) ||
+                          ((b[2] == WAVE_BC_RIGID || b[2] == WAVE_BC_FREE) && b[3] == WAVE_BC_RIGID);
+        if (!x_ok || !y_ok) {
+            delete c;
+            return fail(WAVE_EINVAL, "elastic faces: x PERIODIC/PERIODIC or RIGID/RIGID; "
+                                     "y PERIODIC/PERIODIC or (RIGID|FREE)/RIGID");
+        }
+        st = elastic_coefficients(c, mat);
+        if (st) { delete c; return st; }
+        const size_t eb = elem_bytes(prec);
+        const int fields[5] = {WAVE_F_VX, WAVE_F_VY, WAVE_F_SXX, WAVE_F_SYY, WAVE_F_SXY};
+        for (int fi = 0; fi < 5 && !st; fi++) {
+            st = dev_alloc(c, c->f[fields[fi]], c->total * eb);
+            if (!st && compensated) st = dev_alloc(c, c->t[fields[fi]], c->total * eb);
+        }
+        for (int w = 0; w < 5 && !st; w++) st = upload_coef(c, w);
+        const int nn[2] = {(int)c->n[0], (int)c->n[1]};
+        c->e_blocks = elastic_blocks(nn);
     }
     if (!st) st = dev_alloc(c, c->e_part, sizeof(double) * (size_t)std::max(1u, c->e_blocks));
     if (!st) st = dev_alloc(c, c->e_misc, 16);
@@ -576,6 +669,14 @@ extern "C" wave_status wave_set_initial(wave_ctx *c, wave_field field, const dou
             if (cc->kind == WAVE_ACOUSTIC) {
                 const int64_t idx[3] = {q % nx, (q / nx) % ny, q / (nx * ny)};
                 if (on_rigid_wall_zeroed(cc, field, idx)) s = 0.0;
+            } else {
+                // frictionless rigid walls hold the normal velocity and the
+                // shear stress at zero on the stored wall points
+                const int64_t i = q % nx, j = q / nx;
+                if (cc->bc[1] == WAVE_BC_RIGID && i == nx - 1 &&
+                    (field == WAVE_F_VX || field == WAVE_F_SXY)) s = 0.0;
+                if (cc->bc[3] == WAVE_BC_RIGID && j == ny - 1 &&
+                    (field == WAVE_F_VY || field == WAVE_F_SXY)) s = 0.0;
             }
             store_value(prec, s, dst, q);
             if (!isfinite(load_value(prec, dst, q))) *bad = q;
@@ -647,7 +748,8 @@ extern "C" wave_status wave_get_coefficient(wave_ctx *c, int32_t which, double *
         if (which < 0 || which > c->ndim) return fail(WAVE_EINVAL, "bad coefficient index");
         v = &c->coef_host[which];
     } else {
-        return fail(WAVE_EINVAL, "bad coefficient index");
+        if (which < 0 || which > 4) return fail(WAVE_EINVAL, "bad coefficient index");
+        v = &c->coef_host[which];
     }
     memcpy(host, v->data(), v->size() * sizeof(double));
     return WAVE_OK;
@@ -670,7 +772,10 @@ extern "C" wave_status wave_set_source(wave_ctx *c, wave_field field, const int6
     for (int ax = 0; ax < c->ndim; ax++)
         if (idx[ax] < 0 || idx[ax] >= c->n[ax]) return fail(WAVE_EINVAL, "source outside grid");
     const double hd1 = c->ndim == 2 ? c->h : c->h * c->h;
-    const double scale = c->kind == WAVE_ACOUSTIC ? c->Z0 / (c->P0 * hd1) : 1.0 / (c->P0 * hd1);
+    // acoustic: added to R before the multiplier; elastic v_y force: added to
+    // the increment after the multiplier, s^ = w * ((dt * Z0) / (P0 * (h * h)))
+    const double scale = c->kind == WAVE_ACOUSTIC ? c->Z0 / (c->P0 * hd1)
+                                                  : (c->dt * c->Z0) / (c->P0 * (c->h * c->h));
     const bool f32 = arith_is_f32(c->prec);
     std::vector<unsigned char> tab(nt * (f32 ? 4 : 2));
     for (int64_t s = 0; s < nt; s++) {
@@ -808,6 +913,54 @@ static wave_status acoustic_steps(wave_ctx *c, int64_t n) {
     return WAVE_OK;
 }
 
+static wave_status elastic_steps(wave_ctx *c, int64_t n) {
+    ElParams e;
+    memset(&e, 0, sizeof e);
+    e.n[0] = (int)c->n[0];
+    e.n[1] = (int)c->n[1];
+    for (int i = 0; i < 4; i++) e.bc[i] = c->bc[i];
+    e.sy = c->pitch;
+    const int fields[5] = {WAVE_F_VX, WAVE_F_VY, WAVE_F_SXX, WAVE_F_SYY, WAVE_F_SXY};
+    for (int i = 0; i < 5; i++) {
+        e.f[i] = c->f[fields[i]].ptr;
+        e.t[i] = c->t[fields[i]].ptr;
+        e.c[i] = c->coef_is_uniform[i] ? nullptr : c->coef[i].ptr;
+        e.c_uni[i] = c->coef_uni[i];
+    }
+    e.src_q = c->src_field == WAVE_F_VY ? c->src_q : -1;
+    e.src = c->src_table.ptr;
+    e.src_nt = c->src_nt;
+    e.e_part = static_cast<double *>(c->e_part.ptr);
+    e.e_count = reinterpret_cast<unsigned *>(static_cast<char *>(c->e_misc.ptr) + 8);
+    e.e_out = static_cast<double *>(c->e_misc.ptr);
+    e.e_factor = 0.5 * c->h * c->P0 * c->P0 * c->dt / c->Z0;
+    const size_t eb = elem_bytes(c->prec);
+    for (int64_t s = 0; s < n; s++) {
+        e.step = c->step;
+        const bool trace = c->e_trace && c->e_trace_pos < c->e_trace_cap;
+        e.energy = (s == n - 1) || trace;
+        cudaEvent_t m0 = mark(c);
+        cudaError_t err = elastic_half_step(e, c->prec, c->comp, 0, c->stream);
+        cudaEvent_t m1 = mark(c);
+        timed(c, 0, m0, m1);
+        if (err == cudaSuccess) err = elastic_half_step(e, c->prec, c->comp, 1, c->stream);
+        cudaEvent_t m2 = mark(c);
+        timed(c, 1, m1, m2);
+        if (err == cudaSuccess && trace)
+            err = cudaMemcpyAsync(c->e_trace + c->e_trace_pos, c->e_misc.ptr, sizeof(double),
+                                  cudaMemcpyDeviceToDevice, c->stream);
+        if (err == cudaSuccess && c->nrec && c->rec_pos < c->rec_cap)
+            err = sample_receivers(c->f[c->rec_field].ptr, (int)eb, is_bf16_storage(c->prec),
+                                   static_cast<const int64_t *>(c->rec_q.ptr), (int)c->nrec,
+                                   c->rec_traces + c->rec_pos * c->nrec, c->stream);
+        if (err != cudaSuccess) return cuda_check(c, err, "wave_step launch");
+        if (trace) c->e_trace_pos++;
+        if (c->nrec && c->rec_pos < c->rec_cap) c->rec_pos++;
+        c->step++;
+    }
+    return WAVE_OK;
+}
+
 extern "C" wave_status wave_step(wave_ctx *c, int64_t n) {
     CHECK_CTX(c);
     if (n < 0) return fail(WAVE_EINVAL, "negative step count");
@@ -816,7 +969,7 @@ extern "C" wave_status wave_step(wave_ctx *c, int64_t n) {
     if (c->kind == WAVE_ACOUSTIC) {
         st = acoustic_steps(c, n);
     } else {
-        st = fail(WAVE_ENOTIMPL, "elastic physics is not built yet");
+        st = elastic_steps(c, n);
     }
     if (!st) c->have_energy = true;
     return st;

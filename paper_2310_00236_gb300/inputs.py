@@ -121,3 +121,21 @@ def acoustic_3d_random(n: int = 512, steps: int = 1000, cfl: float = 0.4, h: flo
     return dict(ndim=3, shape=shape, h=h, dt=cfl * h / vmax, steps=steps,
                 rho=np.full(c.shape, rho), c=c,
                 p0=gaussian(shape, h, ic_sigma_cells * h), P0=1.0)
+
+
+def elastic_2d_layered(n: int = 1024, steps: int = 4000, h: float = 3.0, f0: float = 15.0,
+                       cutoff: float = 0.1):
+    """2D isotropic elastic, n x n cells, spacing h: three horizontal layers
+    y in [0, n/3), [n/3, 2n/3), [2n/3, n) with Vp 2000 / 3000 / 4000 m/s,
+    Vs = Vp / 1.73, rho 2000 / 2300 / 2600 kg/m^3; free top, rigid other
+    sides; Ricker f0 vertical force at (n/2, 10) for `cutoff` seconds (t0 = cutoff/2,
+    sampled at t_n) then source-free; dt = 0.5 h / 4000."""
+    y = np.arange(n)
+    vp1 = np.where(y < n // 3, 2000.0, np.where(y < 2 * n // 3, 3000.0, 4000.0))
+    rho1 = np.where(y < n // 3, 2000.0, np.where(y < 2 * n // 3, 2300.0, 2600.0))
+    vp = np.ascontiguousarray(np.repeat(vp1[:, None], n, 1))
+    rho = np.ascontiguousarray(np.repeat(rho1[:, None], n, 1))
+    dt = 0.5 * h / 4000.0
+    wav = ricker_table(steps, dt, f0, t0=0.5 * cutoff, half_step=False, cutoff=cutoff)
+    return dict(ndim=2, shape=(n, n), h=h, dt=dt, steps=steps, rho=rho, vp=vp, vs=vp / 1.73,
+                src_idx=(n // 2, 10), wavelet=wav, src_steps=int(round(cutoff / dt)))

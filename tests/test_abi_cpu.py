@@ -56,7 +56,11 @@ def _ones(n=(16, 16)):
     (dict(bc=(2, 2, 1, 1, 0, 0)), W.WAVE_EINVAL),          # free surface is elastic only
     (dict(field_scale=-1.0), W.WAVE_EINVAL),
     (dict(rho_scale=0.0), W.WAVE_ERANGE),                   # non-positive material
-    (dict(kind=W.WAVE_ELASTIC, vs=True), W.WAVE_ENOTIMPL),
+    (dict(kind=W.WAVE_ELASTIC, vs=True, n=(16, 16, 16)), W.WAVE_ENOTIMPL),   # elastic is 2D
+    (dict(kind=W.WAVE_ELASTIC, vs=True, bc=(0, 1, 2, 1, 0, 0)), W.WAVE_EINVAL),  # mixed x faces
+    (dict(kind=W.WAVE_ELASTIC, vs=True, bc=(2, 2, 2, 1, 0, 0)), W.WAVE_EINVAL),  # free x faces
+    (dict(kind=W.WAVE_ELASTIC, vs=True, bc=(1, 1, 1, 2, 0, 0)), W.WAVE_EINVAL),  # free bottom
+    (dict(kind=W.WAVE_ELASTIC, vs=False), W.WAVE_EINVAL),                        # no vs
 ])
 def test_create_argument_errors(lib, kw, status):
     n = kw.pop("n", (16, 16))
