@@ -34,12 +34,17 @@ UNIT = "Gpoint-updates/s"
 # written once per launch). Acoustic 3D, uniform a (constant density), per-point b.
 #   velocity half step : read p + v(3) [+ t_v(3)], write v(3) [+ t_v(3)]
 #   pressure half step : read v(3) + p [+ t_p] + b, write p [+ t_p]
+#   one-pass step       : read p [+ t_p] + v(3) [+ t_v(3)] + b, write p [+ t_p] + v(3) [+ t_v(3)]
 BYTES = {
-    ("fp16", True): {"kv": 2 + 6 + 6 + 6 + 6, "kp": 6 + 2 + 2 + 2 + 2 + 2},
-    ("fp16", False): {"kv": 2 + 6 + 6, "kp": 6 + 2 + 2 + 2},
-    ("fp32", False): {"kv": 4 + 12 + 12, "kp": 12 + 4 + 4 + 4},
-    ("fp32", True): {"kv": 4 + 12 + 12 + 12 + 12, "kp": 12 + 4 + 4 + 4 + 4 + 4},
+    ("fp16", True): {"kv": 2 + 6 + 6 + 6 + 6, "kp": 6 + 2 + 2 + 2 + 2 + 2,
+                     "fused": (2 + 2 + 6 + 6 + 2) + (2 + 2 + 6 + 6)},
+    ("fp16", False): {"kv": 2 + 6 + 6, "kp": 6 + 2 + 2 + 2, "fused": (2 + 6 + 2) + (2 + 6)},
+    ("fp32", False): {"kv": 4 + 12 + 12, "kp": 12 + 4 + 4 + 4, "fused": (4 + 12 + 4) + (4 + 12)},
+    ("fp32", True): {"kv": 4 + 12 + 12 + 12 + 12, "kp": 12 + 4 + 4 + 4 + 4 + 4,
+                     "fused": (4 + 4 + 12 + 12 + 4) + (4 + 4 + 12 + 12)},
 }
+KERNEL_NAMES = {"kv": "velocity half step", "kp": "pressure half step",
+                "fused": "one-pass step (both half steps)"}
 
 
 def load_peaks():
@@ -106,6 +111,7 @@ def workload(n: int):
 
 
 ZCHUNK = 0
+KERNEL = 0
 
 
 def run_variant(W, w, prec_name, comp, steps, warmup, timing=True):
@@ -116,7 +122,7 @@ def run_variant(W, w, prec_name, comp, steps, warmup, timing=True):
     stream = torch.cuda.current_stream()
     ctx = W.wave_create(w["shape"], w["h"], w["rho"], w["c"], w["dt"], code, comp,
                         bc=[W.WAVE_BC_RIGID] * 6, field_scale=w["P0"], zchunk=ZCHUNK,
-                        stream=stream.cuda_stream)
+                        kernel=KERNEL, stream=stream.cuda_stream)
     try:
         W.wave_set_initial(ctx, W.WAVE_F_P, w["p0"])
         W.wave_step(ctx, warmup)
@@ -135,9 +141,10 @@ def run_variant(W, w, prec_name, comp, steps, warmup, timing=True):
         e1 = W.wave_energy(ctx)
         kt = {}
         if timing:
-            for kind, name in ((0, "kv"), (1, "kp")):
+            for kind, name in ((0, "kv"), (1, "kp"), (3, "fused")):
                 nl, kms = W.wave_get_timing(ctx, kind)
-                kt[name] = (nl, kms)
+                if nl > 0:
+                    kt[name] = (nl, kms)
             W.wave_set_timing(ctx, False)
     finally:
         W.wave_destroy(ctx)
@@ -295,9 +302,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--zchunk", type=int, default=0, help="z planes per block (0: library default)")
+    ap.add_argument("--kernel", type=int, default=0,
+                    help="0 automatic, 1 one-thread-per-point, 2 two-kernel streaming")
     args = ap.parse_args()
-    global ZCHUNK
+    global ZCHUNK, KERNEL
     ZCHUNK = args.zchunk
+    KERNEL = args.kernel
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -334,7 +344,7 @@ def main():
     nl, kms = kt[dom]
     bpp = BYTES[("fp16", True)][dom]
     achieved = bpp * npts / (kms / nl * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": {"kv": "velocity half step", "kp": "pressure half step"}[dom],
+    roof = {"bound": "hbm", "kernel": KERNEL_NAMES[dom],
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_kind": peak_kind, "traffic": None,
             "bytes_per_point": bpp, "ms_per_launch": kms / nl,

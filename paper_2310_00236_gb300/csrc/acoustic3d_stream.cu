@@ -439,19 +439,24 @@ __global__ void __launch_bounds__(TXV *TY) kp_stream(AcParams prm, int zchunk) {
             pv = at<V>(prm.p, q);
             tv = COMP ? at<V>(prm.tp, q) : V::zero();
         }
-        // x neighbours of v_x: vx[x-2], vx[x-1], vx[x+N]
+        // x neighbours of v_x: vx[x-2], vx[x-1], vx[x+N]. The tile-edge lanes
+        // load theirs from global memory before the shuffles, so those loads
+        // overlap the vector loads above instead of waiting for them.
+        const bool left_edge = active && lx == 0;
+        const bool right_edge = active && (lx == TXV - 1 || x + N >= prm.n[0]);
+        RS el1 = RS(0), el0 = RS(0), err = RS(0);
+        if (left_edge) {
+            el1 = load_x_img<V>(prm.v[0], prm, x - 2, j, k, false);
+            el0 = load_x_img<V>(prm.v[0], prm, x - 1, j, k, false);
+        }
+        if (right_edge) err = load_x_img<V>(prm.v[0], prm, x + N, j, k, false);
         RS l1 = shfl_rs(V::get(vx, N - 2), 1, true);
         RS l0 = shfl_rs(V::get(vx, N - 1), 1, true);
         RS rr = shfl_rs(V::get(vx, 0), 1, false);
+        if (left_edge) { l1 = el1; l0 = el0; }
+        if (right_edge) rr = err;
         sv[buf][row + 2][lx] = vy;
         if (halo_loader) sv[buf][h_local][tid % TXV] = hv;
-        if (active) {
-            if (lx == 0) {
-                l1 = load_x_img<V>(prm.v[0], prm, x - 2, j, k, false);
-                l0 = load_x_img<V>(prm.v[0], prm, x - 1, j, k, false);
-            }
-            if (lx == TXV - 1 || x + N >= prm.n[0]) rr = load_x_img<V>(prm.v[0], prm, x + N, j, k, false);
-        }
         __syncthreads();
         if (active) {
             const AV ownx = V::ld(vx);

@@ -164,7 +164,11 @@ struct wave_ctx {
     int prec = PREC_FP16, comp = 0;
     int kernel_choice = 0;
     int zchunk = 16;
+    bool zchunk_set = false;
     bool use_stream = false;
+    bool use_fused = false;
+    // second set of p, vx, vy, vz and t_vx, t_vy, t_vz for the one-pass step
+    DevBuf alt_f[4], alt_t[4];
     double h = 0, dt = 0, P0 = 1.0, Z0 = 1.0;
     cudaStream_t stream = nullptr;
     bool poisoned = false;
@@ -194,8 +198,8 @@ struct wave_ctx {
     struct TimedLaunch { int kind; cudaEvent_t a, b; };
     std::vector<TimedLaunch> pending;
     std::vector<cudaEvent_t> event_pool;
-    int64_t t_launches[3] = {0, 0, 0};
-    double t_ms[3] = {0, 0, 0};
+    int64_t t_launches[4] = {0, 0, 0, 0};
+    double t_ms[4] = {0, 0, 0, 0};
 
     DevBuf rec_q;
     int64_t nrec = 0;
@@ -245,6 +249,8 @@ static wave_status cuda_check(wave_ctx *c, cudaError_t e, const char *what) {
     c->poisoned = true;
     return fail(WAVE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
+
+static wave_status check_device_error(wave_ctx *c);
 
 #define CHECK_CTX(c)                                                                  \
     do {                                                                              \
@@ -501,6 +507,8 @@ static void destroy_ctx(wave_ctx *c) {
     for (auto &b : c->f) dev_free(c, b);
     for (auto &b : c->t) dev_free(c, b);
     for (auto &b : c->coef) dev_free(c, b);
+    for (auto &b : c->alt_f) dev_free(c, b);
+    for (auto &b : c->alt_t) dev_free(c, b);
     dev_free(c, c->e_part);
     dev_free(c, c->e_misc);
     dev_free(c, c->src_table);
@@ -546,7 +554,7 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
         kchoice = opt->kernel;
         zchunk = opt->zchunk;
     }
-    if (kchoice < 0 || kchoice > 1 || zchunk < 0) return fail(WAVE_EINVAL, "bad kernel options");
+    if (kchoice < 0 || kchoice > 3 || zchunk < 0) return fail(WAVE_EINVAL, "bad kernel options");
     if (!(P0 > 0.0) || !isfinite(P0)) return fail(WAVE_EINVAL, "field_scale must be positive");
     const int64_t npts = grid->n[0] * grid->n[1] * (grid->ndim == 3 ? grid->n[2] : 1);
     if (npts > ((int64_t)1 << 31) - 1) return fail(WAVE_EINVAL, "grid too large (>= 2^31 points)");
@@ -560,7 +568,7 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
     c->prec = prec;
     c->comp = compensated;
     c->kernel_choice = kchoice;
-    if (zchunk > 0) c->zchunk = zchunk;
+    if (zchunk > 0) { c->zchunk = zchunk; c->zchunk_set = true; }
     c->h = spacing[0];
     c->dt = dt;
     c->P0 = P0;
@@ -593,9 +601,19 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
         AcParams prm;
         fill_acoustic_params(c, prm);
         c->e_blocks = acoustic_generic_blocks(prm, c->ndim);
-        c->use_stream = kchoice == 0 && acoustic_stream_supported(prm, c->ndim, c->prec);
+        c->use_fused = kchoice == 3 && acoustic_fused_supported(prm, c->ndim, c->prec);
+        c->use_stream = !c->use_fused && kchoice != 1 &&
+                        acoustic_stream_supported(prm, c->ndim, c->prec);
+        if (c->use_fused && !c->zchunk_set) c->zchunk = 32;
         if (c->use_stream)
             c->e_blocks = std::max(c->e_blocks, acoustic_stream_blocks(prm, c->prec, c->zchunk));
+        if (c->use_fused) {
+            c->e_blocks = std::max(c->e_blocks, acoustic_fused_blocks(prm, c->prec, c->zchunk));
+            for (int fi = 0; fi < 4 && !st; fi++) {
+                st = dev_alloc(c, c->alt_f[fi], c->total * eb);
+                if (!st && fi > 0 && compensated) st = dev_alloc(c, c->alt_t[fi], c->total * eb);
+            }
+        }
     } else {
         const int *b = c->bc;
         const bool x_ok = (b[0] == WAVE_BC_PERIODIC && b[1] == WAVE_BC_PERIODIC) ||
@@ -620,7 +638,7 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
         c->e_blocks = elastic_blocks(nn);
     }
     if (!st) st = dev_alloc(c, c->e_part, sizeof(double) * (size_t)std::max(1u, c->e_blocks));
-    if (!st) st = dev_alloc(c, c->e_misc, 16);
+    if (!st) st = dev_alloc(c, c->e_misc, 32);  // [energy][block counter][error word]
     if (!st) {
         cudaError_t e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) st = fail(WAVE_ECUDA, "wave_create: %s", cudaGetErrorString(e));
@@ -872,6 +890,8 @@ extern "C" wave_status wave_energy(wave_ctx *c, double *E) {
                                       c->stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
     if (err != cudaSuccess) return cuda_check(c, err, "wave_energy");
+    wave_status st = check_device_error(c);
+    if (st) return st;
     *E = e;
     return WAVE_OK;
 }
@@ -886,6 +906,34 @@ static wave_status acoustic_steps(wave_ctx *c, int64_t n) {
         const bool trace = c->e_trace && c->e_trace_pos < c->e_trace_cap;
         prm.energy = (s == n - 1) || trace;
         prm.e_out = static_cast<double *>(c->e_misc.ptr);
+        if (c->use_fused) {
+            const void *in[7] = {c->f[0].ptr, c->f[1].ptr, c->f[2].ptr, c->f[3].ptr,
+                                 c->t[1].ptr, c->t[2].ptr, c->t[3].ptr};
+            void *out[7] = {c->alt_f[0].ptr, c->alt_f[1].ptr, c->alt_f[2].ptr, c->alt_f[3].ptr,
+                            c->alt_t[1].ptr, c->alt_t[2].ptr, c->alt_t[3].ptr};
+            int *err = reinterpret_cast<int *>(static_cast<char *>(c->e_misc.ptr) + 16);
+            cudaEvent_t m0 = mark(c);
+            cudaError_t e = acoustic_fused_step(prm, in, out, c->t[0].ptr, c->prec, c->comp,
+                                                c->zchunk, err, c->stream);
+            cudaEvent_t m1 = mark(c);
+            timed(c, 3, m0, m1);
+            for (int fi = 0; fi < 4; fi++) {
+                std::swap(c->f[fi], c->alt_f[fi]);
+                if (fi > 0) std::swap(c->t[fi], c->alt_t[fi]);
+            }
+            if (e == cudaSuccess && trace)
+                e = cudaMemcpyAsync(c->e_trace + c->e_trace_pos, c->e_misc.ptr, sizeof(double),
+                                    cudaMemcpyDeviceToDevice, c->stream);
+            if (e == cudaSuccess && c->nrec && c->rec_pos < c->rec_cap)
+                e = sample_receivers(c->f[c->rec_field].ptr, (int)eb, is_bf16_storage(c->prec),
+                                     static_cast<const int64_t *>(c->rec_q.ptr), (int)c->nrec,
+                                     c->rec_traces + c->rec_pos * c->nrec, c->stream);
+            if (e != cudaSuccess) return cuda_check(c, e, "wave_step launch");
+            if (trace) c->e_trace_pos++;
+            if (c->nrec && c->rec_pos < c->rec_cap) c->rec_pos++;
+            c->step++;
+            continue;
+        }
         cudaEvent_t m0 = mark(c);
         cudaError_t e = c->use_stream
                             ? acoustic_stream_half_step(prm, c->prec, c->comp, 0, c->zchunk, c->stream)
@@ -975,9 +1023,24 @@ extern "C" wave_status wave_step(wave_ctx *c, int64_t n) {
     return st;
 }
 
+// Read the device error word (set by a bounded wait that expired).
+static wave_status check_device_error(wave_ctx *c) {
+    int err = 0;
+    cudaError_t e = cudaMemcpyAsync(&err, static_cast<char *>(c->e_misc.ptr) + 16, sizeof(int),
+                                    cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "error word");
+    if (err) {
+        c->poisoned = true;
+        return fail(WAVE_ETIMEOUT, "a bounded device wait expired (pipeline stalled)");
+    }
+    return WAVE_OK;
+}
+
 extern "C" wave_status wave_sync(wave_ctx *c) {
     CHECK_CTX(c);
-    return cuda_check(c, cudaStreamSynchronize(c->stream), "wave_sync");
+    wave_status st = cuda_check(c, cudaStreamSynchronize(c->stream), "wave_sync");
+    return st ? st : check_device_error(c);
 }
 
 extern "C" wave_status wave_steps_done(wave_ctx *c, int64_t *steps) {
@@ -1063,14 +1126,14 @@ extern "C" wave_status wave_set_timing(wave_ctx *c, int32_t enable) {
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "wave_set_timing");
     collect_timing(c);
-    for (int k = 0; k < 3; k++) { c->t_launches[k] = 0; c->t_ms[k] = 0.0; }
+    for (int k = 0; k < 4; k++) { c->t_launches[k] = 0; c->t_ms[k] = 0.0; }
     c->timing = enable != 0;
     return WAVE_OK;
 }
 
 extern "C" wave_status wave_get_timing(wave_ctx *c, int32_t kind, int64_t *launches, double *ms) {
     CHECK_CTX(c);
-    if (kind < 0 || kind > 2 || !launches || !ms) return fail(WAVE_EINVAL, "bad timing query");
+    if (kind < 0 || kind > 3 || !launches || !ms) return fail(WAVE_EINVAL, "bad timing query");
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "wave_get_timing");
     collect_timing(c);

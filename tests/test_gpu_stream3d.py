@@ -1,4 +1,4 @@
-"""GPU parity of the 3D streaming kernels against the CPU oracle.
+"""GPU parity of the 3D streaming kernels (two-kernel and one-pass) against the CPU oracle.
 
 Small grids: bit-exact on every stored value, with x tiles that end inside
 the grid, partial y tiles, several z chunks, both boundary kinds, a source and
@@ -29,7 +29,8 @@ def _media(shape, seed):
     return rho, c
 
 
-def _run(shape, bc, prec, comp, steps, zchunk, src=False, energy=False, seed=0):
+def _run(shape, bc, prec, comp, steps, zchunk, src=False, energy=False, seed=0, kernel=2):
+    """kernel 2 = the two-kernel streaming step."""
     h = 10.0
     rho, c = _media(shape, seed)
     dt = 0.4 * h / 4500.0 / np.sqrt(1.5)
@@ -42,7 +43,7 @@ def _run(shape, bc, prec, comp, steps, zchunk, src=False, energy=False, seed=0):
         wav = inputs.ricker_table(steps, dt, 40.0) * 0.5 * h * h / z0
         s = ([shape[0] // 2 + 3, shape[1] // 3, shape[2] // 2], wav)
     ctx, st = acoustic_pair(shape, bc, prec, comp, h, dt, rho, c, p0=p0, v0=v0, src=s,
-                            zchunk=zchunk)
+                            zchunk=zchunk, kernel=kernel)
     try:
         W.wave_step(ctx, steps)
         _, E = st.run(steps, energy=energy)
@@ -107,8 +108,8 @@ def _subbox_expect(w, st_full, prec, comp, steps, points):
     return out
 
 
-@pytest.mark.parametrize("prec,comp", [("fp16", 3), ("fp32", 0)])
-def test_full_size_512_sampled_bit_exact(prec, comp):
+@pytest.mark.parametrize("prec,comp,kernel", [("fp16", 3, 0), ("fp32", 0, 0), ("fp16", 3, 3)])
+def test_full_size_512_sampled_bit_exact(prec, comp, kernel):
     """The benchmark workload's grid and media (512^3, smooth random velocity,
     rho = 1000, p = 0 walls, CFL 0.4) in the benchmark's launch configuration,
     3 steps, sampled at corners, faces, edges, the centre and random interior
@@ -122,7 +123,7 @@ def test_full_size_512_sampled_bit_exact(prec, comp):
     v0 = [0.3 / z0 * rng.standard_normal(w["p0"].shape) for _ in range(3)]
     code, sfmt, afmt = PREC[prec]
     ctx = W.wave_create(w["shape"], w["h"], w["rho"], w["c"], w["dt"], code, comp,
-                        bc=[W.WAVE_BC_RIGID] * 6, field_scale=w["P0"])
+                        bc=[W.WAVE_BC_RIGID] * 6, field_scale=w["P0"], kernel=kernel)
     try:
         W.wave_set_initial(ctx, W.WAVE_F_P, w["p0"])
         for ax in range(3):
@@ -164,3 +165,56 @@ def test_full_size_512_sampled_bit_exact(prec, comp):
     # the sampled field is not trivially zero
     assert np.count_nonzero(got["p"]) > 1000
     assert sum(1 for ex in expect if ex["p"] != 0) > len(pts) // 2
+
+
+# ------------------------------------------------------ one-pass step (fused)
+FUSED_VARIANTS = VARIANTS
+
+
+def _uniform_rho_run(shape, bc, prec, comp, steps, zchunk, src=False, energy=True, seed=0):
+    """The one-pass step needs a uniform density; the sound speed varies."""
+    h = 10.0
+    c = inputs.smooth_random_field(shape, seed, 3.0, 1500.0, 4500.0)
+    rho = np.full(c.shape, 1000.0)
+    dt = 0.4 * h / 4500.0 / np.sqrt(1.5)
+    p0 = inputs.gaussian(shape, h, 3.0 * h)
+    rng = np.random.default_rng(seed)
+    p0 = p0 + 0.2 * rng.standard_normal(p0.shape)
+    v0 = [0.1 / 4.5e6 * rng.standard_normal(p0.shape) for _ in range(3)]
+    s = None
+    if src:
+        wav = inputs.ricker_table(steps, dt, 40.0) * 0.5 * h * h / 4.5e6
+        s = ([shape[0] // 2 + 3, shape[1] // 3, shape[2] // 2], wav)
+    ctx, st = acoustic_pair(shape, bc, prec, comp, h, dt, rho, c, p0=p0, v0=v0, src=s,
+                            zchunk=zchunk, kernel=3)
+    try:
+        W.wave_set_timing(ctx, True)
+        W.wave_step(ctx, steps)
+        nl, _ = W.wave_get_timing(ctx, 3)
+        assert nl == steps, "the one-pass kernel did not run"
+        _, E = st.run(steps, energy=energy)
+        bad = compare_acoustic(ctx, st, prec, comp)
+        if energy:
+            e_gpu = W.wave_energy(ctx)
+            e_orc = E[-1] * O.energy_factor(h, dt, 1.0, st.Z0, 3)
+            if not abs(e_gpu - e_orc) <= 2e-6 * abs(e_orc):
+                bad.append(f"energy {e_gpu} vs oracle {e_orc}")
+        W.wave_sync(ctx)
+    finally:
+        W.wave_destroy(ctx)
+    assert not bad, bad
+
+
+@pytest.mark.parametrize("prec,comp", FUSED_VARIANTS)
+def test_fused_ragged_y_z_rigid_many_chunks(prec, comp):
+    nx = 128 if prec != "fp32" else 64
+    _uniform_rho_run((nx, 37, 29), (R, R, R), prec, comp, 7, zchunk=5)
+
+
+@pytest.mark.parametrize("prec,comp", [("fp16", 3), ("bf16", 6), ("fp32", 0), ("fp16_f32arith", 3)])
+def test_fused_periodic_mixed_source(prec, comp):
+    nx = 192 if prec != "fp32" else 96
+    _uniform_rho_run((nx, 20, 17), (P, P, P), prec, comp, 6, zchunk=4, src=True)
+    _uniform_rho_run((nx, 33, 40), (R, P, R), prec, comp, 5, zchunk=32, src=True)
+    _uniform_rho_run((nx, 16, 9), (P, R, P), prec, comp, 9, zchunk=3)
+    _uniform_rho_run((64 if prec != "fp32" else 32, 8, 8), (R, R, R), prec, comp, 11, zchunk=8)
