@@ -110,12 +110,13 @@ typedef struct {
 typedef struct {
     double field_scale;  /* P0 > 0: stored p^ = p / P0 and v^ = v * Z0 / P0
                             (Z0 = max(rho) * max(vp)); default 1.0 */
-    int32_t kernel;      /* 0: automatic (3D: the two-kernel streaming step when n[0] is
-                            a multiple of the 16-byte vector width, else one thread
-                            per point); 1: one-thread-per-point kernels only;
-                            2: two-kernel streaming step; 3: one-pass step (both
-                            half steps in one kernel; needs n[0] a multiple of 64
-                            (32 for binary32) and a uniform density, else as 0) */
+    int32_t kernel;      /* 0: automatic (3D: the one-pass step where it applies, else
+                            the two-kernel streaming step when n[0] is a multiple of
+                            the 16-byte vector width, else one thread per point);
+                            1: one-thread-per-point kernels only; 2: two-kernel
+                            streaming step; 3: one-pass step (both half steps in one
+                            kernel; needs n[0] a multiple of 64 (32 for binary32),
+                            rigid x faces and a uniform density, else as 0) */
     int32_t zchunk;      /* z planes per thread block of the 3D kernels (0: automatic) */
     int32_t reserved[6];
 } wave_options;

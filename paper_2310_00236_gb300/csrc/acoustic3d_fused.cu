@@ -1,31 +1,36 @@
-// acoustic3d_fused.cu -- one-pass 3D acoustic leapfrog step with an
-// asynchronous shared-memory pipeline.
+// acoustic3d_fused.cu -- one-pass 3D acoustic leapfrog step with a TMA
+// shared-memory pipeline.
 //
 // The step of Algorithm 1 / 2 (Section 4) extended to 3D,
 //   v_c^{n+1/2} = v_c^{n-1/2} + a_c D_c(p^n)                 (c = x, y, z)
 //   p^{n+1}     = p^n + b (Dx vx + Dy vy + Dz vz [+ s])       (v at n+1/2)
-// is done in a single sweep: each CTA recomputes the new velocities it needs
-// in a halo around its tile (x: 2 left, 1 right; y: 2 above, 1 below; z: the
-// previous planes of its own columns), so p is updated without a second pass
-// over the velocities. Every operation is the same, in the same order, as in
-// the two-kernel path, so the results are bit-identical.
+// in a single sweep: each CTA recomputes the new velocities it needs in a halo
+// around its tile (x: 2 left, 1 right; y: 2 above, 1 below; z: the previous
+// planes of its own columns), so p is updated without a second pass over the
+// velocities. Every operation is the same, in the same order, as in the
+// two-kernel path, so the results are bit-identical.
 //
-// Data movement: old state is read from one set of buffers and the new state
-// written to the other (the context swaps them each step), because
-// neighbouring CTAs read old values in their halos. A producer warp streams
-// rows of the old state into two shared-memory rings with bulk asynchronous
-// copies (cp.async.bulk, completion counted on mbarriers): a ring of p^n
-// planes running three or more planes ahead (the z stencil of v_z needs
-// planes k..k+3) and a ring of the other arrays of plane k. Four consumer
-// warps compute. Every mbarrier wait is bounded; on expiry the kernel sets an
-// error word and leaves.
+// Data movement: the old state is read from one set of buffers and the new
+// state written to the other (the context swaps them after each step),
+// because neighbouring CTAs read old values in their halos. A producer warp
+// streams tiles of the old state into two shared-memory rings with tensor
+// TMA copies (cp.async.bulk.tensor, one box per array and plane; completion
+// counted on mbarriers): a ring of p^n planes running ahead of the compute
+// (the z stencil of v_z needs planes k..k+3) and a ring of the other arrays of
+// plane k. Row groups whose rows lie outside the grid (their images are read
+// instead) are copied row by row with bulk copies. Four consumer warps
+// compute on 16-byte vectors with packed-pair arithmetic. Every mbarrier wait
+// is bounded; on expiry the kernel sets an error word and leaves.
 //
-// Layout of a CTA: TX x TY = (8 lanes x VEC) x 16 rows of (x, y) columns and a
-// chunk of z planes; one 16-byte vector per consumer thread.
-// Requirements (else the two-kernel path is used): 3D, n[0] a multiple of TX,
-// uniform a_c (constant density).
+// Tile: TX x TY = (8 lanes x VEC) x 16 rows of (x, y) columns, a chunk of z
+// planes. Requirements (else the two-kernel path is used): 3D, n[0] a multiple
+// of TX, rigid x faces, uniform a_c (constant density).
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <string.h>
+
 #include "acoustic_common.cuh"
+#include "vec_policy.cuh"
 #include "wave_kernels.h"
 
 namespace wave {
@@ -66,6 +71,14 @@ __device__ __forceinline__ void bulk_copy(void *dst_smem, const void *src_gmem, 
         "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
+__device__ __forceinline__ void tma_box(void *dst_smem, const CUtensorMap *map, int x, int y, int z,
+                                        uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst_smem)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
 
 // Bounded wait: about 2^22 polls (each poll may suspend briefly), then the
 // error word is set and false returned. Once any block has set the error
@@ -79,29 +92,29 @@ __device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, int *
     atomicExch(err, 1);
     return false;
 }
-
 // Shorter bounded wait that ignores the error word (draining copies in flight).
 __device__ __forceinline__ void drain_phase(uint64_t *bar, uint32_t parity) {
     for (uint32_t it = 0; it < (1u << 16); it++)
         if (mbar_try_wait(bar, parity)) return;
 }
 
-// ------------------------------------------------------------ the kernel
+// ------------------------------------------------------------ the layout
 template <class P>
-struct FusedShape {
+struct FShape {
     using S = typename P::S;
-    static constexpr int VEC = 16 / sizeof(S);  // elements per 16-byte vector
-    static constexpr int LANES = 8;             // consumer lanes per row
-    static constexpr int TX = LANES * VEC;      // tile width (elements)
-    static constexpr int TY = 16;               // tile rows
-    static constexpr int HALO = VEC;            // x halo per side in the wide rows (16 bytes)
+    static constexpr int VEC = 16 / sizeof(S);
+    static constexpr int LANES = 8;
+    static constexpr int TX = LANES * VEC;
+    static constexpr int TY = 16;
+    static constexpr int HALO = VEC;              // 16-byte x halo blocks of the wide rows
     static constexpr int WIDE = TX + 2 * HALO;
-    static constexpr int SP = 6;                // p ring depth (planes)
-    static constexpr int SO = 3;                // other-array ring depth
-    // p plane: own rows wide, 3 halo rows above and below narrow
+    static constexpr int SP = 5;                  // p ring depth (planes k..k+3 and one ahead)
+    static constexpr int SO = 2;                  // other-array ring depth (one ahead)
+    // p plane: TY wide own rows, 3 narrow halo rows above, 3 below
+    static constexpr int P_HALO = TY * WIDE;
     static constexpr int P_ELEMS = TY * WIDE + 6 * TX;
-    // other arrays of plane k: vx, tvx wide (own rows); vy, tvy rows y0-2..y0+TY;
-    // vz, tvz (plane k+1), tp, b own
+    // other arrays: vx, tvx wide own rows; vy, tvy rows y0-2..y0+TY; vz, tvz
+    // (plane k+1), tp, b own rows. Every region starts on a 128-byte boundary.
     static constexpr int O_VX = 0;
     static constexpr int O_TVX = O_VX + TY * WIDE;
     static constexpr int O_VY = O_TVX + TY * WIDE;
@@ -111,55 +124,69 @@ struct FusedShape {
     static constexpr int O_TP = O_TVZ + TY * TX;
     static constexpr int O_B = O_TP + TY * TX;
     static constexpr int O_ELEMS = O_B + TY * TX;
-    // new-velocity exchange buffers (double buffered): vx wide own rows, vy rows y0-2..y0+TY
-    static constexpr int N_VX = 0;
+    // new-velocity exchange (double buffered): vx wide own rows, vy rows y0-2..y0+TY
     static constexpr int N_VY = TY * WIDE;
     static constexpr int N_ELEMS = N_VY + (TY + 3) * TX;
-    static constexpr size_t SMEM =
-        sizeof(S) * ((size_t)SP * P_ELEMS + (size_t)SO * O_ELEMS + 2 * (size_t)N_ELEMS) +
-        sizeof(uint64_t) * (2 * (SP + SO) + 1) + 128;
+    static constexpr size_t RING_BYTES =
+        sizeof(S) * ((size_t)SP * P_ELEMS + (size_t)SO * O_ELEMS + 2 * (size_t)N_ELEMS);
+    static constexpr size_t SMEM = RING_BYTES + sizeof(uint64_t) * (2 * (SP + SO) + 1) + 128;
+    static_assert((P_ELEMS * sizeof(S)) % 128 == 0 && (O_ELEMS * sizeof(S)) % 128 == 0 &&
+                      (N_ELEMS * sizeof(S)) % 128 == 0 && (O_VY * sizeof(S)) % 128 == 0 &&
+                      (O_TVY * sizeof(S)) % 128 == 0 && (O_VZ * sizeof(S)) % 128 == 0 &&
+                      (P_HALO * sizeof(S)) % 128 == 0 && ((P_HALO + 3 * TX) * sizeof(S)) % 128 == 0,
+                  "TMA destinations must be 128-byte aligned");
+};
+
+struct FusedMaps {
+    CUtensorMap p_own, p_halo, vx, tvx, vy, tvy, vz, tvz, tp, b;
 };
 
 struct FusedParams {
-    AcParams a;            // n, bc, strides, coefficients, source, energy (p/v fields unused)
+    AcParams a;  // grid, boundaries, strides, multipliers, source, energy
     const void *p_in, *vx_in, *vy_in, *vz_in, *tvx_in, *tvy_in, *tvz_in;
     void *p_out, *vx_out, *vy_out, *vz_out, *tvx_out, *tvy_out, *tvz_out;
-    void *tp;              // in place
+    void *tp;    // in place
     int zchunk;
-    int *err;              // set to 1 when a bounded wait expires
+    int *err;    // set to 1 when a bounded wait expires
 };
 
-template <class P>
-__device__ __forceinline__ typename P::A sgn_ld(typename P::S s, int sign) {
-    if (sign == 0) return P::zero();
-    typename P::A v = P::ld(s);
-    return sign > 0 ? v : P::neg(v);
+template <class V>
+__device__ __forceinline__ typename V::Raw signed_raw(const typename V::Raw &r, int sign) {
+    return sign > 0 ? r : (sign < 0 ? V::rneg(r) : V::zero());
 }
 
 template <class P, int COMP, bool ENERGY>
-__global__ void __launch_bounds__(160, 2) fused_step(FusedParams fp) {
-    using SH = FusedShape<P>;
+__global__ void __launch_bounds__(160, 3)
+    fused_step(const __grid_constant__ FusedParams fp, const __grid_constant__ FusedMaps maps) {
+    using SH = FShape<P>;
     using S = typename P::S;
-    using A = typename P::A;
+    using V = typename VecOf<P>::T;
+    using Raw = typename V::Raw;
+    using AV = typename V::AV;
+    using RS = typename V::RS;
     constexpr int VEC = SH::VEC, TX = SH::TX, TY = SH::TY, WIDE = SH::WIDE, HALO = SH::HALO;
     constexpr int SP = SH::SP, SO = SH::SO;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    S *pring = reinterpret_cast<S *>(smem_raw);
+    static_assert(V::N == VEC, "vector width");
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+    S *pring = reinterpret_cast<S *>(base);
     S *oring = pring + SP * SH::P_ELEMS;
     S *nbuf = oring + SO * SH::O_ELEMS;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(nbuf + 2 * SH::N_ELEMS);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + SH::RING_BYTES);
     uint64_t *p_full = bars, *p_empty = bars + SP, *o_full = bars + 2 * SP, *o_empty = bars + 2 * SP + SO;
-    // barrier of the four consumer warps (an mbarrier, so that its waits are bounded too)
     uint64_t *c_bar = bars + 2 * (SP + SO);
 
     const AcParams &prm = fp.a;
     const int nx = prm.n[0], ny = prm.n[1], nz = prm.n[2];
-    const int bcx = prm.bc[0], bcy = prm.bc[1], bcz = prm.bc[2];
+    const int bcy = prm.bc[1], bcz = prm.bc[2];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * fp.zchunk;
     const int z1 = min(z0 + fp.zchunk, nz);
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
+    const int64_t sy = prm.sy, sz = prm.sz;
+    constexpr int eb = sizeof(S);
 
     if (tid == 0) {
         for (int s = 0; s < SP; s++) { mbar_init(&p_full[s], 1); mbar_init(&p_empty[s], 4); }
@@ -169,114 +196,107 @@ __global__ void __launch_bounds__(160, 2) fused_step(FusedParams fp) {
     }
     __syncthreads();
 
-    const int64_t sy = prm.sy, sz = prm.sz;
-    const int eb = sizeof(S);
-
     if (warp == 4) {
         // ================================================= producer warp
         const int lane = tid & 31;
-        // mapped global row start (element index) for field kind along y/z;
-        // wall rows (sign 0) copy row 0 of plane 0 (any valid memory).
+        // element offset of the (mapped) source row; rows and planes farther
+        // than two past the grid are never read and copy row 0
         auto row_src = [&](int my, int mz, bool node_y, bool node_z) -> int64_t {
-            // rows and planes farther than two past the grid are never read by
-            // the consumers (and one reflection does not reach them): copy row 0
             if (my < -3 || my > ny + 2 || mz < -3 || mz > nz + 2) return 0;
             int jy, kz;
-            int s1 = node_y ? img_node(my, ny, bcy, jy) : img_half(my, ny, bcy, jy);
-            int s2 = node_z ? img_node(mz, nz, bcz, kz) : img_half(mz, nz, bcz, kz);
+            const int s1 = node_y ? img_node(my, ny, bcy, jy) : img_half(my, ny, bcy, jy);
+            const int s2 = node_z ? img_node(mz, nz, bcz, kz) : img_half(mz, nz, bcz, kz);
             if (s1 == 0 || s2 == 0) return 0;
             return sy * jy + sz * (int64_t)kz;
         };
-        // Issue the copies of one wide row: the own part [x0, x0+TX) plus the
-        // 16-byte halo blocks left and right when they are inside the grid or
-        // wrap around it (periodic). Returns bytes issued.
-        auto wide_row = [&](S *dst, const S *base, int64_t rowoff, uint64_t *bar, bool issue) -> uint32_t {
+        auto plane_of = [&](int m, bool node) -> int {
+            if (m < -3 || m > nz + 2) return 0;
+            int kz;
+            const int s = node ? img_node(m, nz, bcz, kz) : img_half(m, nz, bcz, kz);
+            return s == 0 ? 0 : kz;
+        };
+        // a wide row by bulk copies: the own part and the halo blocks that lie
+        // inside the grid (at the grid's x faces the consumers read images)
+        auto wide_row = [&](S *dst, const S *src, int64_t rowoff, uint64_t *bar, bool issue) -> uint32_t {
             uint32_t bytes = TX * eb;
-            if (issue) bulk_copy(dst + HALO, base + rowoff + x0, TX * eb, bar);
-            int lx0 = x0 - HALO;
-            if (lx0 >= 0 || bcx == BC_PERIODIC) {
-                int src = lx0 >= 0 ? lx0 : lx0 + nx;
-                if (issue) bulk_copy(dst, base + rowoff + src, HALO * eb, bar);
+            if (issue) bulk_copy(dst + HALO, src + rowoff + x0, TX * eb, bar);
+            if (x0 - HALO >= 0) {
+                if (issue) bulk_copy(dst, src + rowoff + x0 - HALO, HALO * eb, bar);
                 bytes += HALO * eb;
             }
-            int rx0 = x0 + TX;
-            if (rx0 < nx || bcx == BC_PERIODIC) {
-                int src = rx0 < nx ? rx0 : rx0 - nx;
-                if (issue) bulk_copy(dst + HALO + TX, base + rowoff + src, HALO * eb, bar);
+            if (x0 + TX < nx) {
+                if (issue) bulk_copy(dst + HALO + TX, src + rowoff + x0 + TX, HALO * eb, bar);
                 bytes += HALO * eb;
             }
             return bytes;
         };
-        // Work items of one p plane m: TY wide own rows + 6 narrow halo rows.
-        auto p_plane = [&](int m, S *dst, uint64_t *bar, bool issue, int part) -> uint32_t {
+        const bool own_box = y0 + TY <= ny;            // all own rows inside the grid
+        const bool top_box = y0 >= 3;                  // p rows y0-3..y0-1 inside
+        const bool bot_box = y0 + TY + 3 <= ny;        // p rows y0+TY..y0+TY+2 inside
+        const bool vy_box = y0 >= 2 && y0 + TY + 1 <= ny;  // v_y rows y0-2..y0+TY inside
+        // one p plane: the boxes (lane 0) and the row-by-row groups (spread over lanes)
+        auto p_plane = [&](int m, S *dst, uint64_t *bar, bool issue) -> uint32_t {
             const S *pin = static_cast<const S *>(fp.p_in);
+            const int mz = plane_of(m, true);
             uint32_t bytes = 0;
-            for (int r = part; r < TY + 6; r += 32) {
-                if (r < TY) {
-                    int my = y0 + r;
-                    bytes += wide_row(dst + r * WIDE, pin, row_src(my, m, true, true), bar, issue);
+            if (own_box) {
+                if (issue && lane == 0) tma_box(dst, &maps.p_own, x0 - HALO, y0, mz, bar);
+                bytes += TY * WIDE * eb;
+            } else {
+                for (int r = 0; r < TY; r++)
+                    bytes += wide_row(dst + r * WIDE, pin, row_src(y0 + r, m, true, true), bar,
+                                      issue && lane == r);
+            }
+            for (int side = 0; side < 2; side++) {
+                S *hd = dst + SH::P_HALO + side * 3 * TX;
+                const int ybase = side == 0 ? y0 - 3 : y0 + TY;
+                if (side == 0 ? top_box : bot_box) {
+                    if (issue && lane == 0) tma_box(hd, &maps.p_halo, x0, ybase, mz, bar);
                 } else {
-                    int h = r - TY;  // 0..5 -> rows y0-3, y0-2, y0-1, y0+TY, y0+TY+1, y0+TY+2
-                    int my = h < 3 ? y0 - 3 + h : y0 + TY + (h - 3);
-                    if (issue) bulk_copy(dst + TY * WIDE + h * TX, pin + row_src(my, m, true, true) + x0,
-                                         TX * eb, bar);
-                    bytes += TX * eb;
+                    for (int h = 0; h < 3; h++)
+                        if (issue && lane == 16 + side * 3 + h)
+                            bulk_copy(hd + h * TX, pin + row_src(ybase + h, m, true, true) + x0, TX * eb, bar);
                 }
+                bytes += 3 * TX * eb;
             }
             return bytes;
         };
-        auto o_stage = [&](int k, S *dst, uint64_t *bar, bool issue, int part) -> uint32_t {
+        // the other arrays of iteration k (warm-up iterations k < z0: v_z, t_vz only)
+        auto o_stage = [&](int k, S *dst, uint64_t *bar, bool issue) -> uint32_t {
             uint32_t bytes = 0;
-            const bool full_set = k >= z0;
-            // rows: 0..TY-1 vx, TY..2TY-1 tvx, then 19 vy, 19 tvy, then TY each vz, tvz, tp, b
-            const int nrows = full_set ? (2 * TY + 2 * (TY + 3) + 4 * TY) : 2 * TY;
-            for (int r = part; r < nrows; r += 32) {
-                if (!full_set) {
-                    // warm-up planes: only vz, tvz of plane k+1
-                    const bool is_t = r >= TY;
-                    const int rr = is_t ? r - TY : r;
-                    if (is_t && !COMP) continue;
-                    const S *src = static_cast<const S *>(is_t ? fp.tvz_in : fp.vz_in);
-                    S *d = dst + (is_t ? SH::O_TVZ : SH::O_VZ) + rr * TX;
-                    if (issue) bulk_copy(d, src + row_src(y0 + rr, k + 1, true, false) + x0, TX * eb, bar);
-                    bytes += TX * eb;
-                    continue;
+            const int kz1 = plane_of(k + 1, false);
+            if (issue && lane == 0) tma_box(dst + SH::O_VZ, &maps.vz, x0, y0, kz1, bar);
+            bytes += TY * TX * eb;
+            if (COMP) {
+                if (issue && lane == 0) tma_box(dst + SH::O_TVZ, &maps.tvz, x0, y0, kz1, bar);
+                bytes += TY * TX * eb;
+            }
+            if (k < z0) return bytes;
+            if (issue && lane == 0) tma_box(dst + SH::O_VX, &maps.vx, x0 - HALO, y0, k, bar);
+            bytes += TY * WIDE * eb;
+            if (COMP) {
+                if (issue && lane == 0) tma_box(dst + SH::O_TVX, &maps.tvx, x0 - HALO, y0, k, bar);
+                bytes += TY * WIDE * eb;
+            }
+            for (int ca = 0; ca < (COMP ? 2 : 1); ca++) {
+                S *d = dst + (ca ? SH::O_TVY : SH::O_VY);
+                if (vy_box) {
+                    if (issue && lane == 0) tma_box(d, ca ? &maps.tvy : &maps.vy, x0, y0 - 2, k, bar);
+                } else {
+                    const S *src = static_cast<const S *>(ca ? fp.tvy_in : fp.vy_in);
+                    for (int r = 0; r < TY + 3; r++)
+                        if (issue && ((r + ca * 7) % 32) == lane)
+                            bulk_copy(d + r * TX, src + row_src(y0 - 2 + r, k, false, true) + x0, TX * eb, bar);
                 }
-                int rr = r;
-                if (rr < 2 * TY) {
-                    const bool is_t = rr >= TY;
-                    if (is_t && !COMP) continue;
-                    const int row = is_t ? rr - TY : rr;
-                    const S *src = static_cast<const S *>(is_t ? fp.tvx_in : fp.vx_in);
-                    bytes += wide_row(dst + (is_t ? SH::O_TVX : SH::O_VX) + row * WIDE, src,
-                                      row_src(y0 + row, k, true, true), bar, issue);
-                    continue;
-                }
-                rr -= 2 * TY;
-                if (rr < 2 * (TY + 3)) {
-                    const bool is_t = rr >= TY + 3;
-                    if (is_t && !COMP) continue;
-                    const int row = is_t ? rr - (TY + 3) : rr;   // row 0 <-> y0 - 2
-                    const S *src = static_cast<const S *>(is_t ? fp.tvy_in : fp.vy_in);
-                    S *d = dst + (is_t ? SH::O_TVY : SH::O_VY) + row * TX;
-                    if (issue) bulk_copy(d, src + row_src(y0 - 2 + row, k, false, true) + x0, TX * eb, bar);
-                    bytes += TX * eb;
-                    continue;
-                }
-                rr -= 2 * (TY + 3);
-                const int which = rr / TY, row = rr % TY;  // 0 vz, 1 tvz, 2 tp, 3 b
-                if (which == 1 && !COMP) continue;
-                if (which == 2 && !COMP) continue;
-                if (which == 3 && !prm.b) continue;
-                const S *src = which == 0 ? static_cast<const S *>(fp.vz_in)
-                             : which == 1 ? static_cast<const S *>(fp.tvz_in)
-                             : which == 2 ? static_cast<const S *>(fp.tp)
-                                          : static_cast<const S *>(prm.b);
-                const int off = which == 0 ? SH::O_VZ : which == 1 ? SH::O_TVZ : which == 2 ? SH::O_TP : SH::O_B;
-                const int64_t ro = which <= 1 ? row_src(y0 + row, k + 1, true, false)
-                                              : row_src(y0 + row, k, true, true);
-                if (issue) bulk_copy(dst + off + row * TX, src + ro + x0, TX * eb, bar);
-                bytes += TX * eb;
+                bytes += (TY + 3) * TX * eb;
+            }
+            if (COMP) {
+                if (issue && lane == 0) tma_box(dst + SH::O_TP, &maps.tp, x0, y0, k, bar);
+                bytes += TY * TX * eb;
+            }
+            if (prm.b) {
+                if (issue && lane == 0) tma_box(dst + SH::O_B, &maps.b, x0, y0, k, bar);
+                bytes += TY * TX * eb;
             }
             return bytes;
         };
@@ -284,22 +304,20 @@ __global__ void __launch_bounds__(160, 2) fused_step(FusedParams fp) {
             const int slot = cnt % SP;
             if (cnt >= SP && !wait_phase(&p_empty[slot], ((cnt / SP) - 1) & 1, fp.err)) return false;
             S *dst = pring + slot * SH::P_ELEMS;
-            uint32_t total = 0;
-            for (int part = 0; part < 32; part++) total += p_plane(m, dst, nullptr, false, part);
+            const uint32_t total = p_plane(m, dst, nullptr, false);
             if (lane == 0) mbar_expect_tx(&p_full[slot], total);
             __syncwarp();
-            p_plane(m, dst, &p_full[slot], true, lane);
+            p_plane(m, dst, &p_full[slot], true);
             return true;
         };
         auto issue_o = [&](int k, int cnt) -> bool {
             const int slot = cnt % SO;
             if (cnt >= SO && !wait_phase(&o_empty[slot], ((cnt / SO) - 1) & 1, fp.err)) return false;
             S *dst = oring + slot * SH::O_ELEMS;
-            uint32_t total = 0;
-            for (int part = 0; part < 32; part++) total += o_stage(k, dst, nullptr, false, part);
+            const uint32_t total = o_stage(k, dst, nullptr, false);
             if (lane == 0) mbar_expect_tx(&o_full[slot], total);
             __syncwarp();
-            o_stage(k, dst, &o_full[slot], true, lane);
+            o_stage(k, dst, &o_full[slot], true);
             return true;
         };
         int pc = 0, oc = 0;
@@ -308,8 +326,7 @@ __global__ void __launch_bounds__(160, 2) fused_step(FusedParams fp) {
             ok = issue_p(m, pc++);
             if (ok && m >= z0) ok = issue_o(m - 3, oc++);
         }
-        // before leaving, let the copies this warp issued land (bounded)
-        if (lane == 0) {
+        if (lane == 0) {  // let the copies issued by this warp land before leaving
             for (int c = (pc > SP ? pc - SP : 0); c < pc; c++) drain_phase(&p_full[c % SP], (c / SP) & 1);
             for (int c = (oc > SO ? oc - SO : 0); c < oc; c++) drain_phase(&o_full[c % SO], (c / SO) & 1);
         }
@@ -320,19 +337,27 @@ __global__ void __launch_bounds__(160, 2) fused_step(FusedParams fp) {
     const int lx = tid % SH::LANES, row = tid / SH::LANES;
     const int x = x0 + lx * VEC;
     const int j = y0 + row;
-    const bool active = j < ny;  // n[0] is a multiple of TX
-    A a_uni[3];
+    const bool active = j < ny;
+    RS a_raw[3], b_raw;
 #pragma unroll
-    for (int c = 0; c < 3; c++) {
-        S s;
-        from_bits(prm.a_uni[c], s);
-        a_uni[c] = P::ld(s);
-    }
-    S b_s;
-    from_bits(prm.b_uni, b_s);
+    for (int c = 0; c < 3; c++) from_bits(prm.a_uni[c], a_raw[c]);
+    from_bits(prm.b_uni, b_raw);
+    const AV ax = V::splat(V::lds(a_raw[0])), ay = V::splat(V::lds(a_raw[1])),
+             az = V::splat(V::lds(a_raw[2]));
+    const typename P::A ax_s = P::ld(a_raw[0]);
 
-    // v_z^{n+1/2} of the own vector, planes k-2, k-1, k, k+1 (ring of 4)
-    A vzq[4][VEC];
+    auto row_sign = [&](int my) -> int { int t; return img_node(my, ny, bcy, t); };
+    auto plane_sign = [&](int m) -> int { int t; return img_node(m, nz, bcz, t); };
+    // tiles whose p rows y0-3..y0+TY+2 are all inside the grid read no images in y
+    const bool inner_y = y0 >= 3 && y0 + TY + 3 <= ny;
+    // raw p vector of local row lr (-3..TY+2) at the own lane
+    auto p_vec = [&](const S *pst, int lr) -> Raw {
+        const S *ptr = (lr >= 0 && lr < TY) ? pst + lr * WIDE + HALO + lx * VEC
+                                            : pst + SH::P_HALO + (lr < 0 ? lr + 3 : 3 + lr - TY) * TX + lx * VEC;
+        return *reinterpret_cast<const Raw *>(ptr);
+    };
+    auto vec_at = [&](const S *p) -> Raw { return *reinterpret_cast<const Raw *>(p); };
+
     float e_s = 0.f, e_c = 0.f;
     auto eadd = [&](float x_) {
         const float t = __fadd_rn(e_s, x_);
@@ -342,248 +367,168 @@ __global__ void __launch_bounds__(160, 2) fused_step(FusedParams fp) {
         e_s = t;
     };
 
-    // p sample of plane slot at local row lr (-3..TY+2) and column x (global)
-    auto p_row_ptr = [&](const S *pst, int lr) -> const S * {
-        if (lr >= 0 && lr < TY) return pst + lr * WIDE + HALO - x0;  // index by global x
-        const int h = lr < 0 ? lr + 3 : 3 + (lr - TY);
-        return pst + TY * WIDE + h * TX - x0;
-    };
-    // sign of the image for the p row my in plane m (node type in y and z)
-    auto p_sign = [&](int my, int m) -> int {
-        int t1, t2;
-        return img_node(my, ny, bcy, t1) * img_node(m, nz, bcz, t2);
-    };
-    // x image for a value of a wide row of a node-type (p) or half-type (vx) field
-    auto x_img = [&](int mx, bool node, int &sgn) -> int {
-        if (mx >= 0 && mx < nx) { sgn = 1; return mx; }
-        if (bcx == BC_PERIODIC) { sgn = 1; return mx; }  // halo block holds the wrapped values
-        int out;
-        sgn = node ? img_node(mx, nx, bcx, out) : img_half(mx, nx, bcx, out);
-        return out;
-    };
-
-    int pc = 0, oc = 0, nb = 0;
-    bool ok = true;
+    Raw vzq0 = V::zero(), vzq1 = V::zero(), vzq2 = V::zero(), vzq3 = V::zero();
+    int oc = 0, nb = 0, p_waited = 0;
     uint32_t c_phase = 0;
+    bool ok = true;
     auto consumer_sync = [&]() -> bool {
         mbar_arrive(c_bar);
         const bool r = wait_phase(c_bar, c_phase & 1, fp.err);
         c_phase++;
         return r;
     };
-    // p planes waited so far (the consumer waits for plane m when first needed)
-    int p_waited = 0;
-    auto wait_p_upto = [&](int cnt_needed) -> bool {
-        while (p_waited < cnt_needed) {
-            if (!wait_phase(&p_full[p_waited % SP], (p_waited / SP) & 1, fp.err)) return false;
-            p_waited++;
-        }
-        return true;
-    };
 
     for (int k = z0 - 3; k < z1 && ok; k++) {
-        // planes k..k+3 of p: ring counts (k - (z0-3)) .. +3
         const int pbase = k - (z0 - 3);
-        if (!wait_p_upto(pbase + 4)) { ok = false; break; }
+        while (p_waited < pbase + 4) {
+            if (!wait_phase(&p_full[p_waited % SP], (p_waited / SP) & 1, fp.err)) { ok = false; break; }
+            p_waited++;
+        }
+        if (!ok) break;
         const int oslot = oc % SO;
         if (!wait_phase(&o_full[oslot], (oc / SO) & 1, fp.err)) { ok = false; break; }
         const S *ost = oring + oslot * SH::O_ELEMS;
-        const S *pst[4];
-        for (int t = 0; t < 4; t++) pst[t] = pring + ((pbase + t) % SP) * SH::P_ELEMS;
+        const S *pk = pring + (pbase % SP) * SH::P_ELEMS;
 
-        // ---- v_z^{n+1/2} at plane k+1 for the own vector (from p^n planes k..k+3)
+        // ---- v_z^{n+1/2} at plane k+1 of the own vector (p^n planes k..k+3)
+        Raw vzn = V::zero(), tzn = V::zero();
+        const bool inner_z = k >= 0 && k + 3 < nz;  // planes k..k+3 inside the grid
         if (active) {
-            int sg[4];
+            Raw pz[4];
 #pragma unroll
-            for (int t = 0; t < 4; t++) sg[t] = p_sign(j, k + t);
-            const S *vzrow = ost + SH::O_VZ + row * TX + lx * VEC;
-            const S *tzrow = ost + SH::O_TVZ + row * TX + lx * VEC;
-            const int64_t qz = x + sy * j + sz * (int64_t)(k + 1);
-            const bool write_vz = (k + 1 >= z0) && (k + 1 < z1);
-            S vn[VEC], tn[VEC];
-#pragma unroll
-            for (int e = 0; e < VEC; e++) {
-                A f[4];
-#pragma unroll
-                for (int t = 0; t < 4; t++) f[t] = sgn_ld<P>(p_row_ptr(pst[t], row)[x + e], sg[t]);
-                const A D = stencil<P>(f[0], f[1], f[2], f[3]);
-                const A inc = P::mul(a_uni[2], D);
-                // the v_z image along z is even: same stored values at the mapped plane
-                S V = vzrow[e];
-                S T = COMP ? tzrow[e] : S(0);
-                update<P, COMP>(V, T, inc);
-                vn[e] = V;
-                tn[e] = T;
-                vzq[3][e] = P::ld(V);
+            for (int t = 0; t < 4; t++) {
+                const Raw r = p_vec(pring + ((pbase + t) % SP) * SH::P_ELEMS, row);
+                pz[t] = inner_z ? r : signed_raw<V>(r, plane_sign(k + t));
             }
-            if (write_vz) {
-                S *vo = static_cast<S *>(fp.vz_out) + qz;
-                S *to = static_cast<S *>(fp.tvz_out) + qz;
-#pragma unroll
-                for (int e = 0; e < VEC; e++) {
-                    vo[e] = vn[e];
-                    if (COMP) to[e] = tn[e];
-                }
+            const AV D = vstencil<V>(V::ld(pz[0]), V::ld(pz[1]), V::ld(pz[2]), V::ld(pz[3]));
+            vzn = vec_at(ost + SH::O_VZ + row * TX + lx * VEC);
+            tzn = COMP ? vec_at(ost + SH::O_TVZ + row * TX + lx * VEC) : V::zero();
+            V::template update<COMP>(vzn, tzn, V::mul(az, D));
+            if (k + 1 >= z0 && k + 1 < z1) {
+                const int64_t qz = x + sy * j + sz * (int64_t)(k + 1);
+                at<V>(fp.vz_out, qz) = vzn;
+                if (COMP) at<V>(fp.tvz_out, qz) = tzn;
             }
         }
+        vzq3 = vzn;
 
         if (k >= z0) {
-            S *nvx = nbuf + nb * SH::N_ELEMS + SH::N_VX;
-            S *nvy = nbuf + nb * SH::N_ELEMS + SH::N_VY;
-            S vxn[VEC], txn[VEC], vyn[VEC], tyn[VEC];
-            // ---- v_x^{n+1/2} at own points and the x halo (lane 0: x0-2, x0-1;
-            //      last lane: x0+TX), from p^n plane k of the own row
+            S *nvx = nbuf + nb * SH::N_ELEMS;
+            S *nvy = nvx + SH::N_VY;
+            Raw vxn = V::zero(), txn = V::zero(), vyn = V::zero(), tyn = V::zero();
+            // ---- v_x^{n+1/2}: own vector, and the x halo of the tile edge lanes
             if (active) {
-                const S *prow = p_row_ptr(pst[0], row);
-                const int sgr = p_sign(j, k);
-                const S *vxr = ost + SH::O_VX + row * WIDE + HALO - x0;
-                const S *txr = ost + SH::O_TVX + row * WIDE + HALO - x0;
-                auto pval = [&](int mx) -> A {
-                    int s2;
-                    const int ix = x_img(mx, true, s2);
-                    if (s2 == 0) return P::zero();  // the wall node itself: not read
-                    return sgn_ld<P>(prow[ix], s2 * sgr);
-                };
-                auto vx_at = [&](int ix, S &V, S &T) {
-                    // v_x at ix + 1/2 from p at ix-1..ix+2; v_x and t_vx read with the
-                    // even x image (half-type field)
-                    const A D = stencil<P>(pval(ix - 1), pval(ix), pval(ix + 1), pval(ix + 2));
-                    const A inc = P::mul(a_uni[0], D);
-                    int s2;
-                    const int iv = x_img(ix, false, s2);
-                    V = vxr[iv];
-                    T = COMP ? txr[iv] : S(0);
-                    update<P, COMP>(V, T, inc);
-                };
-#pragma unroll
-                for (int e = 0; e < VEC; e++) vx_at(x + e, vxn[e], txn[e]);
+                const S *prow = pk + row * WIDE + HALO - x0;  // indexed by global x
+                const Raw own_p = p_vec(pk, row);
+                RS l0, r0, r1;
+                if (x == 0) l0 = V::rneg_s(prow[1]);               // p[-1] = -p[1]
+                else l0 = prow[x - 1];
+                if (x + VEC == nx) { r0 = RS(0); r1 = V::rneg_s(prow[nx - 1]); }  // wall node, image
+                else { r0 = prow[x + VEC]; r1 = prow[x + VEC + 1]; }
+                const AV own = V::ld(own_p);
+                const AV D = vstencil<V>(V::shr1(own, V::lds(l0)), own, V::shl1(own, V::lds(r0)),
+                                         V::shl2(own, V::lds(r0), V::lds(r1)));
+                vxn = vec_at(ost + SH::O_VX + row * WIDE + HALO + lx * VEC);
+                txn = COMP ? vec_at(ost + SH::O_TVX + row * WIDE + HALO + lx * VEC) : V::zero();
+                V::template update<COMP>(vxn, txn, V::mul(ax, D));
                 S *nrow = nvx + row * WIDE + HALO - x0;
-#pragma unroll
-                for (int e = 0; e < VEC; e++) nrow[x + e] = vxn[e];
-                if (lx == 0) {
-                    S V, T;
-                    vx_at(x0 - 2, V, T);
-                    nrow[x0 - 2] = V;
-                    vx_at(x0 - 1, V, T);
-                    nrow[x0 - 1] = V;
-                }
-                if (lx == SH::LANES - 1) {
-                    S V, T;
-                    vx_at(x0 + TX, V, T);
-                    nrow[x0 + TX] = V;
+                *reinterpret_cast<Raw *>(nrow + x) = vxn;
+                // the x halo of the tile (v_x at x0-2, x0-1, x0+TX), one value per
+                // lane 0, 1, 2, where it lies inside the grid; at the grid's x faces
+                // the reads below take the even images of v_x instead
+                if (lx < 3) {
+                    const int ix = lx == 0 ? x0 - 2 : (lx == 1 ? x0 - 1 : x0 + TX);
+                    if (ix >= 0 && ix < nx) {
+                        const S *vxr = ost + SH::O_VX + row * WIDE + HALO - x0;
+                        const S *txr = ost + SH::O_TVX + row * WIDE + HALO - x0;
+                        const typename P::A D1 = stencil<P>(P::ld(prow[ix - 1]), P::ld(prow[ix]),
+                                                            P::ld(prow[ix + 1]), P::ld(prow[ix + 2]));
+                        S Vv = vxr[ix];
+                        S Tv = COMP ? txr[ix] : S(0);
+                        update<P, COMP>(Vv, Tv, P::mul(ax_s, D1));
+                        nrow[ix] = Vv;
+                    }
                 }
             }
-            // ---- v_y^{n+1/2} at own rows and the halo rows y0-2, y0-1, y0+TY
-            auto vy_at = [&](int lr /* local row of the v_y point, -2..TY */, S *V, S *T) {
-                const int my = y0 + lr;
-                int sg[4];
-                const S *pr[4];
+            // ---- v_y^{n+1/2} at local row lr (-2..TY), lane ln, from p rows lr-1..lr+2
+            auto vy_vec = [&](int lr, int ln, Raw &Vv, Raw &Tv) {
+                Raw pr[4];
 #pragma unroll
                 for (int t = 0; t < 4; t++) {
-                    pr[t] = p_row_ptr(pst[0], lr - 1 + t);
-                    sg[t] = p_sign(my - 1 + t, k);
+                    const int l = lr - 1 + t;
+                    const S *ptr = (l >= 0 && l < TY) ? pk + l * WIDE + HALO + ln * VEC
+                                                      : pk + SH::P_HALO + (l < 0 ? l + 3 : 3 + l - TY) * TX + ln * VEC;
+                    const Raw r = *reinterpret_cast<const Raw *>(ptr);
+                    pr[t] = inner_y ? r : signed_raw<V>(r, row_sign(y0 + l));
                 }
-                const S *vyr = ost + SH::O_VY + (lr + 2) * TX - x0;
-                const S *tyr = ost + SH::O_TVY + (lr + 2) * TX - x0;
-#pragma unroll
-                for (int e = 0; e < VEC; e++) {
-                    const A D = stencil<P>(sgn_ld<P>(pr[0][x + e], sg[0]), sgn_ld<P>(pr[1][x + e], sg[1]),
-                                           sgn_ld<P>(pr[2][x + e], sg[2]), sgn_ld<P>(pr[3][x + e], sg[3]));
-                    const A inc = P::mul(a_uni[1], D);
-                    S Vv = vyr[x + e];
-                    S Tv = COMP ? tyr[x + e] : S(0);
-                    update<P, COMP>(Vv, Tv, inc);
-                    V[e] = Vv;
-                    T[e] = Tv;
-                }
+                const AV D = vstencil<V>(V::ld(pr[0]), V::ld(pr[1]), V::ld(pr[2]), V::ld(pr[3]));
+                Vv = vec_at(ost + SH::O_VY + (lr + 2) * TX + ln * VEC);
+                Tv = COMP ? vec_at(ost + SH::O_TVY + (lr + 2) * TX + ln * VEC) : V::zero();
+                V::template update<COMP>(Vv, Tv, V::mul(ay, D));
+                *reinterpret_cast<Raw *>(nvy + (lr + 2) * TX + ln * VEC) = Vv;
             };
-            // own rows, and the first row past the grid (row ny, the image row
-            // that the last grid row's stencil reads)
-            if (j <= ny) {
-                vy_at(row, vyn, tyn);
-                S *nr = nvy + (row + 2) * TX - x0;
-#pragma unroll
-                for (int e = 0; e < VEC; e++) nr[x + e] = vyn[e];
-            }
-            if (tid < 3 * SH::LANES) {
-                // halo rows: local -2, -1, TY (the images of rows outside the grid
-                // come out right because the inputs are read with their images)
-                const int hr = tid / SH::LANES;
-                const int lr = hr == 0 ? -2 : hr == 1 ? -1 : TY;
-                if (y0 + lr < ny + 2) {
-                    S V[VEC], T[VEC];
-                    vy_at(lr, V, T);
-                    S *nr = nvy + (lr + 2) * TX - x0;
-#pragma unroll
-                    for (int e = 0; e < VEC; e++) nr[x + e] = V[e];
+            // own rows, and row ny (the image row the last grid row reads)
+            if (j <= ny) vy_vec(row, lx, vyn, tyn);
+            {
+                // the halo rows y0-2, y0-1, y0+TY: 3 x LANES vectors, six per warp
+                const int wl = tid & 31;
+                if (wl < 6) {
+                    const int hidx = warp * 6 + wl;
+                    const int hr = hidx / SH::LANES, ln = hidx % SH::LANES;
+                    const int lr = hr == 0 ? -2 : (hr == 1 ? -1 : TY);
+                    if (y0 + lr <= ny) {
+                        Raw Vh, Th;
+                        vy_vec(lr, ln, Vh, Th);
+                    }
                 }
             }
             if (!consumer_sync()) { ok = false; break; }
             // ---- p^{n+1}
             if (active) {
-                const S *vxr = nvx + row * WIDE + HALO - x0;
-                const S *tpr = ost + SH::O_TP + row * TX - x0;
-                const S *br = ost + SH::O_B + row * TX - x0;
-                const S *prow = p_row_ptr(pst[0], row);
-                const int sgr = p_sign(j, k);
-                const int64_t q = x + sy * j + sz * (int64_t)k;
-                S pn[VEC], tpn[VEC];
-#pragma unroll
-                for (int e = 0; e < VEC; e++) {
-                    const int i = x + e;
-                    // node i reads v_x at i-2, i-1, i, i+1 (+1/2); outside the grid the
-                    // even image (rigid) or the wrapped halo (periodic)
-                    // v_x^{n+1/2} at i-2 .. i+1 (+1/2): own values and the halo values
-                    // computed above (outside the grid they were computed from the
-                    // images of their inputs, which reproduces the images of v_x)
-                    A R = stencil<P>(P::ld(vxr[i - 2]), P::ld(vxr[i - 1]), P::ld(vxr[i]),
-                                     P::ld(vxr[i + 1]));
-                    const S *vyc = nvy - x0 + i;
-                    const A Dy = stencil<P>(P::ld(vyc[(row) * TX]), P::ld(vyc[(row + 1) * TX]),
-                                            P::ld(vyc[(row + 2) * TX]), P::ld(vyc[(row + 3) * TX]));
-                    R = P::add(R, Dy);
-                    const A Dz = stencil<P>(vzq[0][e], vzq[1][e], vzq[2][e], vzq[3][e]);
-                    R = P::add(R, Dz);
-                    if (k == prm.src_k && j == prm.src_j && i == prm.src_i && prm.step < prm.src_nt)
-                        R = P::add(R, static_cast<const A *>(prm.src)[prm.step]);
-                    const S bq = prm.b ? br[i] : b_s;
-                    const A inc = P::mul(P::ld(bq), R);
-                    const S pold = (sgr == 0) ? S(0) : prow[i];
-                    S V = pold;
-                    S T = COMP ? tpr[i] : S(0);
-                    update<P, COMP>(V, T, inc);
-                    pn[e] = V;
-                    tpn[e] = T;
-                    if (ENERGY) {
-                        eadd(e_term(P::to_f32(pold), P::to_f32(V), P::to_f32(bq)));
-                        const float fx = P::to_f32(vxn[e]), fy = P::to_f32(vyn[e]);
-                        eadd(e_term(fx, fx, P::to_f32(P::st(a_uni[0]))));
-                        eadd(e_term(fy, fy, P::to_f32(P::st(a_uni[1]))));
-                    }
+                const S *vrow = nvx + row * WIDE + HALO - x0;
+                const AV ownx = V::ld(*reinterpret_cast<const Raw *>(vrow + x));
+                // v_x at x-2, x-1, x+VEC; at the x faces the even images (v_x at 1, 0; nx-1)
+                const RS l1 = x == 0 ? vrow[1] : vrow[x - 2];
+                const RS l0 = x == 0 ? vrow[0] : vrow[x - 1];
+                const RS rr = x + VEC == nx ? vrow[nx - 1] : vrow[x + VEC];
+                AV R = vstencil<V>(V::shr2(ownx, V::lds(l1), V::lds(l0)), V::shr1(ownx, V::lds(l0)),
+                                   ownx, V::shl1(ownx, V::lds(rr)));
+                const S *vyc = nvy + lx * VEC;
+                const AV Dy = vstencil<V>(V::ld(vec_at(vyc + row * TX)), V::ld(vec_at(vyc + (row + 1) * TX)),
+                                          V::ld(vec_at(vyc + (row + 2) * TX)), V::ld(vec_at(vyc + (row + 3) * TX)));
+                R = V::add(R, Dy);
+                const AV Dz = vstencil<V>(V::ld(vzq0), V::ld(vzq1), V::ld(vzq2), V::ld(vzq3));
+                R = V::add(R, Dz);
+                if (k == prm.src_k && j == prm.src_j && prm.src_i >= x && prm.src_i < x + VEC &&
+                    prm.step < prm.src_nt) {
+                    const int e = prm.src_i - x;
+                    V::set(R, e, P::add(V::aget(R, e), static_cast<const typename V::AS *>(prm.src)[prm.step]));
                 }
-                // stores: p, t_p (in place), v_x, t_vx, v_y, t_vy of plane k
-                S *po = static_cast<S *>(fp.p_out) + q;
-                S *to = static_cast<S *>(fp.tp) + q;
-                S *vxo = static_cast<S *>(fp.vx_out) + q;
-                S *txo = static_cast<S *>(fp.tvx_out) + q;
-                S *vyo = static_cast<S *>(fp.vy_out) + q;
-                S *tyo = static_cast<S *>(fp.tvy_out) + q;
-#pragma unroll
-                for (int e = 0; e < VEC; e++) {
-                    po[e] = pn[e];
-                    vxo[e] = vxn[e];
-                    vyo[e] = vyn[e];
-                    if (COMP) {
-                        to[e] = tpn[e];
-                        txo[e] = txn[e];
-                        tyo[e] = tyn[e];
-                    }
+                const Raw bv = prm.b ? vec_at(ost + SH::O_B + row * TX + lx * VEC) : V::zero();
+                const AV bc = prm.b ? V::ld(bv) : V::splat(V::lds(b_raw));
+                const Raw pold = p_vec(pk, row);
+                Raw pn = pold;
+                Raw tpn = COMP ? vec_at(ost + SH::O_TP + row * TX + lx * VEC) : V::zero();
+                V::template update<COMP>(pn, tpn, V::mul(bc, R));
+                const int64_t q = x + sy * j + sz * (int64_t)k;
+                at<V>(fp.p_out, q) = pn;
+                at<V>(fp.vx_out, q) = vxn;
+                at<V>(fp.vy_out, q) = vyn;
+                if (COMP) {
+                    at<V>(fp.tp, q) = tpn;
+                    at<V>(fp.tvx_out, q) = txn;
+                    at<V>(fp.tvy_out, q) = tyn;
                 }
                 if (ENERGY) {
+                    const float aw0 = P::to_f32(a_raw[0]), aw1 = P::to_f32(a_raw[1]), aw2 = P::to_f32(a_raw[2]);
 #pragma unroll
                     for (int e = 0; e < VEC; e++) {
-                        const float fz = P::to_f32(P::st(vzq[2][e]));
-                        eadd(e_term(fz, fz, P::to_f32(P::st(a_uni[2]))));
+                        const float bw = prm.b ? V::f32(bv, e) : P::to_f32(b_raw);
+                        eadd(e_term(V::f32(pold, e), V::f32(pn, e), bw));
+                        const float fx = V::f32(vxn, e), fy = V::f32(vyn, e), fz = V::f32(vzq2, e);
+                        eadd(e_term(fx, fx, aw0));
+                        eadd(e_term(fy, fy, aw1));
+                        eadd(e_term(fz, fz, aw2));
                     }
                 }
             }
@@ -596,16 +541,11 @@ __global__ void __launch_bounds__(160, 2) fused_step(FusedParams fp) {
             mbar_arrive(&p_empty[pbase % SP]);
         }
         oc++;
-        // shift the v_z queue
-#pragma unroll
-        for (int t = 0; t < 3; t++)
-#pragma unroll
-            for (int e = 0; e < VEC; e++) vzq[t][e] = vzq[t + 1][e];
+        vzq0 = vzq1;
+        vzq1 = vzq2;
+        vzq2 = vzq3;
     }
-    (void)pc;
     if (ENERGY) {
-        // every consumer thread of every block takes part in the reduction;
-        // the producer warp has left, so reduce over the consumer warps only
         double val = ok ? (double)e_s + (double)e_c : 0.0;
         for (int off = 16; off > 0; off >>= 1) val += __shfl_down_sync(0xffffffffu, val, off);
         __shared__ double wsum[4];
@@ -638,30 +578,31 @@ __global__ void __launch_bounds__(160, 2) fused_step(FusedParams fp) {
 
 // ------------------------------------------------------------------------
 template <class P, int COMP>
-static cudaError_t launch_t(const FusedParams &fp, bool energy, cudaStream_t st) {
-    using SH = FusedShape<P>;
+static cudaError_t launch_t(const FusedParams &fp, const FusedMaps &maps, bool energy, cudaStream_t st) {
+    using SH = FShape<P>;
     dim3 grid(fp.a.n[0] / SH::TX, (fp.a.n[1] + SH::TY - 1) / SH::TY,
               (fp.a.n[2] + fp.zchunk - 1) / fp.zchunk);
-    const size_t smem = SH::SMEM;
+    const int smem = (int)SH::SMEM;
     cudaError_t e;
     if (energy) {
-        e = cudaFuncSetAttribute(fused_step<P, COMP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(fused_step<P, COMP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        fused_step<P, COMP, true><<<grid, 160, smem, st>>>(fp);
+        fused_step<P, COMP, true><<<grid, 160, smem, st>>>(fp, maps);
     } else {
-        e = cudaFuncSetAttribute(fused_step<P, COMP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(fused_step<P, COMP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        fused_step<P, COMP, false><<<grid, 160, smem, st>>>(fp);
+        fused_step<P, COMP, false><<<grid, 160, smem, st>>>(fp, maps);
     }
     return cudaGetLastError();
 }
 
 template <class P>
-static cudaError_t launch_c(const FusedParams &fp, int comp, bool energy, cudaStream_t st) {
+static cudaError_t launch_c(const FusedParams &fp, const FusedMaps &maps, int comp, bool energy,
+                            cudaStream_t st) {
     switch (comp) {
-    case 0: return launch_t<P, 0>(fp, energy, st);
-    case 3: return launch_t<P, 3>(fp, energy, st);
-    default: return launch_t<P, 6>(fp, energy, st);
+    case 0: return launch_t<P, 0>(fp, maps, energy, st);
+    case 3: return launch_t<P, 3>(fp, maps, energy, st);
+    default: return launch_t<P, 6>(fp, maps, energy, st);
     }
 }
 
@@ -670,6 +611,7 @@ int fused_tile_x(int prec) { return prec == PREC_FP32 ? 32 : 64; }
 bool acoustic_fused_supported(const AcParams &prm, int ndim, int prec) {
     if (ndim != 3 || prec == PREC_FP64) return false;
     if (prm.n[0] % fused_tile_x(prec) != 0 || prm.n[1] < 8 || prm.n[2] < 8) return false;
+    if (prm.bc[0] != BC_RIGID) return false;
     return prm.a[0] == nullptr && prm.a[1] == nullptr && prm.a[2] == nullptr;
 }
 
@@ -677,8 +619,67 @@ unsigned acoustic_fused_blocks(const AcParams &prm, int prec, int zchunk) {
     return (prm.n[0] / fused_tile_x(prec)) * ((prm.n[1] + 15) / 16) * ((prm.n[2] + zchunk - 1) / zchunk);
 }
 
-cudaError_t acoustic_fused_step(const AcParams &prm, const void *const in[7], void *const out[7],
-                                void *tp, int prec, int comp, int zchunk, int *err, cudaStream_t st) {
+// ------------------------------------------------------------ tensor maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encoder() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// One 3D map over an array of the grid (x extent n[0], row pitch in elements).
+static bool encode(CUtensorMap *m, const void *ptr, const int n[3], int64_t pitch, int eb, int bx,
+                   int by) {
+    EncodeTiledFn fn = encoder();
+    if (!fn || !ptr) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2]};
+    const cuuint64_t strides[2] = {(cuuint64_t)(pitch * eb), (cuuint64_t)(pitch * n[1] * eb)};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(m, eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 3,
+                          const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+size_t fused_maps_bytes() { return sizeof(FusedMaps); }
+
+// Fill the maps for one input set: in[] = p, vx, vy, vz, tvx, tvy, tvz.
+bool acoustic_fused_encode(void *out_maps, const AcParams &prm, const void *const in[7], const void *tp,
+                           int prec, int comp) {
+    FusedMaps mp;
+    memset(&mp, 0, sizeof mp);
+    const int eb = prec == PREC_FP32 ? 4 : 2;
+    const int vec = 16 / eb, tx = 8 * vec, wide = tx + 2 * vec, ty = 16;
+    bool ok = encode(&mp.p_own, in[0], prm.n, prm.sy, eb, wide, ty) &&
+              encode(&mp.p_halo, in[0], prm.n, prm.sy, eb, tx, 3) &&
+              encode(&mp.vx, in[1], prm.n, prm.sy, eb, wide, ty) &&
+              encode(&mp.vy, in[2], prm.n, prm.sy, eb, tx, ty + 3) &&
+              encode(&mp.vz, in[3], prm.n, prm.sy, eb, tx, ty);
+    if (ok && comp)
+        ok = encode(&mp.tvx, in[4], prm.n, prm.sy, eb, wide, ty) &&
+             encode(&mp.tvy, in[5], prm.n, prm.sy, eb, tx, ty + 3) &&
+             encode(&mp.tvz, in[6], prm.n, prm.sy, eb, tx, ty) && encode(&mp.tp, tp, prm.n, prm.sy, eb, tx, ty);
+    if (ok && prm.b) ok = encode(&mp.b, prm.b, prm.n, prm.sy, eb, tx, ty);
+    if (ok) memcpy(out_maps, &mp, sizeof mp);
+    return ok;
+}
+
+cudaError_t acoustic_fused_step(const AcParams &prm, const void *maps, const void *const in[7],
+                                void *const out[7], void *tp, int prec, int comp, int zchunk, int *err,
+                                cudaStream_t st) {
     FusedParams fp;
     fp.a = prm;
     fp.p_in = in[0]; fp.vx_in = in[1]; fp.vy_in = in[2]; fp.vz_in = in[3];
@@ -688,13 +689,14 @@ cudaError_t acoustic_fused_step(const AcParams &prm, const void *const in[7], vo
     fp.tp = tp;
     fp.zchunk = zchunk;
     fp.err = err;
+    const FusedMaps &mp = *static_cast<const FusedMaps *>(maps);
     const bool energy = prm.energy != 0;
     switch (prec) {
-    case PREC_FP32: return launch_c<F32>(fp, comp, energy, st);
-    case PREC_FP16: return launch_c<F16>(fp, comp, energy, st);
-    case PREC_BF16: return launch_c<BF16>(fp, comp, energy, st);
-    case PREC_FP16_F32ARITH: return launch_c<F16W>(fp, comp ? 3 : 0, energy, st);
-    case PREC_BF16_F32ARITH: return launch_c<BF16W>(fp, comp ? 3 : 0, energy, st);
+    case PREC_FP32: return launch_c<F32>(fp, mp, comp, energy, st);
+    case PREC_FP16: return launch_c<F16>(fp, mp, comp, energy, st);
+    case PREC_BF16: return launch_c<BF16>(fp, mp, comp, energy, st);
+    case PREC_FP16_F32ARITH: return launch_c<F16W>(fp, mp, comp ? 3 : 0, energy, st);
+    case PREC_BF16_F32ARITH: return launch_c<BF16W>(fp, mp, comp ? 3 : 0, energy, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -167,8 +167,11 @@ struct wave_ctx {
     bool zchunk_set = false;
     bool use_stream = false;
     bool use_fused = false;
-    // second set of p, vx, vy, vz and t_vx, t_vy, t_vz for the one-pass step
+    // second set of p, vx, vy, vz and t_vx, t_vy, t_vz for the one-pass step,
+    // and the tensor maps of both sets (fset: the set the fields point to now)
     DevBuf alt_f[4], alt_t[4];
+    struct alignas(64) MapBlob { unsigned char b[2048]; } fmaps[2];
+    int fset = 0;
     double h = 0, dt = 0, P0 = 1.0, Z0 = 1.0;
     cudaStream_t stream = nullptr;
     bool poisoned = false;
@@ -601,10 +604,10 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
         AcParams prm;
         fill_acoustic_params(c, prm);
         c->e_blocks = acoustic_generic_blocks(prm, c->ndim);
-        c->use_fused = kchoice == 3 && acoustic_fused_supported(prm, c->ndim, c->prec);
+        c->use_fused = (kchoice == 0 || kchoice == 3) && acoustic_fused_supported(prm, c->ndim, c->prec);
         c->use_stream = !c->use_fused && kchoice != 1 &&
                         acoustic_stream_supported(prm, c->ndim, c->prec);
-        if (c->use_fused && !c->zchunk_set) c->zchunk = 32;
+        if (c->use_fused && !c->zchunk_set) c->zchunk = 16;
         if (c->use_stream)
             c->e_blocks = std::max(c->e_blocks, acoustic_stream_blocks(prm, c->prec, c->zchunk));
         if (c->use_fused) {
@@ -612,6 +615,15 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
             for (int fi = 0; fi < 4 && !st; fi++) {
                 st = dev_alloc(c, c->alt_f[fi], c->total * eb);
                 if (!st && fi > 0 && compensated) st = dev_alloc(c, c->alt_t[fi], c->total * eb);
+            }
+            if (!st && fused_maps_bytes() > sizeof(c->fmaps[0].b))
+                st = fail(WAVE_ECUDA, "tensor map block too large");
+            for (int set = 0; set < 2 && !st; set++) {
+                DevBuf *F = set == 0 ? c->f : c->alt_f;
+                DevBuf *T = set == 0 ? c->t : c->alt_t;
+                const void *in[7] = {F[0].ptr, F[1].ptr, F[2].ptr, F[3].ptr, T[1].ptr, T[2].ptr, T[3].ptr};
+                if (!acoustic_fused_encode(c->fmaps[set].b, prm, in, c->t[0].ptr, c->prec, compensated))
+                    st = fail(WAVE_ECUDA, "cuTensorMapEncodeTiled failed for the one-pass step");
             }
         }
     } else {
@@ -913,8 +925,9 @@ static wave_status acoustic_steps(wave_ctx *c, int64_t n) {
                             c->alt_t[1].ptr, c->alt_t[2].ptr, c->alt_t[3].ptr};
             int *err = reinterpret_cast<int *>(static_cast<char *>(c->e_misc.ptr) + 16);
             cudaEvent_t m0 = mark(c);
-            cudaError_t e = acoustic_fused_step(prm, in, out, c->t[0].ptr, c->prec, c->comp,
-                                                c->zchunk, err, c->stream);
+            cudaError_t e = acoustic_fused_step(prm, c->fmaps[c->fset].b, in, out, c->t[0].ptr,
+                                                c->prec, c->comp, c->zchunk, err, c->stream);
+            c->fset ^= 1;
             cudaEvent_t m1 = mark(c);
             timed(c, 3, m0, m1);
             for (int fi = 0; fi < 4; fi++) {

@@ -24,13 +24,18 @@ unsigned acoustic_stream_blocks(const AcParams &prm, int prec, int zchunk);
 cudaError_t acoustic_stream_half_step(const AcParams &prm, int prec, int comp, int half_step,
                                       int zchunk, cudaStream_t st);
 
-// One-pass 3D step (fused velocity and pressure half steps) with an
-// asynchronous shared-memory pipeline; reads in[], writes out[] (p, vx, vy, vz,
-// tvx, tvy, tvz), t_p in place. err: device word set to 1 if a bounded wait expires.
+// One-pass 3D step (fused velocity and pressure half steps) with a TMA
+// shared-memory pipeline; reads in[] (p, vx, vy, vz, tvx, tvy, tvz), writes
+// out[], t_p in place. maps: the tensor maps of the input set (from
+// acoustic_fused_encode). err: device word set to 1 if a bounded wait expires.
 bool acoustic_fused_supported(const AcParams &prm, int ndim, int prec);
 unsigned acoustic_fused_blocks(const AcParams &prm, int prec, int zchunk);
-cudaError_t acoustic_fused_step(const AcParams &prm, const void *const in[7], void *const out[7],
-                                void *tp, int prec, int comp, int zchunk, int *err, cudaStream_t st);
+size_t fused_maps_bytes();
+bool acoustic_fused_encode(void *out_maps, const AcParams &prm, const void *const in[7], const void *tp,
+                           int prec, int comp);
+cudaError_t acoustic_fused_step(const AcParams &prm, const void *maps, const void *const in[7],
+                                void *const out[7], void *tp, int prec, int comp, int zchunk, int *err,
+                                cudaStream_t st);
 
 // Receiver sampling: traces[r] = float(field[q[r]]) for r < nrec.
 cudaError_t sample_receivers(const void *field, int elem_bytes, int is_bf16, const int64_t *q,

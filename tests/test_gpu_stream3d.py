@@ -213,8 +213,14 @@ def test_fused_ragged_y_z_rigid_many_chunks(prec, comp):
 
 @pytest.mark.parametrize("prec,comp", [("fp16", 3), ("bf16", 6), ("fp32", 0), ("fp16_f32arith", 3)])
 def test_fused_periodic_mixed_source(prec, comp):
+    """Periodic y and z, rigid x (the one-pass step reads rigid x images)."""
     nx = 192 if prec != "fp32" else 96
-    _uniform_rho_run((nx, 20, 17), (P, P, P), prec, comp, 6, zchunk=4, src=True)
+    _uniform_rho_run((nx, 20, 17), (R, P, P), prec, comp, 6, zchunk=4, src=True)
     _uniform_rho_run((nx, 33, 40), (R, P, R), prec, comp, 5, zchunk=32, src=True)
-    _uniform_rho_run((nx, 16, 9), (P, R, P), prec, comp, 9, zchunk=3)
+    _uniform_rho_run((nx, 16, 9), (R, R, P), prec, comp, 9, zchunk=3)
     _uniform_rho_run((64 if prec != "fp32" else 32, 8, 8), (R, R, R), prec, comp, 11, zchunk=8)
+
+
+def test_fused_request_with_periodic_x_falls_back_bit_exact():
+    """kernel=3 with periodic x faces runs the two-kernel step, still bit-exact."""
+    _run((128, 20, 17), (P, P, P), "fp16", 3, 6, zchunk=4, src=True, energy=True, kernel=3)
