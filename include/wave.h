@@ -276,6 +276,34 @@ wave_status wave_get_timing(wave_ctx *ctx, int32_t kind, int64_t *launches, doub
  * returns WAVE_ENOTIMPL. */
 wave_status wave_adjoint_step(wave_ctx *ctx, int64_t n, const float *residual_traces);
 
+/*
+ * Batched stepping of many independent 2D acoustic problems ("shots"), for
+ * example the sources of a seismic survey, each with its own grid size,
+ * medium and source. Not in the paper (it runs one problem at a time).
+ *
+ * wave_batch_create -- group nctx existing contexts. All must be 2D acoustic,
+ * share the precision, the compensation and the CUDA stream, and have no
+ * receivers set. The contexts stay valid and owned by the caller; they must
+ * outlive the batch. Errors: EINVAL (mixed contexts, nctx outside 1..1024),
+ * ENOMEM, ECUDA.
+ * wave_batch_step -- advance every context of the batch n steps: each step is
+ * two launches over one work list of (shot, tile) items, with each shot's
+ * arithmetic identical to wave_step on that context alone (the same bits).
+ * The first call with enough steps times the candidate tile shapes and grid
+ * sizes on its first steps (real steps of the problems) and keeps the
+ * fastest; runs of steps are then replayed from a captured CUDA graph when the
+ * stream is not the legacy default stream. The energy of the last step is
+ * available per context through wave_energy. Asynchronous.
+ * wave_batch_info -- the chosen tile shape (bx, by), grid size and the number
+ * of steps per graph replay (0 before tuning / when graphs are not used).
+ */
+typedef struct wave_batch wave_batch;
+wave_status wave_batch_create(int32_t nctx, wave_ctx *const *ctxs, wave_batch **out);
+wave_status wave_batch_step(wave_batch *batch, int64_t n);
+wave_status wave_batch_info(wave_batch *batch, int32_t *bx, int32_t *by, int32_t *grid,
+                            int32_t *graph_steps);
+void wave_batch_destroy(wave_batch *batch);
+
 /* wave_energy_acoustic_static -- the acoustic discrete energy (the quantity
  * wave_energy reports) computed from device arrays the caller already owns,
  * without allocating any device memory. The paper has no counterpart: this is

@@ -11,103 +11,27 @@
 // or compensated update.
 #include <cuda_runtime.h>
 #include "acoustic_common.cuh"
+#include "acoustic_point.cuh"
 #include "wave_kernels.h"
 
 namespace wave {
 
-template <class P>
-__device__ __forceinline__ typename P::A read_signed(const typename P::S *f, int64_t q, int sign) {
-    if (sign == 0) return P::zero();
-    typename P::A v = P::ld(f[q]);
-    return sign > 0 ? v : P::neg(v);
-}
-
 template <class P, int COMP, int NDIM>
 __global__ void __launch_bounds__(128) kv_generic(AcParams prm) {
-    using S = typename P::S;
-    using A = typename P::A;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = (NDIM == 3) ? blockIdx.z : 0;
     if (i >= prm.n[0] || j >= prm.n[1]) return;
-    const int idx[3] = {i, j, k};
-    const int64_t str[3] = {1, prm.sy, prm.sz};
-    const int64_t q = i + prm.sy * j + prm.sz * k;
-    const S *p = static_cast<const S *>(prm.p);
-#pragma unroll
-    for (int c = 0; c < NDIM; c++) {
-        // v_c at m + 1/2 along axis c reads p at nodes m-1, m, m+1, m+2
-        const int m = idx[c];
-        const int64_t base = q - str[c] * m;
-        A f[4];
-#pragma unroll
-        for (int t = 0; t < 4; t++) {
-            int mm;
-            int sg = img_node(m - 1 + t, prm.n[c], prm.bc[c], mm);
-            f[t] = read_signed<P>(p, base + str[c] * mm, sg);
-        }
-        A D = stencil<P>(f[0], f[1], f[2], f[3]);
-        A inc = P::mul(coef<P>(prm.a[c], prm.a_uni[c], q), D);
-        S *v = static_cast<S *>(prm.v[c]);
-        S *tv = static_cast<S *>(prm.tv[c]);
-        S V = v[q];
-        S T = COMP ? tv[q] : S(0);
-        update<P, COMP>(V, T, inc);
-        v[q] = V;
-        if (COMP) tv[q] = T;
-    }
+    kv_point<P, COMP, NDIM>(prm, i, j, k);
 }
 
 template <class P, int COMP, int NDIM>
 __global__ void __launch_bounds__(128) kp_generic(AcParams prm) {
-    using S = typename P::S;
-    using A = typename P::A;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = (NDIM == 3) ? blockIdx.z : 0;
-    const bool inside = i < prm.n[0] && j < prm.n[1];
     double e = 0.0;
-    if (inside) {
-        const int idx[3] = {i, j, k};
-        const int64_t str[3] = {1, prm.sy, prm.sz};
-        const int64_t q = i + prm.sy * j + prm.sz * k;
-        A R = P::zero();
-#pragma unroll
-        for (int c = 0; c < NDIM; c++) {
-            // p at node m along c reads v_c at m-2, m-1, m, m+1 (+1/2)
-            const int m = idx[c];
-            const int64_t base = q - str[c] * m;
-            const S *v = static_cast<const S *>(prm.v[c]);
-            A f[4];
-#pragma unroll
-            for (int t = 0; t < 4; t++) {
-                int mm;
-                img_half(m - 2 + t, prm.n[c], prm.bc[c], mm);
-                f[t] = P::ld(v[base + str[c] * mm]);
-            }
-            A D = stencil<P>(f[0], f[1], f[2], f[3]);
-            R = (c == 0) ? D : P::add(R, D);
-        }
-        if (q == prm.src_q && prm.step < prm.src_nt)
-            R = P::add(R, static_cast<const A *>(prm.src)[prm.step]);
-        A inc = P::mul(coef<P>(prm.b, prm.b_uni, q), R);
-        S *p = static_cast<S *>(prm.p);
-        S *tp = static_cast<S *>(prm.tp);
-        const S p_old = p[q];
-        S V = p_old;
-        S T = COMP ? tp[q] : S(0);
-        update<P, COMP>(V, T, inc);
-        p[q] = V;
-        if (COMP) tp[q] = T;
-        if (prm.energy) {
-            e = (double)e_term(P::to_f32(p_old), P::to_f32(V), coef_f32<P>(prm.b, prm.b_uni, q));
-#pragma unroll
-            for (int c = 0; c < NDIM; c++) {
-                float vc = P::to_f32(static_cast<const S *>(prm.v[c])[q]);
-                e += (double)e_term(vc, vc, coef_f32<P>(prm.a[c], prm.a_uni[c], q));
-            }
-        }
-    }
+    if (i < prm.n[0] && j < prm.n[1]) e = kp_point<P, COMP, NDIM>(prm, i, j, k, prm.step, prm.energy != 0);
     if (prm.energy) energy_reduce(e, prm);
 }
 

@@ -13,6 +13,7 @@
 
 #include "../../include/wave.h"
 #include "acoustic_common.cuh"
+#include "batch.h"
 #include "elastic.h"
 #include "wave_kernels.h"
 
@@ -1160,4 +1161,217 @@ extern "C" wave_status wave_adjoint_step(wave_ctx *c, int64_t n, const float *re
     (void)n;
     (void)residual;
     return fail(WAVE_ENOTIMPL, "adjoint time stepping is not implemented in this build");
+}
+
+// ------------------------------------------------------------------ batches
+struct wave_batch {
+    std::vector<wave_ctx *> ctx;
+    cudaStream_t stream = nullptr;
+    int prec = 0, comp = 0;
+    BatchShot *d_shots = nullptr;
+    int *d_item0 = nullptr;
+    double *d_part = nullptr;
+    std::vector<BatchShot> h_shots;
+    int bx = 32, by = 8, grid = 0, nitems = 0, sms = 1;
+    bool tuned = false;
+    cudaGraphExec_t gexec = nullptr;
+    int gsteps = 0;
+};
+
+static const int kTiles[][2] = {{32, 8}, {64, 4}, {128, 2}, {32, 4}, {64, 2}, {256, 1}};
+static const int kGridMul[] = {2, 4, 8, 16};
+
+// work list of the tile shape (bx, by): first item of each shot
+static int batch_items(wave_batch *b, int bx, int by, std::vector<int> &item0) {
+    item0.assign(b->ctx.size() + 1, 0);
+    for (size_t s = 0; s < b->ctx.size(); s++) {
+        const int64_t nx = b->ctx[s]->n[0], ny = b->ctx[s]->n[1];
+        item0[s + 1] = item0[s] + (int)(((nx + bx - 1) / bx) * ((ny + by - 1) / by));
+    }
+    return item0.back();
+}
+
+static cudaError_t batch_set_shape(wave_batch *b, int bx, int by, int grid) {
+    std::vector<int> item0;
+    b->nitems = batch_items(b, bx, by, item0);
+    b->bx = bx;
+    b->by = by;
+    b->grid = grid;
+    cudaError_t e = cudaMemcpyAsync(b->d_item0, item0.data(), item0.size() * sizeof(int),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e;
+}
+
+static BatchLaunch batch_launch(wave_batch *b) {
+    BatchLaunch L;
+    L.shots = b->d_shots;
+    L.item0 = b->d_item0;
+    L.item_part = b->d_part;
+    L.nshots = (int)b->ctx.size();
+    L.nitems = b->nitems;
+    L.bx = b->bx;
+    L.by = b->by;
+    L.grid = b->grid;
+    return L;
+}
+
+extern "C" void wave_batch_destroy(wave_batch *b) {
+    if (!b) return;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    cudaStreamSynchronize(b->stream);
+    if (b->d_shots) cudaFree(b->d_shots);
+    if (b->d_item0) cudaFree(b->d_item0);
+    if (b->d_part) cudaFree(b->d_part);
+    delete b;
+}
+
+extern "C" wave_status wave_batch_create(int32_t nctx, wave_ctx *const *ctxs, wave_batch **out) {
+    if (!out || !ctxs) return fail(WAVE_EINVAL, "wave_batch_create: NULL argument");
+    *out = nullptr;
+    if (nctx < 1 || nctx > batch_max_shots()) return fail(WAVE_EINVAL, "nctx must be 1..%d", batch_max_shots());
+    for (int i = 0; i < nctx; i++) {
+        const wave_ctx *c = ctxs[i];
+        if (!c) return fail(WAVE_EINVAL, "context %d is NULL", i);
+        if (c->poisoned) return fail(WAVE_ESTATE, "context %d poisoned", i);
+        if (c->kind != WAVE_ACOUSTIC || c->ndim != 2)
+            return fail(WAVE_EINVAL, "context %d: batches take 2D acoustic contexts", i);
+        if (c->prec != ctxs[0]->prec || c->comp != ctxs[0]->comp || c->stream != ctxs[0]->stream)
+            return fail(WAVE_EINVAL, "context %d: precision, compensation and stream must match", i);
+        if (c->nrec) return fail(WAVE_EINVAL, "context %d has receivers (not supported in batches)", i);
+        if (c->e_trace) return fail(WAVE_EINVAL, "context %d has an energy trace (not supported in batches)", i);
+        for (int j = 0; j < i; j++)
+            if (ctxs[j] == c) return fail(WAVE_EINVAL, "context %d appears twice", i);
+    }
+    wave_batch *b = new (std::nothrow) wave_batch();
+    if (!b) return fail(WAVE_ENOMEM, "host allocation failed");
+    b->ctx.assign(ctxs, ctxs + nctx);
+    b->stream = ctxs[0]->stream;
+    b->prec = ctxs[0]->prec;
+    b->comp = ctxs[0]->comp;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    int max_items = 0;
+    std::vector<int> tmp;
+    for (auto &t : kTiles) max_items = std::max(max_items, batch_items(b, t[0], t[1], tmp));
+    cudaError_t e = cudaMalloc(&b->d_shots, sizeof(BatchShot) * nctx);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_item0, sizeof(int) * (nctx + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_part, sizeof(double) * (size_t)max_items);
+    if (e == cudaSuccess) e = batch_set_shape(b, 32, 8, 8 * b->sms);
+    if (e != cudaSuccess) {
+        wave_batch_destroy(b);
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? WAVE_ENOMEM : WAVE_ECUDA, "wave_batch_create: %s",
+                    cudaGetErrorString(e));
+    }
+    *out = b;
+    return WAVE_OK;
+}
+
+// upload every shot's parameters and step counter
+static cudaError_t batch_refresh(wave_batch *b) {
+    b->h_shots.resize(b->ctx.size());
+    for (size_t s = 0; s < b->ctx.size(); s++) {
+        fill_acoustic_params(b->ctx[s], b->h_shots[s].prm);
+        b->h_shots[s].step = b->ctx[s]->step;
+    }
+    return cudaMemcpyAsync(b->d_shots, b->h_shots.data(), sizeof(BatchShot) * b->ctx.size(),
+                           cudaMemcpyHostToDevice, b->stream);
+}
+
+static wave_status batch_fail(wave_batch *b, cudaError_t e, const char *what) {
+    for (auto *c : b->ctx) c->poisoned = true;
+    cudaGetLastError();
+    return fail(WAVE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+extern "C" wave_status wave_batch_step(wave_batch *b, int64_t n) {
+    if (!b) return fail(WAVE_EINVAL, "wave_batch_step: NULL batch");
+    if (n < 0) return fail(WAVE_EINVAL, "negative step count");
+    for (auto *c : b->ctx)
+        if (c->poisoned) return fail(WAVE_ESTATE, "a context of the batch is poisoned");
+    if (n == 0) return WAVE_OK;
+    cudaError_t e = batch_refresh(b);
+    if (e != cudaSuccess) return batch_fail(b, e, "batch upload");
+    int64_t left = n;
+    const int ncand = (int)(sizeof(kTiles) / sizeof(kTiles[0])) * (int)(sizeof(kGridMul) / sizeof(int));
+    if (!b->tuned && left - 1 >= ncand) {
+        // autotune on real steps: every candidate computes the same bits
+        float best = 1e30f;
+        int bi = 0, bg = 0;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (int ti = 0; ti < (int)(sizeof(kTiles) / sizeof(kTiles[0])); ti++) {
+            for (int gm : kGridMul) {
+                e = batch_set_shape(b, kTiles[ti][0], kTiles[ti][1], gm * b->sms);
+                if (e != cudaSuccess) break;
+                cudaEventRecord(e0, b->stream);
+                e = batch_step(batch_launch(b), b->prec, b->comp, false, b->stream);
+                cudaEventRecord(e1, b->stream);
+                if (e != cudaSuccess) break;
+                e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; bi = ti; bg = gm; }
+                left--;
+            }
+            if (e != cudaSuccess) break;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (e != cudaSuccess) return batch_fail(b, e, "batch autotune");
+        e = batch_set_shape(b, kTiles[bi][0], kTiles[bi][1], bg * b->sms);
+        if (e != cudaSuccess) return batch_fail(b, e, "batch shape");
+        b->tuned = true;
+    }
+    const BatchLaunch L = batch_launch(b);
+    int64_t plain = left - 1;  // steps without energy; the last step reduces it
+    const int G = 32;
+    if (b->tuned && b->stream != nullptr && plain >= G) {
+        if (!b->gexec) {
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                for (int s = 0; s < G && e == cudaSuccess; s++) e = batch_step(L, b->prec, b->comp, false, b->stream);
+                cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+                if (e == cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) {  // no graph: fall back to plain launches
+                cudaGetLastError();
+                b->gexec = nullptr;
+            } else {
+                b->gsteps = G;
+            }
+        }
+        while (b->gexec && plain >= G) {
+            e = cudaGraphLaunch(b->gexec, b->stream);
+            if (e != cudaSuccess) return batch_fail(b, e, "graph launch");
+            plain -= G;
+        }
+    }
+    for (int64_t s = 0; s < plain; s++) {
+        e = batch_step(L, b->prec, b->comp, false, b->stream);
+        if (e != cudaSuccess) return batch_fail(b, e, "batch launch");
+    }
+    e = batch_step(L, b->prec, b->comp, true, b->stream);
+    if (e != cudaSuccess) return batch_fail(b, e, "batch launch");
+    for (auto *c : b->ctx) {
+        c->step += n;
+        c->have_energy = true;
+    }
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_batch_info(wave_batch *b, int32_t *bx, int32_t *by, int32_t *grid,
+                                       int32_t *graph_steps) {
+    if (!b) return fail(WAVE_EINVAL, "NULL batch");
+    if (bx) *bx = b->bx;
+    if (by) *by = b->by;
+    if (grid) *grid = b->grid;
+    if (graph_steps) *graph_steps = b->gexec ? b->gsteps : 0;
+    return WAVE_OK;
 }

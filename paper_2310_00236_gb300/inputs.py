@@ -123,6 +123,26 @@ def acoustic_3d_random(n: int = 512, steps: int = 1000, cfl: float = 0.4, h: flo
                 p0=gaussian(shape, h, ic_sigma_cells * h), P0=1.0)
 
 
+def shot_sides(nshots: int = 64, seed: int = 1, lo: int = 256, hi: int = 2048) -> np.ndarray:
+    """Grid sides of a batch of 2D shots: uniform integers in [lo, hi] from
+    numpy's PCG64 with the given seed."""
+    return np.random.default_rng(seed).integers(lo, hi + 1, nshots)
+
+
+def acoustic_2d_shot(i: int, side: int, steps: int = 3000, h: float = 10.0, cfl: float = 0.4,
+                     f0: float = 10.0, rho: float = 1000.0, vmin: float = 1500.0,
+                     vmax: float = 4500.0):
+    """Shot i of a batch: side x side cells, spacing h, its own smooth random
+    velocity (seed 100 + i, filter width side/32 cells, rescaled to
+    [vmin, vmax]), constant density, rigid walls, a Ricker f0 pressure source
+    at node (side/2, 8), dt = cfl h / vmax (the same for every shot)."""
+    c = smooth_random_field((side, side), 100 + i, side / 32.0, vmin, vmax)
+    dt = cfl * h / vmax
+    return dict(ndim=2, shape=(side, side), h=h, dt=dt, steps=steps,
+                rho=np.full(c.shape, rho), c=c, src_idx=[side // 2, 8],
+                wavelet=ricker_table(steps, dt, f0), P0=1e5, z0=rho * vmax)
+
+
 def elastic_2d_layered(n: int = 1024, steps: int = 4000, h: float = 3.0, f0: float = 15.0,
                        cutoff: float = 0.1):
     """2D isotropic elastic, n x n cells, spacing h: three horizontal layers

@@ -34,7 +34,8 @@ EXPORTS = ["wave_set_allocator", "wave_create", "wave_set_initial", "wave_set_so
            "wave_get_field", "wave_get_raw", "wave_set_raw", "wave_get_coefficient",
            "wave_get_state", "wave_set_state", "wave_sync", "wave_steps_done",
            "wave_adjoint_step", "wave_destroy", "wave_last_error", "wave_build_info",
-           "wave_set_timing", "wave_get_timing", "wave_energy_acoustic_static"]
+           "wave_set_timing", "wave_get_timing", "wave_energy_acoustic_static",
+           "wave_batch_create", "wave_batch_step", "wave_batch_info", "wave_batch_destroy"]
 
 
 class WaveError(RuntimeError):
@@ -96,6 +97,10 @@ def lib() -> C.CDLL:
         "wave_get_timing": [vp, i32, C.POINTER(C.c_int64), dp],
         "wave_energy_acoustic_static": [i32, C.POINTER(C.c_int64), C.c_int, vp, vp,
                                         C.POINTER(vp), C.POINTER(vp), vp, C.c_double, vp, vp],
+        "wave_batch_create": [i32, C.POINTER(vp), C.POINTER(vp)],
+        "wave_batch_step": [vp, i64],
+        "wave_batch_info": [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                            C.POINTER(C.c_int32)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -103,6 +108,8 @@ def lib() -> C.CDLL:
         fn.restype = C.c_int
     L.wave_destroy.argtypes = [vp]
     L.wave_destroy.restype = None
+    L.wave_batch_destroy.argtypes = [vp]
+    L.wave_batch_destroy.restype = None
     L.wave_last_error.restype = C.c_char_p
     L.wave_build_info.restype = C.c_char_p
     _lib = L
@@ -314,6 +321,38 @@ def wave_energy_acoustic_static(ndim, n, precision, p_old, p_new, v, a, b, facto
         ndim, nn, int(precision), C.c_void_p(p_old.data_ptr()), C.c_void_p(p_new.data_ptr()),
         vv, aa, C.c_void_p(b.data_ptr()), float(factor), C.c_void_p(device_out.data_ptr()),
         _stream_handle(stream)))
+
+
+class Batch:
+    """Handle of wave_batch_create: the opaque pointer and the contexts."""
+
+    def __init__(self, ptr, ctxs):
+        self.ptr = ptr
+        self.ctxs = list(ctxs)
+
+
+def wave_batch_create(ctxs) -> Batch:
+    arr = (C.c_void_p * len(ctxs))(*[c.ptr for c in ctxs])
+    out = C.c_void_p()
+    _check(lib().wave_batch_create(len(ctxs), arr, C.byref(out)))
+    return Batch(out, ctxs)
+
+
+def wave_batch_step(batch: Batch, n: int):
+    _check(lib().wave_batch_step(batch.ptr, int(n)))
+
+
+def wave_batch_info(batch: Batch):
+    """(bx, by, grid, graph_steps) of the tuned launch configuration."""
+    v = [C.c_int32() for _ in range(4)]
+    _check(lib().wave_batch_info(batch.ptr, *[C.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def wave_batch_destroy(batch: Batch):
+    if batch.ptr:
+        lib().wave_batch_destroy(batch.ptr)
+        batch.ptr = None
 
 
 # ---------------------------------------------------------------- allocator

@@ -36,7 +36,7 @@ def gpu_bits(raw: np.ndarray) -> np.ndarray:
 
 
 def acoustic_pair(shape, bc, prec, comp, h, dt, rho, c, p0=None, v0=None, P0=1.0, src=None,
-                  rec=None, kernel=0, zchunk=0):
+                  rec=None, kernel=0, zchunk=0, stream=None):
     """Create matching GPU context and oracle state. src = (idx, wavelet);
     rec = (field, list of idx). Returns (ctx, oracle_state)."""
     code, sfmt, afmt = PREC[prec]
@@ -46,7 +46,7 @@ def acoustic_pair(shape, bc, prec, comp, h, dt, rho, c, p0=None, v0=None, P0=1.0
         b = bc[ax] if ax < nd else W.WAVE_BC_PERIODIC
         bcw += [b, b]
     ctx = W.wave_create(shape, h, rho, c, dt, code, comp, bc=bcw, field_scale=P0, kernel=kernel,
-                        zchunk=zchunk)
+                        zchunk=zchunk, stream=stream)
     st = O.acoustic_setup(shape, bc, h, dt, rho, c, sfmt, comp, P0=P0, arith_fmt=afmt,
                           p0=p0, v0=v0)
     if p0 is not None:
