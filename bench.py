@@ -247,7 +247,7 @@ def run_batched(W, steps: int, warmup: int, nshots: int = 64):
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)
         e1 = [W.wave_energy(c) for c in ctxs]
-        bx, by, grid, gsteps = W.wave_batch_info(batch)
+        info = W.wave_batch_info(batch)
     finally:
         if batch is not None:
             W.wave_batch_destroy(batch)
@@ -258,7 +258,7 @@ def run_batched(W, steps: int, warmup: int, nshots: int = 64):
     launches_per_step = 3  # velocity and pressure half steps, step-counter advance
     return {"workload": "2d_acoustic_64_shots_sides_256_2048", "shots": int(nshots), "cells": cells,
             "precision": "fp16", "compensation": "sum_3op", "value": gpts, "unit": UNIT,
-            "ms_per_step": ms / steps, "tile": [bx, by], "grid": grid, "graph_steps": gsteps,
+            "ms_per_step": ms / steps, "launch": info,
             "hbm_gbs_algorithmic": BYTES_2D * gpts, "bytes_per_point": BYTES_2D,
             "gpu_launches": launches_per_step * steps + 1,
             "finite": bool(np.all(np.isfinite(e1))), "energy_min": float(min(e1))}

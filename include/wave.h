@@ -294,14 +294,15 @@ wave_status wave_adjoint_step(wave_ctx *ctx, int64_t n, const float *residual_tr
  * fastest; runs of steps are then replayed from a captured CUDA graph when the
  * stream is not the legacy default stream. The energy of the last step is
  * available per context through wave_energy. Asynchronous.
- * wave_batch_info -- the chosen tile shape (bx, by), grid size and the number
- * of steps per graph replay (0 before tuning / when graphs are not used).
+ * wave_batch_info -- the launch configuration in use, written to
+ * info[0 .. min(ninfo, 7) - 1]: kind (0 one thread per point, 1 one warp per
+ * row strip), tile width in points, tile height in rows, threads per block,
+ * blocks, steps per graph replay (0 when no graph is in use), tuned (0/1).
  */
 typedef struct wave_batch wave_batch;
 wave_status wave_batch_create(int32_t nctx, wave_ctx *const *ctxs, wave_batch **out);
 wave_status wave_batch_step(wave_batch *batch, int64_t n);
-wave_status wave_batch_info(wave_batch *batch, int32_t *bx, int32_t *by, int32_t *grid,
-                            int32_t *graph_steps);
+wave_status wave_batch_info(wave_batch *batch, int32_t *info, int32_t ninfo);
 void wave_batch_destroy(wave_batch *batch);
 
 /* wave_energy_acoustic_static -- the acoustic discrete energy (the quantity

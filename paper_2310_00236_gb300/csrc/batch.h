@@ -12,14 +12,25 @@ struct BatchShot {
     int64_t step;   // global step index of the shot (source time index)
 };
 
+// Two kinds of work item:
+//   BATCH_POINTS: a bx x by tile of points, one thread per point (one block per item);
+//   BATCH_STRIPS: a strip of 32 vectors (32 * vec_width x points) by yc rows,
+//                 one warp per item, streaming down the rows.
+enum { BATCH_POINTS = 0, BATCH_STRIPS = 1 };
+
 struct BatchLaunch {
     BatchShot *shots;   // device array [nshots]
     const int *item0;   // device array [nshots + 1]: first work item of each shot
     double *item_part;  // device array [nitems]: per-item energy partials
     int nshots, nitems;
-    int bx, by;         // tile (= thread block) shape, bx * by threads
-    int grid;           // persistent grid size
+    int kind;           // BATCH_POINTS or BATCH_STRIPS
+    int bx, by;         // BATCH_POINTS: tile (= thread block) shape, bx * by threads
+    int yc, wpb;        // BATCH_STRIPS: rows per item, warps per block
+    int grid;           // persistent grid size (blocks)
 };
+
+// Work items of one shot of nx x ny points under a launch shape.
+int64_t batch_items_of(int kind, int bx, int by, int yc, int prec, int64_t nx, int64_t ny);
 
 // One batched step (velocity and pressure half steps of every shot, optional
 // per-shot energy, step counters advanced).

@@ -10,10 +10,17 @@
 // is advanced by a small kernel after each step, so a sequence of steps can be
 // captured once into a CUDA graph and replayed. Energies are reduced per item
 // and then per shot in item order (deterministic).
+//
+// Two item kinds: tiles of points with one thread per point (the arithmetic of
+// acoustic_point.cuh), and row strips with one warp per strip, 16-byte vectors
+// of 8 (binary16 / bfloat16) or 4 (binary32) x points per lane, x neighbours
+// by warp shuffle and a register queue down the rows for the y stencil, so
+// each array is read about once. Both give the same bits.
 #include <cuda_runtime.h>
 
 #include "acoustic_point.cuh"
 #include "batch.h"
+#include "vec_policy.cuh"
 #include "wave_kernels.h"
 
 namespace wave {
@@ -75,6 +82,292 @@ __global__ void __launch_bounds__(256) batch_half_step(BatchShot *shots, const i
     }
 }
 
+// ------------------------------------------------------------------------
+// Row-strip kernels (one warp per item)
+// ------------------------------------------------------------------------
+
+// Row my of a field at x (a whole vector), with the y boundary image; zero
+// for lanes past the grid. node_y: the field sits on nodes along y (odd
+// image for the p = 0 walls) or on half points (even image).
+template <class V>
+__device__ __forceinline__ typename V::Raw row_vec(const void *f, const AcParams &prm, int x, int my,
+                                                   bool node_y, bool active) {
+    int jy;
+    const int sg = node_y ? img_node(my, prm.n[1], prm.bc[1], jy) : img_half(my, prm.n[1], prm.bc[1], jy);
+    if (!active || sg == 0 || jy < 0 || jy >= prm.n[1]) return V::zero();
+    const typename V::Raw r = *reinterpret_cast<const typename V::Raw *>(
+        static_cast<const char *>(f) + (x + prm.sy * (int64_t)jy) * sizeof(typename V::RS));
+    return sg < 0 ? V::rneg(r) : r;
+}
+
+// One value of row j at x index mx, with the x boundary image.
+template <class V>
+__device__ __forceinline__ typename V::RS x_val(const void *f, const AcParams &prm, int mx, int j, bool node_x) {
+    int ix;
+    const int sg = node_x ? img_node(mx, prm.n[0], prm.bc[0], ix) : img_half(mx, prm.n[0], prm.bc[0], ix);
+    if (sg == 0 || ix < 0 || ix >= prm.n[0]) return typename V::RS(0);
+    const typename V::RS v = static_cast<const typename V::RS *>(f)[ix + prm.sy * (int64_t)j];
+    return sg < 0 ? V::rneg_s(v) : v;
+}
+
+template <class RS>
+__device__ __forceinline__ RS shfl_rs(RS v, int delta, bool up) {
+    uint32_t u;
+    if (sizeof(RS) == 2) u = (uint32_t)(*reinterpret_cast<const uint16_t *>(&v));
+    else u = *reinterpret_cast<const uint32_t *>(&v);
+    u = up ? __shfl_up_sync(0xffffffffu, u, delta) : __shfl_down_sync(0xffffffffu, u, delta);
+    RS r;
+    if (sizeof(RS) == 2) *reinterpret_cast<uint16_t *>(&r) = (uint16_t)u;
+    else *reinterpret_cast<uint32_t *>(&r) = u;
+    return r;
+}
+
+// Element e of a raw vector replaced (bit moves only).
+template <class RS, class Raw>
+__device__ __forceinline__ void raw_set(Raw &r, int e, RS s);
+template <>
+__device__ __forceinline__ void raw_set<uint16_t, uint4>(uint4 &r, int e, uint16_t s) {
+    uint32_t *w = (e >> 1) == 0 ? &r.x : (e >> 1) == 1 ? &r.y : (e >> 1) == 2 ? &r.z : &r.w;
+    *w = (e & 1) ? ((*w & 0xFFFFu) | ((uint32_t)s << 16)) : ((*w & 0xFFFF0000u) | s);
+}
+template <>
+__device__ __forceinline__ void raw_set<float, float4>(float4 &r, int e, float s) {
+    if (e == 0) r.x = s; else if (e == 1) r.y = s; else if (e == 2) r.z = s; else r.w = s;
+}
+
+template <class V>
+__device__ __forceinline__ typename V::AV coef_v(const void *arr, uint32_t uni, int64_t q) {
+    if (arr) return V::ld(*reinterpret_cast<const typename V::Raw *>(
+                 static_cast<const char *>(arr) + q * sizeof(typename V::RS)));
+    typename V::RS s;
+    from_bits(uni, s);
+    return V::splat(V::lds(s));
+}
+
+// Store the first nvalid elements of a vector (all of it when nvalid == N).
+template <class V>
+__device__ __forceinline__ void store_vec(void *f, int64_t q, const typename V::Raw &r, int nvalid) {
+    if (nvalid >= V::N) {
+        at<V>(f, q) = r;
+    } else {
+        typename V::RS *s = static_cast<typename V::RS *>(f) + q;
+#pragma unroll
+        for (int e = 0; e < V::N; e++)
+            if (e < nvalid) s[e] = V::get(r, e);
+    }
+}
+
+// Work item -> (shot, strip origin x0, first row y0, end row y1).
+struct StripItem {
+    int s, x0, y0, y1;
+};
+template <int N>
+__device__ __forceinline__ StripItem strip_of(const int *s_item0, int nshots, int item, const BatchShot *shots,
+                                              int yc) {
+    StripItem it;
+    it.s = shot_of(s_item0, nshots, item);
+    const int nx = shots[it.s].prm.n[0], ny = shots[it.s].prm.n[1];
+    const int nstrips = (nx + 32 * N - 1) / (32 * N);
+    const int local = item - s_item0[it.s];
+    it.x0 = (local % nstrips) * (32 * N);
+    it.y0 = (local / nstrips) * yc;
+    it.y1 = min(it.y0 + yc, ny);
+    return it;
+}
+
+// Velocity half step of one strip: v_x += a_x Dx(p), v_y += a_y Dy(p), row by row.
+template <class P, int COMP>
+__global__ void __launch_bounds__(256) batch_kv_strip(const BatchShot *__restrict__ shots, const int *item0,
+                                                      int nshots, int nitems, int yc) {
+    using V = typename VecOf<P>::T;
+    using Raw = typename V::Raw;
+    using AV = typename V::AV;
+    using RS = typename V::RS;
+    constexpr int N = V::N;
+    __shared__ int s_item0[kMaxShots + 1];
+    for (int t = threadIdx.x; t <= nshots; t += blockDim.x) s_item0[t] = item0[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < nitems; item += gridDim.x * wpb) {
+        const StripItem it = strip_of<N>(s_item0, nshots, item, shots, yc);
+        const AcParams prm = shots[it.s].prm;
+        const int nx = prm.n[0];
+        const int x = it.x0 + lane * N;
+        const bool active = x < nx;
+        const int nvalid = active ? min(N, nx - x) : 0;
+        const bool left_edge = active && lane == 0;
+        const bool right_edge = active && (lane == 31 || x + N >= nx);
+        // row queue of the own p vector: rows j-1, j, j+1 (j+2 loaded in the loop)
+        Raw q0 = row_vec<V>(prm.p, prm, x, it.y0 - 1, true, active);
+        Raw q1 = row_vec<V>(prm.p, prm, x, it.y0, true, active);
+        Raw q2 = row_vec<V>(prm.p, prm, x, it.y0 + 1, true, active);
+        for (int j = it.y0; j < it.y1; j++) {
+            const Raw q3 = row_vec<V>(prm.p, prm, x, j + 2, true, active);
+            const int64_t q = x + prm.sy * (int64_t)j;
+            Raw vx = V::zero(), vy = V::zero(), tx = V::zero(), ty = V::zero();
+            if (active) {
+                vx = at<V>(prm.v[0], q);
+                vy = at<V>(prm.v[1], q);
+                if (COMP) {
+                    tx = at<V>(prm.tv[0], q);
+                    ty = at<V>(prm.tv[1], q);
+                }
+            }
+            // x neighbours p[x-1], p[x+N], p[x+N+1]; at strip and grid edges
+            // from memory with the x image, and the own vector's elements past
+            // the grid replaced by their images
+            Raw own = q1;
+            RS l0 = RS(0), r0 = RS(0), r1 = RS(0);
+            if (left_edge) l0 = x_val<V>(prm.p, prm, x - 1, j, true);
+            if (right_edge) {
+                r0 = x_val<V>(prm.p, prm, x + N, j, true);
+                r1 = x_val<V>(prm.p, prm, x + N + 1, j, true);
+#pragma unroll
+                for (int e = 1; e < N; e++)
+                    if (e >= nvalid) raw_set<RS, Raw>(own, e, x_val<V>(prm.p, prm, x + e, j, true));
+            }
+            // (from the fixed-up vector: the lane left of a partial vector
+            // reads its element 1, which may lie past the grid)
+            const RS sl0 = shfl_rs(V::get(own, N - 1), 1, true);
+            const RS sr0 = shfl_rs(V::get(own, 0), 1, false);
+            const RS sr1 = shfl_rs(V::get(own, 1), 1, false);
+            if (!left_edge) l0 = sl0;
+            if (!right_edge) {
+                r0 = sr0;
+                r1 = sr1;
+            }
+            if (active) {
+                const AV o = V::ld(own);
+                // v_x at i + 1/2: p[i-1], p[i], p[i+1], p[i+2]
+                const AV Dx = vstencil<V>(V::shr1(o, V::lds(l0)), o, V::shl1(o, V::lds(r0)),
+                                          V::shl2(o, V::lds(r0), V::lds(r1)));
+                // v_y at j + 1/2: rows j-1, j, j+1, j+2
+                const AV Dy = vstencil<V>(V::ld(q0), V::ld(q1), V::ld(q2), V::ld(q3));
+                V::template update<COMP>(vx, tx, V::mul(coef_v<V>(prm.a[0], prm.a_uni[0], q), Dx));
+                V::template update<COMP>(vy, ty, V::mul(coef_v<V>(prm.a[1], prm.a_uni[1], q), Dy));
+                store_vec<V>(prm.v[0], q, vx, nvalid);
+                store_vec<V>(prm.v[1], q, vy, nvalid);
+                if (COMP) {
+                    store_vec<V>(prm.tv[0], q, tx, nvalid);
+                    store_vec<V>(prm.tv[1], q, ty, nvalid);
+                }
+            }
+            q0 = q1;
+            q1 = q2;
+            q2 = q3;
+        }
+    }
+}
+
+// Pressure half step of one strip: p += b (Dx v_x + Dy v_y [+ s]), with the
+// item's energy terms p^n p^{n+1} / b + v_x^2 / a_x + v_y^2 / a_y.
+template <class P, int COMP, bool ENERGY>
+__global__ void __launch_bounds__(256) batch_kp_strip(const BatchShot *__restrict__ shots, const int *item0,
+                                                      int nshots, int nitems, int yc, double *item_part) {
+    using V = typename VecOf<P>::T;
+    using Raw = typename V::Raw;
+    using AV = typename V::AV;
+    using RS = typename V::RS;
+    constexpr int N = V::N;
+    __shared__ int s_item0[kMaxShots + 1];
+    for (int t = threadIdx.x; t <= nshots; t += blockDim.x) s_item0[t] = item0[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < nitems; item += gridDim.x * wpb) {
+        const StripItem it = strip_of<N>(s_item0, nshots, item, shots, yc);
+        const AcParams prm = shots[it.s].prm;
+        const int64_t step = shots[it.s].step;
+        const int nx = prm.n[0];
+        const int x = it.x0 + lane * N;
+        const bool active = x < nx;
+        const int nvalid = active ? min(N, nx - x) : 0;
+        const bool left_edge = active && lane == 0;
+        const bool right_edge = active && (lane == 31 || x + N >= nx);
+        // row queue of the own v_y vector: rows j-2, j-1, j (j+1 loaded in the loop)
+        Raw r0 = row_vec<V>(prm.v[1], prm, x, it.y0 - 2, false, active);
+        Raw r1 = row_vec<V>(prm.v[1], prm, x, it.y0 - 1, false, active);
+        Raw r2 = row_vec<V>(prm.v[1], prm, x, it.y0, false, active);
+        double e_acc = 0.0;
+        for (int j = it.y0; j < it.y1; j++) {
+            const Raw r3 = row_vec<V>(prm.v[1], prm, x, j + 1, false, active);
+            const int64_t q = x + prm.sy * (int64_t)j;
+            Raw vx = V::zero(), pv = V::zero(), tv = V::zero();
+            if (active) {
+                vx = at<V>(prm.v[0], q);
+                pv = at<V>(prm.p, q);
+                if (COMP) tv = at<V>(prm.tp, q);
+            }
+            // x neighbours v_x[x-2], v_x[x-1], v_x[x+N] (half-point images)
+            Raw own = vx;
+            RS l1 = RS(0), l0 = RS(0), rr = RS(0);
+            if (left_edge) {
+                l1 = x_val<V>(prm.v[0], prm, x - 2, j, false);
+                l0 = x_val<V>(prm.v[0], prm, x - 1, j, false);
+            }
+            if (right_edge) {
+                rr = x_val<V>(prm.v[0], prm, x + N, j, false);
+#pragma unroll
+                for (int e = 1; e < N; e++)
+                    if (e >= nvalid) raw_set<RS, Raw>(own, e, x_val<V>(prm.v[0], prm, x + e, j, false));
+            }
+            const RS sl1 = shfl_rs(V::get(vx, N - 2), 1, true);
+            const RS sl0 = shfl_rs(V::get(vx, N - 1), 1, true);
+            const RS srr = shfl_rs(V::get(vx, 0), 1, false);
+            if (!left_edge) {
+                l1 = sl1;
+                l0 = sl0;
+            }
+            if (!right_edge) rr = srr;
+            if (active) {
+                const AV o = V::ld(own);
+                // node i reads v_x at i-2, i-1, i, i+1 (+1/2)
+                AV R = vstencil<V>(V::shr2(o, V::lds(l1), V::lds(l0)), V::shr1(o, V::lds(l0)), o,
+                                   V::shl1(o, V::lds(rr)));
+                R = V::add(R, vstencil<V>(V::ld(r0), V::ld(r1), V::ld(r2), V::ld(r3)));
+                if (j == prm.src_j && prm.src_i >= x && prm.src_i < x + N && step < prm.src_nt) {
+                    const typename V::AS s_ = static_cast<const typename V::AS *>(prm.src)[step];
+#pragma unroll
+                    for (int e = 0; e < N; e++)
+                        if (e == prm.src_i - x) V::set(R, e, P::add(V::aget(R, e), s_));
+                }
+                const Raw pold = pv;
+                V::template update<COMP>(pv, tv, V::mul(coef_v<V>(prm.b, prm.b_uni, q), R));
+                store_vec<V>(prm.p, q, pv, nvalid);
+                if (COMP) store_vec<V>(prm.tp, q, tv, nvalid);
+                if (ENERGY) {
+                    RS bs, as0, as1;
+                    from_bits(prm.b_uni, bs);
+                    from_bits(prm.a_uni[0], as0);
+                    from_bits(prm.a_uni[1], as1);
+                    const Raw bv = prm.b ? at<V>(const_cast<void *>(prm.b), q) : V::zero();
+                    const Raw av0 = prm.a[0] ? at<V>(const_cast<void *>(prm.a[0]), q) : V::zero();
+                    const Raw av1 = prm.a[1] ? at<V>(const_cast<void *>(prm.a[1]), q) : V::zero();
+#pragma unroll
+                    for (int e = 0; e < N; e++) {
+                        if (e >= nvalid) break;
+                        const float bw = prm.b ? V::f32(bv, e) : P::to_f32(bs);
+                        const float aw0 = prm.a[0] ? V::f32(av0, e) : P::to_f32(as0);
+                        const float aw1 = prm.a[1] ? V::f32(av1, e) : P::to_f32(as1);
+                        const float fx = V::f32(vx, e), fy = V::f32(r2, e);
+                        e_acc += (double)e_term(V::f32(pold, e), V::f32(pv, e), bw);
+                        e_acc += (double)e_term(fx, fx, aw0);
+                        e_acc += (double)e_term(fy, fy, aw1);
+                    }
+                }
+            }
+            r0 = r1;
+            r1 = r2;
+            r2 = r3;
+        }
+        if (ENERGY) {
+            for (int off = 16; off > 0; off >>= 1) e_acc += __shfl_down_sync(0xffffffffu, e_acc, off);
+            if (lane == 0) item_part[item] = e_acc;
+        }
+    }
+}
+
 // Per-shot energy: the item partials of each shot summed in item order.
 __global__ void batch_energy_reduce(BatchShot *shots, const int *item0, const double *item_part) {
     const int s = blockIdx.x;
@@ -98,11 +391,22 @@ __global__ void batch_advance(BatchShot *shots, int nshots) {
 
 template <class P, int COMP>
 static cudaError_t launch_pc(const BatchLaunch &L, bool energy, cudaStream_t st) {
-    const int threads = L.bx * L.by;
-    batch_half_step<P, COMP, 0><<<L.grid, threads, 0, st>>>(L.shots, L.item0, L.nshots, L.nitems, L.bx,
-                                                            L.by, 0, L.item_part);
-    batch_half_step<P, COMP, 1><<<L.grid, threads, 0, st>>>(L.shots, L.item0, L.nshots, L.nitems, L.bx,
-                                                            L.by, energy ? 1 : 0, L.item_part);
+    if (L.kind == BATCH_STRIPS) {
+        const int threads = 32 * L.wpb;
+        batch_kv_strip<P, COMP><<<L.grid, threads, 0, st>>>(L.shots, L.item0, L.nshots, L.nitems, L.yc);
+        if (energy)
+            batch_kp_strip<P, COMP, true><<<L.grid, threads, 0, st>>>(L.shots, L.item0, L.nshots, L.nitems, L.yc,
+                                                                      L.item_part);
+        else
+            batch_kp_strip<P, COMP, false><<<L.grid, threads, 0, st>>>(L.shots, L.item0, L.nshots, L.nitems,
+                                                                       L.yc, L.item_part);
+    } else {
+        const int threads = L.bx * L.by;
+        batch_half_step<P, COMP, 0><<<L.grid, threads, 0, st>>>(L.shots, L.item0, L.nshots, L.nitems, L.bx,
+                                                                L.by, 0, L.item_part);
+        batch_half_step<P, COMP, 1><<<L.grid, threads, 0, st>>>(L.shots, L.item0, L.nshots, L.nitems, L.bx,
+                                                                L.by, energy ? 1 : 0, L.item_part);
+    }
     if (energy) batch_energy_reduce<<<L.nshots, 256, 0, st>>>(L.shots, L.item0, L.item_part);
     batch_advance<<<(L.nshots + 127) / 128, 128, 0, st>>>(L.shots, L.nshots);
     return cudaGetLastError();
@@ -119,8 +423,20 @@ static cudaError_t launch_p(const BatchLaunch &L, int comp, bool energy, cudaStr
 
 int batch_max_shots() { return kMaxShots; }
 
+int64_t batch_items_of(int kind, int bx, int by, int yc, int prec, int64_t nx, int64_t ny) {
+    if (kind == BATCH_STRIPS) {
+        const int64_t tx = 32 * (prec == PREC_FP32 ? 4 : 8);
+        return ((nx + tx - 1) / tx) * ((ny + yc - 1) / yc);
+    }
+    return ((nx + bx - 1) / bx) * ((ny + by - 1) / by);
+}
+
 cudaError_t batch_step(const BatchLaunch &L, int prec, int comp, bool energy, cudaStream_t st) {
-    if (L.bx * L.by > 256 || (L.bx * L.by) % 32 != 0) return cudaErrorInvalidValue;
+    if (L.kind == BATCH_STRIPS) {
+        if (L.wpb < 1 || L.wpb > 8 || L.yc < 1) return cudaErrorInvalidValue;
+    } else if (L.bx * L.by > 256 || (L.bx * L.by) % 32 != 0) {
+        return cudaErrorInvalidValue;
+    }
     switch (prec) {
     case PREC_FP32: return launch_p<F32>(L, comp, energy, st);
     case PREC_FP16: return launch_p<F16>(L, comp, energy, st);

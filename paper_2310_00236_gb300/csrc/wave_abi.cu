@@ -1172,31 +1172,41 @@ struct wave_batch {
     int *d_item0 = nullptr;
     double *d_part = nullptr;
     std::vector<BatchShot> h_shots;
-    int bx = 32, by = 8, grid = 0, nitems = 0, sms = 1;
+    int shape = 0, nitems = 0, sms = 1;
     bool tuned = false;
     cudaGraphExec_t gexec = nullptr;
     int gsteps = 0;
 };
 
-static const int kTiles[][2] = {{32, 8}, {64, 4}, {128, 2}, {32, 4}, {64, 2}, {256, 1}};
-static const int kGridMul[] = {2, 4, 8, 16};
+// Launch shapes the autotuner tries (every one computes the same bits).
+struct BatchShape {
+    int kind, bx, by, yc, wpb, grid_per_sm;
+};
+static const BatchShape kShapes[] = {
+    {BATCH_POINTS, 32, 8, 0, 0, 4},  {BATCH_POINTS, 32, 8, 0, 0, 8},
+    {BATCH_STRIPS, 0, 0, 16, 8, 4},  {BATCH_STRIPS, 0, 0, 16, 8, 8},
+    {BATCH_STRIPS, 0, 0, 32, 8, 4},  {BATCH_STRIPS, 0, 0, 32, 8, 8},
+    {BATCH_STRIPS, 0, 0, 64, 8, 4},  {BATCH_STRIPS, 0, 0, 64, 8, 8},
+    {BATCH_STRIPS, 0, 0, 16, 4, 8},  {BATCH_STRIPS, 0, 0, 16, 4, 16},
+    {BATCH_STRIPS, 0, 0, 32, 4, 8},  {BATCH_STRIPS, 0, 0, 32, 4, 16},
+    {BATCH_STRIPS, 0, 0, 64, 4, 8},  {BATCH_STRIPS, 0, 0, 64, 4, 16},
+};
+constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
+constexpr int kDefaultShape = 5;
 
-// work list of the tile shape (bx, by): first item of each shot
-static int batch_items(wave_batch *b, int bx, int by, std::vector<int> &item0) {
+// work list of a launch shape: first item of each shot
+static int batch_items(wave_batch *b, const BatchShape &sh, std::vector<int> &item0) {
     item0.assign(b->ctx.size() + 1, 0);
-    for (size_t s = 0; s < b->ctx.size(); s++) {
-        const int64_t nx = b->ctx[s]->n[0], ny = b->ctx[s]->n[1];
-        item0[s + 1] = item0[s] + (int)(((nx + bx - 1) / bx) * ((ny + by - 1) / by));
-    }
+    for (size_t s = 0; s < b->ctx.size(); s++)
+        item0[s + 1] = item0[s] + (int)batch_items_of(sh.kind, sh.bx, sh.by, sh.yc, b->prec, b->ctx[s]->n[0],
+                                                      b->ctx[s]->n[1]);
     return item0.back();
 }
 
-static cudaError_t batch_set_shape(wave_batch *b, int bx, int by, int grid) {
+static cudaError_t batch_set_shape(wave_batch *b, int shape) {
     std::vector<int> item0;
-    b->nitems = batch_items(b, bx, by, item0);
-    b->bx = bx;
-    b->by = by;
-    b->grid = grid;
+    b->shape = shape;
+    b->nitems = batch_items(b, kShapes[shape], item0);
     cudaError_t e = cudaMemcpyAsync(b->d_item0, item0.data(), item0.size() * sizeof(int),
                                     cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -1204,15 +1214,19 @@ static cudaError_t batch_set_shape(wave_batch *b, int bx, int by, int grid) {
 }
 
 static BatchLaunch batch_launch(wave_batch *b) {
+    const BatchShape &sh = kShapes[b->shape];
     BatchLaunch L;
     L.shots = b->d_shots;
     L.item0 = b->d_item0;
     L.item_part = b->d_part;
     L.nshots = (int)b->ctx.size();
     L.nitems = b->nitems;
-    L.bx = b->bx;
-    L.by = b->by;
-    L.grid = b->grid;
+    L.kind = sh.kind;
+    L.bx = sh.bx;
+    L.by = sh.by;
+    L.yc = sh.yc;
+    L.wpb = sh.wpb;
+    L.grid = sh.grid_per_sm * b->sms;
     return L;
 }
 
@@ -1254,11 +1268,11 @@ extern "C" wave_status wave_batch_create(int32_t nctx, wave_ctx *const *ctxs, wa
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     int max_items = 0;
     std::vector<int> tmp;
-    for (auto &t : kTiles) max_items = std::max(max_items, batch_items(b, t[0], t[1], tmp));
+    for (const auto &sh : kShapes) max_items = std::max(max_items, batch_items(b, sh, tmp));
     cudaError_t e = cudaMalloc(&b->d_shots, sizeof(BatchShot) * nctx);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_item0, sizeof(int) * (nctx + 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_part, sizeof(double) * (size_t)max_items);
-    if (e == cudaSuccess) e = batch_set_shape(b, 32, 8, 8 * b->sms);
+    if (e == cudaSuccess) e = batch_set_shape(b, kDefaultShape);
     if (e != cudaSuccess) {
         wave_batch_destroy(b);
         cudaGetLastError();
@@ -1295,34 +1309,33 @@ extern "C" wave_status wave_batch_step(wave_batch *b, int64_t n) {
     cudaError_t e = batch_refresh(b);
     if (e != cudaSuccess) return batch_fail(b, e, "batch upload");
     int64_t left = n;
-    const int ncand = (int)(sizeof(kTiles) / sizeof(kTiles[0])) * (int)(sizeof(kGridMul) / sizeof(int));
-    if (!b->tuned && left - 1 >= ncand) {
+    if (!b->tuned && left - 1 >= kNumShapes) {
         // autotune on real steps: every candidate computes the same bits
         float best = 1e30f;
-        int bi = 0, bg = 0;
+        int bi = kDefaultShape;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        for (int ti = 0; ti < (int)(sizeof(kTiles) / sizeof(kTiles[0])); ti++) {
-            for (int gm : kGridMul) {
-                e = batch_set_shape(b, kTiles[ti][0], kTiles[ti][1], gm * b->sms);
-                if (e != cudaSuccess) break;
-                cudaEventRecord(e0, b->stream);
-                e = batch_step(batch_launch(b), b->prec, b->comp, false, b->stream);
-                cudaEventRecord(e1, b->stream);
-                if (e != cudaSuccess) break;
-                e = cudaEventSynchronize(e1);
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) { best = ms; bi = ti; bg = gm; }
-                left--;
-            }
+        for (int si = 0; si < kNumShapes && e == cudaSuccess; si++) {
+            e = batch_set_shape(b, si);
             if (e != cudaSuccess) break;
+            cudaEventRecord(e0, b->stream);
+            e = batch_step(batch_launch(b), b->prec, b->comp, false, b->stream);
+            cudaEventRecord(e1, b->stream);
+            if (e != cudaSuccess) break;
+            e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bi = si;
+            }
+            left--;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (e != cudaSuccess) return batch_fail(b, e, "batch autotune");
-        e = batch_set_shape(b, kTiles[bi][0], kTiles[bi][1], bg * b->sms);
+        e = batch_set_shape(b, bi);
         if (e != cudaSuccess) return batch_fail(b, e, "batch shape");
         b->tuned = true;
     }
@@ -1366,12 +1379,12 @@ extern "C" wave_status wave_batch_step(wave_batch *b, int64_t n) {
     return WAVE_OK;
 }
 
-extern "C" wave_status wave_batch_info(wave_batch *b, int32_t *bx, int32_t *by, int32_t *grid,
-                                       int32_t *graph_steps) {
-    if (!b) return fail(WAVE_EINVAL, "NULL batch");
-    if (bx) *bx = b->bx;
-    if (by) *by = b->by;
-    if (grid) *grid = b->grid;
-    if (graph_steps) *graph_steps = b->gexec ? b->gsteps : 0;
+extern "C" wave_status wave_batch_info(wave_batch *b, int32_t *info, int32_t ninfo) {
+    if (!b || !info) return fail(WAVE_EINVAL, "NULL argument");
+    const BatchShape &sh = kShapes[b->shape];
+    const int32_t v[7] = {sh.kind, sh.kind == BATCH_STRIPS ? 32 * (b->prec == WAVE_FP32 ? 4 : 8) : sh.bx,
+                          sh.kind == BATCH_STRIPS ? sh.yc : sh.by, sh.kind == BATCH_STRIPS ? 32 * sh.wpb : sh.bx * sh.by,
+                          sh.grid_per_sm * b->sms, b->gexec ? b->gsteps : 0, b->tuned ? 1 : 0};
+    for (int i = 0; i < ninfo && i < 7; i++) info[i] = v[i];
     return WAVE_OK;
 }

@@ -99,8 +99,7 @@ def lib() -> C.CDLL:
                                         C.POINTER(vp), C.POINTER(vp), vp, C.c_double, vp, vp],
         "wave_batch_create": [i32, C.POINTER(vp), C.POINTER(vp)],
         "wave_batch_step": [vp, i64],
-        "wave_batch_info": [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
-                            C.POINTER(C.c_int32)],
+        "wave_batch_info": [vp, C.POINTER(C.c_int32), i32],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -342,11 +341,13 @@ def wave_batch_step(batch: Batch, n: int):
     _check(lib().wave_batch_step(batch.ptr, int(n)))
 
 
-def wave_batch_info(batch: Batch):
-    """(bx, by, grid, graph_steps) of the tuned launch configuration."""
-    v = [C.c_int32() for _ in range(4)]
-    _check(lib().wave_batch_info(batch.ptr, *[C.byref(x) for x in v]))
-    return tuple(x.value for x in v)
+def wave_batch_info(batch: Batch) -> dict:
+    """The launch configuration in use (kind, tile, threads, blocks, graph
+    steps, tuned)."""
+    v = (C.c_int32 * 7)()
+    _check(lib().wave_batch_info(batch.ptr, v, 7))
+    return {"kind": ("points", "strips")[v[0]], "tile_x": v[1], "tile_y": v[2], "threads": v[3],
+            "blocks": v[4], "graph_steps": v[5], "tuned": bool(v[6])}
 
 
 def wave_batch_destroy(batch: Batch):
