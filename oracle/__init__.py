@@ -63,6 +63,10 @@ def lib():
         L.orc_acoustic_run.argtypes = ([C.c_void_p] + [dp] * 8 + [dp] * 4 +
                                        [i64, i64, i64, i64, dp, C.c_int32, i64,
                                         C.POINTER(C.c_int64), dp, dp])
+        L.orc_acoustic_adjoint.restype = C.c_int
+        L.orc_acoustic_adjoint.argtypes = ([C.c_void_p] + [dp] * 4 + [dp] * 4 + [dp] +
+                                           [i64, i64, i64, i64, dp, i64, C.POINTER(C.c_int64),
+                                            dp, dp, dp, dp, dp])
         L.orc_acoustic_coefficients.restype = C.c_int
         L.orc_acoustic_coefficients.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double,
                                                 dp, dp, dp, dp, dp, dp, dp]
@@ -212,6 +216,42 @@ class AcousticState:
             raise MemoryError("oracle run failed")
         self.step += nsteps
         return traces, en
+
+
+def acoustic_adjoint(st: AcousticState, c, nsteps: int, rec_index, residual=None, d_obs=None):
+    """Discrete adjoint (reverse mode) of `nsteps` binary64 steps from the
+    state `st` (not modified), for the pressure traces at rec_index.
+
+    J = 1/2 sum (trace - d_obs)^2 when d_obs is given (residual = trace -
+    d_obs), else the adjoint of the linear functional sum residual * trace.
+    c: the velocity model the coefficients b were made from.
+    Returns dict(traces, J, grad_b, grad_c, p0_bar). The state must be binary64
+    without compensation.
+
+    Pinned by tests/test_oracle_adjoint.py: the dot-product identity
+    <F x, y> = <x, F^T y> of the linear map from the initial pressure to the
+    traces, and central finite differences of the forward misfit in c.
+    """
+    ri = np.ascontiguousarray(rec_index, dtype=np.int64)
+    nrec = ri.size
+    if d_obs is not None:
+        tr, _ = st.copy().run(nsteps, 0, ri)
+        residual = tr - np.asarray(d_obs, dtype=np.float64).reshape(nsteps, nrec)
+    res = _f64(np.asarray(residual, dtype=np.float64).reshape(nsteps, nrec))
+    traces = np.zeros((nsteps, nrec))
+    gb, gc, p0b = np.zeros(st.shape), np.zeros(st.shape), np.zeros(st.shape)
+    src = None if st.src is None else _f64(st.src)
+    rc = lib().orc_acoustic_adjoint(
+        C.byref(st.cfg), _dp(_f64(st.p)), _dp(_f64(st.v[0])), _dp(_f64(st.v[1])), _dp(_f64(st.v[2])),
+        _dp(st.a[0]), _dp(st.a[1]), _dp(st.a[2]), _dp(st.b), _dp(_f64(c).reshape(st.shape)), nsteps,
+        st.step, st.src_index, 0 if src is None else src.size, _dp(src), nrec,
+        ri.ctypes.data_as(C.POINTER(C.c_int64)), _dp(res), _dp(traces), _dp(gb), _dp(gc), _dp(p0b))
+    if rc == -2:
+        raise ValueError("the adjoint oracle takes binary64 states without compensation")
+    if rc != 0:
+        raise MemoryError("oracle adjoint failed")
+    J = None if d_obs is None else 0.5 * float(np.sum(res * res))
+    return {"traces": traces, "J": J, "grad_b": gb, "grad_c": gc, "p0_bar": p0b}
 
 
 def acoustic_coefficients(cfg: AcousticCfg, h: float, dt: float, P0: float, rho, c):

@@ -360,6 +360,161 @@ int orc_acoustic_run(const orc_acoustic_cfg *cfg, double *p, double *tp, double 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Discrete adjoint of the acoustic leapfrog (not in the paper).            */
+/* ------------------------------------------------------------------------ */
+
+/* Misfit J = 1/2 sum_s sum_r (trace[s][r] - d_obs[s][r])^2 of the pressure
+ * traces that orc_acoustic_run records (trace[s] = p^(s+1) at the receivers),
+ * and its derivatives, by reverse-mode differentiation of the binary64
+ * scheme (store, arithmetic and stencil formats binary64, no compensation).
+ *
+ * Forward step s (as orc_acoustic_run):
+ *   v_c^(s+1/2) = v_c^(s-1/2) + a_c * D_c p^s              (gather over 4 taps)
+ *   p^(s+1)     = p^s + b * R^s,  R^s = sum_c D_c v_c^(s+1/2) + src^s
+ * Reverse of step s, with adjoints pbar (of p^(s+1)) and vbar (of v^(s+1/2)):
+ *   pbar += the residual of step s at the receiver points;
+ *   bbar += pbar * R^s;   vbar_c += D_c^T (b * pbar)       (scatter over 4 taps)
+ *   pbar += sum_c D_c^T (a_c * vbar_c)
+ * Every transpose is the scatter of the forward gather, tap by tap, with the
+ * boundary images' signs; pbar then holds the adjoint of p^s. The forward
+ * velocity history is kept in full (small problems only).
+ * Outputs (any may be NULL): traces [nsteps][nrec]; grad_b = dJ/db;
+ * grad_c = dJ/dc through b = dt rho c^2 / (Z0 h), i.e. grad_b * 2 b / c with
+ * Z0 held fixed (J does not depend on Z0: it only scales the velocity unit);
+ * p0_bar = dJ/dp^0 (the adjoint state at step 0).
+ * residual: dJ/dtrace [nsteps][nrec] (= trace - d_obs for the L2 misfit).
+ * Returns 0, -1 (allocation), -2 (cfg not binary64 without compensation). */
+int orc_acoustic_adjoint(const orc_acoustic_cfg *cfg, const double *p_init, const double *vx_init,
+                         const double *vy_init, const double *vz_init, const double *ax_c,
+                         const double *ay_c, const double *az_c, const double *b_c, const double *c,
+                         int64_t nsteps, int64_t step0, int64_t src_index, int64_t src_nt,
+                         const double *src, int64_t nrec, const int64_t *rec_index,
+                         const double *residual, double *traces, double *grad_b, double *grad_c,
+                         double *p0_bar)
+{
+    if (cfg->store_fmt != ORC_FP64 || cfg->arith_fmt != ORC_FP64 || cfg->stencil_fmt != ORC_FP64 ||
+        cfg->comp != 0)
+        return -2;
+    const int64_t *n = cfg->n;
+    const int nd = cfg->ndim;
+    const int64_t npts = n[0] * n[1] * n[2];
+    const double *a[3] = {ax_c, ay_c, az_c};
+    const double *vinit[3] = {vx_init, vy_init, vz_init};
+    const double c1 = 9.0 / 8.0, c2 = 1.0 / 24.0;
+    /* forward taps: weights of D = c1 (f[+1/2] - f[-1/2]) - c2 (f[+3/2] - f[-3/2]) */
+    const double w[4] = {c2, -c1, c1, -c2};
+
+    double *work = (double *)calloc((size_t)npts * 9, sizeof(double));
+    double *hist = (double *)malloc((size_t)npts * nd * (size_t)(nsteps > 0 ? nsteps : 1) * sizeof(double));
+    double *tr = (double *)calloc((size_t)(nsteps * nrec > 0 ? nsteps * nrec : 1), sizeof(double));
+    if (!work || !hist || !tr) {
+        free(work);
+        free(hist);
+        free(tr);
+        return -1;
+    }
+    double *p = work, *tp = work + npts, *v[3], *tv[3];
+    for (int ax = 0; ax < 3; ax++) {
+        v[ax] = work + (2 + 2 * ax) * npts;
+        tv[ax] = work + (3 + 2 * ax) * npts;
+    }
+    double *pbar = work + 8 * npts;
+    memcpy(p, p_init, (size_t)npts * sizeof(double));
+    for (int ax = 0; ax < nd; ax++)
+        if (vinit[ax]) memcpy(v[ax], vinit[ax], (size_t)npts * sizeof(double));
+
+    /* forward, keeping v^(s+1/2) and the traces */
+    for (int64_t s = 0; s < nsteps; s++) {
+        int rc = orc_acoustic_run(cfg, p, tp, v[0], tv[0], v[1], tv[1], v[2], tv[2], a[0], a[1], a[2],
+                                  b_c, 1, step0 + s, src_index, src_nt, src, 0, nrec, rec_index,
+                                  nrec ? tr + s * nrec : NULL, NULL);
+        if (rc) {
+            free(work);
+            free(hist);
+            free(tr);
+            return -1;
+        }
+        for (int ax = 0; ax < nd; ax++)
+            memcpy(hist + ((size_t)s * nd + ax) * npts, v[ax], (size_t)npts * sizeof(double));
+    }
+    if (traces && nrec) memcpy(traces, tr, (size_t)(nsteps * nrec) * sizeof(double));
+
+    /* reverse sweep; the buffers p, tp and v are reused as pbar scratch and vbar */
+    double *vbar[3] = {v[0], v[1], v[2]};
+    double *Rbar = tp;
+    memset(pbar, 0, (size_t)npts * sizeof(double));
+    for (int ax = 0; ax < 3; ax++) memset(vbar[ax], 0, (size_t)npts * sizeof(double));
+    double *gb = grad_b ? grad_b : tv[0];
+    memset(gb, 0, (size_t)npts * sizeof(double));
+    for (int64_t s = nsteps - 1; s >= 0; s--) {
+        const int64_t gstep = step0 + s;
+        for (int64_t r = 0; r < nrec; r++) {
+            const int64_t q = rec_index[r];
+            if (q >= 0 && q < npts) pbar[q] += residual[s * nrec + r];
+        }
+        /* reverse of the pressure half step */
+        for (int64_t k = 0; k < n[2]; k++)
+            for (int64_t j = 0; j < n[1]; j++)
+                for (int64_t i = 0; i < n[0]; i++) {
+                    const int64_t q = lin(n, i, j, k);
+                    const int64_t idx[3] = {i, j, k};
+                    double R = 0.0;
+                    for (int cx = 0; cx < nd; cx++) {
+                        const double *vh = hist + ((size_t)s * nd + cx) * npts;
+                        const int64_t m = idx[cx];
+                        double f[4];
+                        for (int t = 0; t < 4; t++) f[t] = read_axis(vh, n, cfg->bc, cx, 0, i, j, k, m - 2 + t);
+                        R += c1 * (f[2] - f[1]) - c2 * (f[3] - f[0]);
+                    }
+                    if (src && q == src_index && gstep < src_nt) R += src[gstep];
+                    gb[q] += pbar[q] * R;
+                    Rbar[q] = b_c[q] * pbar[q];
+                }
+        for (int64_t k = 0; k < n[2]; k++)
+            for (int64_t j = 0; j < n[1]; j++)
+                for (int64_t i = 0; i < n[0]; i++) {
+                    const int64_t q = lin(n, i, j, k);
+                    const int64_t idx[3] = {i, j, k};
+                    for (int cx = 0; cx < nd; cx++) {
+                        const int64_t m = idx[cx];
+                        for (int t = 0; t < 4; t++) {
+                            int64_t mm, at[3] = {i, j, k};
+                            int sg = map_axis(m - 2 + t, n[cx], cfg->bc[cx], 0, &mm);
+                            if (sg == 0) continue;
+                            at[cx] = mm;
+                            vbar[cx][lin(n, at[0], at[1], at[2])] += sg * w[t] * Rbar[q];
+                        }
+                    }
+                }
+        /* reverse of the velocity half step: v_c at m + 1/2 read p at m-1 .. m+2 */
+        for (int64_t k = 0; k < n[2]; k++)
+            for (int64_t j = 0; j < n[1]; j++)
+                for (int64_t i = 0; i < n[0]; i++) {
+                    const int64_t q = lin(n, i, j, k);
+                    const int64_t idx[3] = {i, j, k};
+                    for (int cx = 0; cx < nd; cx++) {
+                        const double g = a[cx][q] * vbar[cx][q];
+                        const int64_t m = idx[cx];
+                        for (int t = 0; t < 4; t++) {
+                            int64_t mm, at[3] = {i, j, k};
+                            int sg = map_axis(m - 1 + t, n[cx], cfg->bc[cx], 1, &mm);
+                            if (sg == 0) continue;
+                            at[cx] = mm;
+                            pbar[lin(n, at[0], at[1], at[2])] += sg * w[t] * g;
+                        }
+                    }
+                }
+    }
+    if (grad_c)
+        for (int64_t q = 0; q < npts; q++) grad_c[q] = gb[q] * 2.0 * b_c[q] / c[q];
+    if (p0_bar) memcpy(p0_bar, pbar, (size_t)npts * sizeof(double));
+    free(work);
+    free(hist);
+    free(tr);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Coefficient preparation and scaling (Section 5 "Range"; units chosen so  */
 /* that coefficients and fields stay inside the half-precision range).      */
 /* ------------------------------------------------------------------------ */
