@@ -271,10 +271,40 @@ wave_status wave_steps_done(wave_ctx *ctx, int64_t *steps);
 wave_status wave_set_timing(wave_ctx *ctx, int32_t enable);
 wave_status wave_get_timing(wave_ctx *ctx, int32_t kind, int64_t *launches, double *ms);
 
-/* wave_adjoint_step -- adjoint time stepping for the gradient with respect to
- * the velocity model. Not in the paper; not implemented in this build:
- * returns WAVE_ENOTIMPL. */
+/*
+ * Gradient of a trace misfit with respect to the velocity model, by the
+ * discrete adjoint of the acoustic scheme (not in the paper; acoustic only).
+ *
+ * wave_record -- run nsteps forward steps from the current state exactly as
+ * wave_step does (receivers and the energy trace record as usual), keeping
+ * ncheckpoints snapshots of the state (0: ceil(sqrt(nsteps))), one at the start
+ * of each segment of K = ceil(nsteps / ncheckpoints) steps, and the end state.
+ * Receivers, if set, must record p. Resets the adjoint: the adjoint fields
+ * and the gradient start at zero at step nsteps. Memory: (ncheckpoints + 1)
+ * states + K velocity fields + 3-5 binary32 fields. Errors: ENOTIMPL
+ * (elastic), EINVAL, ENOMEM, ECUDA.
+ *
+ * wave_adjoint_step -- n steps of the adjoint backwards in time from the
+ * current adjoint step t (t = nsteps after wave_record; n <= t). residual:
+ * device array [nsteps][nrec] (binary32), residual[s * nrec + r] = dJ/dd_sr,
+ * the derivative of the misfit J with respect to sample r of step s of the
+ * recorded traces (for J = 1/2 sum (d - d_obs)^2 it is d - d_obs); it may be
+ * NULL when no receivers are set. Each step injects its residual row at the
+ * receivers, accumulates the gradient and takes one leapfrog step of the
+ * adjoint fields (binary32) with the multipliers negated. The forward
+ * velocities of the step are replayed from the nearest checkpoint (one
+ * segment at a time, bit-identical to the recorded run). On return the
+ * forward fields again hold the end state of the recorded run.
+ * Errors: ESTATE (no recorded run), EINVAL, ECUDA.
+ *
+ * wave_get_gradient -- dJ/dc at every node (binary32, x fastest, unpitched,
+ * n[0]*n[1]*n[2] values) into the caller's device array device_out, for the
+ * adjoint steps taken so far; the full gradient once steps_left is 0.
+ * device_out may be NULL to query steps_left only. Asynchronous.
+ */
+wave_status wave_record(wave_ctx *ctx, int64_t nsteps, int64_t ncheckpoints);
 wave_status wave_adjoint_step(wave_ctx *ctx, int64_t n, const float *residual_traces);
+wave_status wave_get_gradient(wave_ctx *ctx, float *device_out, int64_t *steps_left);
 
 /*
  * Batched stepping of many independent 2D acoustic problems ("shots"), for

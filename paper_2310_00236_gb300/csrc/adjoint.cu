@@ -1,0 +1,126 @@
+// adjoint.cu -- kernels of the discrete adjoint (gradient of a trace misfit
+// with respect to the velocity model). Not in the paper.
+//
+// Forward step n (scaled variables, rounded multipliers a, b):
+//   v^{n+1/2} = v^{n-1/2} + a G p^n,    p^{n+1} = p^n + b (Dv v^{n+1/2} + s^n)
+// with G the staggered gradient and Dv the staggered divergence. On the
+// unknowns the scheme updates, Dv^T = -G and G^T = -Dv (the discrete
+// operator is skew). Reverse-mode differentiation of the step, written for
+// mu~ = b * pbar and nu~ = a * vbar, is therefore the same leapfrog with the
+// multipliers negated, run backwards in time:
+//   mu~ += b r^n at the receivers (r^n: dJ/dtrace of step n)
+//   g   += mu~ * (Dv v^{n+1/2} + s^n)                 (dJ/db = g / b)
+//   nu~ = nu~ - a G mu~,   mu~ = mu~ - b Dv nu~
+// and dJ/dc = (2 / c) g, since b is proportional to c^2. The rigid-wall nodes
+// (p held at zero) take no residual, which keeps mu~ zero there and makes the
+// skew form exact. The leapfrog half steps reuse the binary32 forward kernels;
+// this file holds the residual injection, the gradient accumulation and the
+// final scaling.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "acoustic_common.cuh"
+#include "adjoint.h"
+
+namespace wave {
+
+// mu[q_r] += w_r * res[r] for every receiver, in receiver order (one thread:
+// receivers may share a point, and the order fixes the rounding).
+__global__ void adj_inject_kernel(float *mu, const int64_t *rec_q, const float *rec_w, const float *res,
+                                  int nrec) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int r = 0; r < nrec; r++) {
+        const float w = rec_w[r];
+        if (w != 0.f) mu[rec_q[r]] = __fadd_rn(mu[rec_q[r]], __fmul_rn(w, res[r]));
+    }
+}
+
+template <int FMT>
+__device__ __forceinline__ float ld_f32(const void *f, int64_t q) {
+    if (FMT == ADJ_F32) return static_cast<const float *>(f)[q];
+    const uint16_t u = static_cast<const uint16_t *>(f)[q];
+    if (FMT == ADJ_BF16) return __uint_as_float((uint32_t)u << 16);
+    __half_raw hr;
+    hr.x = u;
+    return __half2float(__half(hr));
+}
+
+// g += mu * (sum_c D_c v_c + s) at every p node, in binary32, from the forward
+// velocities of the step (storage format FMT) and the scaled source value.
+template <int FMT, int NDIM>
+__global__ void __launch_bounds__(128) adj_grad_kernel(AdjGradParams P) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = NDIM == 3 ? (int)blockIdx.z : 0;
+    if (i >= P.n[0] || j >= P.n[1]) return;
+    const int idx[3] = {i, j, k};
+    const int64_t str[3] = {1, P.sy, P.sz};
+    const int64_t q = i + P.sy * j + P.sz * k;
+    const float c1 = 1.125f, c2 = 1.0f / 24.0f;
+    float R = 0.f;
+#pragma unroll
+    for (int c = 0; c < NDIM; c++) {
+        const int m = idx[c];
+        const int64_t base = q - str[c] * m;
+        float f[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            int mm;
+            img_half(m - 2 + t, P.n[c], P.bc[c], mm);
+            f[t] = ld_f32<FMT>(P.v[c], base + str[c] * mm);
+        }
+        R += c1 * (f[2] - f[1]) - c2 * (f[3] - f[0]);
+    }
+    if (q == P.src_q) R += P.src_value;
+    P.g[q] += P.mu[q] * R;
+}
+
+// out[i + nx (j + ny k)] = g[q] * two_over_c[...]: dJ/dc, unpitched.
+__global__ void adj_finish_kernel(float *out, const float *g, const float *two_over_c, int nx, int ny,
+                                  int nz, int64_t sy, int64_t sz) {
+    const int64_t npts = (int64_t)nx * ny * nz;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < npts;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(u % nx);
+        const int j = (int)((u / nx) % ny);
+        const int k = (int)(u / ((int64_t)nx * ny));
+        out[u] = g[i + sy * j + sz * k] * two_over_c[u];
+    }
+}
+
+cudaError_t adj_inject(float *mu, const int64_t *rec_q, const float *rec_w, const float *res, int nrec,
+                       cudaStream_t st) {
+    if (nrec <= 0) return cudaSuccess;
+    adj_inject_kernel<<<1, 32, 0, st>>>(mu, rec_q, rec_w, res, nrec);
+    return cudaGetLastError();
+}
+
+template <int FMT>
+static void launch_grad(const AdjGradParams &P, int ndim, cudaStream_t st) {
+    dim3 block(32, 4, 1);
+    dim3 grid((P.n[0] + 31) / 32, (P.n[1] + 3) / 4, ndim == 3 ? P.n[2] : 1);
+    if (ndim == 3) adj_grad_kernel<FMT, 3><<<grid, block, 0, st>>>(P);
+    else adj_grad_kernel<FMT, 2><<<grid, block, 0, st>>>(P);
+}
+
+cudaError_t adj_grad(const AdjGradParams &P, int ndim, int fmt, cudaStream_t st) {
+    switch (fmt) {
+    case ADJ_F32: launch_grad<ADJ_F32>(P, ndim, st); break;
+    case ADJ_BF16: launch_grad<ADJ_BF16>(P, ndim, st); break;
+    default: launch_grad<ADJ_F16>(P, ndim, st); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t adj_finish(float *out, const float *g, const float *two_over_c, const int n[3], int64_t sy,
+                       int64_t sz, cudaStream_t st) {
+    const int64_t npts = (int64_t)n[0] * n[1] * n[2];
+    const int blocks = (int)std::min<int64_t>((npts + 255) / 256, 65535);
+    adj_finish_kernel<<<blocks, 256, 0, st>>>(out, g, two_over_c, n[0], n[1], n[2], sy, sz);
+    return cudaGetLastError();
+}
+
+}  // namespace wave

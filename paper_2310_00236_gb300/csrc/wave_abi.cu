@@ -13,6 +13,7 @@
 
 #include "../../include/wave.h"
 #include "acoustic_common.cuh"
+#include "adjoint.h"
 #include "batch.h"
 #include "elastic.h"
 #include "wave_kernels.h"
@@ -210,6 +211,25 @@ struct wave_ctx {
     int rec_field = 0;
     float *rec_traces = nullptr;
     int64_t rec_cap = 0, rec_pos = 0;
+
+    std::vector<float> src_host;    // scaled source values (arithmetic format, as binary32)
+    std::vector<float> two_over_c;  // acoustic: 2 / c per node (dJ/dc = (2 / c) dJ/db * b)
+
+    // recorded forward run and adjoint state (wave_record / wave_adjoint_step)
+    struct Adjoint {
+        bool active = false;
+        int64_t nsteps = 0, step0 = 0, K = 0, ncp = 0, t = 0;
+        int narr = 0;
+        DevBuf cps;                   // ncp + 1 snapshots of narr arrays; slot ncp: the end state
+        std::vector<int64_t> cp_step;
+        DevBuf seg;                   // v^{n+1/2} of up to K steps (ndim arrays each)
+        int64_t seg_lo = -1, seg_n = 0;
+        DevBuf mu, nu[3], g;          // binary32, pitched like the fields
+        DevBuf na[3], nb;             // negated multipliers (binary32) where per-point
+        uint32_t na_uni[3] = {0, 0, 0}, nb_uni = 0;
+        DevBuf rec_w;                 // residual weight per receiver (b, 0 on rigid walls)
+        DevBuf two_over_c;            // device copy, unpitched
+    } adj;
 };
 
 static bool field_valid(const wave_ctx *c, int field) {
@@ -296,6 +316,8 @@ static wave_status acoustic_coefficients(wave_ctx *c, const wave_materials *mat)
     const double h = c->h, dt = c->dt;
     const double tiny = min_normal(c->prec);
     for (int w = 0; w < 4; w++) c->coef_host[w].assign(npts, 0.0);
+    c->two_over_c.resize(npts);
+    for (int64_t q = 0; q < npts; q++) c->two_over_c[q] = (float)(2.0 / mat->vp[q]);
     std::vector<double> &b = c->coef_host[0];
     const int64_t nx = c->n[0], ny = c->n[1];
     const int64_t str[3] = {1, nx, nx * ny};
@@ -506,6 +528,22 @@ static void collect_timing(wave_ctx *c) {
     for (auto e : seen) c->event_pool.push_back(e);
 }
 
+static void adjoint_free(wave_ctx *c) {
+    auto &A = c->adj;
+    dev_free(c, A.cps);
+    dev_free(c, A.seg);
+    dev_free(c, A.mu);
+    dev_free(c, A.g);
+    dev_free(c, A.nb);
+    dev_free(c, A.rec_w);
+    dev_free(c, A.two_over_c);
+    for (int ax = 0; ax < 3; ax++) {
+        dev_free(c, A.nu[ax]);
+        dev_free(c, A.na[ax]);
+    }
+    A = wave_ctx::Adjoint();
+}
+
 static void destroy_ctx(wave_ctx *c) {
     if (!c) return;
     for (auto &b : c->f) dev_free(c, b);
@@ -517,6 +555,7 @@ static void destroy_ctx(wave_ctx *c) {
     dev_free(c, c->e_misc);
     dev_free(c, c->src_table);
     dev_free(c, c->rec_q);
+    adjoint_free(c);
     cudaStreamSynchronize(c->stream);
     collect_timing(c);
     for (auto e : c->event_pool) cudaEventDestroy(e);
@@ -809,15 +848,18 @@ extern "C" wave_status wave_set_source(wave_ctx *c, wave_field field, const int6
                                                   : (c->dt * c->Z0) / (c->P0 * (c->h * c->h));
     const bool f32 = arith_is_f32(c->prec);
     std::vector<unsigned char> tab(nt * (f32 ? 4 : 2));
+    std::vector<float> host(nt);
     for (int64_t s = 0; s < nt; s++) {
         if (!isfinite(wavelet[s])) return fail(WAVE_ERANGE, "wavelet sample %lld", (long long)s);
         double v = wavelet[s] * scale;
         if (f32) {
             float x = (float)v;
             memcpy(&tab[4 * s], &x, 4);
+            host[s] = x;
         } else {
             uint16_t hb = is_bf16_storage(c->prec) ? round_bits16(v, 7, 8) : round_bits16(v, 10, 5);
             memcpy(&tab[2 * s], &hb, 2);
+            host[s] = (float)(is_bf16_storage(c->prec) ? bf16_to_double(hb) : half_to_double(hb));
         }
     }
     wave_status st = dev_alloc(c, c->src_table, tab.size());
@@ -829,6 +871,7 @@ extern "C" wave_status wave_set_source(wave_ctx *c, wave_field field, const int6
     c->src_q = idx[0] + c->pitch * idx[1] + (c->ndim == 3 ? c->plane * idx[2] : 0);
     c->src_nt = nt;
     c->src_field = field;
+    c->src_host.swap(host);
     return WAVE_OK;
 }
 
@@ -1156,11 +1199,247 @@ extern "C" wave_status wave_get_timing(wave_ctx *c, int32_t kind, int64_t *launc
     return WAVE_OK;
 }
 
+// ------------------------------------------------------------------ adjoint
+// Arrays of a snapshot: p, v_c and, with compensation, t_p, t_v_c.
+static int snapshot_arrays(wave_ctx *c, DevBuf **out) {
+    int k = 0;
+    for (int a = 0; a <= c->ndim; a++) out[k++] = &c->f[a];
+    if (c->comp)
+        for (int a = 0; a <= c->ndim; a++) out[k++] = &c->t[a];
+    return k;
+}
+
+// save (to_slot) or restore (from slot) the forward state
+static cudaError_t snapshot_copy(wave_ctx *c, int64_t slot, bool save) {
+    DevBuf *arr[8];
+    const int na = snapshot_arrays(c, arr);
+    const size_t bytes = (size_t)c->total * elem_bytes(c->prec);
+    char *base = static_cast<char *>(c->adj.cps.ptr) + (size_t)slot * na * bytes;
+    for (int a = 0; a < na; a++) {
+        void *dst = save ? (void *)(base + a * bytes) : arr[a]->ptr;
+        const void *src = save ? arr[a]->ptr : (const void *)(base + a * bytes);
+        cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// binary32 copy of a multiplier, negated (per-point arrays only)
+static wave_status upload_neg_coef(wave_ctx *c, DevBuf &dst, const std::vector<double> &v) {
+    std::vector<float> tmp((size_t)c->total, 0.f);
+    const int64_t nx = c->n[0], ny = c->n[1];
+    for (int64_t q = 0; q < (int64_t)v.size(); q++) {
+        const int64_t i = q % nx, j = (q / nx) % ny, k = q / (nx * ny);
+        tmp[i + c->pitch * j + c->plane * k] = -(float)v[q];
+    }
+    wave_status st = dev_alloc(c, dst, tmp.size() * sizeof(float));
+    if (st) return st;
+    cudaError_t e = cudaMemcpyAsync(dst.ptr, tmp.data(), tmp.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_check(c, e, "adjoint multipliers");
+}
+
+extern "C" wave_status wave_record(wave_ctx *c, int64_t nsteps, int64_t ncheckpoints) {
+    CHECK_CTX(c);
+    if (c->kind != WAVE_ACOUSTIC) return fail(WAVE_ENOTIMPL, "the adjoint covers the acoustic system");
+    if (nsteps < 1) return fail(WAVE_EINVAL, "nsteps must be positive");
+    if (c->nrec && c->rec_field != WAVE_F_P) return fail(WAVE_EINVAL, "adjoint receivers must record p");
+    adjoint_free(c);
+    auto &A = c->adj;
+    int64_t ncp = ncheckpoints > 0 ? ncheckpoints : (int64_t)ceil(sqrt((double)nsteps));
+    ncp = std::max<int64_t>(1, std::min(ncp, nsteps));
+    A.K = (nsteps + ncp - 1) / ncp;
+    A.ncp = (nsteps + A.K - 1) / A.K;
+    A.nsteps = nsteps;
+    A.step0 = c->step;
+    DevBuf *arr[8];
+    A.narr = snapshot_arrays(c, arr);
+    const size_t eb = elem_bytes(c->prec);
+    const size_t abytes = (size_t)c->total * eb, fbytes = (size_t)c->total * sizeof(float);
+    wave_status st = dev_alloc(c, A.cps, (size_t)(A.ncp + 1) * A.narr * abytes);
+    if (!st) st = dev_alloc(c, A.seg, (size_t)A.K * c->ndim * abytes);
+    if (!st) st = dev_alloc(c, A.mu, fbytes);
+    if (!st) st = dev_alloc(c, A.g, fbytes);
+    for (int ax = 0; ax < c->ndim && !st; ax++) st = dev_alloc(c, A.nu[ax], fbytes);
+    if (st) {
+        adjoint_free(c);
+        return st;
+    }
+    // negated binary32 multipliers of the adjoint leapfrog
+    for (int ax = 0; ax < c->ndim && !st; ax++) {
+        if (c->coef_is_uniform[1 + ax]) {
+            const float v = -(float)c->coef_host[1 + ax][0];
+            memcpy(&A.na_uni[ax], &v, 4);
+        } else {
+            st = upload_neg_coef(c, A.na[ax], c->coef_host[1 + ax]);
+        }
+    }
+    if (!st) {
+        if (c->coef_is_uniform[0]) {
+            const float v = -(float)c->coef_host[0][0];
+            memcpy(&A.nb_uni, &v, 4);
+        } else {
+            st = upload_neg_coef(c, A.nb, c->coef_host[0]);
+        }
+    }
+    // residual weights: b at each receiver, 0 on the rigid-wall nodes
+    if (!st && c->nrec) {
+        std::vector<int64_t> q(c->nrec);
+        cudaError_t e = cudaMemcpy(q.data(), c->rec_q.ptr, c->nrec * sizeof(int64_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_check(c, e, "receiver read-back");
+        std::vector<float> w(c->nrec);
+        for (int64_t r = 0; r < c->nrec; r++) {
+            const int64_t idx[3] = {q[r] % c->pitch, (q[r] / c->pitch) % c->n[1], q[r] / c->plane};
+            bool wall = false;
+            for (int ax = 0; ax < c->ndim; ax++) wall |= c->bc[2 * ax] == WAVE_BC_RIGID && idx[ax] == 0;
+            const int64_t u = idx[0] + c->n[0] * (idx[1] + c->n[1] * idx[2]);
+            w[r] = wall ? 0.f : (float)c->coef_host[0][c->coef_is_uniform[0] ? 0 : u];
+        }
+        st = dev_alloc(c, A.rec_w, w.size() * sizeof(float));
+        if (!st) {
+            e = cudaMemcpyAsync(A.rec_w.ptr, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            st = cuda_check(c, e, "receiver weights");
+        }
+    }
+    if (!st) {
+        st = dev_alloc(c, A.two_over_c, c->two_over_c.size() * sizeof(float));
+        if (!st) {
+            cudaError_t e = cudaMemcpyAsync(A.two_over_c.ptr, c->two_over_c.data(),
+                                            c->two_over_c.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                            c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            st = cuda_check(c, e, "velocity upload");
+        }
+    }
+    if (st) {
+        adjoint_free(c);
+        return st;
+    }
+    // forward run with a snapshot at the start of every segment of K steps
+    A.cp_step.assign(A.ncp + 1, 0);
+    for (int64_t i = 0; i < A.ncp; i++) {
+        A.cp_step[i] = c->step;
+        cudaError_t e = snapshot_copy(c, i, true);
+        if (e != cudaSuccess) return cuda_check(c, e, "checkpoint");
+        st = acoustic_steps(c, std::min(A.K, nsteps - i * A.K));
+        if (st) return st;
+    }
+    A.cp_step[A.ncp] = c->step;
+    cudaError_t e = snapshot_copy(c, A.ncp, true);
+    if (e != cudaSuccess) return cuda_check(c, e, "end state");
+    c->have_energy = true;
+    A.t = nsteps;
+    A.active = true;
+    return WAVE_OK;
+}
+
+// Replay segment si from its checkpoint, keeping v^{n+1/2} of every step.
+static wave_status adjoint_replay(wave_ctx *c, int64_t si) {
+    auto &A = c->adj;
+    cudaError_t e = snapshot_copy(c, si, false);
+    if (e != cudaSuccess) return cuda_check(c, e, "checkpoint restore");
+    c->step = A.cp_step[si];
+    const int64_t lo = si * A.K, len = std::min(A.K, A.nsteps - lo);
+    const int64_t nrec = c->nrec;
+    double *etr = c->e_trace;
+    c->nrec = 0;
+    c->e_trace = nullptr;
+    const size_t bytes = (size_t)c->total * elem_bytes(c->prec);
+    wave_status st = WAVE_OK;
+    for (int64_t m = 0; m < len && !st; m++) {
+        st = acoustic_steps(c, 1);
+        for (int ax = 0; ax < c->ndim && !st; ax++) {
+            e = cudaMemcpyAsync(static_cast<char *>(A.seg.ptr) + (size_t)(m * c->ndim + ax) * bytes, c->f[1 + ax].ptr,
+                                bytes, cudaMemcpyDeviceToDevice, c->stream);
+            st = cuda_check(c, e, "replay copy");
+        }
+    }
+    c->nrec = nrec;
+    c->e_trace = etr;
+    if (st) return st;
+    A.seg_lo = lo;
+    A.seg_n = len;
+    return WAVE_OK;
+}
+
 extern "C" wave_status wave_adjoint_step(wave_ctx *c, int64_t n, const float *residual) {
     CHECK_CTX(c);
-    (void)n;
-    (void)residual;
-    return fail(WAVE_ENOTIMPL, "adjoint time stepping is not implemented in this build");
+    auto &A = c->adj;
+    if (!A.active) return fail(WAVE_ESTATE, "no recorded run: call wave_record first");
+    if (n < 0 || n > A.t) return fail(WAVE_EINVAL, "n = %lld outside 0..%lld", (long long)n, (long long)A.t);
+    if (c->nrec && !residual) return fail(WAVE_EINVAL, "residual traces are NULL");
+    if (n == 0) return WAVE_OK;
+    AcParams prm;
+    memset(&prm, 0, sizeof prm);
+    for (int ax = 0; ax < 3; ax++) {
+        prm.n[ax] = (int)c->n[ax];
+        prm.bc[ax] = ax < c->ndim ? (c->bc[2 * ax] == WAVE_BC_PERIODIC ? BC_PERIODIC : BC_RIGID) : BC_PERIODIC;
+        prm.v[ax] = A.nu[ax].ptr;
+        prm.a[ax] = A.na[ax].ptr;
+        prm.a_uni[ax] = A.na_uni[ax];
+    }
+    prm.sy = c->pitch;
+    prm.sz = c->plane;
+    prm.p = A.mu.ptr;
+    prm.b = A.nb.ptr;
+    prm.b_uni = A.nb_uni;
+    prm.src_q = -1;
+    prm.src_i = prm.src_j = prm.src_k = -1;
+    const bool stream_ok = acoustic_stream_supported(prm, c->ndim, PREC_FP32);
+    AdjGradParams gp;
+    memset(&gp, 0, sizeof gp);
+    for (int ax = 0; ax < 3; ax++) {
+        gp.n[ax] = prm.n[ax];
+        gp.bc[ax] = prm.bc[ax];
+    }
+    gp.sy = c->pitch;
+    gp.sz = c->plane;
+    gp.mu = static_cast<const float *>(A.mu.ptr);
+    gp.g = static_cast<float *>(A.g.ptr);
+    const int fmt = c->prec == PREC_FP32 ? ADJ_F32 : is_bf16_storage(c->prec) ? ADJ_BF16 : ADJ_F16;
+    const size_t bytes = (size_t)c->total * elem_bytes(c->prec);
+    for (int64_t r = 0; r < n; r++) {
+        const int64_t s = A.t - 1;  // recorded step being reversed
+        if (!(s >= A.seg_lo && s < A.seg_lo + A.seg_n)) {
+            wave_status st = adjoint_replay(c, s / A.K);
+            if (st) return st;
+        }
+        cudaError_t e = adj_inject(static_cast<float *>(A.mu.ptr), static_cast<const int64_t *>(c->rec_q.ptr),
+                                   static_cast<const float *>(A.rec_w.ptr), residual + s * c->nrec, (int)c->nrec,
+                                   c->stream);
+        if (e == cudaSuccess)
+            e = stream_ok ? acoustic_stream_half_step(prm, PREC_FP32, 0, 0, c->zchunk, c->stream)
+                          : acoustic_generic_half_step(prm, c->ndim, PREC_FP32, 0, 0, c->stream);
+        const int64_t gstep = A.step0 + s;
+        gp.src_q = (c->src_q >= 0 && gstep < c->src_nt) ? c->src_q : -1;
+        gp.src_value = gp.src_q >= 0 ? c->src_host[gstep] : 0.f;
+        for (int ax = 0; ax < c->ndim; ax++)
+            gp.v[ax] = static_cast<const char *>(A.seg.ptr) + (size_t)((s - A.seg_lo) * c->ndim + ax) * bytes;
+        if (e == cudaSuccess) e = adj_grad(gp, c->ndim, fmt, c->stream);
+        if (e == cudaSuccess)
+            e = stream_ok ? acoustic_stream_half_step(prm, PREC_FP32, 0, 1, c->zchunk, c->stream)
+                          : acoustic_generic_half_step(prm, c->ndim, PREC_FP32, 0, 1, c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "adjoint step");
+        A.t--;
+    }
+    // the forward fields show the end of the recorded run again
+    cudaError_t e = snapshot_copy(c, A.ncp, false);
+    c->step = A.cp_step[A.ncp];
+    return cuda_check(c, e, "end state restore");
+}
+
+extern "C" wave_status wave_get_gradient(wave_ctx *c, float *device_out, int64_t *steps_left) {
+    CHECK_CTX(c);
+    auto &A = c->adj;
+    if (!A.active) return fail(WAVE_ESTATE, "no recorded run: call wave_record first");
+    if (steps_left) *steps_left = A.t;
+    if (!device_out) return WAVE_OK;
+    int n[3] = {(int)c->n[0], (int)c->n[1], (int)c->n[2]};
+    cudaError_t e = adj_finish(device_out, static_cast<const float *>(A.g.ptr),
+                               static_cast<const float *>(A.two_over_c.ptr), n, c->pitch, c->plane, c->stream);
+    return cuda_check(c, e, "gradient");
 }
 
 // ------------------------------------------------------------------ batches

@@ -35,7 +35,8 @@ EXPORTS = ["wave_set_allocator", "wave_create", "wave_set_initial", "wave_set_so
            "wave_get_state", "wave_set_state", "wave_sync", "wave_steps_done",
            "wave_adjoint_step", "wave_destroy", "wave_last_error", "wave_build_info",
            "wave_set_timing", "wave_get_timing", "wave_energy_acoustic_static",
-           "wave_batch_create", "wave_batch_step", "wave_batch_info", "wave_batch_destroy"]
+           "wave_batch_create", "wave_batch_step", "wave_batch_info", "wave_batch_destroy",
+           "wave_record", "wave_get_gradient"]
 
 
 class WaveError(RuntimeError):
@@ -97,6 +98,8 @@ def lib() -> C.CDLL:
         "wave_get_timing": [vp, i32, C.POINTER(C.c_int64), dp],
         "wave_energy_acoustic_static": [i32, C.POINTER(C.c_int64), C.c_int, vp, vp,
                                         C.POINTER(vp), C.POINTER(vp), vp, C.c_double, vp, vp],
+        "wave_record": [vp, i64, i64],
+        "wave_get_gradient": [vp, vp, C.POINTER(C.c_int64)],
         "wave_batch_create": [i32, C.POINTER(vp), C.POINTER(vp)],
         "wave_batch_step": [vp, i64],
         "wave_batch_info": [vp, C.POINTER(C.c_int32), i32],
@@ -131,6 +134,11 @@ def _check(st: int):
 def _f64(a):
     a = np.ascontiguousarray(a, dtype=np.float64)
     return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _torch():
+    import torch
+    return torch
 
 
 class Context:
@@ -290,9 +298,30 @@ def wave_steps_done(ctx: Context) -> int:
     return s.value
 
 
+def wave_record(ctx: Context, nsteps: int, ncheckpoints: int = 0):
+    """Forward run of nsteps steps with checkpoints for the adjoint."""
+    _check(lib().wave_record(ctx.ptr, int(nsteps), int(ncheckpoints)))
+
+
 def wave_adjoint_step(ctx: Context, n: int, residual=None):
-    ptr = None if residual is None else C.c_void_p(residual.data_ptr())
+    """n adjoint steps; residual: device float32 tensor [nsteps, nrec]."""
+    ptr = None
+    if residual is not None:
+        if residual.dtype != _torch().float32 or not residual.is_cuda or not residual.is_contiguous():
+            raise TypeError("residual must be a contiguous float32 CUDA tensor")
+        ptr = C.c_void_p(residual.data_ptr())
     _check(lib().wave_adjoint_step(ctx.ptr, int(n), ptr))
+
+
+def wave_get_gradient(ctx: Context, out=None):
+    """dJ/dc as a float32 CUDA tensor shaped like the fields ((z,) y, x);
+    returns (gradient, adjoint steps left)."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(tuple(ctx.n[:ctx.ndim][::-1]), dtype=torch.float32, device="cuda")
+    left = C.c_int64()
+    _check(lib().wave_get_gradient(ctx.ptr, C.c_void_p(out.data_ptr()), C.byref(left)))
+    return out, left.value
 
 
 def wave_set_timing(ctx: Context, enable: bool):
