@@ -264,6 +264,67 @@ def run_batched(W, steps: int, warmup: int, nshots: int = 64):
             "finite": bool(np.all(np.isfinite(e1))), "energy_min": float(min(e1))}
 
 
+def run_adjoint(W, steps: int, n: int = 256, nshots: int = 16):
+    """Gradient of the trace misfit for the 3D inversion experiment (256^3,
+    16 shots x 64 receivers): per shot, the recorded fp16 + sum_3op forward
+    run with ceil(sqrt(steps)) checkpoints, the residual, the binary32 adjoint
+    with replayed segments, and the gradient added to the total. Observed
+    traces come from the true model (not timed). Value: shots * n^3 * steps
+    per second of the timed region (forward-equivalent point-updates)."""
+    import torch
+    from paper_2310_00236_gb300 import inputs
+    w = inputs.acoustic_3d_adjoint(n=n, steps=steps)
+    stream = torch.cuda.current_stream()
+    amp = 0.5 * w["P0"] * w["h"] ** 2 / w["z0"]
+    nrec = len(w["receivers"])
+
+    def shot_ctx(c, src):
+        ctx = W.wave_create(w["shape"], w["h"], w["rho"], c, w["dt"], W.WAVE_FP16, W.WAVE_COMP_3OP,
+                            bc=[W.WAVE_BC_RIGID] * 6, field_scale=w["P0"], stream=stream.cuda_stream)
+        W.wave_set_source(ctx, W.WAVE_F_P, src, w["wavelet"] * amp)
+        tr = torch.zeros((steps, nrec), dtype=torch.float32, device="cuda")
+        W.wave_set_receivers(ctx, W.WAVE_F_P, w["receivers"], tr, steps)
+        return ctx, tr
+
+    shots = w["shots"][:nshots]
+    d_obs = []
+    for src in shots:
+        ctx, tr = shot_ctx(w["c_true"], src)
+        try:
+            W.wave_step(ctx, steps)
+            torch.cuda.synchronize()
+            d_obs.append(tr)
+        finally:
+            W.wave_destroy(ctx)
+    grad = torch.zeros(tuple(w["shape"][::-1]), dtype=torch.float32, device="cuda")
+    ms_total, J = 0.0, 0.0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for si, src in enumerate(shots):
+        ctx, tr = shot_ctx(w["c0"], src)
+        try:
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            W.wave_record(ctx, steps, 0)
+            res = (tr - d_obs[si]).contiguous()
+            W.wave_adjoint_step(ctx, steps, res)
+            g, _ = W.wave_get_gradient(ctx)
+            grad += g
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms_total += ev0.elapsed_time(ev1)
+            J += 0.5 * float((res.double() ** 2).sum())
+        finally:
+            W.wave_destroy(ctx)
+    gn = float(torch.linalg.vector_norm(grad))
+    return {"workload": "3d_acoustic_adjoint_256_16shots_64rec", "n": n, "shots": len(shots),
+            "receivers": nrec, "steps": steps, "checkpoints": int(np.ceil(np.sqrt(steps))),
+            "forward": "fp16+sum_3op", "adjoint": "fp32",
+            "value": len(shots) * n ** 3 * steps / (ms_total * 1e-3) / 1e9, "unit": UNIT + " (gradient)",
+            "ms_per_shot": ms_total / len(shots), "misfit": J, "grad_norm": gn,
+            "finite": bool(np.isfinite(gn) and gn > 0)}
+
+
 # ------------------------------------------------------------ CPU oracle
 def oracle_sample(target_s: float = 12.0, n: int = 64):
     """The CPU oracle (fp16 + sum_3op emulation, OpenMP on all host cores) on a
@@ -416,7 +477,9 @@ def main():
 
     elastic = None
     batched = None
+    adjoint = None
     if not args.no_compare:
+        adjoint = run_adjoint(W, min(args.steps, 1500))
         elastic = run_elastic(W, min(args.steps, 4000), args.warmup)
         batched = run_batched(W, min(args.steps, 3000), args.warmup)
         batched["frac"] = batched["hbm_gbs_algorithmic"] / peak
@@ -443,7 +506,7 @@ def main():
                            "l2": "working set 2.4 GB > L2 (no flush needed)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": sum(v[0] for v in kt.values()), "compare": compare,
-                "elastic": elastic, "batched": batched,
+                "elastic": elastic, "batched": batched, "adjoint": adjoint,
                 "energy_drift": drift16}
         print(json.dumps(line), flush=True)
 

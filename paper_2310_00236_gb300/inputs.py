@@ -123,6 +123,40 @@ def acoustic_3d_random(n: int = 512, steps: int = 1000, cfl: float = 0.4, h: flo
                 p0=gaussian(shape, h, ic_sigma_cells * h), P0=1.0)
 
 
+def gaussian_smooth(field: np.ndarray, sigma_cells: float) -> np.ndarray:
+    """Periodic Gaussian filter of a (z, y, x) or (y, x) array (FFT), the same
+    kernel smooth_random_field applies to its noise."""
+    spec = np.fft.rfftn(field)
+    shp = field.shape
+    for ax, n in enumerate(shp):
+        k = np.fft.rfftfreq(n) if ax == len(shp) - 1 else np.fft.fftfreq(n)
+        g = np.exp(-2.0 * (np.pi * sigma_cells * k) ** 2)
+        s = [1] * len(shp)
+        s[ax] = g.size
+        spec *= g.reshape(s)
+    return np.ascontiguousarray(np.fft.irfftn(spec, s=shp, axes=tuple(range(len(shp)))))
+
+
+def acoustic_3d_adjoint(n: int = 256, steps: int = 1500, h: float = 10.0, cfl: float = 0.4,
+                        f0: float = 10.0, rho: float = 1000.0, vmin: float = 1500.0,
+                        vmax: float = 4500.0, start_sigma_cells: float = 32.0):
+    """3D acoustic inversion experiment: the smooth random velocity of
+    acoustic_3d_random (seed 0, filter width 16 n / 512 cells) as the true
+    model, the true model Gaussian-filtered with start_sigma_cells as the
+    start model, constant density, rigid walls, 16 shots on a 4 x 4 grid and 64
+    receivers on an 8 x 8 grid, both at depth index 2 (z), Ricker f0 sources,
+    dt = cfl h / vmax. Index tuples are (i, j, k)."""
+    shape = (n, n, n)
+    c_true = smooth_random_field(shape, 0, 16.0 * n / 512, vmin, vmax)
+    c0 = np.clip(gaussian_smooth(c_true, start_sigma_cells), vmin, vmax)
+    dt = cfl * h / vmax
+    shots = [(int(n * (a + 0.5) / 4), int(n * (b + 0.5) / 4), 2) for b in range(4) for a in range(4)]
+    recs = [(int(n * (a + 0.5) / 8), int(n * (b + 0.5) / 8), 2) for b in range(8) for a in range(8)]
+    return dict(ndim=3, shape=shape, h=h, dt=dt, steps=steps, rho=np.full(c_true.shape, rho),
+                c_true=c_true, c0=np.ascontiguousarray(c0), shots=shots, receivers=recs,
+                wavelet=ricker_table(steps, dt, f0), P0=1.0, z0=rho * vmax)
+
+
 def shot_sides(nshots: int = 64, seed: int = 1, lo: int = 256, hi: int = 2048) -> np.ndarray:
     """Grid sides of a batch of 2D shots: uniform integers in [lo, hi] from
     numpy's PCG64 with the given seed."""
