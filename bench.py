@@ -417,6 +417,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--zchunk", type=int, default=0, help="z planes per block (0: library default)")
+    ap.add_argument("--shots", type=int, default=16, help="shots of the adjoint leg")
+    ap.add_argument("--leg", default="all", choices=["all", "batched", "adjoint", "elastic"],
+                    help="run one secondary workload alone and print its JSON (profiling aid)")
     ap.add_argument("--kernel", type=int, default=0,
                     help="0 automatic, 1 one-thread-per-point, 2 two-kernel streaming")
     args = ap.parse_args()
@@ -436,6 +439,17 @@ def main():
     if not os.path.exists(B.LIB):
         raise SystemExit("libwave.so missing: run __graft_entry__.build() first")
     W.lib()
+
+    if args.leg != "all":
+        if args.leg == "batched":
+            out = run_batched(W, args.steps, args.warmup)
+        elif args.leg == "adjoint":
+            out = run_adjoint(W, args.steps, n=args.n if args.n != 512 else 256, nshots=args.shots)
+        else:
+            out = run_elastic(W, args.steps, args.warmup)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
 
     w = workload(args.n)
     npts = int(np.prod(w["shape"]))

@@ -501,8 +501,11 @@ __global__ void __launch_bounds__(160, 3)
                 R = V::add(R, Dz);
                 if (k == prm.src_k && j == prm.src_j && prm.src_i >= x && prm.src_i < x + VEC &&
                     prm.step < prm.src_nt) {
-                    const int e = prm.src_i - x;
-                    V::set(R, e, P::add(V::aget(R, e), static_cast<const typename V::AS *>(prm.src)[prm.step]));
+                    const typename V::AS sv_ = static_cast<const typename V::AS *>(prm.src)[prm.step];
+                    // element index known at compile time: R stays in registers
+#pragma unroll
+                    for (int e = 0; e < VEC; e++)
+                        if (e == prm.src_i - x) V::set(R, e, P::add(V::aget(R, e), sv_));
                 }
                 const Raw bv = prm.b ? vec_at(ost + SH::O_B + row * TX + lx * VEC) : V::zero();
                 const AV bc = prm.b ? V::ld(bv) : V::splat(V::lds(b_raw));

@@ -249,9 +249,11 @@ __global__ void __launch_bounds__(TXV *TY) kp_stream(AcParams prm, int zchunk) {
             R = V::add(R, Dz);
             if (k == prm.src_k && j == prm.src_j && prm.src_i >= x && prm.src_i < x + N &&
                 prm.step < prm.src_nt) {
-                const int e = prm.src_i - x;
                 const typename V::AS sv_ = static_cast<const typename V::AS *>(prm.src)[prm.step];
-                V::set(R, e, P::add(V::aget(R, e), sv_));
+                // element index known at compile time: R stays in registers
+#pragma unroll
+                for (int e = 0; e < N; e++)
+                    if (e == prm.src_i - x) V::set(R, e, P::add(V::aget(R, e), sv_));
             }
             AV inc = V::mul(coef_vec<V>(prm.b, prm.b_uni, q), R);
             Raw pold = pv;
