@@ -523,15 +523,20 @@ __global__ void __launch_bounds__(160, 3)
                     at<V>(fp.tvy_out, q) = tyn;
                 }
                 if (ENERGY) {
-                    const float aw0 = P::to_f32(a_raw[0]), aw1 = P::to_f32(a_raw[1]), aw2 = P::to_f32(a_raw[2]);
+                    // v^2 / a with the uniform a as a product by its reciprocal;
+                    // the four terms of a point summed in binary32, then added
+                    // to the compensated accumulator
+                    const float ia0 = __frcp_rn(P::to_f32(a_raw[0])), ia1 = __frcp_rn(P::to_f32(a_raw[1])),
+                                ia2 = __frcp_rn(P::to_f32(a_raw[2]));
 #pragma unroll
                     for (int e = 0; e < VEC; e++) {
                         const float bw = prm.b ? V::f32(bv, e) : P::to_f32(b_raw);
-                        eadd(e_term(V::f32(pold, e), V::f32(pn, e), bw));
                         const float fx = V::f32(vxn, e), fy = V::f32(vyn, e), fz = V::f32(vzq2, e);
-                        eadd(e_term(fx, fx, aw0));
-                        eadd(e_term(fy, fy, aw1));
-                        eadd(e_term(fz, fz, aw2));
+                        float t = e_term(V::f32(pold, e), V::f32(pn, e), bw);
+                        t = __fadd_rn(t, __fmul_rn(__fmul_rn(fx, fx), ia0));
+                        t = __fadd_rn(t, __fmul_rn(__fmul_rn(fy, fy), ia1));
+                        t = __fadd_rn(t, __fmul_rn(__fmul_rn(fz, fz), ia2));
+                        eadd(t);
                     }
                 }
             }

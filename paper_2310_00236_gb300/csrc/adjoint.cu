@@ -27,15 +27,21 @@
 
 namespace wave {
 
-// mu[q_r] += w_r * res[r] for every receiver, in receiver order (one thread:
-// receivers may share a point, and the order fixes the rounding).
-__global__ void adj_inject_kernel(float *mu, const int64_t *rec_q, const float *rec_w, const float *res,
-                                  int nrec) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    for (int r = 0; r < nrec; r++) {
+// mu[q_r] += w_r * res[r] for every receiver. One thread per distinct point:
+// group g holds receivers order[start[g] .. start[g+1]) (ascending receiver
+// index), so points shared by several receivers add them in receiver order.
+__global__ void adj_inject_kernel(float *mu, const int64_t *rec_q, const float *rec_w, const int *order,
+                                  const int *start, int ngroups, const float *res) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ngroups) return;
+    const int r0 = order[start[g]];
+    float acc = mu[rec_q[r0]];
+    for (int u = start[g]; u < start[g + 1]; u++) {
+        const int r = order[u];
         const float w = rec_w[r];
-        if (w != 0.f) mu[rec_q[r]] = __fadd_rn(mu[rec_q[r]], __fmul_rn(w, res[r]));
+        if (w != 0.f) acc = __fadd_rn(acc, __fmul_rn(w, res[r]));
     }
+    mu[rec_q[r0]] = acc;
 }
 
 template <int FMT>
@@ -91,10 +97,10 @@ __global__ void adj_finish_kernel(float *out, const float *g, const float *two_o
     }
 }
 
-cudaError_t adj_inject(float *mu, const int64_t *rec_q, const float *rec_w, const float *res, int nrec,
-                       cudaStream_t st) {
-    if (nrec <= 0) return cudaSuccess;
-    adj_inject_kernel<<<1, 32, 0, st>>>(mu, rec_q, rec_w, res, nrec);
+cudaError_t adj_inject(float *mu, const int64_t *rec_q, const float *rec_w, const int *order, const int *start,
+                       int ngroups, const float *res, cudaStream_t st) {
+    if (ngroups <= 0) return cudaSuccess;
+    adj_inject_kernel<<<(ngroups + 127) / 128, 128, 0, st>>>(mu, rec_q, rec_w, order, start, ngroups, res);
     return cudaGetLastError();
 }
 

@@ -228,6 +228,8 @@ struct wave_ctx {
         DevBuf na[3], nb;             // negated multipliers (binary32) where per-point
         uint32_t na_uni[3] = {0, 0, 0}, nb_uni = 0;
         DevBuf rec_w;                 // residual weight per receiver (b, 0 on rigid walls)
+        DevBuf rec_order, rec_start;  // receivers grouped by point, in receiver order
+        int ngroups = 0;
         DevBuf two_over_c;            // device copy, unpitched
     } adj;
 };
@@ -536,6 +538,8 @@ static void adjoint_free(wave_ctx *c) {
     dev_free(c, A.g);
     dev_free(c, A.nb);
     dev_free(c, A.rec_w);
+    dev_free(c, A.rec_order);
+    dev_free(c, A.rec_start);
     dev_free(c, A.two_over_c);
     for (int ax = 0; ax < 3; ax++) {
         dev_free(c, A.nu[ax]);
@@ -953,14 +957,15 @@ extern "C" wave_status wave_energy(wave_ctx *c, double *E) {
 }
 
 // -------------------------------------------------------------------- step
-static wave_status acoustic_steps(wave_ctx *c, int64_t n) {
+// energy_last: reduce the discrete energy on the last step (wave_energy reads it)
+static wave_status acoustic_steps(wave_ctx *c, int64_t n, bool energy_last = true) {
     AcParams prm;
     fill_acoustic_params(c, prm);
     const size_t eb = elem_bytes(c->prec);
     for (int64_t s = 0; s < n; s++) {
         prm.step = c->step;
         const bool trace = c->e_trace && c->e_trace_pos < c->e_trace_cap;
-        prm.energy = (s == n - 1) || trace;
+        prm.energy = (energy_last && s == n - 1) || trace;
         prm.e_out = static_cast<double *>(c->e_misc.ptr);
         if (c->use_fused) {
             const void *in[7] = {c->f[0].ptr, c->f[1].ptr, c->f[2].ptr, c->f[3].ptr,
@@ -1296,9 +1301,25 @@ extern "C" wave_status wave_record(wave_ctx *c, int64_t nsteps, int64_t ncheckpo
             const int64_t u = idx[0] + c->n[0] * (idx[1] + c->n[1] * idx[2]);
             w[r] = wall ? 0.f : (float)c->coef_host[0][c->coef_is_uniform[0] ? 0 : u];
         }
+        // group the receivers by point (stable: receiver order within a point)
+        std::vector<int> order(c->nrec), start;
+        for (int64_t r = 0; r < c->nrec; r++) order[r] = (int)r;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return q[a] < q[b]; });
+        for (int64_t u = 0; u < c->nrec; u++)
+            if (u == 0 || q[order[u]] != q[order[u - 1]]) start.push_back((int)u);
+        A.ngroups = (int)start.size();
+        start.push_back((int)c->nrec);
         st = dev_alloc(c, A.rec_w, w.size() * sizeof(float));
+        if (!st) st = dev_alloc(c, A.rec_order, order.size() * sizeof(int));
+        if (!st) st = dev_alloc(c, A.rec_start, start.size() * sizeof(int));
         if (!st) {
             e = cudaMemcpyAsync(A.rec_w.ptr, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(A.rec_order.ptr, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                    c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(A.rec_start.ptr, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                    c->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
             st = cuda_check(c, e, "receiver weights");
         }
@@ -1349,7 +1370,7 @@ static wave_status adjoint_replay(wave_ctx *c, int64_t si) {
     const size_t bytes = (size_t)c->total * elem_bytes(c->prec);
     wave_status st = WAVE_OK;
     for (int64_t m = 0; m < len && !st; m++) {
-        st = acoustic_steps(c, 1);
+        st = acoustic_steps(c, 1, false);
         for (int ax = 0; ax < c->ndim && !st; ax++) {
             e = cudaMemcpyAsync(static_cast<char *>(A.seg.ptr) + (size_t)(m * c->ndim + ax) * bytes, c->f[1 + ax].ptr,
                                 bytes, cudaMemcpyDeviceToDevice, c->stream);
@@ -1407,7 +1428,8 @@ extern "C" wave_status wave_adjoint_step(wave_ctx *c, int64_t n, const float *re
             if (st) return st;
         }
         cudaError_t e = adj_inject(static_cast<float *>(A.mu.ptr), static_cast<const int64_t *>(c->rec_q.ptr),
-                                   static_cast<const float *>(A.rec_w.ptr), residual + s * c->nrec, (int)c->nrec,
+                                   static_cast<const float *>(A.rec_w.ptr), static_cast<const int *>(A.rec_order.ptr),
+                                   static_cast<const int *>(A.rec_start.ptr), A.ngroups, residual + s * c->nrec,
                                    c->stream);
         if (e == cudaSuccess)
             e = stream_ok ? acoustic_stream_half_step(prm, PREC_FP32, 0, 0, c->zchunk, c->stream)

@@ -25,7 +25,8 @@ R, P = W.WAVE_BC_RIGID, W.WAVE_BC_PERIODIC
 
 def _case(shape, bc, nsteps, seed=0, const_rho=False):
     """Smooth random true and start models, Ricker source near the y = 0 (2D)
-    or z = 0 (3D) face, receivers at seeded nodes (one on a wall node)."""
+    or z = 0 (3D) face, receivers at seeded nodes (one on a wall node, two
+    sharing a point)."""
     nd = len(shape)
     h = 10.0
     dt = 0.4 * h / 4500.0
@@ -42,6 +43,7 @@ def _case(shape, bc, nsteps, seed=0, const_rho=False):
     rng = np.random.default_rng(seed + 3)
     rec = [tuple(int(rng.integers(1, s - 1)) for s in shape) for _ in range(9)]
     rec.append(tuple([0] + [s // 3 for s in shape[1:]]))  # on the x = 0 face
+    rec.append(rec[1])  # two receivers on one point
     return dict(shape=shape, bc=bc, nd=nd, h=h, dt=dt, rho=rho, c_true=c_true, c0=c0, wav=wav,
                 src=src, rec=rec, nsteps=nsteps)
 
