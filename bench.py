@@ -48,6 +48,12 @@ BYTES = {
 #   pressure: read v(2) + p + t_p + b, write p + t_p         = 4 + 6 + 4
 BYTES_2D = (2 + 8 + 8) + (4 + 6 + 4)
 
+# DRAM bytes per grid point of one launch (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture on a 256^3 case, divided by the
+# points; traffic grows with the points). Kept only while the kernel is the one
+# that was captured: profiles/acoustic3d_fused_fp16_kahan_512.md.
+MEASURED_TRAFFIC_PER_POINT = {("fp16", True, "fused"): 550.07e6 / 256 ** 3}
+
 KERNEL_NAMES = {"kv": "velocity half step", "kp": "pressure half step",
                 "fused": "one-pass step (both half steps)"}
 
@@ -475,7 +481,9 @@ def main():
     achieved = bpp * npts / (kms / nl * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": KERNEL_NAMES[dom],
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_kind": peak_kind, "traffic": None,
+            "peak_kind": peak_kind,
+            "traffic": (MEASURED_TRAFFIC_PER_POINT[("fp16", True, dom)] * npts
+                        if ("fp16", True, dom) in MEASURED_TRAFFIC_PER_POINT else None),
             "bytes_per_point": bpp, "ms_per_launch": kms / nl,
             "shares": {k: kt[k][1] / sum(v[1] for v in kt.values()) for k in kt}}
     drift16 = abs(r16["e1"] - r16["e0"]) / abs(r16["e0"])

@@ -112,11 +112,14 @@ typedef struct {
                             (Z0 = max(rho) * max(vp)); default 1.0 */
     int32_t kernel;      /* 0: automatic (3D: the one-pass step where it applies, else
                             the two-kernel streaming step when n[0] is a multiple of
-                            the 16-byte vector width, else one thread per point);
+                            the 16-byte vector width, else one thread per point;
+                            2D acoustic: row strips, one warp per strip of 16-byte
+                            vectors, any size);
                             1: one-thread-per-point kernels only; 2: two-kernel
                             streaming step; 3: one-pass step (both half steps in one
                             kernel; needs n[0] a multiple of 64 (32 for binary32),
-                            rigid x faces and a uniform density, else as 0) */
+                            rigid x faces and a uniform density, else as 0).
+                            Every choice gives the same bits. */
     int32_t zchunk;      /* z planes per thread block of the 3D kernels (0: automatic) */
     int32_t reserved[6];
 } wave_options;
@@ -266,7 +269,8 @@ wave_status wave_steps_done(wave_ctx *ctx, int64_t *steps);
  * on the context's stream. wave_get_timing synchronises and returns, for one
  * kernel kind, the launches and their summed device time (milliseconds) since
  * timing was last enabled. Kinds: 0 velocity half step, 1 pressure (or stress)
- * half step including source and energy, 2 receiver sampling. Enabling resets
+ * half step including source and energy, 2 receiver sampling, 3 a whole step
+ * in one launch sequence (3D one-pass kernel, 2D row strips). Enabling resets
  * the totals. Not part of the method; a measurement aid. */
 wave_status wave_set_timing(wave_ctx *ctx, int32_t enable);
 wave_status wave_get_timing(wave_ctx *ctx, int32_t kind, int64_t *launches, double *ms);

@@ -156,6 +156,9 @@ static void parallel_for(int64_t n, F f) {
     for (auto &x : th) x.join();
 }
 
+// Launch shape of the row-strip kernels for single 2D problems.
+constexpr int kStripRows = 16, kStripWarps = 4;
+
 // ---------------------------------------------------------------- context
 struct wave_ctx {
     int kind = WAVE_ACOUSTIC;
@@ -169,6 +172,10 @@ struct wave_ctx {
     bool zchunk_set = false;
     bool use_stream = false;
     bool use_fused = false;
+    // 2D: the row-strip kernels of the batches, as a batch of one
+    bool use_strips = false;
+    int strip_items = 0, strip_grid = 0;
+    DevBuf strip_shot, strip_item0, strip_part;
     // second set of p, vx, vy, vz and t_vx, t_vy, t_vz for the one-pass step,
     // and the tensor maps of both sets (fset: the set the fields point to now)
     DevBuf alt_f[4], alt_t[4];
@@ -550,6 +557,9 @@ static void adjoint_free(wave_ctx *c) {
 
 static void destroy_ctx(wave_ctx *c) {
     if (!c) return;
+    dev_free(c, c->strip_shot);
+    dev_free(c, c->strip_item0);
+    dev_free(c, c->strip_part);
     for (auto &b : c->f) dev_free(c, b);
     for (auto &b : c->t) dev_free(c, b);
     for (auto &b : c->coef) dev_free(c, b);
@@ -652,6 +662,25 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
         c->use_stream = !c->use_fused && kchoice != 1 &&
                         acoustic_stream_supported(prm, c->ndim, c->prec);
         if (c->use_fused && !c->zchunk_set) c->zchunk = 16;
+        if (c->ndim == 2 && kchoice != 1) {
+            // row strips of 16 rows, 4 warps per block, at most 16 blocks per SM
+            c->use_strips = true;
+            c->strip_items = (int)batch_items_of(BATCH_STRIPS, 0, 0, kStripRows, c->prec, c->n[0], c->n[1]);
+            int dev = 0, sms = 1;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            c->strip_grid = std::max(1, std::min((c->strip_items + kStripWarps - 1) / kStripWarps, 16 * sms));
+            const int item0[2] = {0, c->strip_items};
+            st = dev_alloc(c, c->strip_shot, sizeof(BatchShot));
+            if (!st) st = dev_alloc(c, c->strip_item0, sizeof(item0));
+            if (!st) st = dev_alloc(c, c->strip_part, sizeof(double) * (size_t)c->strip_items);
+            if (!st) {
+                cudaError_t e = cudaMemcpyAsync(c->strip_item0.ptr, item0, sizeof(item0), cudaMemcpyHostToDevice,
+                                                c->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+                if (e != cudaSuccess) st = fail(WAVE_ECUDA, "wave_create: %s", cudaGetErrorString(e));
+            }
+        }
         if (c->use_stream)
             c->e_blocks = std::max(c->e_blocks, acoustic_stream_blocks(prm, c->prec, c->zchunk));
         if (c->use_fused) {
@@ -962,11 +991,47 @@ static wave_status acoustic_steps(wave_ctx *c, int64_t n, bool energy_last = tru
     AcParams prm;
     fill_acoustic_params(c, prm);
     const size_t eb = elem_bytes(c->prec);
+    BatchLaunch L;
+    if (c->use_strips) {
+        BatchShot shot;
+        shot.prm = prm;
+        shot.step = c->step;
+        cudaError_t e = cudaMemcpyAsync(c->strip_shot.ptr, &shot, sizeof shot, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "wave_step upload");
+        L.shots = static_cast<BatchShot *>(c->strip_shot.ptr);
+        L.item0 = static_cast<const int *>(c->strip_item0.ptr);
+        L.item_part = static_cast<double *>(c->strip_part.ptr);
+        L.nshots = 1;
+        L.nitems = c->strip_items;
+        L.kind = BATCH_STRIPS;
+        L.bx = L.by = 0;
+        L.yc = kStripRows;
+        L.wpb = kStripWarps;
+        L.grid = c->strip_grid;
+    }
     for (int64_t s = 0; s < n; s++) {
         prm.step = c->step;
         const bool trace = c->e_trace && c->e_trace_pos < c->e_trace_cap;
         prm.energy = (energy_last && s == n - 1) || trace;
         prm.e_out = static_cast<double *>(c->e_misc.ptr);
+        if (c->use_strips) {
+            cudaEvent_t m0 = mark(c);
+            cudaError_t e = batch_step(L, c->prec, c->comp, prm.energy != 0, c->stream);
+            cudaEvent_t m1 = mark(c);
+            timed(c, 3, m0, m1);
+            if (e == cudaSuccess && trace)
+                e = cudaMemcpyAsync(c->e_trace + c->e_trace_pos, c->e_misc.ptr, sizeof(double),
+                                    cudaMemcpyDeviceToDevice, c->stream);
+            if (e == cudaSuccess && c->nrec && c->rec_pos < c->rec_cap)
+                e = sample_receivers(c->f[c->rec_field].ptr, (int)eb, is_bf16_storage(c->prec),
+                                     static_cast<const int64_t *>(c->rec_q.ptr), (int)c->nrec,
+                                     c->rec_traces + c->rec_pos * c->nrec, c->stream);
+            if (e != cudaSuccess) return cuda_check(c, e, "wave_step launch");
+            if (trace) c->e_trace_pos++;
+            if (c->nrec && c->rec_pos < c->rec_cap) c->rec_pos++;
+            c->step++;
+            continue;
+        }
         if (c->use_fused) {
             const void *in[7] = {c->f[0].ptr, c->f[1].ptr, c->f[2].ptr, c->f[3].ptr,
                                  c->t[1].ptr, c->t[2].ptr, c->t[3].ptr};
