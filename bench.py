@@ -331,6 +331,59 @@ def run_adjoint(W, steps: int, n: int = 256, nshots: int = 16):
             "finite": bool(np.isfinite(gn) and gn > 0)}
 
 
+def w0_run(W, precision, comp, refine=1, steps=None, energy=True):
+    """One run of the paper's acoustic accuracy experiment (W0) on the GPU:
+    the receiver trace and (energy=True) the energy after every step."""
+    import torch
+    from paper_2310_00236_gb300 import inputs
+    w = inputs.acoustic_2d_w0(refine, steps=steps)
+    n = w["steps"]
+    ctx = W.wave_create(w["shape"], w["h"], w["rho"], w["c"], w["dt"], precision, comp,
+                        bc=[W.WAVE_BC_PERIODIC] * 4 + [0, 0],
+                        stream=torch.cuda.current_stream().cuda_stream)
+    try:
+        # the same physical source on every grid; on the 10-point grid the
+        # scaled increment peaks at 0.5
+        amp = 0.5 * (1.0 / 125.0)
+        W.wave_set_source(ctx, W.WAVE_F_P, w["src_idx"], w["wavelet"] * amp)
+        tr = torch.zeros((n, 1), dtype=torch.float32, device="cuda")
+        W.wave_set_receivers(ctx, W.WAVE_F_P, [w["rec_idx"]], tr, n)
+        en = torch.zeros(n if energy else 1, dtype=torch.float64, device="cuda")
+        if energy:
+            W.wave_set_energy_trace(ctx, en, n)
+        W.wave_step(ctx, n)
+        torch.cuda.synchronize()
+        return tr.cpu().numpy()[:, 0].astype(np.float64), en.cpu().numpy(), w
+    finally:
+        W.wave_destroy(ctx)
+
+
+def run_w0(W, steps=None):
+    """W0 on the GPU path: every storage/update variant on the 10-point grid,
+    binary32 on the 10- and 30-point grids as references. Reports each trace's
+    relative L2 distance to the binary32 10-point run and to the 30-point run,
+    and the relative energy change after the source has stopped."""
+    import time as _t
+    t0 = _t.perf_counter()
+    ref10, e10, w = w0_run(W, W.WAVE_FP32, 0, 1, steps)
+    ref30, _, _ = w0_run(W, W.WAVE_FP32, 0, 3, None if steps is None else 3 * steps, energy=False)
+    ref30 = ref30[2::3][: ref10.size]
+    quiet = int(0.8 / w["dt"])  # source over (t0 = 0.24 s, 5 Hz)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    out = {"workload": "2d_acoustic_w0_600_periodic_cfl0.0125", "steps": int(w["steps"]),
+           "fp32_ppw10_vs_ppw30": rel(ref10, ref30), "variants": {}}
+    for name, prec, comp in (("fp16", W.WAVE_FP16, 0), ("fp16+3op", W.WAVE_FP16, 3), ("fp16+6op", W.WAVE_FP16, 6),
+                             ("bf16", W.WAVE_BF16, 0), ("bf16+3op", W.WAVE_BF16, 3),
+                             ("fp16/f32arith", W.WAVE_FP16_F32ARITH, 0),
+                             ("fp16/f32arith+comp", W.WAVE_FP16_F32ARITH, 3), ("fp32", W.WAVE_FP32, 0)):
+        tr, en, _ = (ref10, e10, None) if name == "fp32" else w0_run(W, prec, comp, 1, steps)
+        e_q = en[quiet:] if en.size > quiet else en
+        out["variants"][name] = {"vs_fp32_ppw10": rel(tr, ref10), "vs_ppw30": rel(tr, ref30),
+                                 "energy_change_after_source": float((e_q[-1] - e_q[0]) / e_q[0])}
+    out["seconds"] = _t.perf_counter() - t0
+    return out
+
+
 # ------------------------------------------------------------ CPU oracle
 def oracle_sample(target_s: float = 12.0, n: int = 64):
     """The CPU oracle (fp16 + sum_3op emulation, OpenMP on all host cores) on a
@@ -424,7 +477,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--zchunk", type=int, default=0, help="z planes per block (0: library default)")
     ap.add_argument("--shots", type=int, default=16, help="shots of the adjoint leg")
-    ap.add_argument("--leg", default="all", choices=["all", "batched", "adjoint", "elastic"],
+    ap.add_argument("--leg", default="all", choices=["all", "batched", "adjoint", "elastic", "w0"],
                     help="run one secondary workload alone and print its JSON (profiling aid)")
     ap.add_argument("--kernel", type=int, default=0,
                     help="0 automatic, 1 one-thread-per-point, 2 two-kernel streaming")
@@ -449,6 +502,8 @@ def main():
     if args.leg != "all":
         if args.leg == "batched":
             out = run_batched(W, args.steps, args.warmup)
+        elif args.leg == "w0":
+            out = run_w0(W)
         elif args.leg == "adjoint":
             out = run_adjoint(W, args.steps, n=args.n if args.n != 512 else 256, nshots=args.shots)
         else:

@@ -157,6 +157,22 @@ def acoustic_3d_adjoint(n: int = 256, steps: int = 1500, h: float = 10.0, cfl: f
                 wavelet=ricker_table(steps, dt, f0), P0=1.0, z0=rho * vmax)
 
 
+def acoustic_2d_w0(refine: int = 1, f0: float = 5.0, steps: int | None = None):
+    """The paper's acoustic accuracy experiment (Section 5): 600 x 600 cells of
+    h = 1/125 m (10 points per wavelength), rho = c = 1, periodic, dt = 1e-4 s
+    (CFL 0.0125), 60000 steps, Ricker f0 pressure source at node (200, 200),
+    receiver at node (400, 400). refine = 3 gives the 30-points-per-wavelength
+    grid of the same domain (h / 3, dt / 3, three times the steps, nodes x 3)."""
+    r = int(refine)
+    n = 600 * r
+    h = 1.0 / (125.0 * r)
+    dt = 1e-4 / r
+    nsteps = 60000 * r if steps is None else steps
+    return dict(ndim=2, shape=(n, n), h=h, dt=dt, steps=nsteps, rho=np.ones((n, n)), c=np.ones((n, n)),
+                src_idx=[200 * r, 200 * r], rec_idx=[400 * r, 400 * r],
+                wavelet=ricker_table(nsteps, dt, f0), refine=r)
+
+
 def shot_sides(nshots: int = 64, seed: int = 1, lo: int = 256, hi: int = 2048) -> np.ndarray:
     """Grid sides of a batch of 2D shots: uniform integers in [lo, hi] from
     numpy's PCG64 with the given seed."""
