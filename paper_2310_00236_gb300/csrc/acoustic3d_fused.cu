@@ -19,8 +19,12 @@
 // (the z stencil of v_z needs planes k..k+3) and a ring of the other arrays of
 // plane k. Row groups whose rows lie outside the grid (their images are read
 // instead) are copied row by row with bulk copies. Four consumer warps
-// compute on 16-byte vectors with packed-pair arithmetic. Every mbarrier wait
-// is bounded; on expiry the kernel sets an error word and leaves.
+// compute on 16-byte vectors with packed-pair arithmetic; each warp owns four
+// rows of the tile and recomputes the v_y rows it needs from its neighbours
+// (two above, one below), so the new velocities are exchanged only inside a
+// warp (__syncwarp) and the warps never wait for each other. t_p and b are
+// read by each thread from global memory. Every mbarrier wait is bounded; on
+// expiry the kernel sets an error word and leaves.
 //
 // Tile: TX x TY = (8 lanes x VEC) x 16 rows of (x, y) columns, a chunk of z
 // planes. Requirements (else the two-kernel path is used): 3D, n[0] a multiple
@@ -114,21 +118,26 @@ struct FShape {
     static constexpr int P_HALO = TY * WIDE;
     static constexpr int P_ELEMS = TY * WIDE + 6 * TX;
     // other arrays: vx, tvx wide own rows; vy, tvy rows y0-2..y0+TY; vz, tvz
-    // (plane k+1), tp, b own rows. Every region starts on a 128-byte boundary.
+    // (plane k+1). Every region starts on a 128-byte boundary. (t_p and b are
+    // read by the consumers straight from global memory: each thread needs only
+    // its own vector, and leaving them out of the ring lets four CTAs share an
+    // SM.)
     static constexpr int O_VX = 0;
     static constexpr int O_TVX = O_VX + TY * WIDE;
     static constexpr int O_VY = O_TVX + TY * WIDE;
     static constexpr int O_TVY = O_VY + (TY + 3) * TX;
     static constexpr int O_VZ = O_TVY + (TY + 3) * TX;
     static constexpr int O_TVZ = O_VZ + TY * TX;
-    static constexpr int O_TP = O_TVZ + TY * TX;
-    static constexpr int O_B = O_TP + TY * TX;
-    static constexpr int O_ELEMS = O_B + TY * TX;
-    // new-velocity exchange (double buffered): vx wide own rows, vy rows y0-2..y0+TY
+    static constexpr int O_ELEMS = O_TVZ + TY * TX;
+    // new-velocity exchange inside each consumer warp (no barrier between
+    // warps): vx wide rows of the tile (each warp writes and reads only its
+    // own rows), then per warp the v_y rows it reads: 2 above its 4 rows, the
+    // 4, 1 below (the neighbouring warps' rows are recomputed, not shared)
     static constexpr int N_VY = TY * WIDE;
-    static constexpr int N_ELEMS = N_VY + (TY + 3) * TX;
+    static constexpr int N_WROWS = TY / 4 + 3;
+    static constexpr int N_ELEMS = N_VY + 4 * N_WROWS * TX;
     static constexpr size_t RING_BYTES =
-        sizeof(S) * ((size_t)SP * P_ELEMS + (size_t)SO * O_ELEMS + 2 * (size_t)N_ELEMS);
+        sizeof(S) * ((size_t)SP * P_ELEMS + (size_t)SO * O_ELEMS + (size_t)N_ELEMS);
     static constexpr size_t SMEM = RING_BYTES + sizeof(uint64_t) * (2 * (SP + SO) + 1) + 128;
     static_assert((P_ELEMS * sizeof(S)) % 128 == 0 && (O_ELEMS * sizeof(S)) % 128 == 0 &&
                       (N_ELEMS * sizeof(S)) % 128 == 0 && (O_VY * sizeof(S)) % 128 == 0 &&
@@ -138,7 +147,7 @@ struct FShape {
 };
 
 struct FusedMaps {
-    CUtensorMap p_own, p_halo, vx, tvx, vy, tvy, vz, tvz, tp, b;
+    CUtensorMap p_own, p_halo, vx, tvx, vy, tvy, vz, tvz;
 };
 
 struct FusedParams {
@@ -156,7 +165,7 @@ __device__ __forceinline__ typename V::Raw signed_raw(const typename V::Raw &r, 
 }
 
 template <class P, int COMP, bool ENERGY>
-__global__ void __launch_bounds__(160, 3)
+__global__ void __launch_bounds__(160, 4)
     fused_step(const __grid_constant__ FusedParams fp, const __grid_constant__ FusedMaps maps) {
     using SH = FShape<P>;
     using S = typename P::S;
@@ -290,14 +299,6 @@ __global__ void __launch_bounds__(160, 3)
                 }
                 bytes += (TY + 3) * TX * eb;
             }
-            if (COMP) {
-                if (issue && lane == 0) tma_box(dst + SH::O_TP, &maps.tp, x0, y0, k, bar);
-                bytes += TY * TX * eb;
-            }
-            if (prm.b) {
-                if (issue && lane == 0) tma_box(dst + SH::O_B, &maps.b, x0, y0, k, bar);
-                bytes += TY * TX * eb;
-            }
             return bytes;
         };
         auto issue_p = [&](int m, int cnt) -> bool {
@@ -368,7 +369,7 @@ __global__ void __launch_bounds__(160, 3)
     };
 
     Raw vzq0 = V::zero(), vzq1 = V::zero(), vzq2 = V::zero(), vzq3 = V::zero();
-    int oc = 0, nb = 0, p_waited = 0;
+    int oc = 0, p_waited = 0;
     uint32_t c_phase = 0;
     bool ok = true;
     auto consumer_sync = [&]() -> bool {
@@ -413,8 +414,11 @@ __global__ void __launch_bounds__(160, 3)
         vzq3 = vzn;
 
         if (k >= z0) {
-            S *nvx = nbuf + nb * SH::N_ELEMS;
-            S *nvy = nvx + SH::N_VY;
+            S *nvx = nbuf;
+            // this warp's v_y exchange rows: tile rows wr0 .. wr0 + N_WROWS - 1
+            const int wr0 = warp * (TY / 4) - 2;
+            S *nvy = nbuf + SH::N_VY + warp * SH::N_WROWS * TX;
+            __syncwarp();  // this warp's reads of the previous plane's exchange rows are done
             Raw vxn = V::zero(), txn = V::zero(), vyn = V::zero(), tyn = V::zero();
             // ---- v_x^{n+1/2}: own vector, and the x halo of the tile edge lanes
             if (active) {
@@ -465,24 +469,32 @@ __global__ void __launch_bounds__(160, 3)
                 Vv = vec_at(ost + SH::O_VY + (lr + 2) * TX + ln * VEC);
                 Tv = COMP ? vec_at(ost + SH::O_TVY + (lr + 2) * TX + ln * VEC) : V::zero();
                 V::template update<COMP>(Vv, Tv, V::mul(ay, D));
-                *reinterpret_cast<Raw *>(nvy + (lr + 2) * TX + ln * VEC) = Vv;
+                *reinterpret_cast<Raw *>(nvy + (lr - wr0) * TX + ln * VEC) = Vv;
             };
             // own rows, and row ny (the image row the last grid row reads)
             if (j <= ny) vy_vec(row, lx, vyn, tyn);
             {
-                // the halo rows y0-2, y0-1, y0+TY: 3 x LANES vectors, six per warp
+                // this warp's halo rows wr0, wr0 + 1 (above) and wr0 + 6 (below):
+                // 3 x LANES vectors on lanes 0..23
                 const int wl = tid & 31;
-                if (wl < 6) {
-                    const int hidx = warp * 6 + wl;
-                    const int hr = hidx / SH::LANES, ln = hidx % SH::LANES;
-                    const int lr = hr == 0 ? -2 : (hr == 1 ? -1 : TY);
+                if (wl < 3 * SH::LANES) {
+                    const int hr = wl / SH::LANES, ln = wl % SH::LANES;
+                    const int lr = hr == 0 ? wr0 : (hr == 1 ? wr0 + 1 : wr0 + 2 + TY / 4);
                     if (y0 + lr <= ny) {
                         Raw Vh, Th;
                         vy_vec(lr, ln, Vh, Th);
                     }
                 }
             }
-            if (!consumer_sync()) { ok = false; break; }
+            // own t_p and b vectors from global memory, issued before the
+            // exchange reads so that their latency overlaps them
+            const int64_t q = x + sy * j + sz * (int64_t)k;
+            Raw tpn = V::zero(), bv = V::zero();
+            if (active) {
+                if (COMP) tpn = *reinterpret_cast<const Raw *>(static_cast<const S *>(fp.tp) + q);
+                if (prm.b) bv = __ldg(reinterpret_cast<const Raw *>(static_cast<const S *>(prm.b) + q));
+            }
+            __syncwarp();
             // ---- p^{n+1}
             if (active) {
                 const S *vrow = nvx + row * WIDE + HALO - x0;
@@ -493,9 +505,9 @@ __global__ void __launch_bounds__(160, 3)
                 const RS rr = x + VEC == nx ? vrow[nx - 1] : vrow[x + VEC];
                 AV R = vstencil<V>(V::shr2(ownx, V::lds(l1), V::lds(l0)), V::shr1(ownx, V::lds(l0)),
                                    ownx, V::shl1(ownx, V::lds(rr)));
-                const S *vyc = nvy + lx * VEC;
-                const AV Dy = vstencil<V>(V::ld(vec_at(vyc + row * TX)), V::ld(vec_at(vyc + (row + 1) * TX)),
-                                          V::ld(vec_at(vyc + (row + 2) * TX)), V::ld(vec_at(vyc + (row + 3) * TX)));
+                const S *vyc = nvy + (row - 2 - wr0) * TX + lx * VEC;  // rows row-2 .. row+1
+                const AV Dy = vstencil<V>(V::ld(vec_at(vyc)), V::ld(vec_at(vyc + TX)),
+                                          V::ld(vec_at(vyc + 2 * TX)), V::ld(vec_at(vyc + 3 * TX)));
                 R = V::add(R, Dy);
                 const AV Dz = vstencil<V>(V::ld(vzq0), V::ld(vzq1), V::ld(vzq2), V::ld(vzq3));
                 R = V::add(R, Dz);
@@ -507,13 +519,10 @@ __global__ void __launch_bounds__(160, 3)
                     for (int e = 0; e < VEC; e++)
                         if (e == prm.src_i - x) V::set(R, e, P::add(V::aget(R, e), sv_));
                 }
-                const Raw bv = prm.b ? vec_at(ost + SH::O_B + row * TX + lx * VEC) : V::zero();
                 const AV bc = prm.b ? V::ld(bv) : V::splat(V::lds(b_raw));
                 const Raw pold = p_vec(pk, row);
                 Raw pn = pold;
-                Raw tpn = COMP ? vec_at(ost + SH::O_TP + row * TX + lx * VEC) : V::zero();
                 V::template update<COMP>(pn, tpn, V::mul(bc, R));
-                const int64_t q = x + sy * j + sz * (int64_t)k;
                 at<V>(fp.p_out, q) = pn;
                 at<V>(fp.vx_out, q) = vxn;
                 at<V>(fp.vy_out, q) = vyn;
@@ -540,7 +549,6 @@ __global__ void __launch_bounds__(160, 3)
                     }
                 }
             }
-            nb ^= 1;
         }
         // release the stages this iteration consumed: the other arrays of k, p plane k
         __syncwarp();
@@ -679,8 +687,8 @@ bool acoustic_fused_encode(void *out_maps, const AcParams &prm, const void *cons
     if (ok && comp)
         ok = encode(&mp.tvx, in[4], prm.n, prm.sy, eb, wide, ty) &&
              encode(&mp.tvy, in[5], prm.n, prm.sy, eb, tx, ty + 3) &&
-             encode(&mp.tvz, in[6], prm.n, prm.sy, eb, tx, ty) && encode(&mp.tp, tp, prm.n, prm.sy, eb, tx, ty);
-    if (ok && prm.b) ok = encode(&mp.b, prm.b, prm.n, prm.sy, eb, tx, ty);
+             encode(&mp.tvz, in[6], prm.n, prm.sy, eb, tx, ty);
+    (void)tp;
     if (ok) memcpy(out_maps, &mp, sizeof mp);
     return ok;
 }
