@@ -120,7 +120,8 @@ typedef struct {
                             kernel; needs n[0] a multiple of 64 (32 for binary32),
                             rigid x faces and a uniform density, else as 0).
                             Every choice gives the same bits. */
-    int32_t zchunk;      /* z planes per thread block of the 3D kernels (0: automatic) */
+    int32_t zchunk;      /* z planes per thread block of the 3D kernels; rows per
+                            work item of the 2D row strips (0: automatic) */
     int32_t reserved[6];
 } wave_options;
 

@@ -37,4 +37,14 @@ struct ElParams {
 cudaError_t elastic_half_step(const ElParams &e, int prec, int comp, int half, cudaStream_t st);
 unsigned elastic_blocks(const int n[2]);
 
+// Row-strip kernels (elastic_strips.cu): one warp per strip of 32 16-byte
+// vectors by yc rows; the energy goes through item partials.
+struct ElStripLaunch {
+    int nitems, yc, wpb, grid;
+    double *item_part;  // [nitems]
+};
+int elastic_strip_items(int prec, int nx, int ny, int yc);
+cudaError_t elastic_strip_half_step(const ElParams &e, int prec, int comp, int half, const ElStripLaunch &L,
+                                    cudaStream_t st);
+
 }  // namespace wave

@@ -13,31 +13,10 @@
 #include <cuda_runtime.h>
 #include "acoustic_common.cuh"
 #include "elastic.h"
+#include "elastic_common.cuh"
 #include "wave_kernels.h"
 
 namespace wave {
-
-enum { EBC_PERIODIC = 0, EBC_RIGID = 1, EBC_FREE = 2 };
-
-// Image of index m along an axis with N points (see elastic.h for the rules).
-// Returns +1 / -1 (sign) or 0 (reads zero).
-__device__ __forceinline__ int emap(int m, int N, int lo, int hi, bool node, bool odd, int &out) {
-    if (m >= 0 && m < N) { out = m; return 1; }
-    const int bc = m < 0 ? lo : hi;
-    if (bc == EBC_PERIODIC) { out = m < 0 ? m + N : m - N; return 1; }
-    if (bc == EBC_FREE) return 0;
-    if (node) {
-        out = m < 0 ? -1 - m : 2 * N - 1 - m;
-        return odd ? -1 : 1;
-    }
-    if (m == -1) {
-        if (odd) return 0;
-        out = 0;
-        return 1;
-    }
-    out = m < 0 ? -2 - m : 2 * N - 2 - m;
-    return odd ? -1 : 1;
-}
 
 // Stencil of field f along axis ax at point (i, j): f node-type along ax read at
 // indices m-1..m+2, half-type at m-2..m+1.
@@ -65,8 +44,6 @@ __device__ __forceinline__ typename P::A estencil(const void *fv, const ElParams
     return stencil<P>(v[0], v[1], v[2], v[3]);
 }
 
-enum { F_VX = 0, F_VY = 1, F_SXX = 2, F_SYY = 3, F_SXY = 4 };
-enum { C_BX = 0, C_BY = 1, C_L2M = 2, C_LAM = 3, C_MU = 4 };
 
 template <class P, int COMP>
 __global__ void __launch_bounds__(128) el_v(ElParams e) {

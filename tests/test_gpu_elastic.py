@@ -36,10 +36,10 @@ def layered(shape, seed=0, smooth=True):
     return rho, np.minimum(vp, 4000.0), np.minimum(vp, 4000.0) / 1.73
 
 
-def elastic_pair(shape, bc, prec, comp, h, dt, rho, vp, vs, init, P0, src=None):
+def elastic_pair(shape, bc, prec, comp, h, dt, rho, vp, vs, init, P0, src=None, kernel=0):
     code, sfmt, afmt = PREC[prec]
     ctx = W.wave_create(shape, h, rho, vp, dt, code, comp, vs=vs, bc=list(bc) + [0, 0],
-                        kind=W.WAVE_ELASTIC, field_scale=P0)
+                        kind=W.WAVE_ELASTIC, field_scale=P0, kernel=kernel)
     st = O.elastic_setup(shape, bc, h, dt, rho, vp, vs, sfmt, comp, P0=P0, arith_fmt=afmt,
                          init=init)
     for name, fid in FIELDS:
@@ -84,7 +84,7 @@ def _init(shape, seed, P0):
             "vx": 0.02 * P0 / 1.04e7 * rng.standard_normal(g.shape)}
 
 
-def _run(shape, bc, prec, comp, steps, src=False, energy=False, seed=0):
+def _run(shape, bc, prec, comp, steps, src=False, energy=False, seed=0, kernel=0):
     h = 3.0
     rho, vp, vs = layered(shape, seed)
     dt = 0.5 * h / 4000.0
@@ -94,7 +94,8 @@ def _run(shape, bc, prec, comp, steps, src=False, energy=False, seed=0):
         z0 = float(rho.max() * vp.max())
         wav = np.sin(np.arange(steps) * 0.3) * 0.5 * P0 * h * h / (dt * z0)
         s = ([shape[0] // 2, min(10, shape[1] - 1)], wav)
-    ctx, st = elastic_pair(shape, bc, prec, comp, h, dt, rho, vp, vs, _init(shape, seed, P0), P0, s)
+    ctx, st = elastic_pair(shape, bc, prec, comp, h, dt, rho, vp, vs, _init(shape, seed, P0), P0, s,
+                           kernel=kernel)
     try:
         W.wave_step(ctx, steps)
         _, E = st.run(steps, energy=energy)
@@ -114,15 +115,27 @@ VARIANTS = [("fp16", 0), ("fp16", 3), ("fp16", 6), ("bf16", 3), ("bf16", 6), ("f
 BCS = [(RIG, RIG, FREE, RIG), (PER, PER, FREE, RIG), (PER, PER, PER, PER), (RIG, RIG, RIG, RIG)]
 
 
+# kernel 0: row strips (the default); kernel 1: one thread per point
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("prec,comp", VARIANTS)
-def test_elastic_bit_exact_free_top_rigid_sides(prec, comp):
-    _run((37, 29), BCS[0], prec, comp, 25, src=True, energy=True)
+def test_elastic_bit_exact_free_top_rigid_sides(prec, comp, kernel):
+    _run((37, 29), BCS[0], prec, comp, 25, src=True, energy=True, kernel=kernel)
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("bc", BCS)
-def test_elastic_bit_exact_all_boundaries(bc):
-    _run((64, 48), bc, "fp16", 6, 30, src=True, energy=True)
-    _run((8, 8), bc, "fp16", 3, 20)
+def test_elastic_bit_exact_all_boundaries(bc, kernel):
+    _run((64, 48), bc, "fp16", 6, 30, src=True, energy=True, kernel=kernel)
+    _run((8, 8), bc, "fp16", 3, 20, kernel=kernel)
+
+
+@pytest.mark.parametrize("shape", [(257, 40), (300, 23), (513, 17), (9, 70)])
+@pytest.mark.parametrize("bc", [BCS[0], BCS[2]])
+def test_elastic_strips_ragged(shape, bc):
+    # strips cut by the grid's x extent (ragged last vector, lanes past the
+    # grid), periodic x wrapping across strip boundaries, row chunks cut by ny
+    _run(shape, bc, "fp16", 3, 12, src=True, energy=True)
+    _run(shape, bc, "fp32", 0, 12, energy=True)
 
 
 def test_elastic_receivers():
