@@ -370,6 +370,12 @@ __global__ void __launch_bounds__(160, 4)
 
     Raw vzq0 = V::zero(), vzq1 = V::zero(), vzq2 = V::zero(), vzq3 = V::zero();
     int oc = 0, p_waited = 0;
+    // ring positions kept incrementally (no division by the ring depth):
+    // the next p stage to wait for and its phase, the slot of plane k
+    int pw_slot = 0, pk_slot = 0;
+    uint32_t pw_phase = 0;
+    // own-column p^n of planes k, k+1, k+2 (z images applied), plane k+3 loaded each iteration
+    Raw pq0 = V::zero(), pq1 = V::zero(), pq2 = V::zero();
     uint32_t c_phase = 0;
     bool ok = true;
     auto consumer_sync = [&]() -> bool {
@@ -382,26 +388,34 @@ __global__ void __launch_bounds__(160, 4)
     for (int k = z0 - 3; k < z1 && ok; k++) {
         const int pbase = k - (z0 - 3);
         while (p_waited < pbase + 4) {
-            if (!wait_phase(&p_full[p_waited % SP], (p_waited / SP) & 1, fp.err)) { ok = false; break; }
+            if (!wait_phase(&p_full[pw_slot], pw_phase, fp.err)) { ok = false; break; }
             p_waited++;
+            if (++pw_slot == SP) { pw_slot = 0; pw_phase ^= 1u; }
         }
         if (!ok) break;
         const int oslot = oc % SO;
         if (!wait_phase(&o_full[oslot], (oc / SO) & 1, fp.err)) { ok = false; break; }
         const S *ost = oring + oslot * SH::O_ELEMS;
-        const S *pk = pring + (pbase % SP) * SH::P_ELEMS;
+        const S *pk = pring + pk_slot * SH::P_ELEMS;
 
         // ---- v_z^{n+1/2} at plane k+1 of the own vector (p^n planes k..k+3)
         Raw vzn = V::zero(), tzn = V::zero();
         const bool inner_z = k >= 0 && k + 3 < nz;  // planes k..k+3 inside the grid
+        Raw pq3 = V::zero();
         if (active) {
-            Raw pz[4];
-#pragma unroll
-            for (int t = 0; t < 4; t++) {
-                const Raw r = p_vec(pring + ((pbase + t) % SP) * SH::P_ELEMS, row);
-                pz[t] = inner_z ? r : signed_raw<V>(r, plane_sign(k + t));
+            auto plane = [&](int t) -> Raw {
+                int sl = pk_slot + t;
+                if (sl >= SP) sl -= SP;
+                const Raw r = p_vec(pring + sl * SH::P_ELEMS, row);
+                return inner_z ? r : signed_raw<V>(r, plane_sign(k + t));
+            };
+            if (k == z0 - 3) {
+                pq0 = plane(0);
+                pq1 = plane(1);
+                pq2 = plane(2);
             }
-            const AV D = vstencil<V>(V::ld(pz[0]), V::ld(pz[1]), V::ld(pz[2]), V::ld(pz[3]));
+            pq3 = plane(3);
+            const AV D = vstencil<V>(V::ld(pq0), V::ld(pq1), V::ld(pq2), V::ld(pq3));
             vzn = vec_at(ost + SH::O_VZ + row * TX + lx * VEC);
             tzn = COMP ? vec_at(ost + SH::O_TVZ + row * TX + lx * VEC) : V::zero();
             V::template update<COMP>(vzn, tzn, V::mul(az, D));
@@ -423,7 +437,7 @@ __global__ void __launch_bounds__(160, 4)
             // ---- v_x^{n+1/2}: own vector, and the x halo of the tile edge lanes
             if (active) {
                 const S *prow = pk + row * WIDE + HALO - x0;  // indexed by global x
-                const Raw own_p = p_vec(pk, row);
+                const Raw own_p = pq0;  // plane k is inside the grid: no image
                 RS l0, r0, r1;
                 if (x == 0) l0 = V::rneg_s(prow[1]);               // p[-1] = -p[1]
                 else l0 = prow[x - 1];
@@ -437,6 +451,10 @@ __global__ void __launch_bounds__(160, 4)
                 V::template update<COMP>(vxn, txn, V::mul(ax, D));
                 S *nrow = nvx + row * WIDE + HALO - x0;
                 *reinterpret_cast<Raw *>(nrow + x) = vxn;
+                // final: store now, so that the registers are free for the rest of the plane
+                const int64_t qv = x + sy * j + sz * (int64_t)k;
+                at<V>(fp.vx_out, qv) = vxn;
+                if (COMP) at<V>(fp.tvx_out, qv) = txn;
                 // the x halo of the tile (v_x at x0-2, x0-1, x0+TX), one value per
                 // lane 0, 1, 2, where it lies inside the grid; at the grid's x faces
                 // the reads below take the even images of v_x instead
@@ -473,6 +491,11 @@ __global__ void __launch_bounds__(160, 4)
             };
             // own rows, and row ny (the image row the last grid row reads)
             if (j <= ny) vy_vec(row, lx, vyn, tyn);
+            if (active) {
+                const int64_t qv = x + sy * j + sz * (int64_t)k;
+                at<V>(fp.vy_out, qv) = vyn;
+                if (COMP) at<V>(fp.tvy_out, qv) = tyn;
+            }
             {
                 // this warp's halo rows wr0, wr0 + 1 (above) and wr0 + 6 (below):
                 // 3 x LANES vectors on lanes 0..23
@@ -520,17 +543,11 @@ __global__ void __launch_bounds__(160, 4)
                         if (e == prm.src_i - x) V::set(R, e, P::add(V::aget(R, e), sv_));
                 }
                 const AV bc = prm.b ? V::ld(bv) : V::splat(V::lds(b_raw));
-                const Raw pold = p_vec(pk, row);
+                const Raw pold = pq0;
                 Raw pn = pold;
                 V::template update<COMP>(pn, tpn, V::mul(bc, R));
                 at<V>(fp.p_out, q) = pn;
-                at<V>(fp.vx_out, q) = vxn;
-                at<V>(fp.vy_out, q) = vyn;
-                if (COMP) {
-                    at<V>(fp.tp, q) = tpn;
-                    at<V>(fp.tvx_out, q) = txn;
-                    at<V>(fp.tvy_out, q) = tyn;
-                }
+                if (COMP) at<V>(fp.tp, q) = tpn;
                 if (ENERGY) {
                     // v^2 / a with the uniform a as a product by its reciprocal;
                     // the four terms of a point summed in binary32, then added
@@ -554,12 +571,16 @@ __global__ void __launch_bounds__(160, 4)
         __syncwarp();
         if ((tid & 31) == 0) {
             mbar_arrive(&o_empty[oslot]);
-            mbar_arrive(&p_empty[pbase % SP]);
+            mbar_arrive(&p_empty[pk_slot]);
         }
         oc++;
+        if (++pk_slot == SP) pk_slot = 0;
         vzq0 = vzq1;
         vzq1 = vzq2;
         vzq2 = vzq3;
+        pq0 = pq1;
+        pq1 = pq2;
+        pq2 = pq3;
     }
     if (ENERGY) {
         double val = ok ? (double)e_s + (double)e_c : 0.0;
