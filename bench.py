@@ -284,31 +284,37 @@ def run_adjoint(W, steps: int, n: int = 256, nshots: int = 16):
     amp = 0.5 * w["P0"] * w["h"] ** 2 / w["z0"]
     nrec = len(w["receivers"])
 
-    def shot_ctx(c, src):
-        ctx = W.wave_create(w["shape"], w["h"], w["rho"], c, w["dt"], W.WAVE_FP16, W.WAVE_COMP_3OP,
-                            bc=[W.WAVE_BC_RIGID] * 6, field_scale=w["P0"], stream=stream.cuda_stream)
+    def make_ctx(c):
+        return W.wave_create(w["shape"], w["h"], w["rho"], c, w["dt"], W.WAVE_FP16, W.WAVE_COMP_3OP,
+                             bc=[W.WAVE_BC_RIGID] * 6, field_scale=w["P0"], stream=stream.cuda_stream)
+
+    def start_shot(ctx, src):
+        # one context serves every shot: zero the state, new source, new traces
+        W.wave_reset(ctx)
         W.wave_set_source(ctx, W.WAVE_F_P, src, w["wavelet"] * amp)
         tr = torch.zeros((steps, nrec), dtype=torch.float32, device="cuda")
         W.wave_set_receivers(ctx, W.WAVE_F_P, w["receivers"], tr, steps)
-        return ctx, tr
+        return tr
 
     shots = w["shots"][:nshots]
     d_obs = []
-    for src in shots:
-        ctx, tr = shot_ctx(w["c_true"], src)
-        try:
+    ctx = make_ctx(w["c_true"])
+    try:
+        for src in shots:
+            tr = start_shot(ctx, src)
             W.wave_step(ctx, steps)
             torch.cuda.synchronize()
             d_obs.append(tr)
-        finally:
-            W.wave_destroy(ctx)
+    finally:
+        W.wave_destroy(ctx)
     grad = torch.zeros(tuple(w["shape"][::-1]), dtype=torch.float32, device="cuda")
     ms_total, J = 0.0, 0.0
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    for si, src in enumerate(shots):
-        ctx, tr = shot_ctx(w["c0"], src)
-        try:
+    ctx = make_ctx(w["c0"])
+    try:
+        for si, src in enumerate(shots):
+            tr = start_shot(ctx, src)
             torch.cuda.synchronize()
             ev0.record(stream)
             W.wave_record(ctx, steps, 0)
@@ -320,8 +326,8 @@ def run_adjoint(W, steps: int, n: int = 256, nshots: int = 16):
             torch.cuda.synchronize()
             ms_total += ev0.elapsed_time(ev1)
             J += 0.5 * float((res.double() ** 2).sum())
-        finally:
-            W.wave_destroy(ctx)
+    finally:
+        W.wave_destroy(ctx)
     gn = float(torch.linalg.vector_norm(grad))
     return {"workload": "3d_acoustic_adjoint_256_16shots_64rec", "n": n, "shots": len(shots),
             "receivers": nrec, "steps": steps, "checkpoints": int(np.ceil(np.sqrt(steps))),

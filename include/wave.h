@@ -276,6 +276,12 @@ wave_status wave_steps_done(wave_ctx *ctx, int64_t *steps);
 wave_status wave_set_timing(wave_ctx *ctx, int32_t enable);
 wave_status wave_get_timing(wave_ctx *ctx, int32_t kind, int64_t *launches, double *ms);
 
+/* wave_reset -- zero every field and compensation and the step counter, and
+ * restart the receiver and energy traces at their first row; the medium,
+ * source, receivers and any adjoint buffers are kept (for running many shots
+ * on one context). Asynchronous. */
+wave_status wave_reset(wave_ctx *ctx);
+
 /*
  * Gradient of a trace misfit with respect to the velocity model, by the
  * discrete adjoint of the acoustic scheme (not in the paper; acoustic only).

@@ -97,6 +97,22 @@ __global__ void adj_finish_kernel(float *out, const float *g, const float *two_o
     }
 }
 
+// dst[i] = -(binary32 value of the multiplier src[i]), over the pitched array.
+template <int FMT>
+__global__ void adj_neg_coef_kernel(const void *src, float *dst, int64_t total) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = -ld_f32<FMT>(src, i);
+}
+
+cudaError_t adj_neg_coef(const void *src, int fmt, float *dst, int64_t total, cudaStream_t st) {
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 65535);
+    if (fmt == ADJ_F32) adj_neg_coef_kernel<ADJ_F32><<<blocks, 256, 0, st>>>(src, dst, total);
+    else if (fmt == ADJ_BF16) adj_neg_coef_kernel<ADJ_BF16><<<blocks, 256, 0, st>>>(src, dst, total);
+    else adj_neg_coef_kernel<ADJ_F16><<<blocks, 256, 0, st>>>(src, dst, total);
+    return cudaGetLastError();
+}
+
 cudaError_t adj_inject(float *mu, const int64_t *rec_q, const float *rec_w, const int *order, const int *start,
                        int ngroups, const float *res, cudaStream_t st) {
     if (ngroups <= 0) return cudaSuccess;

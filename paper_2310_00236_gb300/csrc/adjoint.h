@@ -21,6 +21,8 @@ struct AdjGradParams {
 // order / start: receivers grouped by point (see adjoint.cu), ngroups points
 cudaError_t adj_inject(float *mu, const int64_t *rec_q, const float *rec_w, const int *order, const int *start,
                        int ngroups, const float *res, cudaStream_t st);
+// dst[i] = -src[i] as binary32 (src in storage format fmt), i < total
+cudaError_t adj_neg_coef(const void *src, int fmt, float *dst, int64_t total, cudaStream_t st);
 cudaError_t adj_grad(const AdjGradParams &P, int ndim, int fmt, cudaStream_t st);
 cudaError_t adj_finish(float *out, const float *g, const float *two_over_c, const int n[3], int64_t sy,
                        int64_t sz, cudaStream_t st);

@@ -241,13 +241,14 @@ struct wave_ctx {
         DevBuf seg;                   // v^{n+1/2} of up to K steps (ndim arrays each)
         int64_t seg_lo = -1, seg_n = 0;
         DevBuf mu, nu[3], g;          // binary32, pitched like the fields
-        DevBuf na[3], nb;             // negated multipliers (binary32) where per-point
         uint32_t na_uni[3] = {0, 0, 0}, nb_uni = 0;
         DevBuf rec_w;                 // residual weight per receiver (b, 0 on rigid walls)
         DevBuf rec_order, rec_start;  // receivers grouped by point, in receiver order
         int ngroups = 0;
-        DevBuf two_over_c;            // device copy, unpitched
     } adj;
+    // made by the first wave_record, kept for the context's lifetime
+    DevBuf adj_na[3], adj_nb;         // negated multipliers (binary32) where per-point
+    DevBuf adj_two_over_c;            // 2 / c, unpitched
 };
 
 static bool field_valid(const wave_ctx *c, int field) {
@@ -256,7 +257,7 @@ static bool field_valid(const wave_ctx *c, int field) {
            field == WAVE_F_SYY || field == WAVE_F_SXY;
 }
 
-static wave_status dev_alloc(wave_ctx *c, DevBuf &b, size_t bytes) {
+static wave_status dev_alloc(wave_ctx *c, DevBuf &b, size_t bytes, bool zero = true) {
     b.bytes = bytes;
     if (bytes == 0) return WAVE_OK;
     if (g_alloc) {
@@ -273,6 +274,7 @@ static wave_status dev_alloc(wave_ctx *c, DevBuf &b, size_t bytes) {
                         "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
         }
     }
+    if (!zero) return WAVE_OK;
     cudaError_t e = cudaMemsetAsync(b.ptr, 0, bytes, c->stream);
     if (e != cudaSuccess) return fail(WAVE_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     return WAVE_OK;
@@ -552,15 +554,10 @@ static void adjoint_free(wave_ctx *c) {
     dev_free(c, A.seg);
     dev_free(c, A.mu);
     dev_free(c, A.g);
-    dev_free(c, A.nb);
     dev_free(c, A.rec_w);
     dev_free(c, A.rec_order);
     dev_free(c, A.rec_start);
-    dev_free(c, A.two_over_c);
-    for (int ax = 0; ax < 3; ax++) {
-        dev_free(c, A.nu[ax]);
-        dev_free(c, A.na[ax]);
-    }
+    for (int ax = 0; ax < 3; ax++) dev_free(c, A.nu[ax]);
     A = wave_ctx::Adjoint();
 }
 
@@ -579,6 +576,9 @@ static void destroy_ctx(wave_ctx *c) {
     dev_free(c, c->src_table);
     dev_free(c, c->rec_q);
     adjoint_free(c);
+    for (auto &b : c->adj_na) dev_free(c, b);
+    dev_free(c, c->adj_nb);
+    dev_free(c, c->adj_two_over_c);
     cudaStreamSynchronize(c->stream);
     collect_timing(c);
     for (auto e : c->event_pool) cudaEventDestroy(e);
@@ -1300,6 +1300,27 @@ extern "C" wave_status wave_get_timing(wave_ctx *c, int32_t kind, int64_t *launc
     return WAVE_OK;
 }
 
+// Zero every field and compensation (both buffer sets) and the step counter.
+extern "C" wave_status wave_reset(wave_ctx *c) {
+    CHECK_CTX(c);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 7 && e == cudaSuccess; i++) {
+        if (c->f[i].ptr) e = cudaMemsetAsync(c->f[i].ptr, 0, c->f[i].bytes, c->stream);
+        if (e == cudaSuccess && c->t[i].ptr) e = cudaMemsetAsync(c->t[i].ptr, 0, c->t[i].bytes, c->stream);
+    }
+    for (int i = 0; i < 4 && e == cudaSuccess; i++) {
+        if (c->alt_f[i].ptr) e = cudaMemsetAsync(c->alt_f[i].ptr, 0, c->alt_f[i].bytes, c->stream);
+        if (e == cudaSuccess && c->alt_t[i].ptr) e = cudaMemsetAsync(c->alt_t[i].ptr, 0, c->alt_t[i].bytes, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_check(c, e, "wave_reset");
+    c->step = 0;
+    c->have_energy = false;
+    c->rec_pos = 0;
+    c->e_trace_pos = 0;
+    c->adj.active = false;
+    return WAVE_OK;
+}
+
 // ------------------------------------------------------------------ adjoint
 // Arrays of a snapshot: p, v_c and, with compensation, t_p, t_v_c.
 static int snapshot_arrays(wave_ctx *c, DevBuf **out) {
@@ -1325,20 +1346,14 @@ static cudaError_t snapshot_copy(wave_ctx *c, int64_t slot, bool save) {
     return cudaSuccess;
 }
 
-// binary32 copy of a multiplier, negated (per-point arrays only)
-static wave_status upload_neg_coef(wave_ctx *c, DevBuf &dst, const std::vector<double> &v) {
-    std::vector<float> tmp((size_t)c->total, 0.f);
-    const int64_t nx = c->n[0], ny = c->n[1];
-    for (int64_t q = 0; q < (int64_t)v.size(); q++) {
-        const int64_t i = q % nx, j = (q / nx) % ny, k = q / (nx * ny);
-        tmp[i + c->pitch * j + c->plane * k] = -(float)v[q];
-    }
-    wave_status st = dev_alloc(c, dst, tmp.size() * sizeof(float));
+// binary32 copy of a per-point multiplier, negated, converted on the device
+static wave_status make_neg_coef(wave_ctx *c, DevBuf &dst, int w) {
+    if (dst.ptr) return WAVE_OK;
+    wave_status st = dev_alloc(c, dst, (size_t)c->total * sizeof(float), false);
     if (st) return st;
-    cudaError_t e = cudaMemcpyAsync(dst.ptr, tmp.data(), tmp.size() * sizeof(float), cudaMemcpyHostToDevice,
-                                    c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    return cuda_check(c, e, "adjoint multipliers");
+    const int fmt = c->prec == PREC_FP32 ? ADJ_F32 : is_bf16_storage(c->prec) ? ADJ_BF16 : ADJ_F16;
+    return cuda_check(c, adj_neg_coef(c->coef[w].ptr, fmt, static_cast<float *>(dst.ptr), c->total, c->stream),
+                      "adjoint multipliers");
 }
 
 extern "C" wave_status wave_record(wave_ctx *c, int64_t nsteps, int64_t ncheckpoints) {
@@ -1346,6 +1361,11 @@ extern "C" wave_status wave_record(wave_ctx *c, int64_t nsteps, int64_t ncheckpo
     if (c->kind != WAVE_ACOUSTIC) return fail(WAVE_ENOTIMPL, "the adjoint covers the acoustic system");
     if (nsteps < 1) return fail(WAVE_EINVAL, "nsteps must be positive");
     if (c->nrec && c->rec_field != WAVE_F_P) return fail(WAVE_EINVAL, "adjoint receivers must record p");
+    // the snapshot and replay buffers of a previous record are kept when they
+    // are large enough (re-allocating gigabytes per shot costs more than a step)
+    DevBuf keep_cps = c->adj.cps, keep_seg = c->adj.seg;
+    c->adj.cps = DevBuf();
+    c->adj.seg = DevBuf();
     adjoint_free(c);
     auto &A = c->adj;
     int64_t ncp = ncheckpoints > 0 ? ncheckpoints : (int64_t)ceil(sqrt((double)nsteps));
@@ -1358,8 +1378,19 @@ extern "C" wave_status wave_record(wave_ctx *c, int64_t nsteps, int64_t ncheckpo
     A.narr = snapshot_arrays(c, arr);
     const size_t eb = elem_bytes(c->prec);
     const size_t abytes = (size_t)c->total * eb, fbytes = (size_t)c->total * sizeof(float);
-    wave_status st = dev_alloc(c, A.cps, (size_t)(A.ncp + 1) * A.narr * abytes);
-    if (!st) st = dev_alloc(c, A.seg, (size_t)A.K * c->ndim * abytes);
+    // snapshots and replayed velocities are written before they are read
+    const size_t cps_bytes = (size_t)(A.ncp + 1) * A.narr * abytes, seg_bytes = (size_t)A.K * c->ndim * abytes;
+    wave_status st = WAVE_OK;
+    if (keep_cps.ptr && keep_cps.bytes >= cps_bytes) A.cps = keep_cps;
+    else {
+        dev_free(c, keep_cps);
+        st = dev_alloc(c, A.cps, cps_bytes, false);
+    }
+    if (keep_seg.ptr && keep_seg.bytes >= seg_bytes) A.seg = keep_seg;
+    else {
+        dev_free(c, keep_seg);
+        if (!st) st = dev_alloc(c, A.seg, seg_bytes, false);
+    }
     if (!st) st = dev_alloc(c, A.mu, fbytes);
     if (!st) st = dev_alloc(c, A.g, fbytes);
     for (int ax = 0; ax < c->ndim && !st; ax++) st = dev_alloc(c, A.nu[ax], fbytes);
@@ -1373,7 +1404,7 @@ extern "C" wave_status wave_record(wave_ctx *c, int64_t nsteps, int64_t ncheckpo
             const float v = -(float)c->coef_host[1 + ax][0];
             memcpy(&A.na_uni[ax], &v, 4);
         } else {
-            st = upload_neg_coef(c, A.na[ax], c->coef_host[1 + ax]);
+            st = make_neg_coef(c, c->adj_na[ax], 1 + ax);
         }
     }
     if (!st) {
@@ -1381,7 +1412,7 @@ extern "C" wave_status wave_record(wave_ctx *c, int64_t nsteps, int64_t ncheckpo
             const float v = -(float)c->coef_host[0][0];
             memcpy(&A.nb_uni, &v, 4);
         } else {
-            st = upload_neg_coef(c, A.nb, c->coef_host[0]);
+            st = make_neg_coef(c, c->adj_nb, 0);
         }
     }
     // residual weights: b at each receiver, 0 on the rigid-wall nodes
@@ -1420,13 +1451,12 @@ extern "C" wave_status wave_record(wave_ctx *c, int64_t nsteps, int64_t ncheckpo
             st = cuda_check(c, e, "receiver weights");
         }
     }
-    if (!st) {
-        st = dev_alloc(c, A.two_over_c, c->two_over_c.size() * sizeof(float));
+    if (!st && !c->adj_two_over_c.ptr) {
+        st = dev_alloc(c, c->adj_two_over_c, c->two_over_c.size() * sizeof(float), false);
         if (!st) {
-            cudaError_t e = cudaMemcpyAsync(A.two_over_c.ptr, c->two_over_c.data(),
+            cudaError_t e = cudaMemcpyAsync(c->adj_two_over_c.ptr, c->two_over_c.data(),
                                             c->two_over_c.size() * sizeof(float), cudaMemcpyHostToDevice,
                                             c->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
             st = cuda_check(c, e, "velocity upload");
         }
     }
@@ -1440,7 +1470,7 @@ extern "C" wave_status wave_record(wave_ctx *c, int64_t nsteps, int64_t ncheckpo
         A.cp_step[i] = c->step;
         cudaError_t e = snapshot_copy(c, i, true);
         if (e != cudaSuccess) return cuda_check(c, e, "checkpoint");
-        st = acoustic_steps(c, std::min(A.K, nsteps - i * A.K));
+        st = acoustic_steps(c, std::min(A.K, nsteps - i * A.K), i == A.ncp - 1);
         if (st) return st;
     }
     A.cp_step[A.ncp] = c->step;
@@ -1494,13 +1524,13 @@ extern "C" wave_status wave_adjoint_step(wave_ctx *c, int64_t n, const float *re
         prm.n[ax] = (int)c->n[ax];
         prm.bc[ax] = ax < c->ndim ? (c->bc[2 * ax] == WAVE_BC_PERIODIC ? BC_PERIODIC : BC_RIGID) : BC_PERIODIC;
         prm.v[ax] = A.nu[ax].ptr;
-        prm.a[ax] = A.na[ax].ptr;
+        prm.a[ax] = c->adj_na[ax].ptr;
         prm.a_uni[ax] = A.na_uni[ax];
     }
     prm.sy = c->pitch;
     prm.sz = c->plane;
     prm.p = A.mu.ptr;
-    prm.b = A.nb.ptr;
+    prm.b = c->adj_nb.ptr;
     prm.b_uni = A.nb_uni;
     prm.src_q = -1;
     prm.src_i = prm.src_j = prm.src_k = -1;
@@ -1556,7 +1586,7 @@ extern "C" wave_status wave_get_gradient(wave_ctx *c, float *device_out, int64_t
     if (!device_out) return WAVE_OK;
     int n[3] = {(int)c->n[0], (int)c->n[1], (int)c->n[2]};
     cudaError_t e = adj_finish(device_out, static_cast<const float *>(A.g.ptr),
-                               static_cast<const float *>(A.two_over_c.ptr), n, c->pitch, c->plane, c->stream);
+                               static_cast<const float *>(c->adj_two_over_c.ptr), n, c->pitch, c->plane, c->stream);
     return cuda_check(c, e, "gradient");
 }
 
