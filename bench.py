@@ -162,6 +162,71 @@ def run_variant(W, w, prec_name, comp, steps, warmup, timing=True):
     return {"ms": ms, "e0": e0, "e1": e1, "kt": kt}
 
 
+def run_variants(W, w, steps, traced=100):
+    """Every storage / arithmetic / update variant on the benchmark workload:
+    Gpoint-updates/s over `steps` timed steps, then the largest relative
+    energy change over `traced` further steps (energy after every step)."""
+    import torch
+    out = {}
+    stream = torch.cuda.current_stream()
+    for prec_name, comp in (("fp16", 0), ("fp16", 3), ("fp16", 6), ("bf16", 0), ("bf16", 3), ("bf16", 6),
+                            ("fp16_f32arith", 0), ("fp16_f32arith", 3), ("bf16_f32arith", 0),
+                            ("bf16_f32arith", 3), ("fp32", 0)):
+        ctx = W.wave_create(w["shape"], w["h"], w["rho"], w["c"], w["dt"], W.PRECISIONS[prec_name], comp,
+                            bc=[W.WAVE_BC_RIGID] * 6, field_scale=w["P0"], stream=stream.cuda_stream)
+        try:
+            W.wave_set_initial(ctx, W.WAVE_F_P, w["p0"])
+            W.wave_step(ctx, 3)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            W.wave_step(ctx, steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            en = torch.zeros(traced, dtype=torch.float64, device="cuda")
+            W.wave_set_energy_trace(ctx, en, traced)
+            W.wave_step(ctx, traced)
+            e = en.cpu().numpy()
+        finally:
+            W.wave_destroy(ctx)
+        npts = int(np.prod(w["shape"]))
+        out[f"{prec_name}+{comp}op" if comp else prec_name] = {
+            "value": npts * steps / (ms * 1e-3) / 1e9, "ms_per_step": ms / steps,
+            "energy_drift_max": float(np.max(np.abs(e - e[0])) / abs(e[0]))}
+    return out
+
+
+def run_cfg1(W, steps=2000):
+    """The 2D acoustic configuration (256^2, rho = c = 1, p = 0 walls, centred
+    Gaussian, CFL 0.5), fp16 + sum_3op: L2-resident, latency-bound."""
+    import torch
+    from paper_2310_00236_gb300 import inputs
+    w = inputs.acoustic_2d_gaussian(256, steps)
+    stream = torch.cuda.Stream()  # a created stream: the library replays step graphs on it
+    ctx = W.wave_create(w["shape"], w["h"], w["rho"], w["c"], w["dt"], W.WAVE_FP16, W.WAVE_COMP_3OP,
+                        bc=[W.WAVE_BC_RIGID] * 4 + [0, 0], stream=stream.cuda_stream)
+    try:
+        W.wave_set_initial(ctx, W.WAVE_F_P, w["p0"])
+        W.wave_step(ctx, 3)
+        e0 = W.wave_energy(ctx)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        W.wave_step(ctx, steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        e1 = W.wave_energy(ctx)
+    finally:
+        W.wave_destroy(ctx)
+    return {"workload": "2d_acoustic_256_gaussian_rigid_cfl0.5", "precision": "fp16", "compensation": "sum_3op",
+            "steps": steps, "value": 256 * 256 * steps / (ms * 1e-3) / 1e9, "unit": UNIT,
+            "us_per_step": ms * 1e3 / steps, "energy_drift": abs(e1 - e0) / abs(e0)}
+
+
 def run_e2e(W, w, prec_name, comp, steps):
     """Same workload through the public API with host buffers: host initial
     pressure in, K steps, host pressure field and energy out."""
@@ -542,6 +607,7 @@ def main():
     achieved = bpp * npts / (kms / nl * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": KERNEL_NAMES[dom],
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "frac_of_nominal_7900": achieved / 7900.0,
             "peak_kind": peak_kind,
             "traffic": (MEASURED_TRAFFIC_PER_POINT[("fp16", True, dom)] * npts
                         if ("fp16", True, dom) in MEASURED_TRAFFIC_PER_POINT else None),
@@ -561,7 +627,11 @@ def main():
     elastic = None
     batched = None
     adjoint = None
+    variants = None
+    cfg1 = None
     if not args.no_compare:
+        variants = run_variants(W, w, min(args.steps, 100))
+        cfg1 = run_cfg1(W)
         adjoint = run_adjoint(W, min(args.steps, 1500))
         elastic = run_elastic(W, min(args.steps, 4000), args.warmup)
         batched = run_batched(W, min(args.steps, 3000), args.warmup)
@@ -589,7 +659,8 @@ def main():
                            "l2": "working set 2.4 GB > L2 (no flush needed)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": sum(v[0] for v in kt.values()), "compare": compare,
-                "elastic": elastic, "batched": batched, "adjoint": adjoint,
+                "elastic": elastic, "batched": batched, "adjoint": adjoint, "variants": variants,
+                "cfg1": cfg1,
                 "energy_drift": drift16}
         print(json.dumps(line), flush=True)
 

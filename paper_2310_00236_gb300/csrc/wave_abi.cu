@@ -162,7 +162,7 @@ static void parallel_for(int64_t n, F f) {
 // items, large grids long ones that re-read fewer halo rows). Measured on
 // 1024^2: 2 rows per item 50.6 (elastic) and 71.5 (acoustic) Gpt/s, 16 rows
 // 16.4 and 31.9.
-constexpr int kStripWarps = 4;
+constexpr int kStripWarps = 4, kStripGraphSteps = 32;
 static int strip_rows_for(int64_t nstrips, int64_t ny, int sms) {
     const int64_t r = nstrips * ny / (12 * (int64_t)sms);
     return (int)std::max<int64_t>(1, std::min<int64_t>(16, r));
@@ -184,6 +184,7 @@ struct wave_ctx {
     // 2D: the row-strip kernels of the batches, as a batch of one
     bool use_strips = false;
     int strip_items = 0, strip_grid = 0, strip_rows = 16;
+    cudaGraphExec_t strip_graph = nullptr;  // kStripGraphSteps plain strip steps
     DevBuf strip_shot, strip_item0, strip_part;
     // second set of p, vx, vy, vz and t_vx, t_vy, t_vz for the one-pass step,
     // and the tensor maps of both sets (fset: the set the fields point to now)
@@ -563,6 +564,7 @@ static void adjoint_free(wave_ctx *c) {
 
 static void destroy_ctx(wave_ctx *c) {
     if (!c) return;
+    if (c->strip_graph) cudaGraphExecDestroy(c->strip_graph);
     dev_free(c, c->strip_shot);
     dev_free(c, c->strip_item0);
     dev_free(c, c->strip_part);
@@ -1030,6 +1032,34 @@ static wave_status acoustic_steps(wave_ctx *c, int64_t n, bool energy_last = tru
         L.yc = c->strip_rows;
         L.wpb = kStripWarps;
         L.grid = c->strip_grid;
+        // plain runs (no receivers, no energy trace) on a created stream: the
+        // steps before the last are replayed from a graph of kStripGraphSteps
+        // steps (the source's step index lives in device memory)
+        const bool plain = !c->nrec && !c->e_trace && c->stream != nullptr && !c->timing;
+        if (plain && n - 1 >= kStripGraphSteps) {
+            if (!c->strip_graph) {
+                cudaGraph_t g = nullptr;
+                e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    for (int t = 0; t < kStripGraphSteps && e == cudaSuccess; t++)
+                        e = batch_step(L, c->prec, c->comp, false, c->stream);
+                    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+                    if (e == cudaSuccess) e = e2;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&c->strip_graph, g, 0);
+                if (g) cudaGraphDestroy(g);
+                if (e != cudaSuccess) {  // no graph: plain launches below
+                    cudaGetLastError();
+                    c->strip_graph = nullptr;
+                }
+            }
+            while (c->strip_graph && n - 1 >= kStripGraphSteps) {
+                e = cudaGraphLaunch(c->strip_graph, c->stream);
+                if (e != cudaSuccess) return cuda_check(c, e, "graph launch");
+                n -= kStripGraphSteps;
+                c->step += kStripGraphSteps;
+            }
+        }
     }
     for (int64_t s = 0; s < n; s++) {
         prm.step = c->step;

@@ -240,3 +240,30 @@ def test_errors_reported_not_faulted():
         assert np.isfinite(W.wave_energy(ctx))
     finally:
         W.wave_destroy(ctx)
+
+
+def test_2d_graph_replay_on_side_stream_bit_exact():
+    """Plain 2D stepping on a created stream replays captured step graphs; the
+    result equals the oracle, across calls and with a source."""
+    import torch
+    shape = (96, 70)
+    h = 10.0
+    rho, c = _media(shape, 5, h)
+    dt = 0.4 * h / 4500.0
+    z0 = float(np.max(rho) * np.max(c))
+    steps = [70, 33, 5, 64]
+    wav = inputs.ricker_table(sum(steps), dt, 40.0) * 0.5 * h / z0
+    stream = torch.cuda.Stream()
+    ctx, st = acoustic_pair(shape, (R, P), "fp16", 3, h, dt, rho, c,
+                            p0=inputs.gaussian(shape, h, 2.5 * h), src=([30, 20], wav), stream=stream.cuda_stream)
+    try:
+        for n in steps:
+            W.wave_step(ctx, n)
+        _, E = st.run(sum(steps), energy=True)
+        bad = compare_acoustic(ctx, st, "fp16", 3)
+        e_orc = E[-1] * O.energy_factor(h, dt, 1.0, st.Z0, 2)
+        if not abs(W.wave_energy(ctx) - e_orc) <= 2e-6 * abs(e_orc):
+            bad.append(f"energy {W.wave_energy(ctx)} vs {e_orc}")
+    finally:
+        W.wave_destroy(ctx)
+    assert not bad, bad
