@@ -276,6 +276,14 @@ wave_status wave_steps_done(wave_ctx *ctx, int64_t *steps);
 wave_status wave_set_timing(wave_ctx *ctx, int32_t enable);
 wave_status wave_get_timing(wave_ctx *ctx, int32_t kind, int64_t *launches, double *ms);
 
+/* wave_selftest_timeout -- run the device error path on purpose: a kernel
+ * waits on an mbarrier that nothing completes, with a short poll limit, sets
+ * the context's error word when the wait expires and returns. The call then
+ * reports what a stalled pipeline reports: WAVE_ETIMEOUT, and the context is
+ * poisoned (WAVE_ESTATE afterwards); the CUDA context and other wave contexts
+ * stay usable. Nothing faults or hangs. Not part of the method; a test aid. */
+wave_status wave_selftest_timeout(wave_ctx *ctx);
+
 /* wave_reset -- zero every field and compensation and the step counter, and
  * restart the receiver and energy traces at their first row; the medium,
  * source, receivers and any adjoint buffers are kept (for running many shots

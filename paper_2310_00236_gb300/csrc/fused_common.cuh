@@ -59,13 +59,16 @@ __device__ __forceinline__ void tma_box(void *dst_smem, const CUtensorMap *map, 
 // error word is set and false returned. Once any block has set the error
 // word, waits give up at their next check so that the whole grid leaves fast.
 constexpr uint32_t kWaitPolls = 1u << 22;
-__device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, int *err) {
-    for (uint32_t it = 0; it < kWaitPolls; it++) {
+__device__ __forceinline__ bool wait_phase_limit(uint64_t *bar, uint32_t parity, int *err, uint32_t polls) {
+    for (uint32_t it = 0; it < polls; it++) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 1023u) == 1023u && *reinterpret_cast<volatile int *>(err)) return false;
     }
     atomicExch(err, 1);
     return false;
+}
+__device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, int *err) {
+    return wait_phase_limit(bar, parity, err, kWaitPolls);
 }
 // Shorter bounded wait that ignores the error word (draining copies in flight).
 __device__ __forceinline__ void drain_phase(uint64_t *bar, uint32_t parity) {

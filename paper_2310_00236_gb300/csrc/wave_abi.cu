@@ -1225,6 +1225,15 @@ static wave_status check_device_error(wave_ctx *c) {
     return WAVE_OK;
 }
 
+extern "C" wave_status wave_selftest_timeout(wave_ctx *c) {
+    CHECK_CTX(c);
+    int *err = reinterpret_cast<int *>(static_cast<char *>(c->e_misc.ptr) + 16);
+    cudaError_t e = selftest_wait(err, 1024, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "self-test");
+    return check_device_error(c);
+}
+
 extern "C" wave_status wave_sync(wave_ctx *c) {
     CHECK_CTX(c);
     wave_status st = cuda_check(c, cudaStreamSynchronize(c->stream), "wave_sync");

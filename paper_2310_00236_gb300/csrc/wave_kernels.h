@@ -37,6 +37,10 @@ cudaError_t acoustic_fused_step(const AcParams &prm, const void *maps, const voi
                                 void *const out[7], void *tp, int prec, int comp, int zchunk, int *err,
                                 cudaStream_t st);
 
+// A bounded mbarrier wait that nothing completes (polls iterations), setting
+// *err to 1 when it expires: the self-test of the device error path.
+cudaError_t selftest_wait(int *err, uint32_t polls, cudaStream_t st);
+
 // Receiver sampling: traces[r] = float(field[q[r]]) for r < nrec.
 cudaError_t sample_receivers(const void *field, int elem_bytes, int is_bf16, const int64_t *q,
                              int nrec, float *traces, cudaStream_t st);

@@ -36,7 +36,7 @@ EXPORTS = ["wave_set_allocator", "wave_create", "wave_set_initial", "wave_set_so
            "wave_adjoint_step", "wave_destroy", "wave_last_error", "wave_build_info",
            "wave_set_timing", "wave_get_timing", "wave_energy_acoustic_static",
            "wave_batch_create", "wave_batch_step", "wave_batch_info", "wave_batch_destroy",
-           "wave_record", "wave_get_gradient", "wave_reset"]
+           "wave_record", "wave_get_gradient", "wave_reset", "wave_selftest_timeout"]
 
 
 class WaveError(RuntimeError):
@@ -100,6 +100,7 @@ def lib() -> C.CDLL:
                                         C.POINTER(vp), C.POINTER(vp), vp, C.c_double, vp, vp],
         "wave_record": [vp, i64, i64],
         "wave_reset": [vp],
+        "wave_selftest_timeout": [vp],
         "wave_get_gradient": [vp, vp, C.POINTER(C.c_int64)],
         "wave_batch_create": [i32, C.POINTER(vp), C.POINTER(vp)],
         "wave_batch_step": [vp, i64],
@@ -297,6 +298,11 @@ def wave_steps_done(ctx: Context) -> int:
     s = C.c_int64()
     _check(lib().wave_steps_done(ctx.ptr, C.byref(s)))
     return s.value
+
+
+def wave_selftest_timeout(ctx: Context):
+    """Force a bounded device wait to expire; raises WaveError(ETIMEOUT)."""
+    _check(lib().wave_selftest_timeout(ctx.ptr))
 
 
 def wave_reset(ctx: Context):

@@ -267,3 +267,27 @@ def test_2d_graph_replay_on_side_stream_bit_exact():
     finally:
         W.wave_destroy(ctx)
     assert not bad, bad
+
+
+def test_bounded_wait_expiry_reports_timeout_and_leaves_gpu_usable():
+    """A wait that nothing completes runs out, the host reads ETIMEOUT, the
+    context is poisoned, and a new context on the same device steps normally."""
+    shape = (16, 16)
+    ones = np.ones((16, 16))
+    ctx = W.wave_create(shape, 0.1, ones, ones, 0.02, W.WAVE_FP16, 3)
+    try:
+        with pytest.raises(W.WaveError) as e:
+            W.wave_selftest_timeout(ctx)
+        assert e.value.status == W.WAVE_ETIMEOUT
+        with pytest.raises(W.WaveError) as e:
+            W.wave_step(ctx, 1)
+        assert e.value.status == W.WAVE_ESTATE
+    finally:
+        W.wave_destroy(ctx)
+    ctx = W.wave_create(shape, 0.1, ones, ones, 0.02, W.WAVE_FP16, 3)
+    try:
+        W.wave_set_initial(ctx, W.WAVE_F_P, ones * 0.5)
+        W.wave_step(ctx, 3)
+        assert np.isfinite(W.wave_energy(ctx))
+    finally:
+        W.wave_destroy(ctx)
