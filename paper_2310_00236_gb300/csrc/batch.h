@@ -9,7 +9,8 @@ namespace wave {
 // One shot of a batch, resident in device memory.
 struct BatchShot {
     AcParams prm;   // the shot's grid, fields, multipliers, source, energy slot
-    int64_t step;   // global step index of the shot (source time index)
+    int64_t step;   // index of the shot's last step taken (the next step's velocity
+                    // launch advances it before the pressure launch reads it)
 };
 
 // Two kinds of work item:

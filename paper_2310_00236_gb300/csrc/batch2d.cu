@@ -38,10 +38,20 @@ __device__ __forceinline__ int shot_of(const int *item0, int nshots, int item) {
     return lo;
 }
 
+// The velocity launch of a step advances every shot's step counter first (block
+// 0): the counters hold the previous step's index between steps, and the
+// pressure launch, which reads them for the source, runs after this launch
+// has completed.
+__device__ __forceinline__ void advance_counters(BatchShot *shots, int nshots) {
+    if (blockIdx.x == 0)
+        for (int s = threadIdx.x; s < nshots; s += blockDim.x) shots[s].step++;
+}
+
 template <class P, int COMP, int HALF>
 __global__ void __launch_bounds__(256) batch_half_step(BatchShot *shots, const int *item0, int nshots,
                                                       int nitems, int bx, int by, int energy,
                                                       double *item_part) {
+    if (HALF == 0) advance_counters(shots, nshots);
     __shared__ int s_item0[kMaxShots + 1];
     __shared__ AcParams s_prm;
     __shared__ int64_t s_step;
@@ -177,8 +187,9 @@ __device__ __forceinline__ StripItem strip_of(const int *s_item0, int nshots, in
 
 // Velocity half step of one strip: v_x += a_x Dx(p), v_y += a_y Dy(p), row by row.
 template <class P, int COMP>
-__global__ void __launch_bounds__(256) batch_kv_strip(const BatchShot *__restrict__ shots, const int *item0,
+__global__ void __launch_bounds__(256) batch_kv_strip(BatchShot *shots, const int *item0,
                                                       int nshots, int nitems, int yc) {
+    advance_counters(shots, nshots);
     using V = typename VecOf<P>::T;
     using Raw = typename V::Raw;
     using AV = typename V::AV;
@@ -384,11 +395,6 @@ __global__ void batch_energy_reduce(BatchShot *shots, const int *item0, const do
     }
 }
 
-__global__ void batch_advance(BatchShot *shots, int nshots) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < nshots) shots[s].step++;
-}
-
 template <class P, int COMP>
 static cudaError_t launch_pc(const BatchLaunch &L, bool energy, cudaStream_t st) {
     if (L.kind == BATCH_STRIPS) {
@@ -408,7 +414,6 @@ static cudaError_t launch_pc(const BatchLaunch &L, bool energy, cudaStream_t st)
                                                                 L.by, energy ? 1 : 0, L.item_part);
     }
     if (energy) batch_energy_reduce<<<L.nshots, 256, 0, st>>>(L.shots, L.item0, L.item_part);
-    batch_advance<<<(L.nshots + 127) / 128, 128, 0, st>>>(L.shots, L.nshots);
     return cudaGetLastError();
 }
 

@@ -1019,7 +1019,7 @@ static wave_status acoustic_steps(wave_ctx *c, int64_t n, bool energy_last = tru
     if (c->use_strips) {
         BatchShot shot;
         shot.prm = prm;
-        shot.step = c->step;
+        shot.step = c->step - 1;  // the velocity launch of the step advances it
         cudaError_t e = cudaMemcpyAsync(c->strip_shot.ptr, &shot, sizeof shot, cudaMemcpyHostToDevice, c->stream);
         if (e != cudaSuccess) return cuda_check(c, e, "wave_step upload");
         L.shots = static_cast<BatchShot *>(c->strip_shot.ptr);
@@ -1754,7 +1754,7 @@ static cudaError_t batch_refresh(wave_batch *b) {
     b->h_shots.resize(b->ctx.size());
     for (size_t s = 0; s < b->ctx.size(); s++) {
         fill_acoustic_params(b->ctx[s], b->h_shots[s].prm);
-        b->h_shots[s].step = b->ctx[s]->step;
+        b->h_shots[s].step = b->ctx[s]->step - 1;  // the velocity launch of a step advances it
     }
     return cudaMemcpyAsync(b->d_shots, b->h_shots.data(), sizeof(BatchShot) * b->ctx.size(),
                            cudaMemcpyHostToDevice, b->stream);
