@@ -257,7 +257,7 @@ def run_elastic(W, steps: int, warmup: int):
     import torch
     from paper_2310_00236_gb300 import inputs
     w = inputs.elastic_2d_layered()
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()  # a created stream: the library replays step graphs on it
     ctx = W.wave_create(w["shape"], w["h"], w["rho"], w["vp"], w["dt"], W.WAVE_FP16,
                         W.WAVE_COMP_6OP, vs=w["vs"], bc=[1, 1, 2, 1, 0, 0], kind=W.WAVE_ELASTIC,
                         field_scale=1e5, stream=stream.cuda_stream)

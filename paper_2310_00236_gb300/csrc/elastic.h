@@ -27,6 +27,8 @@ struct ElParams {
     const void *src;            // arithmetic-format increments per global step
     int64_t src_nt;
     int64_t step;
+    int64_t *step_dev;          // strips: the step index in device memory (read by the
+                                // velocity launch, advanced by the stress launch), or nullptr
     int energy;
     double *e_part;
     unsigned int *e_count;

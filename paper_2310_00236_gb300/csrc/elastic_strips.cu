@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(256) el_v_strip(const ElParams e, int nitems, 
     const int wpb = blockDim.x >> 5;
     const int src_i = e.src_q >= 0 ? (int)(e.src_q % e.sy) : -1;
     const int src_j = e.src_q >= 0 ? (int)(e.src_q / e.sy) : -1;
+    const int64_t step = e.step_dev ? *e.step_dev : e.step;
     for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < nitems; item += gridDim.x * wpb) {
         const Item it = item_of<N>(e, item, yc);
         const int x = it.x0 + lane * N;
@@ -195,8 +196,8 @@ __global__ void __launch_bounds__(256) el_v_strip(const ElParams e, int nitems, 
                 // vy: Dx sxy + Dy syy [+ s]
                 R = V::add(dxsxy, vstencil<V>(V::ld(b0), V::ld(b1), V::ld(b2), V::ld(b3)));
                 AV inc = V::mul(X::coefv(e.c[C_BY], e.c_uni[C_BY], q), R);
-                if (j == src_j && src_i >= x && src_i < x + N && e.step < e.src_nt) {
-                    const typename V::AS sv = static_cast<const typename V::AS *>(e.src)[e.step];
+                if (j == src_j && src_i >= x && src_i < x + N && step < e.src_nt) {
+                    const typename V::AS sv = static_cast<const typename V::AS *>(e.src)[step];
 #pragma unroll
                     for (int k = 0; k < N; k++)
                         if (k == src_i - x) V::set(inc, k, P::add(V::aget(inc, k), sv));
@@ -218,6 +219,8 @@ __global__ void __launch_bounds__(256) el_v_strip(const ElParams e, int nitems, 
 // Stress half step on row strips, with the item's energy terms.
 template <class P, int COMP, bool ENERGY>
 __global__ void __launch_bounds__(256) el_s_strip(const ElParams e, int nitems, int yc, double *item_part) {
+    // the velocity launch of this step has read the step index: advance it
+    if (e.step_dev && blockIdx.x == 0 && threadIdx.x == 0) ++*e.step_dev;
     using V = typename VecOf<P>::T;
     using X = ElStrip<V>;
     using Raw = typename V::Raw;

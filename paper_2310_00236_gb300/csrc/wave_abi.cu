@@ -747,7 +747,7 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
         }
     }
     if (!st) st = dev_alloc(c, c->e_part, sizeof(double) * (size_t)std::max(1u, c->e_blocks));
-    if (!st) st = dev_alloc(c, c->e_misc, 32);  // [energy][block counter][error word]
+    if (!st) st = dev_alloc(c, c->e_misc, 32);  // [energy][block counter][error word][step index]
     if (!st) {
         cudaError_t e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) st = fail(WAVE_ECUDA, "wave_create: %s", cudaGetErrorString(e));
@@ -1162,16 +1162,52 @@ static wave_status elastic_steps(wave_ctx *c, int64_t n) {
     e.e_out = static_cast<double *>(c->e_misc.ptr);
     e.e_factor = 0.5 * c->h * c->P0 * c->P0 * c->dt / c->Z0;
     const size_t eb = elem_bytes(c->prec);
+    ElStripLaunch L;
+    L.nitems = c->strip_items;
+    L.yc = c->strip_rows;
+    L.wpb = kStripWarps;
+    L.grid = c->strip_grid;
+    L.item_part = static_cast<double *>(c->strip_part.ptr);
+    if (c->use_strips) {
+        // the step index lives in device memory, so runs of steps can be
+        // replayed from a graph (plain runs on a created stream)
+        e.step_dev = reinterpret_cast<int64_t *>(static_cast<char *>(c->e_misc.ptr) + 24);
+        cudaError_t err = cudaMemcpyAsync(e.step_dev, &c->step, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+        if (err != cudaSuccess) return cuda_check(c, err, "wave_step upload");
+        const bool plain = !c->nrec && !c->e_trace && c->stream != nullptr && !c->timing;
+        if (plain && n - 1 >= kStripGraphSteps) {
+            if (!c->strip_graph) {
+                cudaGraph_t g = nullptr;
+                e.energy = 0;
+                err = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+                if (err == cudaSuccess) {
+                    for (int t = 0; t < kStripGraphSteps && err == cudaSuccess; t++) {
+                        err = elastic_strip_half_step(e, c->prec, c->comp, 0, L, c->stream);
+                        if (err == cudaSuccess) err = elastic_strip_half_step(e, c->prec, c->comp, 1, L, c->stream);
+                    }
+                    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+                    if (err == cudaSuccess) err = e2;
+                }
+                if (err == cudaSuccess) err = cudaGraphInstantiate(&c->strip_graph, g, 0);
+                if (g) cudaGraphDestroy(g);
+                if (err != cudaSuccess) {  // no graph: plain launches below
+                    cudaGetLastError();
+                    c->strip_graph = nullptr;
+                }
+            }
+            while (c->strip_graph && n - 1 >= kStripGraphSteps) {
+                err = cudaGraphLaunch(c->strip_graph, c->stream);
+                if (err != cudaSuccess) return cuda_check(c, err, "graph launch");
+                n -= kStripGraphSteps;
+                c->step += kStripGraphSteps;
+            }
+        }
+    }
     for (int64_t s = 0; s < n; s++) {
         e.step = c->step;
         const bool trace = c->e_trace && c->e_trace_pos < c->e_trace_cap;
         e.energy = (s == n - 1) || trace;
-        ElStripLaunch L;
-        L.nitems = c->strip_items;
-        L.yc = c->strip_rows;
-        L.wpb = kStripWarps;
-        L.grid = c->strip_grid;
-        L.item_part = static_cast<double *>(c->strip_part.ptr);
         cudaEvent_t m0 = mark(c);
         cudaError_t err = c->use_strips ? elastic_strip_half_step(e, c->prec, c->comp, 0, L, c->stream)
                                         : elastic_half_step(e, c->prec, c->comp, 0, c->stream);

@@ -239,3 +239,38 @@ def test_elastic_full_size_1024_sampled_bit_exact():
                 if g != r:
                     bad.append(f"{name}{suffix} at {(i, j)}: gpu {g:#x} oracle {r:#x}")
     assert not bad, bad[:10]
+
+
+def test_elastic_graph_replay_on_side_stream_bit_exact():
+    """Plain elastic stepping on a created stream replays captured step graphs
+    (the step index of the source lives in device memory): oracle bits across
+    calls, with the source active."""
+    import torch
+    shape = (70, 44)
+    h = 3.0
+    rho, vp, vs = layered(shape, 3)
+    dt = 0.5 * h / 4000.0
+    P0 = 1e5
+    steps = [70, 40, 3]
+    n = sum(steps)
+    z0 = float(rho.max() * vp.max())
+    wav = np.sin(np.arange(n) * 0.2) * 0.5 * P0 * h * h / (dt * z0)
+    code, sfmt, afmt = PREC["fp16"]
+    stream = torch.cuda.Stream()
+    ctx = W.wave_create(shape, h, rho, vp, dt, code, 6, vs=vs, bc=list(BCS[0]) + [0, 0],
+                        kind=W.WAVE_ELASTIC, field_scale=P0, stream=stream.cuda_stream)
+    st = O.elastic_setup(shape, BCS[0], h, dt, rho, vp, vs, sfmt, 6, P0=P0, arith_fmt=afmt,
+                         init=_init(shape, 3, P0))
+    try:
+        for name, fid in FIELDS:
+            W.wave_set_initial(ctx, fid, _init(shape, 3, P0)[name]) if name in ("sxx", "syy", "sxy", "vx") else None
+        W.wave_set_source(ctx, W.WAVE_F_VY, [35, 10], wav)
+        st.src_index = 35 + shape[0] * 10
+        st.src = O.elastic_scale_source(wav, dt, st.Z0, P0, h, afmt)
+        for m in steps:
+            W.wave_step(ctx, m)
+        st.run(n)
+        bad = compare(ctx, st, "fp16", 6)
+    finally:
+        W.wave_destroy(ctx)
+    assert not bad, bad
