@@ -456,27 +456,40 @@ def run_w0(W, steps=None):
 
 
 # ------------------------------------------------------------ CPU oracle
-def oracle_sample(target_s: float = 12.0, n: int = 64):
-    """The CPU oracle (fp16 + sum_3op emulation, OpenMP on all host cores) on a
-    bounded sample of the workload: an n^3 grid of the same recipe. Runs
+def _oracle_rate(O, w, n, fmt, comp, target_s):
+    """Grid points per second of the oracle solver on the sample grid, over
     batches of steps until target_s seconds have elapsed."""
+    st = O.acoustic_setup(w["shape"], (1, 1, 1), w["h"], w["dt"], w["rho"], w["c"], fmt, comp, p0=w["p0"])
+    st.run(2)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < target_s:
+        st.run(4)
+        steps += 4
+    dt = time.perf_counter() - t0
+    return n ** 3 * steps / dt, steps, dt
+
+
+def oracle_sample(target_s: float = 12.0, n: int = 64):
+    """The CPU oracle on a bounded sample of the workload, an n^3 grid of the
+    same recipe: the fp16 + sum_3op emulation on all host cores for target_s
+    seconds (the reported value), then, for context, the binary64 solver on
+    all cores and the fp16 emulation on one core, target_s / 4 seconds each."""
     import oracle as O
     from paper_2310_00236_gb300 import inputs
     w = inputs.acoustic_3d_random(n=n, sigma_cells=16.0 * n / 512, ic_sigma_cells=6.0 * n / 512,
                                   smooth_dtype=np.float64)
-    st = O.acoustic_setup(w["shape"], (1, 1, 1), w["h"], w["dt"], w["rho"], w["c"], O.FP16, 3,
-                          p0=w["p0"])
-    st.run(2)
-    steps, t0 = 0, time.perf_counter()
-    batch = 4
-    while time.perf_counter() - t0 < target_s:
-        st.run(batch)
-        steps += batch
-    dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": n ** 3 * steps / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n}^3 grid of the same recipe, fp16+sum_3op emulation, {steps} steps, "
-                      f"{dt:.1f} s"}
+    cores = O.set_threads()
+    r16, steps, dt = _oracle_rate(O, w, n, O.FP16, 3, target_s)
+    r64, s64, d64 = _oracle_rate(O, w, n, O.FP64, 0, target_s / 4)
+    O.set_threads(1)
+    try:
+        r1, s1, d1 = _oracle_rate(O, w, n, O.FP16, 3, target_s / 4)
+    finally:
+        O.set_threads(cores)
+    return {"value": r16 / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n}^3 grid of the same recipe, fp16+sum_3op emulation, {steps} steps, {dt:.1f} s",
+            "fp64_solver": {"value": r64 / 1e9, "cores": cores, "sample": f"{s64} steps, {d64:.1f} s"},
+            "fp16_one_core": {"value": r1 / 1e9, "cores": 1, "sample": f"{s1} steps, {d1:.1f} s"}}
 
 
 # ------------------------------------------------------------------ main
@@ -522,7 +535,7 @@ def main_reference(args):
     st.run(args.steps)
     dt = time.perf_counter() - t0
     value = n ** 3 * args.steps / dt / 1e9
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = O.set_threads()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16",

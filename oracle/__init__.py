@@ -58,6 +58,8 @@ def lib():
         L.orc_sum_op_array.argtypes = [i64, C.c_int, dp, dp, C.c_int, dp, dp]
         L.orc_stencil_c2.restype = C.c_double
         L.orc_stencil_c2.argtypes = [C.c_int]
+        L.orc_set_threads.restype = C.c_int
+        L.orc_set_threads.argtypes = [C.c_int]
         L.orc_acoustic_apply_walls.argtypes = [C.c_void_p, dp, dp, dp, dp]
         L.orc_acoustic_run.restype = C.c_int
         L.orc_acoustic_run.argtypes = ([C.c_void_p] + [dp] * 8 + [dp] * 4 +
@@ -141,6 +143,14 @@ def stencil_c2(fmt: int) -> float:
 # --------------------------------------------------------------------------
 # Acoustic solver (Eq. 1, Algorithms 1 and 2)
 # --------------------------------------------------------------------------
+
+def set_threads(n: int = 0) -> int:
+    """Set the OpenMP thread count of the solvers (n <= 0 leaves it) and return
+    the count in force. The results do not depend on it: every parallel loop
+    writes disjoint points and the energy partial sums are combined in a fixed
+    order (pinned by the thread-count invariance test)."""
+    return int(lib().orc_set_threads(int(n)))
+
 
 class AcousticCfg(C.Structure):
     _fields_ = [("ndim", C.c_int32), ("bc", C.c_int32 * 3), ("n", C.c_int64 * 3),

@@ -29,6 +29,7 @@
  */
 #include <math.h>
 #include <float.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -191,6 +192,16 @@ static double stencil(double fm3, double fm1, double fp1, double fp3, int f)
 }
 
 double orc_stencil_c2(int fmt) { return orc_round(1.0 / 24.0, fmt); }
+
+/* Threads used by the OpenMP loops of the solvers (n <= 0: leave unchanged).
+ * Returns the count now in force. Timing only: the results do not depend on
+ * it, since every parallel loop writes disjoint points and the energy sums
+ * are taken in a fixed order. */
+int orc_set_threads(int n)
+{
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+}
 
 /* Solution update V += inc of Algorithm 1 (comp = 0) or the compensated update
  * of Algorithm 2 (comp = 3 or 6). The carried compensation T is added to the

@@ -169,3 +169,23 @@ def test_fp64_equals_fp32_to_roundoff(oracle_lib):
         r[fmt] = st.p
     err = np.linalg.norm(r[O.FP32] - r[O.FP64]) / np.linalg.norm(r[O.FP64])
     assert 0 < err < 1e-5
+
+
+def test_results_independent_of_thread_count(oracle_lib):
+    """The OpenMP loops write disjoint points and combine the energy partial
+    sums in a fixed order, so one thread and all threads give identical bits
+    (the CPU baseline times both)."""
+    w = inputs.acoustic_3d_random(n=24, sigma_cells=2.0, ic_sigma_cells=2.0, smooth_dtype=np.float64)
+    out = []
+    before = O.set_threads()
+    try:
+        for t in (1, max(2, before)):
+            O.set_threads(t)
+            st = O.acoustic_setup(w["shape"], (1, 0, 1), w["h"], w["dt"], w["rho"], w["c"], O.FP16, 3,
+                                  p0=w["p0"])
+            _, E = st.run(6, energy=True)
+            out.append((st.p.copy(), st.v[0].copy(), np.array(E)))
+    finally:
+        O.set_threads(before)
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
