@@ -17,8 +17,12 @@
 // TMA copies (cp.async.bulk.tensor, one box per array and plane; completion
 // counted on mbarriers): a ring of p^n planes running ahead of the compute
 // (the z stencil of v_z needs planes k..k+3) and a ring of the other arrays of
-// plane k. Row groups whose rows lie outside the grid (their images are read
-// instead) are copied row by row with bulk copies. Four consumer warps
+// plane k. With rigid y walls the boxes are used at the y faces too: the rows
+// past a face are filled with zeros and the consumers read the mirror rows,
+// which lie inside the tile, with the image's sign. With periodic y walls the
+// row groups that cross a face are copied row by row (bulk copies) from the
+// wrapped rows. (Row-by-row copies made the face tiles 4x slower than the
+// interior ones.) Four consumer warps
 // compute on 16-byte vectors with packed-pair arithmetic; each warp owns four
 // rows of the tile and recomputes the v_y rows it needs from its neighbours
 // (two above, one below), so the new velocities are exchanged only inside a
@@ -159,10 +163,15 @@ __global__ void __launch_bounds__(160, 4)
             }
             return bytes;
         };
-        const bool own_box = y0 + TY <= ny;            // all own rows inside the grid
-        const bool top_box = y0 >= 3;                  // p rows y0-3..y0-1 inside
-        const bool bot_box = y0 + TY + 3 <= ny;        // p rows y0+TY..y0+TY+2 inside
-        const bool vy_box = y0 >= 2 && y0 + TY + 1 <= ny;  // v_y rows y0-2..y0+TY inside
+        // Boxes wherever their rows lie inside the grid. With rigid y walls
+        // boxes are used everywhere: the rows past the y faces are filled with
+        // zeros and the consumers read the mirror rows inside the tile instead;
+        // periodic y faces copy the wrapped rows row by row.
+        const bool rigid_y = bcy == BC_RIGID;
+        const bool own_box = rigid_y || y0 + TY <= ny;            // all own rows inside the grid
+        const bool top_box = rigid_y || y0 >= 3;                  // p rows y0-3..y0-1 inside
+        const bool bot_box = rigid_y || y0 + TY + 3 <= ny;        // p rows y0+TY..y0+TY+2 inside
+        const bool vy_box = rigid_y || (y0 >= 2 && y0 + TY + 1 <= ny);  // v_y rows y0-2..y0+TY inside
         // one p plane: the boxes (lane 0) and the row-by-row groups (spread over lanes)
         auto p_plane = [&](int m, S *dst, uint64_t *bar, bool issue) -> uint32_t {
             const S *pin = static_cast<const S *>(fp.p_in);
@@ -271,6 +280,10 @@ __global__ void __launch_bounds__(160, 4)
     auto plane_sign = [&](int m) -> int { int t; return img_node(m, nz, bcz, t); };
     // tiles whose p rows y0-3..y0+TY+2 are all inside the grid read no images in y
     const bool inner_y = y0 >= 3 && y0 + TY + 3 <= ny;
+    // rigid y walls: rows past the y faces were loaded as zeros; the images are
+    // read from the mirror rows, which lie inside the tile's rows (p: odd
+    // about the wall nodes 0 and ny, the wall row itself zero; v_y: even)
+    const bool rigid_y = bcy == BC_RIGID;
     // raw p vector of local row lr (-3..TY+2) at the own lane
     auto p_vec = [&](const S *pst, int lr) -> Raw {
         const S *ptr = (lr >= 0 && lr < TY) ? pst + lr * WIDE + HALO + lx * VEC
@@ -397,15 +410,30 @@ __global__ void __launch_bounds__(160, 4)
                 Raw pr[4];
 #pragma unroll
                 for (int t = 0; t < 4; t++) {
-                    const int l = lr - 1 + t;
+                    int l = lr - 1 + t, sg = 1;
+                    if (!inner_y) {
+                        if (rigid_y) {
+                            int jm;
+                            sg = img_node(y0 + l, ny, bcy, jm);
+                            l = sg == 0 ? 0 : jm - y0;  // the wall row reads as zero
+                        } else {
+                            sg = row_sign(y0 + l);  // the rows hold their images
+                        }
+                    }
                     const S *ptr = (l >= 0 && l < TY) ? pk + l * WIDE + HALO + ln * VEC
                                                       : pk + SH::P_HALO + (l < 0 ? l + 3 : 3 + l - TY) * TX + ln * VEC;
                     const Raw r = *reinterpret_cast<const Raw *>(ptr);
-                    pr[t] = inner_y ? r : signed_raw<V>(r, row_sign(y0 + l));
+                    pr[t] = inner_y ? r : signed_raw<V>(r, sg);
                 }
                 const AV D = vstencil<V>(V::ld(pr[0]), V::ld(pr[1]), V::ld(pr[2]), V::ld(pr[3]));
-                Vv = vec_at(ost + SH::O_VY + (lr + 2) * TX + ln * VEC);
-                Tv = COMP ? vec_at(ost + SH::O_TVY + (lr + 2) * TX + ln * VEC) : V::zero();
+                int lv = lr;
+                if (!inner_y && rigid_y) {
+                    int jm;
+                    img_half(y0 + lr, ny, bcy, jm);
+                    lv = jm - y0;
+                }
+                Vv = vec_at(ost + SH::O_VY + (lv + 2) * TX + ln * VEC);
+                Tv = COMP ? vec_at(ost + SH::O_TVY + (lv + 2) * TX + ln * VEC) : V::zero();
                 V::template update<COMP>(Vv, Tv, V::mul(ay, D));
                 *reinterpret_cast<Raw *>(nvy + (lr - wr0) * TX + ln * VEC) = Vv;
             };

@@ -211,6 +211,16 @@ def test_fused_ragged_y_z_rigid_many_chunks(prec, comp):
     _uniform_rho_run((nx, 37, 29), (R, R, R), prec, comp, 7, zchunk=5)
 
 
+@pytest.mark.parametrize("ny", [8, 17, 19, 34, 50])
+def test_fused_rigid_y_faces_every_tail(ny):
+    """Rigid y walls: the tiles at the y faces load whole boxes (rows past the
+    faces read as zero) and take the images from the mirror rows inside the
+    tile. Row counts that leave 1, 2, 3 and 16 rows in the last tile, and one
+    tile spanning both faces."""
+    _uniform_rho_run((64, ny, 11), (R, R, R), "fp16", 3, 9, zchunk=4, src=True)
+    _uniform_rho_run((32, ny, 9), (R, R, P), "fp32", 0, 6, zchunk=3)
+
+
 @pytest.mark.parametrize("prec,comp", [("fp16", 3), ("bf16", 6), ("fp32", 0), ("fp16_f32arith", 3)])
 def test_fused_periodic_mixed_source(prec, comp):
     """Periodic y and z, rigid x (the one-pass step reads rigid x images)."""
