@@ -52,7 +52,7 @@ BYTES_2D = (2 + 8 + 8) + (4 + 6 + 4)
 # dram__bytes_write.sum from one ncu capture on a 384^3 case, divided by the
 # points; traffic grows with the points). Kept only while the kernel is the one
 # that was captured: profiles/acoustic3d_fused_fp16_kahan_512.md.
-MEASURED_TRAFFIC_PER_POINT = {("fp16", True, "fused"): (1088.901e6 + 863.844e6) / 384 ** 3}
+MEASURED_TRAFFIC_PER_POINT = {("fp16", True, "fused"): (1064.997e6 + 862.244e6) / 384 ** 3}
 
 KERNEL_NAMES = {"kv": "velocity half step", "kp": "pressure half step",
                 "fused": "one-pass step (both half steps)"}
