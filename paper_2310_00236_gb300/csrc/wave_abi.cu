@@ -252,6 +252,12 @@ struct wave_ctx {
         DevBuf seg;                   // v^{n+1/2} of up to K steps (ndim arrays each)
         int64_t seg_lo = -1, seg_n = 0;
         DevBuf mu, nu[3], g;          // binary32, pitched like the fields
+        // one-pass adjoint leapfrog (3D, uniform a_c): the second buffer set
+        // of mu~, nu~ and the tensor maps of both sets (fm[fset]: current)
+        bool fused = false;
+        DevBuf mu_alt, nu_alt[3];
+        MapBlob fm[2];
+        int fset = 0;
         uint32_t na_uni[3] = {0, 0, 0}, nb_uni = 0;
         DevBuf rec_w;                 // residual weight per receiver (b, 0 on rigid walls)
         DevBuf rec_order, rec_start;  // receivers grouped by point, in receiver order
@@ -564,11 +570,15 @@ static void adjoint_free(wave_ctx *c) {
     dev_free(c, A.cps);
     dev_free(c, A.seg);
     dev_free(c, A.mu);
+    dev_free(c, A.mu_alt);
     dev_free(c, A.g);
     dev_free(c, A.rec_w);
     dev_free(c, A.rec_order);
     dev_free(c, A.rec_start);
-    for (int ax = 0; ax < 3; ax++) dev_free(c, A.nu[ax]);
+    for (int ax = 0; ax < 3; ax++) {
+        dev_free(c, A.nu[ax]);
+        dev_free(c, A.nu_alt[ax]);
+    }
     A = wave_ctx::Adjoint();
 }
 
@@ -1446,6 +1456,8 @@ static wave_status make_neg_coef(wave_ctx *c, DevBuf &dst, int w) {
                       "adjoint multipliers");
 }
 
+static wave_status adjoint_fused_setup(wave_ctx *c);
+
 extern "C" wave_status wave_record(wave_ctx *c, int64_t nsteps, int64_t ncheckpoints) {
     CHECK_CTX(c);
     if (c->kind != WAVE_ACOUSTIC) return fail(WAVE_ENOTIMPL, "the adjoint covers the acoustic system");
@@ -1550,6 +1562,7 @@ extern "C" wave_status wave_record(wave_ctx *c, int64_t nsteps, int64_t ncheckpo
             st = cuda_check(c, e, "velocity upload");
         }
     }
+    if (!st) st = adjoint_fused_setup(c);
     if (st) {
         adjoint_free(c);
         return st;
@@ -1601,14 +1614,10 @@ static wave_status adjoint_replay(wave_ctx *c, int64_t si) {
     return WAVE_OK;
 }
 
-extern "C" wave_status wave_adjoint_step(wave_ctx *c, int64_t n, const float *residual) {
-    CHECK_CTX(c);
-    auto &A = c->adj;
-    if (!A.active) return fail(WAVE_ESTATE, "no recorded run: call wave_record first");
-    if (n < 0 || n > A.t) return fail(WAVE_EINVAL, "n = %lld outside 0..%lld", (long long)n, (long long)A.t);
-    if (c->nrec && !residual) return fail(WAVE_EINVAL, "residual traces are NULL");
-    if (n == 0) return WAVE_OK;
-    AcParams prm;
+// Leapfrog parameters of the adjoint sweep on the current mu~, nu~: the
+// negated binary32 multipliers, no source, no energy.
+static void adjoint_params(const wave_ctx *c, AcParams &prm) {
+    const auto &A = c->adj;
     memset(&prm, 0, sizeof prm);
     for (int ax = 0; ax < 3; ax++) {
         prm.n[ax] = (int)c->n[ax];
@@ -1624,6 +1633,43 @@ extern "C" wave_status wave_adjoint_step(wave_ctx *c, int64_t n, const float *re
     prm.b_uni = A.nb_uni;
     prm.src_q = -1;
     prm.src_i = prm.src_j = prm.src_k = -1;
+}
+
+// Second buffer set and tensor maps for the one-pass adjoint leapfrog, where
+// the one-pass step applies (3D, uniform a_c, rigid x faces). Without them the
+// sweep runs the two half-step kernels; both give the same bits.
+static wave_status adjoint_fused_setup(wave_ctx *c) {
+    auto &A = c->adj;
+    AcParams prm;
+    adjoint_params(c, prm);
+    A.fused = false;
+    if (!c->use_fused || !acoustic_fused_supported(prm, c->ndim, PREC_FP32) ||
+        fused_maps_bytes() > sizeof(A.fm[0].b))
+        return WAVE_OK;
+    const size_t fbytes = (size_t)c->total * sizeof(float);
+    wave_status st = dev_alloc(c, A.mu_alt, fbytes);
+    for (int ax = 0; ax < c->ndim && !st; ax++) st = dev_alloc(c, A.nu_alt[ax], fbytes);
+    if (st) return st;
+    for (int set = 0; set < 2; set++) {
+        const void *in[7] = {set ? A.mu_alt.ptr : A.mu.ptr, set ? A.nu_alt[0].ptr : A.nu[0].ptr,
+                             set ? A.nu_alt[1].ptr : A.nu[1].ptr, set ? A.nu_alt[2].ptr : A.nu[2].ptr,
+                             nullptr, nullptr, nullptr};
+        if (!acoustic_fused_encode(A.fm[set].b, prm, in, nullptr, PREC_FP32, 0)) return WAVE_OK;
+    }
+    A.fset = 0;
+    A.fused = true;
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_adjoint_step(wave_ctx *c, int64_t n, const float *residual) {
+    CHECK_CTX(c);
+    auto &A = c->adj;
+    if (!A.active) return fail(WAVE_ESTATE, "no recorded run: call wave_record first");
+    if (n < 0 || n > A.t) return fail(WAVE_EINVAL, "n = %lld outside 0..%lld", (long long)n, (long long)A.t);
+    if (c->nrec && !residual) return fail(WAVE_EINVAL, "residual traces are NULL");
+    if (n == 0) return WAVE_OK;
+    AcParams prm;
+    adjoint_params(c, prm);
     const bool stream_ok = acoustic_stream_supported(prm, c->ndim, PREC_FP32);
     AdjGradParams gp;
     memset(&gp, 0, sizeof gp);
@@ -1633,7 +1679,6 @@ extern "C" wave_status wave_adjoint_step(wave_ctx *c, int64_t n, const float *re
     }
     gp.sy = c->pitch;
     gp.sz = c->plane;
-    gp.mu = static_cast<const float *>(A.mu.ptr);
     gp.g = static_cast<float *>(A.g.ptr);
     const int fmt = c->prec == PREC_FP32 ? ADJ_F32 : is_bf16_storage(c->prec) ? ADJ_BF16 : ADJ_F16;
     const size_t bytes = (size_t)c->total * elem_bytes(c->prec);
@@ -1647,18 +1692,37 @@ extern "C" wave_status wave_adjoint_step(wave_ctx *c, int64_t n, const float *re
                                    static_cast<const float *>(A.rec_w.ptr), static_cast<const int *>(A.rec_order.ptr),
                                    static_cast<const int *>(A.rec_start.ptr), A.ngroups, residual + s * c->nrec,
                                    c->stream);
-        if (e == cudaSuccess)
-            e = stream_ok ? acoustic_stream_half_step(prm, PREC_FP32, 0, 0, c->zchunk, c->stream)
-                          : acoustic_generic_half_step(prm, c->ndim, PREC_FP32, 0, 0, c->stream);
         const int64_t gstep = A.step0 + s;
         gp.src_q = (c->src_q >= 0 && gstep < c->src_nt) ? c->src_q : -1;
         gp.src_value = gp.src_q >= 0 ? c->src_host[gstep] : 0.f;
+        gp.mu = static_cast<const float *>(A.mu.ptr);
         for (int ax = 0; ax < c->ndim; ax++)
             gp.v[ax] = static_cast<const char *>(A.seg.ptr) + (size_t)((s - A.seg_lo) * c->ndim + ax) * bytes;
-        if (e == cudaSuccess) e = adj_grad(gp, c->ndim, fmt, c->stream);
-        if (e == cudaSuccess)
-            e = stream_ok ? acoustic_stream_half_step(prm, PREC_FP32, 0, 1, c->zchunk, c->stream)
-                          : acoustic_generic_half_step(prm, c->ndim, PREC_FP32, 0, 1, c->stream);
+        if (A.fused) {
+            // g reads mu~ after the injection and before the pressure update,
+            // as in the two-kernel order below (the velocity update leaves mu~)
+            if (e == cudaSuccess) e = adj_grad(gp, c->ndim, fmt, c->stream);
+            const void *in[7] = {A.mu.ptr, A.nu[0].ptr, A.nu[1].ptr, A.nu[2].ptr, nullptr, nullptr, nullptr};
+            void *out[7] = {A.mu_alt.ptr, A.nu_alt[0].ptr, A.nu_alt[1].ptr, A.nu_alt[2].ptr,
+                            nullptr, nullptr, nullptr};
+            int *err = reinterpret_cast<int *>(static_cast<char *>(c->e_misc.ptr) + 16);
+            prm.p = A.mu.ptr;
+            for (int ax = 0; ax < 3; ax++) prm.v[ax] = A.nu[ax].ptr;
+            if (e == cudaSuccess)
+                e = acoustic_fused_step(prm, A.fm[A.fset].b, in, out, nullptr, PREC_FP32, 0, c->zchunk, err,
+                                        c->stream);
+            A.fset ^= 1;
+            std::swap(A.mu, A.mu_alt);
+            for (int ax = 0; ax < 3; ax++) std::swap(A.nu[ax], A.nu_alt[ax]);
+        } else {
+            if (e == cudaSuccess)
+                e = stream_ok ? acoustic_stream_half_step(prm, PREC_FP32, 0, 0, c->zchunk, c->stream)
+                              : acoustic_generic_half_step(prm, c->ndim, PREC_FP32, 0, 0, c->stream);
+            if (e == cudaSuccess) e = adj_grad(gp, c->ndim, fmt, c->stream);
+            if (e == cudaSuccess)
+                e = stream_ok ? acoustic_stream_half_step(prm, PREC_FP32, 0, 1, c->zchunk, c->stream)
+                              : acoustic_generic_half_step(prm, c->ndim, PREC_FP32, 0, 1, c->stream);
+        }
         if (e != cudaSuccess) return cuda_check(c, e, "adjoint step");
         A.t--;
     }

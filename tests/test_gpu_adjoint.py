@@ -65,11 +65,11 @@ def _observed(k):
     return tr
 
 
-def _gpu_gradient(k, prec, comp, d_obs, ncp=0, splits=None):
+def _gpu_gradient(k, prec, comp, d_obs, ncp=0, splits=None, kernel=0):
     import torch
     code = PREC[prec][0]
     ctx = W.wave_create(k["shape"], k["h"], k["rho"], k["c0"], k["dt"], code, comp,
-                        bc=[b for b in k["bc"] for _ in range(2)] + [0] * (6 - 2 * k["nd"]))
+                        bc=[b for b in k["bc"] for _ in range(2)] + [0] * (6 - 2 * k["nd"]), kernel=kernel)
     try:
         W.wave_set_source(ctx, W.WAVE_F_P, k["src"], k["wav"])
         n, nrec = k["nsteps"], len(k["rec"])
@@ -132,6 +132,20 @@ def test_adjoint_checkpoints_and_splits_bit_identical(prec, comp, const_rho):
     for ncp, splits in ((1, None), (5, [7, 30]), (37, [1] * 37), (0, [36, 1])):
         g, _ = _gpu_gradient(k, prec, comp, d_obs, ncp=ncp, splits=splits)
         assert np.array_equal(g, g0), (ncp, splits)
+
+
+@pytest.mark.parametrize("prec,comp", [("fp16", 3), ("fp32", 0)])
+def test_one_pass_adjoint_equals_two_kernel_adjoint(prec, comp):
+    """Constant density, rigid x and n[0] = 64: the adjoint sweep runs the
+    one-pass step on ping-pong buffers (kernel 0); with the streaming kernels
+    forced (kernel 2) it runs the two half steps. Same gradient bits."""
+    k = _case((64, 24, 16), (R, R, P), 23, const_rho=True)
+    d_obs = _observed(k)
+    g_one, tr_one = _gpu_gradient(k, prec, comp, d_obs, ncp=4, splits=[9, 14])
+    g_two, tr_two = _gpu_gradient(k, prec, comp, d_obs, ncp=4, splits=[9, 14], kernel=2)
+    assert np.array_equal(tr_one, tr_two)
+    assert np.array_equal(g_one, g_two)
+    assert np.abs(g_one).max() > 0
 
 
 def test_autograd_function_matches_abi_and_oracle():
