@@ -281,7 +281,9 @@ def acoustic_coefficients(cfg: AcousticCfg, h: float, dt: float, P0: float, rho,
 
 
 def scale_pressure(p, P0, fmt):
-    """p^ = RN(p / P0). parity unpinned beyond the rounding pins."""
+    """p^ = RN(p / P0) (Section 3's scaled pressure). Pinned by the rounding
+    pins and by the physical-units standing mode (a wrong P0 changes the
+    physical solution read back as P0 p^)."""
     p = _f64(p)
     out = np.empty_like(p)
     lib().orc_scale_pressure(p.size, _dp(p), P0, fmt, _dp(out))
@@ -289,7 +291,9 @@ def scale_pressure(p, P0, fmt):
 
 
 def scale_velocity(v, Z0, P0, fmt):
-    """v^ = RN(v * Z0 / P0). parity unpinned beyond the rounding pins."""
+    """v^ = RN(v * Z0 / P0) (Section 3's scaled velocity). Pinned by the
+    rounding pins and by the physical-units standing mode with rho, c, P0 far
+    from 1 (a wrong or missing Z0 or P0 fails it)."""
     v = _f64(v)
     out = np.empty_like(v)
     lib().orc_scale_velocity(v.size, _dp(v), Z0, P0, fmt, _dp(out))
