@@ -54,34 +54,106 @@ __device__ __forceinline__ float ld_f32(const void *f, int64_t q) {
     return __half2float(__half(hr));
 }
 
+// Eight consecutive storage values from v at q (q a multiple of 8: 16-byte
+// aligned for 16-bit storage, 32-byte for binary32), as binary32.
+template <int FMT>
+__device__ __forceinline__ void ld8(const void *v, int64_t q, float f[8]) {
+    if (FMT == ADJ_F32) {
+        const float4 *p = reinterpret_cast<const float4 *>(static_cast<const float *>(v) + q);
+        const float4 a = __ldg(p), b = __ldg(p + 1);
+        f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
+        f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
+        return;
+    }
+    const uint4 u = __ldg(reinterpret_cast<const uint4 *>(static_cast<const uint16_t *>(v) + q));
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+        const uint16_t h = (uint16_t)(e & 1 ? w[e >> 1] >> 16 : w[e >> 1] & 0xFFFFu);
+        if (FMT == ADJ_BF16) {
+            f[e] = __uint_as_float((uint32_t)h << 16);
+        } else {
+            __half_raw hr;
+            hr.x = h;
+            f[e] = __half2float(__half(hr));
+        }
+    }
+}
+
 // g += mu * (sum_c D_c v_c + s) at every p node, in binary32, from the forward
 // velocities of the step (storage format FMT) and the scaled source value.
+// One thread per 8 consecutive x nodes: the x stencils share 11 values of v_x,
+// the y and z stencils read 4 rows / planes of 8 values each. Per node the
+// operations and their order are those of one stencil per axis, x then y then z.
 template <int FMT, int NDIM>
 __global__ void __launch_bounds__(128) adj_grad_kernel(AdjGradParams P) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i0 = (blockIdx.x * blockDim.x + threadIdx.x) * 8;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = NDIM == 3 ? (int)blockIdx.z : 0;
-    if (i >= P.n[0] || j >= P.n[1]) return;
-    const int idx[3] = {i, j, k};
-    const int64_t str[3] = {1, P.sy, P.sz};
-    const int64_t q = i + P.sy * j + P.sz * k;
+    const int nx = P.n[0];
+    if (i0 >= nx || j >= P.n[1]) return;
+    const int64_t row = P.sy * j + P.sz * k;  // element (0, j, k)
     const float c1 = 1.125f, c2 = 1.0f / 24.0f;
-    float R = 0.f;
+    float R[8];
+    // x: v_x at i0-2 .. i0+8 (images outside 0..nx-1)
+    {
+        float f[11];
+        if (i0 >= 2 && i0 + 9 <= nx) {
+            ld8<FMT>(P.v[0], row + i0, f + 2);
+            f[0] = ld_f32<FMT>(P.v[0], row + i0 - 2);
+            f[1] = ld_f32<FMT>(P.v[0], row + i0 - 1);
+            f[10] = ld_f32<FMT>(P.v[0], row + i0 + 8);
+        } else {
+            // the nodes below nx read x indices up to nx; past that the
+            // values only feed nodes that are not stored, and are not loaded
 #pragma unroll
-    for (int c = 0; c < NDIM; c++) {
-        const int m = idx[c];
-        const int64_t base = q - str[c] * m;
-        float f[4];
+            for (int t = 0; t < 11; t++) {
+                f[t] = 0.f;
+                if (i0 - 2 + t <= nx) {
+                    int mm;
+                    img_half(i0 - 2 + t, nx, P.bc[0], mm);
+                    f[t] = ld_f32<FMT>(P.v[0], row + mm);
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 8; e++) R[e] = 0.f + (c1 * (f[e + 2] - f[e + 1]) - c2 * (f[e + 3] - f[e]));
+    }
+    // y and z: rows j-2 .. j+1 and planes k-2 .. k+1 of the own 8 columns
+#pragma unroll
+    for (int c = 1; c < NDIM; c++) {
+        const int m = c == 1 ? j : k;
+        const int64_t str = c == 1 ? P.sy : P.sz;
+        float f[4][8];
 #pragma unroll
         for (int t = 0; t < 4; t++) {
             int mm;
             img_half(m - 2 + t, P.n[c], P.bc[c], mm);
-            f[t] = ld_f32<FMT>(P.v[c], base + str[c] * mm);
+            ld8<FMT>(P.v[c], row - str * m + str * mm + i0, f[t]);
         }
-        R += c1 * (f[2] - f[1]) - c2 * (f[3] - f[0]);
+#pragma unroll
+        for (int e = 0; e < 8; e++) R[e] += c1 * (f[2][e] - f[1][e]) - c2 * (f[3][e] - f[0][e]);
     }
-    if (q == P.src_q) R += P.src_value;
-    P.g[q] += P.mu[q] * R;
+    const int64_t q0 = row + i0;
+    if (P.src_q >= q0 && P.src_q < q0 + 8) {
+#pragma unroll
+        for (int e = 0; e < 8; e++)
+            if (q0 + e == P.src_q) R[e] += P.src_value;
+    }
+    float4 *g4 = reinterpret_cast<float4 *>(P.g + q0);
+    const float4 *m4 = reinterpret_cast<const float4 *>(P.mu + q0);
+    if (i0 + 8 <= nx) {
+        const float4 ma = m4[0], mb = m4[1];
+        float4 ga = g4[0], gb = g4[1];
+        ga.x += ma.x * R[0]; ga.y += ma.y * R[1]; ga.z += ma.z * R[2]; ga.w += ma.w * R[3];
+        gb.x += mb.x * R[4]; gb.y += mb.y * R[5]; gb.z += mb.z * R[6]; gb.w += mb.w * R[7];
+        g4[0] = ga;
+        g4[1] = gb;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; e++)
+            if (i0 + e < nx) P.g[q0 + e] += P.mu[q0 + e] * R[e];
+    }
 }
 
 // out[i + nx (j + ny k)] = g[q] * two_over_c[...]: dJ/dc, unpitched.
@@ -122,8 +194,9 @@ cudaError_t adj_inject(float *mu, const int64_t *rec_q, const float *rec_w, cons
 
 template <int FMT>
 static void launch_grad(const AdjGradParams &P, int ndim, cudaStream_t st) {
+    // 32 x 4 threads of 8 x nodes each: 256 x 4 nodes per block
     dim3 block(32, 4, 1);
-    dim3 grid((P.n[0] + 31) / 32, (P.n[1] + 3) / 4, ndim == 3 ? P.n[2] : 1);
+    dim3 grid((P.n[0] + 255) / 256, (P.n[1] + 3) / 4, ndim == 3 ? P.n[2] : 1);
     if (ndim == 3) adj_grad_kernel<FMT, 3><<<grid, block, 0, st>>>(P);
     else adj_grad_kernel<FMT, 2><<<grid, block, 0, st>>>(P);
 }
