@@ -10,6 +10,8 @@
 * Mirror symmetry, zero state, and the paper's compensation finding in the
   elastic case (Appendix A: fp16 without compensation loses energy, with
   sum_6op it does not).
+* The analytic standing P wave in physical units (rho, vp, P0 far from 1):
+  the Z0 / P0 scaling of stresses, velocities and multipliers.
 """
 import os
 from fractions import Fraction
@@ -267,3 +269,55 @@ def test_elastic_zero_state_stays_zero(oracle_lib):
         st.run(10)
         for k in O.ELASTIC_FIELDS:
             assert not np.any(st.f[k]) and not np.any(st.t[k])
+
+
+def _standing_p_wave(nx, cfl, nsteps, rho, vp, P0, S, L):
+    """Standing P wave along x in a periodic homogeneous medium, independent
+    of y, in physical units: with rho dvx/dt = d(sxx)/dx, d(sxx)/dt =
+    (lambda + 2 mu) d(vx)/dx and d(syy)/dt = lambda d(vx)/dx,
+      sxx = S cos(w t) cos(k x),  syy = lambda / (lambda + 2 mu) sxx,
+      vx = -S k / (rho w) sin(w t) sin(k x),  w = vp k,  k = 2 pi / L,
+    with the stresses at nodes i h and vx at (i + 1/2) h. Returns the largest
+    errors after nsteps of sxx and syy (relative to S) and of vx (relative to
+    S / (rho vp)), the state read back as P0 s^ and P0 v^ / Z0."""
+    ny = 8
+    h = L / nx
+    vs = vp / 1.73
+    mu = rho * vs * vs
+    lam = rho * vp * vp - 2.0 * mu
+    dt = cfl * h / vp
+    k = 2.0 * np.pi / L
+    w = vp * k
+    x = np.arange(nx) * h
+    xh = x + 0.5 * h
+
+    def fields(ts, tv):
+        sxx = S * np.cos(w * ts) * np.cos(k * x)
+        vx = -S * k / (rho * w) * np.sin(w * tv) * np.sin(k * xh)
+        return [np.repeat(f[None, :], ny, 0) for f in (sxx, lam / (lam + 2 * mu) * sxx, vx)]
+
+    sxx0, syy0, vx0 = fields(0.0, -0.5 * dt)
+    full = np.full((ny, nx), 1.0)
+    st = O.elastic_setup((nx, ny), (PER,) * 4, h, dt, rho * full, vp * full, vs * full, O.FP64, 0,
+                         P0=P0, init={"sxx": sxx0, "syy": syy0, "vx": vx0})
+    st.run(nsteps)
+    sxx, syy, vx = fields(nsteps * dt, (nsteps - 0.5) * dt)
+    es = max(np.max(np.abs(st.f["sxx"] * P0 - sxx)), np.max(np.abs(st.f["syy"] * P0 - syy))) / S
+    ev = np.max(np.abs(st.f["vx"] * P0 / st.Z0 - vx)) / (S / (rho * vp))
+    return es, ev
+
+
+def test_elastic_scaled_variables_reproduce_physical_units(oracle_lib):
+    """Scaled elastic variables (s^ = s / P0, v^ = v Z0 / P0, Z0 = max rho *
+    max vp) with rho = 2200 kg/m^3, vp = 3000 m/s, P0 = 1e5 Pa on a 256 m
+    periodic box give, read back in physical units, the same relative errors
+    against the analytic standing P wave as the nondimensional problem (rho =
+    vp = L = 1, P0 = 1), which is the same discrete problem up to rounding;
+    the errors are the scheme's own (about 1e-4 here). A wrong Z0 or P0 in
+    the scaling of stresses, velocities or multipliers fails it."""
+    nx, cfl, nsteps = 64, 0.5, 96
+    es, ev = _standing_p_wave(nx, cfl, nsteps, 2200.0, 3000.0, 1.0e5, 3.0e6, 256.0)
+    es1, ev1 = _standing_p_wave(nx, cfl, nsteps, 1.0, 1.0, 1.0, 1.0, 1.0)
+    assert 1e-7 < es1 < 1e-2 and 1e-7 < ev1 < 1e-2, (es1, ev1)
+    assert abs(es - es1) <= 1e-9 + 1e-6 * es1, (es, es1)
+    assert abs(ev - ev1) <= 1e-9 + 1e-6 * ev1, (ev, ev1)
