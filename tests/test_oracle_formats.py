@@ -170,3 +170,23 @@ def test_stencil_c2_fp16_value(oracle_lib):
     assert O.stencil_c2(O.FP16) == float(np.float16(1.0 / 24.0))
     assert O.stencil_c2(O.FP32) == float(np.float32(1.0 / 24.0))
     assert O.stencil_c2(O.FP64) == 1.0 / 24.0
+
+
+def test_rounding_exhaustive_all_binary32(oracle_lib, tmp_path):
+    """Every finite binary32 bit pattern (2^32 - 2^24) rounds to binary16 and
+    to bfloat16 exactly as the independent references in
+    tests/exhaustive/rounding_all_binary32.c (the compiler's _Float16
+    conversion; the round-to-nearest-even bit formula) do, sign included.
+    About a minute on 8 cores."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    src = os.path.join(os.path.dirname(__file__), "exhaustive", "rounding_all_binary32.c")
+    exe = str(tmp_path / "rounding_all_binary32")
+    subprocess.check_call([gcc, "-O2", "-fopenmp", src, "-o", exe, "-ldl", "-lm"])
+    out = subprocess.run([exe, O.build()], capture_output=True, text=True, timeout=900, check=True).stdout
+    words = out.split()
+    got = dict(zip(words[0::2], map(int, words[1::2])))
+    assert got == {"checked": 2 ** 32 - 2 ** 24, "fp16_mismatches": 0, "bf16_mismatches": 0}, out
