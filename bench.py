@@ -492,6 +492,59 @@ def oracle_sample(target_s: float = 12.0, n: int = 64):
             "fp16_one_core": {"value": r1 / 1e9, "cores": 1, "sample": f"{s1} steps, {d1:.1f} s"}}
 
 
+def oracle_per_config(budget: float = 2.0):
+    """CPU baseline per workload: the oracle's binary64 solver and its fp16
+    emulation (sum_3op acoustic, sum_6op elastic), on one thread and on every
+    host core, in Mpoint-updates/s: config 1 (2D acoustic 256^2), a 64^3
+    sample of the 3D recipe, config 2 (2D elastic 1024^2). Each figure times
+    about `budget` seconds of steps after one untimed step."""
+    import oracle as O
+    from paper_2310_00236_gb300 import inputs
+
+    def rate(make, pts):
+        st = make()
+        st.run(1)
+        t0 = time.perf_counter()
+        st.run(1)
+        one = time.perf_counter() - t0
+        k = max(1, int(budget / max(one, 1e-6)))
+        t0 = time.perf_counter()
+        st.run(k)
+        return pts * k / (time.perf_counter() - t0) / 1e6, k
+
+    def acoustic(w, fmt, comp):
+        bc = (O.BC_RIGID,) * w["ndim"]
+        return lambda: O.acoustic_setup(w["shape"], bc, w["h"], w["dt"], w["rho"], w["c"], fmt, comp,
+                                        p0=w["p0"])
+
+    w1 = inputs.acoustic_2d_gaussian(256, 2000)
+    w3 = inputs.acoustic_3d_random(n=64, sigma_cells=2.0, ic_sigma_cells=0.75, smooth_dtype=np.float64)
+    we = inputs.elastic_2d_layered(n=1024, steps=4000)
+    g = inputs.gaussian(we["shape"], we["h"], 20 * we["h"]) * 1e5
+
+    def elastic(fmt, comp):
+        return lambda: O.elastic_setup(we["shape"], (O.EBC_RIGID, O.EBC_RIGID, O.EBC_FREE, O.EBC_RIGID),
+                                       we["h"], we["dt"], we["rho"], we["vp"], we["vs"], fmt, comp, P0=1e5,
+                                       init={"sxx": g, "syy": g})
+
+    cores = O.set_threads()
+    out = {"kind": "oracle", "unit": "Mpoint-updates/s", "cores": cores, "nproc": os.cpu_count()}
+    cases = [("cfg1_2d_acoustic_256", 256 * 256, acoustic(w1, O.FP64, 0), acoustic(w1, O.FP16, 3)),
+             ("cfg3_3d_acoustic_sample_64", 64 ** 3, acoustic(w3, O.FP64, 0), acoustic(w3, O.FP16, 3)),
+             ("cfg2_2d_elastic_1024", 1024 * 1024, elastic(O.FP64, 0), elastic(O.FP16, 6))]
+    try:
+        for name, pts, m64, m16 in cases:
+            row = {}
+            for threads in (1, cores):
+                O.set_threads(threads)
+                row[f"fp64_{threads}t"] = round(rate(m64, pts)[0], 2)
+                row[f"fp16_emulation_{threads}t"] = round(rate(m16, pts)[0], 2)
+            out[name] = row
+    finally:
+        O.set_threads(cores)
+    return out
+
+
 # ------------------------------------------------------------------ main
 def dist_setup(backend):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -561,7 +614,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--zchunk", type=int, default=0, help="z planes per block (0: library default)")
     ap.add_argument("--shots", type=int, default=16, help="shots of the adjoint leg")
-    ap.add_argument("--leg", default="all", choices=["all", "batched", "adjoint", "elastic", "w0"],
+    ap.add_argument("--leg", default="all",
+                    choices=["all", "batched", "adjoint", "elastic", "w0", "cpu_baseline"],
                     help="run one secondary workload alone and print its JSON (profiling aid)")
     ap.add_argument("--kernel", type=int, default=0,
                     help="0 automatic, 1 one-thread-per-point, 2 two-kernel streaming")
@@ -573,6 +627,9 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return main_reference(args)
+    if args.leg == "cpu_baseline":  # the CPU oracle per workload; no GPU involved
+        print(json.dumps(oracle_per_config()), flush=True)
+        return
 
     import torch
     ws, rank, local = dist_setup("nccl")
