@@ -1,0 +1,20 @@
+"""bench.py's CPU-baseline leg on CPU: the per-workload oracle timings keep
+their keys and report the thread counts in force (tiny time budget)."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def test_cpu_baseline_leg_per_workload(oracle_lib):
+    import bench
+    import oracle as O
+    before = O.set_threads()
+    d = bench.oracle_per_config(budget=0.02)
+    assert O.set_threads() == before  # the thread count is restored
+    assert d["kind"] == "oracle" and d["unit"] == "Mpoint-updates/s" and d["cores"] == before
+    for name in ("cfg1_2d_acoustic_256", "cfg3_3d_acoustic_sample_64", "cfg2_2d_elastic_1024"):
+        row = d[name]
+        assert set(row) == {"fp64_1t", "fp16_emulation_1t", f"fp64_{before}t", f"fp16_emulation_{before}t"}
+        assert all(v > 0 for v in row.values())
