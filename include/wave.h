@@ -300,8 +300,10 @@ wave_status wave_reset(wave_ctx *ctx);
  * of each segment of K = ceil(nsteps / ncheckpoints) steps, and the end state.
  * Receivers, if set, must record p. Resets the adjoint: the adjoint fields
  * and the gradient start at zero at step nsteps. Memory: (ncheckpoints + 1)
- * states + K velocity fields + 3-5 binary32 fields. Errors: ENOTIMPL
- * (elastic), EINVAL, ENOMEM, ECUDA.
+ * states + K velocity fields + 3-5 binary32 fields (6-9 where the context
+ * runs the one-pass 3D step: the adjoint leapfrog then uses it too, on a
+ * second set of adjoint fields). Errors: ENOTIMPL (elastic), EINVAL, ENOMEM,
+ * ECUDA.
  *
  * wave_adjoint_step -- n steps of the adjoint backwards in time from the
  * current adjoint step t (t = nsteps after wave_record; n <= t). residual:
