@@ -190,3 +190,32 @@ def test_rounding_exhaustive_all_binary32(oracle_lib, tmp_path):
     words = out.split()
     got = dict(zip(words[0::2], map(int, words[1::2])))
     assert got == {"checked": 2 ** 32 - 2 ** 24, "fp16_mismatches": 0, "bf16_mismatches": 0}, out
+
+
+@pytest.fixture(scope="module")
+def ops_all_pairs_exe(tmp_path_factory):
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    src = os.path.join(os.path.dirname(__file__), "exhaustive", "ops_all_pairs.c")
+    exe = str(tmp_path_factory.mktemp("exhaustive") / "ops_all_pairs")
+    subprocess.check_call([gcc, "-O2", "-fopenmp", src, "-o", exe, "-ldl", "-lm"])
+    return exe
+
+
+@pytest.mark.parametrize("fmt,op", [(O.FP16, 0), (O.FP16, 2), (O.BF16, 0), (O.BF16, 2)])
+def test_arithmetic_exhaustive_all_pairs(oracle_lib, ops_all_pairs_exe, fmt, op):
+    """Every pair of finite binary16 (bfloat16) operands: the oracle's a + b and
+    a * b equal the references of tests/exhaustive/ops_all_pairs.c, computed in
+    binary32 and rounded by the compiler's _Float16 conversion (by the
+    round-to-nearest-even bit formula), value and sign; a - b is a + (-b).
+    10 to 30 s each on 8 cores."""
+    import subprocess
+    out = subprocess.run([ops_all_pairs_exe, O.build(), str(fmt), str(op)], capture_output=True, text=True,
+                         timeout=900, check=True).stdout
+    words = out.split()
+    got = dict(zip(words[0::2], map(int, words[1::2])))
+    nfin = 63488 if fmt == O.FP16 else 65280
+    assert got == {"pairs": nfin * nfin, "mismatches": 0}, out
