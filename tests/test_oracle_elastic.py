@@ -321,3 +321,23 @@ def test_elastic_scaled_variables_reproduce_physical_units(oracle_lib):
     assert 1e-7 < es1 < 1e-2 and 1e-7 < ev1 < 1e-2, (es1, ev1)
     assert abs(es - es1) <= 1e-9 + 1e-6 * es1, (es, es1)
     assert abs(ev - ev1) <= 1e-9 + 1e-6 * ev1, (ev, ev1)
+
+
+def test_elastic_vy_source_first_step_closed_form(oracle_lib):
+    """The vertical force source enters v_y's increment outside the 1/rho
+    factor (Eq. 2): from a zero state, one step leaves v_y = w dt / h^2 at the
+    source point in physical units (P0 v^ / Z0) and v_x zero everywhere (the
+    stresses of that step move only through the derivatives of that v_y).
+    This fixes s^ = w dt Z0 / (P0 h^2)."""
+    shape = (12, 10)
+    h, P0, w = 3.0, 1.0e5, 2.5e3
+    rho, vp, vs = _layered(shape, h)
+    dt = 0.5 * h / 4000.0
+    st = O.elastic_setup(shape, (RIG, RIG, FREE, RIG), h, dt, rho, vp, vs, O.FP64, 0, P0=P0)
+    i, j = 6, 5
+    st.src_index = i + shape[0] * j
+    st.src = O.elastic_scale_source(np.array([w, 0.0]), dt, st.Z0, P0, h, O.FP64)
+    st.run(1)
+    vy = st.f["vy"] * P0 / st.Z0
+    np.testing.assert_allclose(vy[j, i], w * dt / h ** 2, rtol=1e-14)
+    assert np.count_nonzero(st.f["vy"]) == 1 and np.count_nonzero(st.f["vx"]) == 0

@@ -241,3 +241,29 @@ def test_scaled_variables_reproduce_physical_units(oracle_lib):
     assert 1e-5 < ep1 < 1e-2 and 1e-5 < ev1 < 1e-2, (ep1, ev1)
     assert abs(ep - ep1) <= 1e-9 + 1e-6 * ep1, (ep, ep1)
     assert abs(ev - ev1) <= 1e-9 + 1e-6 * ev1, (ev, ev1)
+
+
+@pytest.mark.parametrize("shape", [(12, 10), (10, 9, 8)])
+def test_point_source_first_step_closed_form(oracle_lib, shape):
+    """A point source of volume-injection rate w (p_t = rho c^2 (div v + w
+    delta), the delta discretised as 1/h^d, Algorithm 1's source line) in a
+    zero state: after one step v is still zero and p at the source node has
+    grown by dt rho c^2 w / h^d, in physical units (P0 p^), whatever P0 and
+    the medium; nothing else moved. This fixes the source scaling
+    s^ = w Z0 / (P0 h^(d-1)) together with the multiplier b."""
+    nd = len(shape)
+    h, rho0, c0, P0, w = 7.0, 1800.0, 2400.0, 3.0e4, 0.37
+    rho = np.full(tuple(shape[::-1]), rho0)
+    c = np.full(tuple(shape[::-1]), c0)
+    rho.flat[5] = 2200.0                      # Z0 = max rho * max c differs from rho0 c0
+    dt = 0.3 * h / c0
+    st = O.acoustic_setup(shape, (O.BC_RIGID,) * nd, h, dt, rho, c, O.FP64, 0, P0=P0)
+    src = tuple(s // 2 for s in shape)
+    q = int(np.ravel_multi_index(src[::-1], tuple(shape[::-1])))
+    st.src_index = q
+    st.src = O.scale_source(np.array([w, 0.0]), st.Z0, P0, h, nd, O.FP64)
+    st.run(1)
+    expect = dt * rho0 * c0 * c0 * w / h ** nd
+    np.testing.assert_allclose(st.p.flat[q] * P0, expect, rtol=1e-14)
+    assert np.count_nonzero(st.p) == 1
+    assert all(np.count_nonzero(v) == 0 for v in st.v[:nd])
