@@ -267,3 +267,38 @@ def test_point_source_first_step_closed_form(oracle_lib, shape):
     np.testing.assert_allclose(st.p.flat[q] * P0, expect, rtol=1e-14)
     assert np.count_nonzero(st.p) == 1
     assert all(np.count_nonzero(v) == 0 for v in st.v[:nd])
+
+
+def _standing_mode_energy(N, L=640.0, rho=1800.0, c=2500.0, P0=3.0e4, Pamp=2.0e5, k=1, l=2):
+    """Relative gap between the oracle's energy of the physical-units standing
+    mode (scaled energy times energy_factor) and the continuous energy
+    1/2 int (p^2 / (rho c^2) + rho |v|^2) = Pamp^2 L^2 / (8 rho c^2) per unit
+    depth (at t = 0 all of it is in p)."""
+    h = L / N
+    dt = 0.5 * h / c
+    w = c * np.pi * np.hypot(k, l) / L
+    x = np.arange(N) * h
+    xh = x + 0.5 * h
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    p0 = Pamp * np.sin(k * np.pi * X / L) * np.sin(l * np.pi * Y / L)
+    tv = -0.5 * dt
+    Xh, Yn = np.meshgrid(xh, x, indexing="xy")
+    Xn, Yh = np.meshgrid(x, xh, indexing="xy")
+    vx = Pamp * np.sin(w * tv) / (rho * w) * (k * np.pi / L) * np.cos(k * np.pi * Xh / L) * np.sin(l * np.pi * Yn / L)
+    vy = Pamp * np.sin(w * tv) / (rho * w) * (l * np.pi / L) * np.sin(k * np.pi * Xn / L) * np.cos(l * np.pi * Yh / L)
+    st = O.acoustic_setup((N, N), (O.BC_RIGID,) * 2, h, dt, np.full((N, N), rho), np.full((N, N), c),
+                          O.FP64, 0, P0=P0, p0=p0, v0=[vx, vy])
+    _, E = st.run(20, energy=True)
+    E = np.asarray(E) * O.energy_factor(h, dt, P0, st.Z0, 2)
+    return E[0] / (Pamp ** 2 * L ** 2 / (8.0 * rho * c * c)) - 1.0, _drift(E)
+
+
+def test_energy_in_physical_units_converges_to_continuous(oracle_lib):
+    """The discrete energy converted with energy_factor (0.5 h^(d-1) P0^2 dt /
+    Z0) approaches the continuous energy of the standing mode at second order
+    (rho, c, P0 far from 1, so a wrong power of h, P0 or Z0 in the factor is
+    off by orders of magnitude), and is conserved."""
+    e64, d64 = _standing_mode_energy(64)
+    e128, d128 = _standing_mode_energy(128)
+    assert abs(e64) < 2e-3 and abs(e128) < abs(e64) / 3.0, (e64, e128)
+    assert d64 <= 1e-12 and d128 <= 1e-12
