@@ -341,3 +341,40 @@ def test_elastic_vy_source_first_step_closed_form(oracle_lib):
     vy = st.f["vy"] * P0 / st.Z0
     np.testing.assert_allclose(vy[j, i], w * dt / h ** 2, rtol=1e-14)
     assert np.count_nonzero(st.f["vy"]) == 1 and np.count_nonzero(st.f["vx"]) == 0
+
+
+def _p_wave_energy_gap(nx, L=256.0, rho=2200.0, vp=3000.0, P0=1.0e5, S=3.0e6):
+    """Relative gap between the elastic energy of the standing P wave, scaled
+    energy times 0.5 h P0^2 dt / Z0, and the continuous energy: uniaxial strain
+    (syy = lambda / (lambda + 2 mu) sxx, e_yy = 0) stores sxx^2 / (2 (lambda +
+    2 mu)) per unit area, S^2 L H / (4 (lambda + 2 mu)) in the box L x H at t = 0."""
+    ny = 8
+    h = L / nx
+    vs = vp / 1.73
+    mu = rho * vs * vs
+    lam = rho * vp * vp - 2.0 * mu
+    dt = 0.5 * h / vp
+    k = 2.0 * np.pi / L
+    w = vp * k
+    x = np.arange(nx) * h
+    sxx = S * np.cos(k * x)
+    vx = -S * k / (rho * w) * np.sin(w * (-0.5 * dt)) * np.sin(k * (x + 0.5 * h))
+
+    def rep(f):
+        return np.repeat(f[None, :], ny, 0)
+
+    full = np.ones((ny, nx))
+    st = O.elastic_setup((nx, ny), (PER,) * 4, h, dt, rho * full, vp * full, vs * full, O.FP64, 0, P0=P0,
+                         init={"sxx": rep(sxx), "syy": rep(lam / (lam + 2 * mu) * sxx), "vx": rep(vx)})
+    _, E = st.run(10, energy=True)
+    E = np.asarray(E) * 0.5 * h * P0 * P0 * dt / st.Z0
+    return E[0] / (S * S * L * ny * h / (4.0 * (lam + 2.0 * mu))) - 1.0, float(np.ptp(E) / E[0])
+
+
+def test_elastic_energy_in_physical_units_converges_to_continuous(oracle_lib):
+    """The elastic discrete energy in physical units approaches the continuous
+    strain energy of the standing P wave at second order and is conserved."""
+    g64, d64 = _p_wave_energy_gap(64)
+    g128, d128 = _p_wave_energy_gap(128)
+    assert abs(g64) < 2e-3 and abs(g128) < abs(g64) / 3.0, (g64, g128)
+    assert d64 <= 1e-12 and d128 <= 1e-12
