@@ -70,6 +70,8 @@ double orc_round(double x, int fmt)
     return copysign(r, x);
 }
 
+/* Element-wise rounding to a format (Section 2's IEEE model), exposed for the
+ * rounding pins. */
 void orc_round_array(int64_t n, const double *x, int fmt, double *out)
 {
     for (int64_t i = 0; i < n; i++) out[i] = orc_round(x[i], fmt);
@@ -579,13 +581,15 @@ int orc_acoustic_coefficients(const orc_acoustic_cfg *cfg, double h, double dt, 
     return bad;
 }
 
-/* p^ = RN(p / P0) */
+/* Scaled pressure p^ = RN(p / P0): the unit scaling that keeps the values and
+ * multipliers inside the half formats' range (Section 5, "Range"). */
 void orc_scale_pressure(int64_t n, const double *in, double P0, int fmt, double *out)
 {
     for (int64_t i = 0; i < n; i++) out[i] = orc_round(in[i] / P0, fmt);
 }
 
-/* v^ = RN((v * Z0) / P0) */
+/* Scaled velocity v^ = RN((v * Z0) / P0), Z0 = max rho * max c (the same
+ * scaling, Section 5, "Range"). */
 void orc_scale_velocity(int64_t n, const double *in, double Z0, double P0, int fmt, double *out)
 {
     for (int64_t i = 0; i < n; i++) out[i] = orc_round((in[i] * Z0) / P0, fmt);
@@ -602,7 +606,8 @@ void orc_scale_source(int64_t nt, const double *w, double Z0, double P0, double 
     for (int64_t i = 0; i < nt; i++) out[i] = orc_round(w[i] * scale, fmt);
 }
 
-/* Physical energy from the scaled one: E = 0.5 * h^(d-1) * P0^2 * dt / Z0 * E^ */
+/* Physical energy from the scaled one (the discrete energy of Section 3):
+ * E = 0.5 * h^(d-1) * P0^2 * dt / Z0 * E^ */
 double orc_energy_factor(double h, double dt, double P0, double Z0, int ndim)
 {
     const double hd1 = (ndim == 2) ? h : h * h;
@@ -665,8 +670,9 @@ static double e_read(const double *f, const orc_elastic_cfg *c, int ax, int node
     return s > 0 ? v : -v;
 }
 
-/* Points a rigid wall holds at zero: vx and sxy on column N-1 (rigid x),
- * vy and sxy on row N-1 (rigid y-hi). */
+/* Points a rigid wall holds at zero (the elastic boundaries of Appendix A as
+ * read here: frictionless rigid walls on the half points): vx and sxy on
+ * column N-1 (rigid x), vy and sxy on row N-1 (rigid y-hi). */
 void orc_elastic_apply_walls(const orc_elastic_cfg *c, double *vx, double *vy, double *sxy)
 {
     const int64_t nx = c->n[0], ny = c->n[1];
