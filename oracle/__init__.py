@@ -56,6 +56,7 @@ def lib():
         L.orc_round_array.argtypes = [i64, dp, C.c_int, dp]
         L.orc_op_array.argtypes = [i64, C.c_int, dp, dp, C.c_int, dp]
         L.orc_sum_op_array.argtypes = [i64, C.c_int, dp, dp, C.c_int, dp, dp]
+        L.orc_update_array.argtypes = [i64, C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp]
         L.orc_stencil_c2.restype = C.c_double
         L.orc_stencil_c2.argtypes = [C.c_int]
         L.orc_set_threads.restype = C.c_int
@@ -133,6 +134,28 @@ def compensated_sum(variant: int, a, b, fmt: int):
     t = np.empty_like(a)
     lib().orc_sum_op_array(a.size, variant, _dp(a), _dp(b), fmt, _dp(s), _dp(t))
     return s, t
+
+
+def solution_update(comp: int, V, T, inc, store_fmt: int, arith_fmt: int):
+    """The solution update of Algorithms 1 / 2 as the solvers apply it,
+    element-wise: V += inc (comp = 0), or R = T + inc and the compensated sum
+    of (V, R) giving the new (V, T) (comp = 3 or 6). With a wider arithmetic
+    format than the storage format (reading A5: half storage, binary32
+    registers), s = V + R in the arithmetic format, V' = RN(s), T' = RN(s - V').
+    Returns (V', T').
+
+    Pinned in tests/test_oracle_eft.py by properties computed with numpy's own
+    binary16 / binary32 arithmetic (the pair (V', T') represents
+    V + (T + inc) within the rounding of T'; a dropped, negated or unrounded
+    T fails them).
+    """
+    V, T, inc = np.broadcast_arrays(_f64(V), _f64(T), _f64(inc))
+    V, T, inc = _f64(V), _f64(T), _f64(inc)
+    Vo = np.empty_like(V)
+    To = np.empty_like(V)
+    lib().orc_update_array(V.size, comp, arith_fmt, store_fmt, _dp(V), _dp(T), _dp(inc),
+                           _dp(Vo), _dp(To))
+    return Vo, To
 
 
 def stencil_c2(fmt: int) -> float:
@@ -336,6 +359,8 @@ def acoustic_setup(shape, bc, h, dt, rho, c, store_fmt, comp, P0=1.0, arith_fmt=
 # Elastic solver (Eq. 2, Appendix A)
 # --------------------------------------------------------------------------
 EBC_PERIODIC, EBC_RIGID, EBC_FREE = 0, 1, 2
+# not a physical face: fields read zero beyond it (sub-boxes over a domain of dependence)
+EBC_ZERO = 3
 
 
 class ElasticCfg(C.Structure):
@@ -374,7 +399,7 @@ class ElasticState:
 
     def apply_walls(self):
         _elib().orc_elastic_apply_walls(C.byref(self.cfg), _dp(self.f["vx"]), _dp(self.f["vy"]),
-                                        _dp(self.f["sxy"]))
+                                        _dp(self.f["syy"]), _dp(self.f["sxy"]))
 
     def run(self, nsteps, rec_field=2, rec_index=None, energy=False):
         nrec = 0 if rec_index is None else len(rec_index)
@@ -407,7 +432,7 @@ def _elib():
     if not _elib_done:
         dp = C.POINTER(C.c_double)
         i64 = C.c_int64
-        L.orc_elastic_apply_walls.argtypes = [C.c_void_p, dp, dp, dp]
+        L.orc_elastic_apply_walls.argtypes = [C.c_void_p, dp, dp, dp, dp]
         L.orc_elastic_run.restype = C.c_int
         L.orc_elastic_run.argtypes = ([C.c_void_p] + [dp] * 10 + [dp] * 5 +
                                       [i64, i64, i64, i64, dp, C.c_int32, i64,

@@ -232,6 +232,19 @@ static void update(double *V, double *T, double inc, int comp, int af, int sf)
     }
 }
 
+/* Element-wise solution update (the function above), exposed for its pins:
+ * (Vout, Tout) = update of (V, T) by inc. */
+void orc_update_array(int64_t n, int comp, int af, int sf, const double *V, const double *T,
+                      const double *inc, double *Vout, double *Tout)
+{
+    for (int64_t i = 0; i < n; i++) {
+        double v = V[i], t = T[i];
+        update(&v, &t, inc[i], comp, af, sf);
+        Vout[i] = v;
+        Tout[i] = t;
+    }
+}
+
 /* Neumaier-compensated binary64 accumulation, for energies. */
 typedef struct { double s, c; } acc_t;
 static inline void acc_add(acc_t *a, double x)
@@ -619,18 +632,32 @@ double orc_energy_factor(double h, double dt, double P0, double Z0, int ndim)
 /* ------------------------------------------------------------------------ */
 /* Grid (Virieux staggering, the reading of the missing Fig. 1 extended to
  * Eq. 2): sxx, syy at nodes (i, j); vx at (i+1/2, j); vy at (i, j+1/2);
- * sxy at (i+1/2, j+1/2). All fields stored n[0] x n[1], x fastest.
+ * sxy at (i+1/2, j+1/2). All fields stored n[0] x n[1], x fastest; y grows
+ * downwards, row 0 is the top.
  * Boundary kinds per face (x-lo, x-hi, y-lo, y-hi):
  *   ORC_BC_PERIODIC (both faces of an axis): wrap.
  *   ORC_EBC_RIGID: frictionless rigid wall on the half points -1/2 and
  *     N-1/2: the normal velocity and the shear stress are odd about the wall
  *     (zero on it; the stored point at N-1 is held at zero), the tangential
  *     velocity and the normal stresses are even.
- *   ORC_EBC_FREE (y-lo only): traction-free top in zero-extension form: every
- *     field reads zero above row 0.
- * Each closure is a restriction of a skew operator, so the pair (gradient of
- * stress, divergence of velocity) stays an exact negative transpose. */
-enum { ORC_EBC_RIGID = 1, ORC_EBC_FREE = 2 };
+ *   ORC_EBC_FREE (y-lo only): traction-free surface (the free surface in y
+ *     of Appendix A) on the node row j = 0, by stress imaging: syy is held at
+ *     zero on that row, and above it syy and sxy are odd images of the rows
+ *     below (so both tractions vanish on the surface), while vx and vy are
+ *     even images. On the surface row itself syy = 0 leaves
+ *     d(sxx)/dt = (lambda + 2 mu - lambda^2 / (lambda + 2 mu)) d(vx)/dx, so the
+ *     multipliers there are l2m <- that reduced modulus and lam <- 0 (Dy vy
+ *     vanishes on the row because vy is even about it, so syy stays zero).
+ * Each closure keeps the map from stress to velocity the exact negative
+ * adjoint of the map from velocity to strain rate, in an inner product with
+ * unit weights except weight 1/2 on the vx and sxx points of a free surface
+ * row (that row lies on the mirror plane of the images), so the discrete
+ * energy with those weights is exactly conserved. */
+enum { ORC_EBC_RIGID = 1, ORC_EBC_FREE = 2, ORC_EBC_ZERO = 3 };
+/* ORC_EBC_ZERO is not a physical boundary: every field reads zero beyond the
+ * face. It lets a sub-box of a larger grid be stepped over the domain of
+ * dependence of its centre (the values near a cut face are wrong, the centre
+ * is not). */
 
 typedef struct {
     int64_t n[2];
@@ -639,15 +666,24 @@ typedef struct {
 } orc_elastic_cfg;
 
 /* Image of index m along an axis of N points for a field that is node-type
- * (node = 1) or half-type (node = 0) along that axis, with odd parity about a
- * rigid wall when odd = 1. lo_bc / hi_bc are the two faces' kinds.
+ * (node = 1) or half-type (node = 0) along that axis. odd: parity about a
+ * rigid wall (normal velocity, shear stress); odd_free: parity about a free
+ * surface (the stresses syy and sxy that carry a y traction; the velocities
+ * are even). lo_bc / hi_bc are the two faces' kinds.
  * Returns the sign (+1, -1) or 0 for "reads zero". */
-static int e_map(int64_t m, int64_t N, int lo_bc, int hi_bc, int node, int odd, int64_t *out)
+static int e_map(int64_t m, int64_t N, int lo_bc, int hi_bc, int node, int odd, int odd_free,
+                 int64_t *out)
 {
     if (m >= 0 && m < N) { *out = m; return 1; }
     int bc = m < 0 ? lo_bc : hi_bc;
     if (bc == ORC_BC_PERIODIC) { *out = ((m % N) + N) % N; return 1; }
-    if (bc == ORC_EBC_FREE) return 0;
+    if (bc == ORC_EBC_ZERO) return 0;
+    if (bc == ORC_EBC_FREE) {
+        /* mirror plane: the node row 0 (free surfaces are low faces only);
+         * node m <-> -m, half point m + 1/2 <-> -1-m */
+        *out = node ? -m : -1 - m;
+        return odd_free ? -1 : 1;
+    }
     /* rigid wall at -1/2 (low) or N-1/2 (high) */
     if (node) {                       /* node m <-> -1-m, 2N-1-m */
         *out = m < 0 ? -1 - m : 2 * N - 1 - m;
@@ -660,20 +696,22 @@ static int e_map(int64_t m, int64_t N, int lo_bc, int hi_bc, int node, int odd, 
 }
 
 static double e_read(const double *f, const orc_elastic_cfg *c, int ax, int node, int odd,
-                     int64_t i, int64_t j, int64_t m)
+                     int odd_free, int64_t i, int64_t j, int64_t m)
 {
     int64_t idx[2] = {i, j}, mm;
-    int s = e_map(m, c->n[ax], c->bc[2 * ax], c->bc[2 * ax + 1], node, odd, &mm);
+    int s = e_map(m, c->n[ax], c->bc[2 * ax], c->bc[2 * ax + 1], node, odd, odd_free, &mm);
     if (s == 0) return 0.0;
     idx[ax] = mm;
     double v = f[idx[0] + c->n[0] * idx[1]];
     return s > 0 ? v : -v;
 }
 
-/* Points a rigid wall holds at zero (the elastic boundaries of Appendix A as
- * read here: frictionless rigid walls on the half points): vx and sxy on
- * column N-1 (rigid x), vy and sxy on row N-1 (rigid y-hi). */
-void orc_elastic_apply_walls(const orc_elastic_cfg *c, double *vx, double *vy, double *sxy)
+/* Points a boundary holds at zero (the elastic boundaries of Appendix A as
+ * read here): vx and sxy on column N-1 (rigid x, frictionless walls on the
+ * half points), vy and sxy on row N-1 (rigid y-hi), syy on row 0 (free
+ * surface at y-lo). */
+void orc_elastic_apply_walls(const orc_elastic_cfg *c, double *vx, double *vy, double *syy,
+                             double *sxy)
 {
     const int64_t nx = c->n[0], ny = c->n[1];
     for (int64_t j = 0; j < ny; j++)
@@ -681,6 +719,7 @@ void orc_elastic_apply_walls(const orc_elastic_cfg *c, double *vx, double *vy, d
             int64_t q = i + nx * j;
             if (c->bc[1] == ORC_EBC_RIGID && i == nx - 1) { vx[q] = 0.0; sxy[q] = 0.0; }
             if (c->bc[3] == ORC_EBC_RIGID && j == ny - 1) { vy[q] = 0.0; sxy[q] = 0.0; }
+            if (c->bc[2] == ORC_EBC_FREE && j == 0) syy[q] = 0.0;
         }
 }
 
@@ -689,14 +728,14 @@ void orc_elastic_apply_walls(const orc_elastic_cfg *c, double *vx, double *vy, d
  * half point, base = target index) or base-2..base+1 (half-type f targeted at
  * a node, base = target index). */
 static double e_stencil(const double *f, const orc_elastic_cfg *c, int ax, int node, int odd,
-                        int64_t i, int64_t j, int fmt)
+                        int odd_free, int64_t i, int64_t j, int fmt)
 {
     const int64_t m = ax == 0 ? i : j;
     const int64_t first = node ? m - 1 : m - 2;
-    double a0 = e_read(f, c, ax, node, odd, i, j, first);
-    double a1 = e_read(f, c, ax, node, odd, i, j, first + 1);
-    double a2 = e_read(f, c, ax, node, odd, i, j, first + 2);
-    double a3 = e_read(f, c, ax, node, odd, i, j, first + 3);
+    double a0 = e_read(f, c, ax, node, odd, odd_free, i, j, first);
+    double a1 = e_read(f, c, ax, node, odd, odd_free, i, j, first + 1);
+    double a2 = e_read(f, c, ax, node, odd, odd_free, i, j, first + 2);
+    double a3 = e_read(f, c, ax, node, odd, odd_free, i, j, first + 3);
     return stencil(a0, a1, a2, a3, fmt);
 }
 
@@ -707,9 +746,11 @@ static double e_stencil(const double *f, const orc_elastic_cfg *c, int ax, int n
  *   syy += (lam * Dx vx) + (l2m * Dy vy)
  *   sxy += mu * (Dx vy + Dy vx)
  * Energy (scaled) after each step, with the rounded multipliers:
- *   E = sum vx^2/bx + sum vy^2/by
- *     + sum over nodes (l2m (sxx sxx' + syy syy') - lam (sxx syy' + syy sxx')) / (l2m^2 - lam^2)
- *     + sum sxy sxy' / mu              (primes: after the step) */
+ *   E = sum w vx^2/bx + sum vy^2/by
+ *     + sum over nodes w (l2m (sxx sxx' + syy syy') - lam (sxx syy' + syy sxx')) / (l2m^2 - lam^2)
+ *     + sum sxy sxy' / mu              (primes: after the step)
+ * with w = 1/2 on the row of a free surface (there lam = 0 and syy = 0, so the
+ * node term is sxx sxx' / l2m with the reduced modulus) and w = 1 elsewhere. */
 int orc_elastic_run(const orc_elastic_cfg *c, double *vx, double *tvx, double *vy, double *tvy,
                     double *sxx, double *tsxx, double *syy, double *tsyy, double *sxy,
                     double *tsxy, const double *bx, const double *by, const double *l2m,
@@ -727,14 +768,16 @@ int orc_elastic_run(const orc_elastic_cfg *c, double *vx, double *tvx, double *v
         for (int64_t j = 0; j < ny; j++)
             for (int64_t i = 0; i < nx; i++) {
                 const int64_t q = i + nx * j;
-                /* vx at (i+1/2, j): sxx node-type in x (even); sxy half-type in y (odd) */
-                double R = add_f(e_stencil(sxx, c, 0, 1, 0, i, j, stf),
-                                 e_stencil(sxy, c, 1, 0, 1, i, j, stf), stf);
+                /* vx at (i+1/2, j): sxx node-type in x (even); sxy half-type in y (odd at
+                 * rigid walls and at the free surface) */
+                double R = add_f(e_stencil(sxx, c, 0, 1, 0, 1, i, j, stf),
+                                 e_stencil(sxy, c, 1, 0, 1, 1, i, j, stf), stf);
                 double inc = orc_round(mul_f(bx[q], R, stf), af);
                 update(&vx[q], &tvx[q], inc, comp, af, sf);
-                /* vy at (i, j+1/2): sxy half-type in x (odd); syy node-type in y (even) */
-                R = add_f(e_stencil(sxy, c, 0, 0, 1, i, j, stf),
-                          e_stencil(syy, c, 1, 1, 0, i, j, stf), stf);
+                /* vy at (i, j+1/2): sxy half-type in x (odd); syy node-type in y (even at
+                 * rigid walls, odd at the free surface) */
+                R = add_f(e_stencil(sxy, c, 0, 0, 1, 1, i, j, stf),
+                          e_stencil(syy, c, 1, 1, 0, 1, i, j, stf), stf);
                 inc = orc_round(mul_f(by[q], R, stf), af);
                 if (src && q == src_index && gstep < src_nt) inc = add_f(inc, src[gstep], af);
                 update(&vy[q], &tvy[q], inc, comp, af, sf);
@@ -744,25 +787,27 @@ int orc_elastic_run(const orc_elastic_cfg *c, double *vx, double *tvx, double *v
             acc_t e = {0.0, 0.0};
             for (int64_t i = 0; i < nx; i++) {
                 const int64_t q = i + nx * j;
-                /* nodes: vx half-type in x (odd), vy half-type in y (odd) */
-                const double dxvx = e_stencil(vx, c, 0, 0, 1, i, j, stf);
-                const double dyvy = e_stencil(vy, c, 1, 0, 1, i, j, stf);
+                /* nodes: vx half-type in x (odd), vy half-type in y (odd at rigid walls,
+                 * even at the free surface) */
+                const double dxvx = e_stencil(vx, c, 0, 0, 1, 0, i, j, stf);
+                const double dyvy = e_stencil(vy, c, 1, 0, 1, 0, i, j, stf);
                 const double sxx0 = sxx[q], syy0 = syy[q], sxy0 = sxy[q];
                 double inc = orc_round(add_f(mul_f(l2m[q], dxvx, stf), mul_f(lam[q], dyvy, stf), stf), af);
                 update(&sxx[q], &tsxx[q], inc, comp, af, sf);
                 inc = orc_round(add_f(mul_f(lam[q], dxvx, stf), mul_f(l2m[q], dyvy, stf), stf), af);
                 update(&syy[q], &tsyy[q], inc, comp, af, sf);
                 /* sxy at (i+1/2, j+1/2): vy node-type in x (even), vx node-type in y (even) */
-                double R = add_f(e_stencil(vy, c, 0, 1, 0, i, j, stf),
-                                 e_stencil(vx, c, 1, 1, 0, i, j, stf), stf);
+                double R = add_f(e_stencil(vy, c, 0, 1, 0, 0, i, j, stf),
+                                 e_stencil(vx, c, 1, 1, 0, 0, i, j, stf), stf);
                 inc = orc_round(mul_f(mu[q], R, stf), af);
                 update(&sxy[q], &tsxy[q], inc, comp, af, sf);
                 if (energy) {
-                    acc_add(&e, vx[q] * vx[q] / bx[q]);
+                    const double w = (c->bc[2] == ORC_EBC_FREE && j == 0) ? 0.5 : 1.0;
+                    acc_add(&e, w * (vx[q] * vx[q] / bx[q]));
                     acc_add(&e, vy[q] * vy[q] / by[q]);
                     const double det = l2m[q] * l2m[q] - lam[q] * lam[q];
-                    acc_add(&e, (l2m[q] * (sxx0 * sxx[q] + syy0 * syy[q]) -
-                                 lam[q] * (sxx0 * syy[q] + syy0 * sxx[q])) / det);
+                    acc_add(&e, w * ((l2m[q] * (sxx0 * sxx[q] + syy0 * syy[q]) -
+                                      lam[q] * (sxx0 * syy[q] + syy0 * sxx[q])) / det));
                     if (mu[q] > 0.0) acc_add(&e, sxy0 * sxy[q] / mu[q]);
                 }
             }
@@ -791,6 +836,11 @@ int orc_elastic_run(const orc_elastic_cfg *c, double *vx, double *tvx, double *v
  *   l2m = ((dt * (lambda + 2.0 * mu)) / Z0) / h,  lam = ((dt * lambda) / Z0) / h
  *   mu_xy = 4 / (1/mu00 + 1/mu10 + 1/mu01 + 1/mu11) (0 if any is 0)
  *   mu = ((dt * mu_xy) / Z0) / h
+ * On the row of a free surface (y-lo FREE, j = 0), where syy = 0:
+ *   M = ((4.0 * mu) * (lambda + mu)) / (lambda + 2.0 * mu)
+ *     (= lambda + 2 mu - lambda^2 / (lambda + 2 mu), the modulus of sxx
+ *     under zero normal traction)
+ *   l2m = ((dt * M) / Z0) / h,  lam = 0
  * The neighbour index i+1 (j+1) wraps on periodic axes and is clamped to the
  * last point otherwise. Returns 0, or 1 if bx, by, l2m are not positive
  * normal numbers or lam, mu are neither zero nor normal, or l2m <= |lam|. */
@@ -825,8 +875,14 @@ int orc_elastic_coefficients(const orc_elastic_cfg *c, double h, double dt, cons
             LAMEMU(i + nx * j1, m01, l01);
             LAMEMU(i1 + nx * j1, m11, l11);
             (void)l10; (void)l01; (void)l11;
-            l2m[q] = orc_round(((dt * (l00 + 2.0 * m00)) / Z0) / h, sf);
-            lam[q] = orc_round(((dt * l00) / Z0) / h, sf);
+            if (c->bc[2] == ORC_EBC_FREE && j == 0) {
+                const double M = ((4.0 * m00) * (l00 + m00)) / (l00 + 2.0 * m00);
+                l2m[q] = orc_round(((dt * M) / Z0) / h, sf);
+                lam[q] = 0.0;
+            } else {
+                l2m[q] = orc_round(((dt * (l00 + 2.0 * m00)) / Z0) / h, sf);
+                lam[q] = orc_round(((dt * l00) / Z0) / h, sf);
+            }
             double mh = 0.0;
             if (m00 > 0.0 && m10 > 0.0 && m01 > 0.0 && m11 > 0.0)
                 mh = 4.0 / (1.0 / m00 + 1.0 / m10 + 1.0 / m01 + 1.0 / m11);

@@ -12,7 +12,12 @@
   sum_6op it does not).
 * The analytic standing P wave in physical units (rho, vp, P0 far from 1):
   the Z0 / P0 scaling of stresses, velocities and multipliers.
+* The free surface (Appendix A: free surface in y) is traction free: a
+  vertically incident P pulse comes back with syy reversed and v_y doubled on
+  the surface (a rigid wall keeps the sign), and the analytic Rayleigh wave of
+  a homogeneous half-space is reproduced with second-order convergence.
 """
+from scipy.optimize import brentq
 import os
 from fractions import Fraction
 
@@ -37,8 +42,11 @@ def _weights():
     return w
 
 
-def _ext(N, lo, hi, node, odd):
-    """Dense image map from N stored values to positions -3..N+2."""
+def _ext(N, lo, hi, node, odd, odd_free):
+    """Dense image map from N stored values to positions -3..N+2. Rigid walls
+    sit on the half points -1/2 and N-1/2 (parity `odd`); a free surface sits
+    on the node 0 (parity `odd_free`: odd for the stresses that carry a y
+    traction, even for the velocities)."""
     E = np.zeros((N + 6, N))
     for r in range(N + 6):
         m = r - 3
@@ -49,7 +57,8 @@ def _ext(N, lo, hi, node, odd):
         if bc == PER:
             E[r, m % N] = 1.0
         elif bc == FREE:
-            pass
+            # mirror about y = 0: node -m <-> m, half point -(m + 1/2) <-> m + 1/2
+            E[r, -m if node else -1 - m] = -1.0 if odd_free else 1.0
         elif node:
             E[r, (-1 - m) if m < 0 else (2 * N - 1 - m)] = -1.0 if odd else 1.0
         else:
@@ -61,11 +70,11 @@ def _ext(N, lo, hi, node, odd):
     return E
 
 
-def _diff(N, lo, hi, src_node, odd):
+def _diff(N, lo, hi, src_node, odd, odd_free):
     """Undivided derivative of a field that is node-type (src_node) or
     half-type along the axis, evaluated at the other kind of point."""
     w = _weights()
-    E = _ext(N, lo, hi, src_node, odd)
+    E = _ext(N, lo, hi, src_node, odd, odd_free)
     D = np.zeros((N, N))
     for m in range(N):
         first = m - 1 if src_node else m - 2
@@ -81,7 +90,8 @@ def _along(mat, ax, shape):
 
 
 FIELDS = ("vx", "vy", "sxx", "syy", "sxy")
-# (target, source field, axis, source node-type along axis, odd about rigid walls)
+# (target, source field, axis, source node-type along axis, odd about rigid
+# walls); the parity about a free surface is odd for stresses, even for velocities
 MAPS = [("vx", "sxx", 0, True, False), ("vx", "sxy", 1, False, True),
         ("vy", "sxy", 0, False, True), ("vy", "syy", 1, True, False),
         ("sxx", "vx", 0, False, True), ("syy", "vy", 1, False, True),
@@ -119,14 +129,27 @@ CASES = [((8, 8), (RIG, RIG, FREE, RIG)), ((8, 7), (PER, PER, FREE, RIG)),
 
 
 def _held(shape, bc, name):
-    """Mask of points a rigid wall holds at zero."""
+    """Mask of points a boundary holds at zero: the normal velocity and the
+    shear stress on the stored points of a rigid wall, syy on a free surface."""
     nx, ny = shape
     m = np.zeros((ny, nx), bool)
     if bc[1] == RIG and name in ("vx", "sxy"):
         m[:, nx - 1] = True
     if bc[3] == RIG and name in ("vy", "sxy"):
         m[ny - 1, :] = True
+    if bc[2] == FREE and name == "syy":
+        m[0, :] = True
     return m.ravel()
+
+
+def _weight(shape, bc, name):
+    """Energy weight of each point: 1/2 for vx and sxx on the row of a free
+    surface (the mirror plane of the images), 1 elsewhere."""
+    nx, ny = shape
+    w = np.ones((ny, nx))
+    if bc[2] == FREE and name in ("vx", "sxx"):
+        w[0, :] = 0.5
+    return w.ravel()
 
 
 @pytest.mark.parametrize("shape,bc", CASES)
@@ -134,17 +157,20 @@ def test_elastic_operators_brute_force_and_skew(oracle_lib, shape, bc):
     maps = _impulse_maps(shape, bc)
     for tgt, src, ax, node, odd in MAPS:
         N = shape[ax]
-        ref = _along(_diff(N, bc[2 * ax], bc[2 * ax + 1], node, odd), ax, shape)
+        odd_free = src.startswith("s")
+        ref = _along(_diff(N, bc[2 * ax], bc[2 * ax + 1], node, odd, odd_free), ax, shape)
         np.testing.assert_array_equal(maps[(tgt, src)], ref, err_msg=f"{src}->{tgt}")
-    # skew: the stress-to-velocity map is minus the transpose of the
-    # velocity-to-strain-rate map, on the unknowns not held at zero
+    # skew: the stress-to-velocity map G is minus the adjoint of the
+    # velocity-to-strain-rate map D in the weighted inner products, on the
+    # unknowns not held at zero: W_v G = -(W_s D)^T
     pairs = [(("vx", "sxx"), ("sxx", "vx")), (("vx", "sxy"), ("sxy", "vx")),
              (("vy", "sxy"), ("sxy", "vy")), (("vy", "syy"), ("syy", "vy"))]
     for (a, b), (c, d) in pairs:
         fa, fb = ~_held(shape, bc, a), ~_held(shape, bc, b)
         G = maps[(a, b)][np.ix_(fa, fb)]
         D = maps[(c, d)][np.ix_(fb, fa)]
-        np.testing.assert_array_equal(G, -D.T, err_msg=f"{a}<-{b}")
+        wa, wb = _weight(shape, bc, a)[fa], _weight(shape, bc, b)[fb]
+        np.testing.assert_array_equal(wa[:, None] * G, -(wb[:, None] * D).T, err_msg=f"{a}<-{b}")
 
 
 def _layered(shape, h):
@@ -378,3 +404,121 @@ def test_elastic_energy_in_physical_units_converges_to_continuous(oracle_lib):
     g128, d128 = _p_wave_energy_gap(128)
     assert abs(g64) < 2e-3 and abs(g128) < abs(g64) / 3.0, (g64, g128)
     assert d64 <= 1e-12 and d128 <= 1e-12
+
+
+def _vertical_p_pulse(top, ny=400, y0=100, width=6.0):
+    """A plane P pulse (uniform in x, periodic x) of syy amplitude 1 at depth
+    y0 in a homogeneous medium (rho = vp = h = 1, uniaxial strain: sxx =
+    lambda / (lambda + 2 mu) syy), v = 0. It splits into an up- and a down-going
+    pulse of amplitude 1/2. After 2 y0 / vp the up-going one has come back to
+    y0 from the top face. Returns syy there then, and the largest |v_y| on the
+    top row (in units of the incident 1 / (rho vp)) meanwhile."""
+    nx = 8
+    rho = np.ones((ny, nx))
+    vp = np.ones((ny, nx))
+    vs = vp / 1.73
+    mu = rho * vs * vs
+    lam = rho * vp * vp - 2.0 * mu
+    dt = 0.5
+    g = np.repeat(np.exp(-0.5 * ((np.arange(ny) - y0) / width) ** 2)[:, None], nx, 1)
+    st = O.elastic_setup((nx, ny), (PER, PER, top, RIG), 1.0, dt, rho, vp, vs, O.FP64, 0,
+                         init={"syy": g, "sxx": g * lam / (lam + 2.0 * mu)})
+    vmax = 0.0
+    for _ in range(int(round(2 * y0 / dt))):
+        st.run(1)
+        vmax = max(vmax, float(np.max(np.abs(st.f["vy"][0]))) / st.Z0)
+    return float(st.f["syy"][y0, 0]), vmax
+
+
+def test_free_surface_reflects_p_pulse_with_reversed_stress(oracle_lib):
+    """Zero normal traction reflects a normally incident P wave with the
+    stress reversed (reflection coefficient -1 for syy) and the particle
+    velocity doubled at the surface; a rigid wall (zero normal velocity)
+    reflects it with the stress unchanged and v_y near zero."""
+    s_free, v_free = _vertical_p_pulse(FREE)
+    s_rigid, v_rigid = _vertical_p_pulse(RIG)
+    assert abs(s_free + 0.5) < 5e-3, s_free
+    assert abs(s_rigid - 0.5) < 5e-3, s_rigid
+    # incident v_y amplitude 1/2 (syy / (rho vp)); doubled on the surface
+    assert abs(v_free - 1.0) < 5e-3, v_free
+    assert v_rigid < 0.2, v_rigid
+
+
+def _rayleigh_error(N, top=FREE, depth=4, cfl=0.5):
+    """Largest relative L2 error over the five fields after one period of the
+    analytic Rayleigh wave on a homogeneous half-space y >= 0 with a
+    traction-free surface y = 0 (Poisson solid: vp = sqrt(3) vs; rho = vs = 1,
+    wavelength L = 1 across a periodic x extent, N cells per wavelength, rigid
+    bottom at 4 L where the wave has decayed to below 1e-4).
+    Displacement potentials phi = A e^{-q y} e^{i(kx - wt)}, psi = B e^{-s y}
+    e^{i(kx - wt)}, u_x = phi_x - psi_y, u_y = phi_y + psi_x, with
+    q = k sqrt(1 - c^2/vp^2), s = k sqrt(1 - c^2/vs^2), the phase speed c the
+    root of the Rayleigh equation (2 - c^2/vs^2)^2 = 4 sqrt(1 - c^2/vp^2)
+    sqrt(1 - c^2/vs^2), and B fixed by sxy = 0 on the surface (syy = 0 there
+    follows from the Rayleigh equation)."""
+    L, rho0, beta = 1.0, 1.0, 1.0
+    alpha = np.sqrt(3.0)
+    h = L / N
+    nx, ny = N, depth * N
+    mu = rho0 * beta ** 2
+    lam = rho0 * alpha ** 2 - 2.0 * mu
+    f = lambda xi: (2 - xi) ** 2 - 4 * np.sqrt(1 - xi * beta ** 2 / alpha ** 2) * np.sqrt(1 - xi)
+    xi = brentq(f, 0.5, 0.99)
+    c = beta * np.sqrt(xi)
+    k = 2 * np.pi / L
+    w = c * k
+    q = k * np.sqrt(1 - c ** 2 / alpha ** 2)
+    s = k * np.sqrt(1 - c ** 2 / beta ** 2)
+    A = 1.0
+    B = -2j * k * q * A / (k * k * (2 - xi))
+
+    def amp(y):
+        eq, es = np.exp(-q * y), np.exp(-s * y)
+        ux = 1j * k * A * eq + s * B * es
+        uy = -q * A * eq + 1j * k * B * es
+        return ux, uy, -1j * k * q * A * eq - s * s * B * es, q * q * A * eq - 1j * k * s * B * es
+
+    def fields(ts, tv):
+        xn, xh = np.arange(nx) * h, (np.arange(nx) + 0.5) * h
+        yn, yh = np.arange(ny) * h, (np.arange(ny) + 0.5) * h
+        ph = lambda x, t: np.exp(1j * (k * x[None, :] - w * t))
+        ux, uy, dux, duy = amp(yn)
+        exx, eyy = 1j * k * ux[:, None] * ph(xn, ts), duy[:, None] * ph(xn, ts)
+        out = {"sxx": np.real((lam + 2 * mu) * exx + lam * eyy),
+               "syy": np.real(lam * exx + (lam + 2 * mu) * eyy),
+               "vx": np.real(-1j * w * ux[:, None] * ph(xh, tv))}
+        ux, uy, dux, duy = amp(yh)
+        out["vy"] = np.real(-1j * w * uy[:, None] * ph(xn, tv))
+        out["sxy"] = np.real(mu * (dux[:, None] + 1j * k * uy[:, None]) * ph(xh, ts))
+        return out
+
+    dt = cfl * h / alpha
+    n = int(round(L / c / dt))
+    full = np.ones((ny, nx))
+    st = O.elastic_setup((nx, ny), (PER, PER, top, RIG), h, dt, rho0 * full, alpha * full, beta * full,
+                         O.FP64, 0, init=fields(0.0, -0.5 * dt))
+    # the exact syy vanishes on the surface row, which the closure holds at zero
+    st.run(n)
+    ref = fields(n * dt, (n - 0.5) * dt)
+    err = {}
+    for name, r in ref.items():
+        num = st.f[name] / st.Z0 if name in ("vx", "vy") else st.f[name]
+        err[name] = np.linalg.norm(num - r) / np.linalg.norm(r)
+    return max(err.values()), err
+
+
+def test_free_surface_rayleigh_wave_converges(oracle_lib):
+    """The Rayleigh wave is the free surface's own mode: its phase speed
+    (0.9194 vs here) and its decay with depth are fixed by the two traction
+    conditions, so a wrong image parity, a missing reduced modulus on the
+    surface row or a rigid top gives an O(1) error. With the closure the error
+    after one period falls at second order in h for the stresses and v_y
+    (about 1.5 for v_x, whose surface row sits on the mirror plane)."""
+    e32, d32 = _rayleigh_error(32)
+    e64, d64 = _rayleigh_error(64)
+    assert e64 < 7e-3, d64
+    for name in ("sxx", "syy", "vy", "sxy"):
+        assert d32[name] / d64[name] > 3.4, (name, d32[name], d64[name])
+    assert d32["vx"] / d64["vx"] > 2.5, (d32["vx"], d64["vx"])
+    e_rigid, _ = _rayleigh_error(32, top=RIG)
+    assert e_rigid > 0.5, e_rigid
