@@ -161,18 +161,24 @@ wave_status wave_set_allocator(wave_alloc_fn alloc, wave_free_fn free_fn, void *
  *   at the shear points mu_xy = 4 / (1/mu00 + 1/mu10 + 1/mu01 + 1/mu11), the
  *   harmonic mean of the four surrounding nodes (0 if any is 0), and
  *   mu = ((dt * mu_xy) / Z0) / h. Neighbours past the last point wrap
- *   (periodic) or are clamped.
+ *   (periodic) or are clamped. On the row of a free surface (j = 0):
+ *   l2m = ((dt * M) / Z0) / h with M = ((4 * mu) * (lambda + mu)) /
+ *   (lambda + 2 * mu), the modulus of sxx under zero normal traction, and
+ *   lam = 0.
  * Elastic boundaries: x faces PERIODIC/PERIODIC or RIGID/RIGID; y faces
  * PERIODIC/PERIODIC or (RIGID or FREE)/RIGID. RIGID is a frictionless rigid
  * wall on the half points -1/2 and N-1/2 (normal velocity and shear stress odd
  * about it and zero on it, the other fields even); the stored points on the
- * high wall are held at zero. FREE (y-lo) is a traction-free top in
- * zero-extension form: every field reads zero above row 0. Both keep the
- * discrete operator skew, so the energy is conserved in exact arithmetic.
+ * high wall are held at zero. FREE (y-lo) is the traction-free surface of
+ * Appendix A, on the node row 0, by stress imaging: syy is held at zero on
+ * row 0, and above it syy and sxy read as odd images and vx, vy as even images
+ * of the rows below. Both keep the discrete operator skew (with weight 1/2 on
+ * the vx and sxx points of the surface row), so the energy is conserved in
+ * exact arithmetic.
  * Errors: EINVAL (bad grid, spacing, dt, enum, NULL pointer, unsupported BC),
  * ERANGE (a multiplier is not a positive normal number of the storage format,
- * or a material value is not positive and finite), ENOTIMPL (WAVE_FP64),
- * ENOMEM, ECUDA.
+ * or a material value is not positive and finite; a free surface needs
+ * vs > 0 on its row), ENOTIMPL (WAVE_FP64), ENOMEM, ECUDA.
  */
 wave_status wave_create(const wave_grid *grid, const double spacing[3],
                         const wave_materials *mat, double dt, wave_precision prec,
@@ -183,8 +189,8 @@ wave_status wave_create(const wave_grid *grid, const double spacing[3],
  * benchmark configurations start from a Gaussian pressure). host_values holds
  * one physical value per grid point (x fastest). Stored values are
  * RN(p / P0) for pressure and stresses, RN((v * Z0) / P0) for velocities,
- * rounded once to the storage format. Values a rigid wall holds at zero are
- * set to zero. The field's compensation is reset to zero. Acoustic p is
+ * rounded once to the storage format. Values a rigid wall or a free surface
+ * holds at zero are set to zero. The field's compensation is reset to zero. Acoustic p is
  * p^0; velocities are v^{-1/2}. Synchronous with respect to host_values.
  * Errors: EINVAL (field not in this physics, NULL), ERANGE (non-finite input
  * or a value that overflows the storage format). */
@@ -227,7 +233,8 @@ wave_status wave_set_energy_trace(wave_ctx *ctx, double *device_energy, int64_t 
  * the discrete system conserves an energy; its formula is the leapfrog form):
  *   acoustic  E = 0.5 h^(d-1) P0^2 dt / Z0 * ( sum v^2 / a + sum p^n p^{n+1} / b )
  *   elastic   E = 0.5 h P0^2 dt / Z0 * ( sum v^2 / b_v + sum sigma^n . C^-1 sigma^{n+1} )
- * with the stored (rounded) values and multipliers; compensations are not
+ * with the stored (rounded) values and multipliers (the vx and normal-stress
+ * terms of a free surface row weighted 1/2); compensations are not
  * included. Products are formed in binary32 (exact for half and bfloat16
  * operands), divided once, summed with compensation per thread and in binary64
  * across threads. Synchronises the stream. ESTATE if no step has run yet. */
@@ -360,9 +367,10 @@ void wave_batch_destroy(wave_batch *batch);
  * wave_energy reports) computed from device arrays the caller already owns,
  * without allocating any device memory. The paper has no counterpart: this is
  * an entry point for callers that cannot call cudaMalloc, such as a host
- * framework that owns the whole device heap and hands out only views, code
- * running while a CUDA stream is captured into a graph, or a real-time loop
- * whose memory budget forbids allocation after start-up.
+ * framework that reserves the whole device heap at start-up and hands out only
+ * views of it (its own cudaMalloc would fail or break the framework's
+ * accounting), or a real-time loop whose memory budget forbids allocation
+ * after start-up (an allocation can block, fragment the heap or fail).
  *   ndim, n      grid (2D or 3D), cells per axis
  *   prec         storage format of every array below (the *_F32ARITH codes
  *                mean half / bfloat16 storage)
@@ -376,8 +384,10 @@ void wave_batch_destroy(wave_batch *batch);
  * doubles (64 KiB plus a counter) that every GPU loading the library holds until
  * the process exits; each block covers 2048 points, so grids above
  * WAVE_ENERGY_STATIC_MAX_BLOCKS * 2048 = 16,777,216 points are rejected with
- * WAVE_EINVAL. The first call on a device looks up the array's device address
- * with that device current: make that first call before any stream capture.
+ * WAVE_EINVAL. The first call on a device (and the first after the device's
+ * context is replaced, e.g. by cudaDeviceReset) looks up the array's device
+ * address with that device current: make that first call before any stream
+ * capture. Each call clears the array's block counter before its kernel runs.
  * All calls share the one array: calls that overlap on the GPU (two streams,
  * two host threads) race and return wrong sums. */
 #define WAVE_ENERGY_STATIC_MAX_BLOCKS 8192

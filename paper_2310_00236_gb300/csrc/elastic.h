@@ -6,10 +6,14 @@
 //     normal velocity and the shear stress are odd about it (zero on it; the
 //     stored point N-1 lies on the high wall and is held at zero), the
 //     tangential velocity and the normal stresses are even;
-//   free (y-lo only): traction-free top in zero-extension form, every field
-//     reads zero above row 0.
-// Each is a restriction of a skew-adjoint operator, so the discrete energy is
-// exactly conserved in exact arithmetic.
+//   free (y-lo only): traction-free surface on the node row 0 by stress
+//     imaging: syy is held at zero on row 0 and, above it, syy and sxy are odd
+//     images and vx, vy even images of the rows below; on row 0 the host puts
+//     the modulus of sxx under zero normal traction into l2m and zero into lam.
+// Each keeps the stress-to-velocity map the exact negative adjoint of the
+// velocity-to-strain-rate map (with weight 1/2 on the vx and sxx points of a
+// free surface row), so the discrete energy is exactly conserved in exact
+// arithmetic.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

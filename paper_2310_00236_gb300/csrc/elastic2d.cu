@@ -22,7 +22,7 @@ namespace wave {
 // indices m-1..m+2, half-type at m-2..m+1.
 template <class P>
 __device__ __forceinline__ typename P::A estencil(const void *fv, const ElParams &e, int ax, bool node,
-                                                  bool odd, int i, int j) {
+                                                  bool odd, bool odd_free, int i, int j) {
     using S = typename P::S;
     using A = typename P::A;
     const S *f = static_cast<const S *>(fv);
@@ -32,7 +32,7 @@ __device__ __forceinline__ typename P::A estencil(const void *fv, const ElParams
 #pragma unroll
     for (int t = 0; t < 4; t++) {
         int mm;
-        const int sg = emap(first + t, e.n[ax], e.bc[2 * ax], e.bc[2 * ax + 1], node, odd, mm);
+        const int sg = emap(first + t, e.n[ax], e.bc[2 * ax], e.bc[2 * ax + 1], node, odd, odd_free, mm);
         if (sg == 0) {
             v[t] = P::zero();
         } else {
@@ -53,18 +53,18 @@ __global__ void __launch_bounds__(128) el_v(ElParams e) {
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= e.n[0] || j >= e.n[1]) return;
     const int64_t q = i + e.sy * (int64_t)j;
-    // vx: sxx node-type in x (even), sxy half-type in y (odd)
-    A R = P::add(estencil<P>(e.f[F_SXX], e, 0, true, false, i, j),
-                 estencil<P>(e.f[F_SXY], e, 1, false, true, i, j));
+    // vx: sxx node-type in x (even), sxy half-type in y (odd at walls and surface)
+    A R = P::add(estencil<P>(e.f[F_SXX], e, 0, true, false, true, i, j),
+                 estencil<P>(e.f[F_SXY], e, 1, false, true, true, i, j));
     A inc = P::mul(coef<P>(e.c[C_BX], e.c_uni[C_BX], q), R);
     S *vx = static_cast<S *>(e.f[F_VX]), *tvx = static_cast<S *>(e.t[F_VX]);
     S V = vx[q], T = COMP ? tvx[q] : S(0);
     update<P, COMP>(V, T, inc);
     vx[q] = V;
     if (COMP) tvx[q] = T;
-    // vy: sxy half-type in x (odd), syy node-type in y (even)
-    R = P::add(estencil<P>(e.f[F_SXY], e, 0, false, true, i, j),
-               estencil<P>(e.f[F_SYY], e, 1, true, false, i, j));
+    // vy: sxy half-type in x (odd), syy node-type in y (even at walls, odd at the surface)
+    R = P::add(estencil<P>(e.f[F_SXY], e, 0, false, true, true, i, j),
+               estencil<P>(e.f[F_SYY], e, 1, true, false, true, i, j));
     inc = P::mul(coef<P>(e.c[C_BY], e.c_uni[C_BY], q), R);
     if (q == e.src_q && e.step < e.src_nt) inc = P::add(inc, static_cast<const A *>(e.src)[e.step]);
     S *vy = static_cast<S *>(e.f[F_VY]), *tvy = static_cast<S *>(e.t[F_VY]);
@@ -84,9 +84,9 @@ __global__ void __launch_bounds__(128) el_s(ElParams e) {
     double en = 0.0;
     if (i < e.n[0] && j < e.n[1]) {
         const int64_t q = i + e.sy * (int64_t)j;
-        // nodes: vx half-type in x (odd), vy half-type in y (odd)
-        const A dxvx = estencil<P>(e.f[F_VX], e, 0, false, true, i, j);
-        const A dyvy = estencil<P>(e.f[F_VY], e, 1, false, true, i, j);
+        // nodes: vx half-type in x (odd), vy half-type in y (odd at walls, even at the surface)
+        const A dxvx = estencil<P>(e.f[F_VX], e, 0, false, true, false, i, j);
+        const A dyvy = estencil<P>(e.f[F_VY], e, 1, false, true, false, i, j);
         const A l2m = coef<P>(e.c[C_L2M], e.c_uni[C_L2M], q);
         const A lam = coef<P>(e.c[C_LAM], e.c_uni[C_LAM], q);
         S *sxx = static_cast<S *>(e.f[F_SXX]), *tsxx = static_cast<S *>(e.t[F_SXX]);
@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(128) el_s(ElParams e) {
         if (COMP) tsyy[q] = T;
         const S syy1 = V;
         // sxy: vy node-type in x (even), vx node-type in y (even)
-        const A R = P::add(estencil<P>(e.f[F_VY], e, 0, true, false, i, j),
-                           estencil<P>(e.f[F_VX], e, 1, true, false, i, j));
+        const A R = P::add(estencil<P>(e.f[F_VY], e, 0, true, false, false, i, j),
+                           estencil<P>(e.f[F_VX], e, 1, true, false, false, i, j));
         inc = P::mul(coef<P>(e.c[C_MU], e.c_uni[C_MU], q), R);
         V = sxy0;
         T = COMP ? tsxy[q] : S(0);
@@ -126,8 +126,10 @@ __global__ void __launch_bounds__(128) el_s(ElParams e) {
             const double vyv = P::to_f32(static_cast<const S *>(e.f[F_VY])[q]);
             const double a0 = P::to_f32(sxx0), a1 = P::to_f32(sxx1);
             const double b0 = P::to_f32(syy0), b1 = P::to_f32(syy1);
-            en = vxv * vxv / bx + vyv * vyv / by;
-            en += (L * (a0 * a1 + b0 * b1) - M * (a0 * b1 + b0 * a1)) / (L * L - M * M);
+            // weight 1/2 for vx and the normal stresses on a free surface row
+            const double w = (e.bc[2] == EBC_FREE && j == 0) ? 0.5 : 1.0;
+            en = w * (vxv * vxv / bx) + vyv * vyv / by;
+            en += w * ((L * (a0 * a1 + b0 * b1) - M * (a0 * b1 + b0 * a1)) / (L * L - M * M));
             if (mu > 0.0) en += (double)P::to_f32(sxy0) * (double)P::to_f32(V) / mu;
         }
     }

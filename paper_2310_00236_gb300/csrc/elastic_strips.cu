@@ -34,9 +34,9 @@ struct ElStrip {
 
     // Row my of field f at x (whole vector) with the y image; zero past the grid.
     static __device__ __forceinline__ Raw row(const void *f, const ElParams &e, int x, int my, bool node,
-                                              bool odd, bool active) {
+                                              bool odd, bool odd_free, bool active) {
         int jy;
-        const int sg = emap(my, e.n[1], e.bc[2], e.bc[3], node, odd, jy);
+        const int sg = emap(my, e.n[1], e.bc[2], e.bc[3], node, odd, odd_free, jy);
         if (!active || sg == 0 || jy < 0 || jy >= e.n[1]) return V::zero();
         const Raw r = *reinterpret_cast<const Raw *>(static_cast<const char *>(f) +
                                                      (x + e.sy * (int64_t)jy) * sizeof(RS));
@@ -46,7 +46,8 @@ struct ElStrip {
     static __device__ __forceinline__ RS xval(const void *f, const ElParams &e, int mx, int j, bool node,
                                               bool odd) {
         int ix;
-        const int sg = emap(mx, e.n[0], e.bc[0], e.bc[1], node, odd, ix);
+        // x faces are periodic or rigid (a free surface is a y face)
+        const int sg = emap(mx, e.n[0], e.bc[0], e.bc[1], node, odd, false, ix);
         if (sg == 0 || ix < 0 || ix >= e.n[0]) return RS(0);
         const RS v = static_cast<const RS *>(f)[ix + e.sy * (int64_t)j];
         return sg < 0 ? V::rneg_s(v) : v;
@@ -161,16 +162,17 @@ __global__ void __launch_bounds__(256) el_v_strip(const ElParams e, int nitems, 
         const int nvalid = active ? min(N, e.n[0] - x) : 0;
         const bool le = active && lane == 0;
         const bool re = active && (lane == 31 || x + N >= e.n[0]);
-        // sxy rows j-2 .. j+1 (half points in y, odd); syy rows j-1 .. j+2 (nodes, even)
-        Raw a0 = X::row(e.f[F_SXY], e, x, it.y0 - 2, false, true, active);
-        Raw a1 = X::row(e.f[F_SXY], e, x, it.y0 - 1, false, true, active);
-        Raw a2 = X::row(e.f[F_SXY], e, x, it.y0, false, true, active);
-        Raw b0 = X::row(e.f[F_SYY], e, x, it.y0 - 1, true, false, active);
-        Raw b1 = X::row(e.f[F_SYY], e, x, it.y0, true, false, active);
-        Raw b2 = X::row(e.f[F_SYY], e, x, it.y0 + 1, true, false, active);
+        // sxy rows j-2 .. j+1 (half points in y; odd at walls and surface); syy rows
+        // j-1 .. j+2 (nodes; even at walls, odd at the surface)
+        Raw a0 = X::row(e.f[F_SXY], e, x, it.y0 - 2, false, true, true, active);
+        Raw a1 = X::row(e.f[F_SXY], e, x, it.y0 - 1, false, true, true, active);
+        Raw a2 = X::row(e.f[F_SXY], e, x, it.y0, false, true, true, active);
+        Raw b0 = X::row(e.f[F_SYY], e, x, it.y0 - 1, true, false, true, active);
+        Raw b1 = X::row(e.f[F_SYY], e, x, it.y0, true, false, true, active);
+        Raw b2 = X::row(e.f[F_SYY], e, x, it.y0 + 1, true, false, true, active);
         for (int j = it.y0; j < it.y1; j++) {
-            const Raw a3 = X::row(e.f[F_SXY], e, x, j + 1, false, true, active);
-            const Raw b3 = X::row(e.f[F_SYY], e, x, j + 2, true, false, active);
+            const Raw a3 = X::row(e.f[F_SXY], e, x, j + 1, false, true, true, active);
+            const Raw b3 = X::row(e.f[F_SYY], e, x, j + 2, true, false, true, active);
             const int64_t q = x + e.sy * (int64_t)j;
             Raw sxx = V::zero(), vx = V::zero(), vy = V::zero(), tx = V::zero(), ty = V::zero();
             if (active) {
@@ -236,17 +238,18 @@ __global__ void __launch_bounds__(256) el_s_strip(const ElParams e, int nitems, 
         const int nvalid = active ? min(N, e.n[0] - x) : 0;
         const bool le = active && lane == 0;
         const bool re = active && (lane == 31 || x + N >= e.n[0]);
-        // vy rows j-2 .. j+1 (half points in y, odd); vx rows j-1 .. j+2 (nodes, even)
-        Raw c0 = X::row(e.f[F_VY], e, x, it.y0 - 2, false, true, active);
-        Raw c1 = X::row(e.f[F_VY], e, x, it.y0 - 1, false, true, active);
-        Raw c2 = X::row(e.f[F_VY], e, x, it.y0, false, true, active);
-        Raw d0 = X::row(e.f[F_VX], e, x, it.y0 - 1, true, false, active);
-        Raw d1 = X::row(e.f[F_VX], e, x, it.y0, true, false, active);
-        Raw d2 = X::row(e.f[F_VX], e, x, it.y0 + 1, true, false, active);
+        // vy rows j-2 .. j+1 (half points in y; odd at walls, even at the surface); vx
+        // rows j-1 .. j+2 (nodes, even)
+        Raw c0 = X::row(e.f[F_VY], e, x, it.y0 - 2, false, true, false, active);
+        Raw c1 = X::row(e.f[F_VY], e, x, it.y0 - 1, false, true, false, active);
+        Raw c2 = X::row(e.f[F_VY], e, x, it.y0, false, true, false, active);
+        Raw d0 = X::row(e.f[F_VX], e, x, it.y0 - 1, true, false, false, active);
+        Raw d1 = X::row(e.f[F_VX], e, x, it.y0, true, false, false, active);
+        Raw d2 = X::row(e.f[F_VX], e, x, it.y0 + 1, true, false, false, active);
         double en = 0.0;
         for (int j = it.y0; j < it.y1; j++) {
-            const Raw c3 = X::row(e.f[F_VY], e, x, j + 1, false, true, active);
-            const Raw d3 = X::row(e.f[F_VX], e, x, j + 2, true, false, active);
+            const Raw c3 = X::row(e.f[F_VY], e, x, j + 1, false, true, false, active);
+            const Raw d3 = X::row(e.f[F_VX], e, x, j + 2, true, false, false, active);
             const int64_t q = x + e.sy * (int64_t)j;
             Raw sxx = V::zero(), syy = V::zero(), sxy = V::zero();
             Raw txx = V::zero(), tyy = V::zero(), txy = V::zero();
@@ -292,6 +295,8 @@ __global__ void __launch_bounds__(256) el_s_strip(const ElParams e, int nitems, 
                     float cu[5];
 #pragma unroll
                     for (int w = 0; w < 5; w++) cu[w] = coef_f32<P>(nullptr, e.c_uni[w], 0);
+                    // weight 1/2 for vx and the normal stresses on a free surface row
+                    const double wrow = (e.bc[2] == EBC_FREE && j == 0) ? 0.5 : 1.0;
 #pragma unroll
                     for (int k = 0; k < N; k++) {
                         if (k < nvalid) {
@@ -303,8 +308,8 @@ __global__ void __launch_bounds__(256) el_s_strip(const ElParams e, int nitems, 
                             const double vxv = V::f32(d1, k), vyv = V::f32(c2, k);
                             const double a0 = V::f32(sxx0, k), a1 = V::f32(sxx, k);
                             const double b0 = V::f32(syy0, k), b1 = V::f32(syy, k);
-                            double t = vxv * vxv / bx + vyv * vyv / by;
-                            t += (L * (a0 * a1 + b0 * b1) - M * (a0 * b1 + b0 * a1)) / (L * L - M * M);
+                            double t = wrow * (vxv * vxv / bx) + vyv * vyv / by;
+                            t += wrow * ((L * (a0 * a1 + b0 * b1) - M * (a0 * b1 + b0 * a1)) / (L * L - M * M));
                             if (mu > 0.0) t += (double)V::f32(sxy0, k) * (double)V::f32(sxy, k) / mu;
                             en += t;
                         }

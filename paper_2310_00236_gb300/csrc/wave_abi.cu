@@ -409,6 +409,11 @@ static double round_store(int prec, double v) {
 // lam = ((dt lambda)/Z0)/h; mu_xy = 4 / (sum of 1/mu over the four nodes
 // around the shear point, 0 if any is 0), mu = ((dt mu_xy)/Z0)/h. The
 // neighbour i+1 (j+1) wraps on periodic axes and is clamped otherwise.
+// On the row of a free surface (y-lo FREE, j = 0) syy is zero, so sxx obeys
+// d(sxx)/dt = M d(vx)/dx with M = ((4 mu)(lambda + mu))/(lambda + 2 mu), the
+// modulus under zero normal traction: l2m = ((dt M)/Z0)/h and lam = 0 there
+// (the stress kernels then leave syy at zero on that row, since D_y v_y
+// vanishes on it by the even image of v_y).
 static wave_status elastic_coefficients(wave_ctx *c, const wave_materials *mat) {
     const int64_t nx = c->n[0], ny = c->n[1], npts = nx * ny;
     double rho0 = 0.0, c0 = 0.0;
@@ -441,8 +446,10 @@ static wave_status elastic_coefficients(wave_ctx *c, const wave_materials *mat) 
             lame(i1 + nx * j, m10, l10);
             lame(i + nx * j1, m01, l01);
             lame(i1 + nx * j1, m11, l11);
-            const double l2m = round_store(c->prec, ((dt * (l00 + 2.0 * m00)) / Z0) / h);
-            const double lam = round_store(c->prec, ((dt * l00) / Z0) / h);
+            const bool surface = c->bc[2] == WAVE_BC_FREE && j == 0;
+            const double msurf = ((4.0 * m00) * (l00 + m00)) / (l00 + 2.0 * m00);
+            const double l2m = round_store(c->prec, ((dt * (surface ? msurf : l00 + 2.0 * m00)) / Z0) / h);
+            const double lam = surface ? 0.0 : round_store(c->prec, ((dt * l00) / Z0) / h);
             double mh = 0.0;
             if (m00 > 0.0 && m10 > 0.0 && m01 > 0.0 && m11 > 0.0)
                 mh = 4.0 / (1.0 / m00 + 1.0 / m10 + 1.0 / m01 + 1.0 / m11);
@@ -459,7 +466,8 @@ static wave_status elastic_coefficients(wave_ctx *c, const wave_materials *mat) 
             if (!ok)
                 return fail(WAVE_ERANGE,
                             "elastic multiplier at point %lld outside the storage format's range "
-                            "(rescale units or change dt)", (long long)q);
+                            "(rescale units or change dt%s)", (long long)q,
+                            surface ? "; a free surface needs vs > 0 on its row" : "");
         }
     return WAVE_OK;
 }
@@ -823,12 +831,14 @@ extern "C" wave_status wave_set_initial(wave_ctx *c, wave_field field, const dou
                 if (on_rigid_wall_zeroed(cc, field, idx)) s = 0.0;
             } else {
                 // frictionless rigid walls hold the normal velocity and the
-                // shear stress at zero on the stored wall points
+                // shear stress at zero on the stored wall points; a free
+                // surface holds syy at zero on its row
                 const int64_t i = q % nx, j = q / nx;
                 if (cc->bc[1] == WAVE_BC_RIGID && i == nx - 1 &&
                     (field == WAVE_F_VX || field == WAVE_F_SXY)) s = 0.0;
                 if (cc->bc[3] == WAVE_BC_RIGID && j == ny - 1 &&
                     (field == WAVE_F_VY || field == WAVE_F_SXY)) s = 0.0;
+                if (cc->bc[2] == WAVE_BC_FREE && j == 0 && field == WAVE_F_SYY) s = 0.0;
             }
             store_value(prec, s, dst, q);
             if (!isfinite(load_value(prec, dst, q))) *bad = q;

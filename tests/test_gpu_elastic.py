@@ -220,8 +220,9 @@ def test_elastic_full_size_1024_sampled_bit_exact():
         hi = [min(n, i + M + 1), min(n, j + M + 1)]
         # real faces keep their kind; cut faces read zero (their influence
         # stays outside the checked point's domain of dependence)
-        bc = (RIG if lo[0] == 0 else FREE, RIG if hi[0] == n else FREE,
-              FREE, RIG if hi[1] == n else FREE)
+        Z = O.EBC_ZERO
+        bc = (RIG if lo[0] == 0 else Z, RIG if hi[0] == n else Z,
+              FREE if lo[1] == 0 else Z, RIG if hi[1] == n else Z)
         sub = (hi[0] - lo[0], hi[1] - lo[1])
         cfg = O.elastic_cfg(sub, bc, sfmt, comp, afmt)
         st = O.ElasticState(cfg)
