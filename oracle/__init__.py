@@ -77,6 +77,9 @@ def lib():
         L.orc_scale_velocity.argtypes = [i64, dp, C.c_double, C.c_double, C.c_int, dp]
         L.orc_scale_source.argtypes = [i64, dp, C.c_double, C.c_double, C.c_double, C.c_int,
                                        C.c_int, dp]
+        L.orc_acoustic_half_step.restype = C.c_int
+        L.orc_acoustic_half_step.argtypes = ([C.c_void_p, C.c_int32] + [dp] * 8 + [dp] * 4 + [dp, dp] +
+                                             [i64, i64, i64, dp])
         L.orc_energy_factor.restype = C.c_double
         L.orc_energy_factor.argtypes = [C.c_double] * 4 + [C.c_int]
         _lib = L
@@ -178,11 +181,17 @@ def set_threads(n: int = 0) -> int:
 class AcousticCfg(C.Structure):
     _fields_ = [("ndim", C.c_int32), ("bc", C.c_int32 * 3), ("n", C.c_int64 * 3),
                 ("store_fmt", C.c_int32), ("arith_fmt", C.c_int32),
-                ("stencil_fmt", C.c_int32), ("comp", C.c_int32)]
+                ("stencil_fmt", C.c_int32), ("comp", C.c_int32), ("c2_override", C.c_int32),
+                ("pair_stencil", C.c_int32)]
 
 
-def acoustic_cfg(shape, bc, store_fmt, comp, arith_fmt=None, stencil_fmt=None) -> AcousticCfg:
-    """shape: cells per axis, ordered (x, y[, z]); bc: one code per axis."""
+def acoustic_cfg(shape, bc, store_fmt, comp, arith_fmt=None, stencil_fmt=None,
+                 c2_fmt=None, pair_stencil=False) -> AcousticCfg:
+    """shape: cells per axis, ordered (x, y[, z]); bc: one code per axis.
+    c2_fmt: round the stencil weight 1/24 to this format instead of the
+    stencil format (an experiment on the operator's rounding; None: the
+    scheme). pair_stencil: the stencils read RN(V + T), the stored value plus
+    its compensation, instead of V (an experiment, not the paper's scheme)."""
     nd = len(shape)
     cfg = AcousticCfg()
     cfg.ndim = nd
@@ -193,6 +202,8 @@ def acoustic_cfg(shape, bc, store_fmt, comp, arith_fmt=None, stencil_fmt=None) -
     cfg.arith_fmt = store_fmt if arith_fmt is None else arith_fmt
     cfg.stencil_fmt = cfg.arith_fmt if stencil_fmt is None else stencil_fmt
     cfg.comp = comp
+    cfg.c2_override = 0 if c2_fmt is None else 1 + c2_fmt
+    cfg.pair_stencil = 1 if pair_stencil else 0
     return cfg
 
 
@@ -249,6 +260,28 @@ class AcousticState:
             raise MemoryError("oracle run failed")
         self.step += nsteps
         return traces, en
+
+
+def acoustic_half_step(st: AcousticState, which: int, ghost_lo=None, ghost_hi=None):
+    """One half step of a 3D z slab (domain decomposition along z; not in the
+    paper): which = 0 velocities from p, 1 pressure from the velocities (at
+    global step st.step, which then advances), with the same operations as
+    AcousticState.run. ghost_lo / ghost_hi: the grid planes z0-2, z0-1 and
+    z1, z1+1 of the field the half step differentiates along z (p, then v_z),
+    arrays shaped (2, ny, nx); None where the slab's face is a face of the
+    grid. Pinned by tests/test_zslab_cpu.py: slabs stepped with exchanged
+    ghosts reproduce the whole grid's run bit for bit."""
+    lo = None if ghost_lo is None else _f64(ghost_lo)
+    hi = None if ghost_hi is None else _f64(ghost_hi)
+    src = None if st.src is None else _f64(st.src)
+    rc = lib().orc_acoustic_half_step(
+        C.byref(st.cfg), int(which), _dp(st.p), _dp(st.tp), _dp(st.v[0]), _dp(st.tv[0]), _dp(st.v[1]),
+        _dp(st.tv[1]), _dp(st.v[2]), _dp(st.tv[2]), _dp(st.a[0]), _dp(st.a[1]), _dp(st.a[2]), _dp(st.b),
+        _dp(lo), _dp(hi), st.step, st.src_index, 0 if src is None else src.size, _dp(src))
+    if rc != 0:
+        raise ValueError("the slab half step takes 3D states without pair_stencil")
+    if which == 1:
+        st.step += 1
 
 
 def acoustic_adjoint(st: AcousticState, c, nsteps: int, rec_index, residual=None, d_obs=None):
@@ -336,12 +369,18 @@ def energy_factor(h, dt, P0, Z0, ndim) -> float:
 
 
 def acoustic_setup(shape, bc, h, dt, rho, c, store_fmt, comp, P0=1.0, arith_fmt=None,
-                   stencil_fmt=None, p0=None, v0=None):
+                   stencil_fmt=None, p0=None, v0=None, c2_fmt=None, coef_fmt=None,
+                   pair_stencil=False):
     """Build a ready-to-run AcousticState from physical inputs: coefficients
-    (rounded once), scaled and rounded initial fields, walls applied."""
-    cfg = acoustic_cfg(shape, bc, store_fmt, comp, arith_fmt, stencil_fmt)
+    (rounded once), scaled and rounded initial fields, walls applied.
+    c2_fmt / coef_fmt: round the stencil weight 1/24 / the multipliers a and b
+    to these formats instead of the scheme's (experiments that separate the
+    operator's rounding from the rest; None: the scheme); pair_stencil: see
+    acoustic_cfg."""
+    cfg = acoustic_cfg(shape, bc, store_fmt, comp, arith_fmt, stencil_fmt, c2_fmt, pair_stencil)
     st = AcousticState(cfg)
-    a, b, Z0, ok = acoustic_coefficients(cfg, h, dt, P0, rho, c)
+    ccfg = cfg if coef_fmt is None else acoustic_cfg(shape, bc, coef_fmt, comp)
+    a, b, Z0, ok = acoustic_coefficients(ccfg, h, dt, P0, rho, c)
     if not ok:
         raise ValueError("coefficient outside the storage format's normal range")
     st.a, st.b, st.Z0, st.P0, st.h, st.dt = a, b, Z0, P0, h, dt

@@ -161,6 +161,17 @@ typedef struct {
     int32_t arith_fmt;
     int32_t stencil_fmt;
     int32_t comp;
+    /* 0: C2 = RN(1/24) in the stencil format (the scheme). 1 + F: C2 rounded
+     * to format F instead, every other operation unchanged -- an experiment
+     * that separates the rounding of the operator's weight from the rest
+     * (the "Operator" remark of Section 5). */
+    int32_t c2_override;
+    /* 0: the stencils read the stored values V (the scheme of Algorithms 1
+     * and 2). 1: they read RN(V + T) in the stencil format, the stored value
+     * plus its carried compensation -- not the paper's scheme: an experiment
+     * that measures what the stencil's reading of the rounded stored value
+     * costs. */
+    int32_t pair_stencil;
 } orc_acoustic_cfg;
 
 static inline int64_t lin(const int64_t n[3], int64_t i, int64_t j, int64_t k)
@@ -184,13 +195,17 @@ static double read_axis(const double *f, const int64_t n[3], const int32_t bc[3]
  * (Section 3), evaluated as D = C1*(f[+1/2] - f[-1/2]) - C2*(f[+3/2] - f[-3/2])
  * with C1 = 9/8 and C2 = 1/24 rounded to the stencil format. The value is the
  * undivided difference (the 1/h factor lives in the coefficient). */
-static double stencil(double fm3, double fm1, double fp1, double fp3, int f)
+static double stencil_w(double fm3, double fm1, double fp1, double fp3, int f, double c2)
 {
     const double c1 = 9.0 / 8.0;
-    const double c2 = orc_round(1.0 / 24.0, f);
     double t1 = sub_f(fp1, fm1, f);
     double t2 = sub_f(fp3, fm3, f);
     return sub_f(mul_f(c1, t1, f), mul_f(c2, t2, f), f);
+}
+
+static double stencil(double fm3, double fm1, double fp1, double fp3, int f)
+{
+    return stencil_w(fm3, fm1, fp1, fp3, f, orc_round(1.0 / 24.0, f));
 }
 
 double orc_stencil_c2(int fmt) { return orc_round(1.0 / 24.0, fmt); }
@@ -285,6 +300,98 @@ void orc_acoustic_apply_walls(const orc_acoustic_cfg *cfg, double *p, double *vx
             }
 }
 
+/* Ghost planes along z for a slab of a larger grid (domain decomposition
+ * along z; not in the paper): lo holds the global planes z0-2, z0-1 below the
+ * slab, hi the planes z1, z1+1 above it, each n[0]*n[1] values x fastest, of
+ * the field a half step differentiates along z. NULL: that face is a face of
+ * the grid and its boundary rule applies. */
+typedef struct { const double *lo, *hi; } zghost;
+
+/* read_axis, except that along z a face with ghost planes reads them */
+static double read_axis_g(const double *f, const int64_t n[3], const int32_t bc[3], int ax, int node,
+                          int64_t i, int64_t j, int64_t k, int64_t m, const zghost *g)
+{
+    if (ax == 2 && g) {
+        if (m < 0 && g->lo) return g->lo[i + n[0] * (j + n[1] * (m + 2))];
+        if (m >= n[2] && g->hi) return g->hi[i + n[0] * (j + n[1] * (m - n[2]))];
+    }
+    return read_axis(f, n, bc, ax, node, i, j, k, m);
+}
+
+/* Velocity half step of Algorithms 1 / 2: v_c^{n+1/2} = v_c^{n-1/2} + a_c D_c(p^n),
+ * with D_c reading pr (the stored p, or RN(p + t_p) for pair_stencil). */
+static void velocity_half(const orc_acoustic_cfg *cfg, const double *pr, double *const v[3],
+                          double *const tv[3], const double *const a[3], double c2, const zghost *g)
+{
+    const int64_t *n = cfg->n;
+    const int nd = cfg->ndim;
+    const int sf = cfg->store_fmt, af = cfg->arith_fmt, stf = cfg->stencil_fmt, comp = cfg->comp;
+#pragma omp parallel for schedule(static)
+    for (int64_t jk = 0; jk < n[1] * n[2]; jk++) {
+        const int64_t j = jk % n[1], k = jk / n[1];
+        for (int64_t i = 0; i < n[0]; i++) {
+            const int64_t q = lin(n, i, j, k);
+            const int64_t idx[3] = {i, j, k};
+            for (int c = 0; c < nd; c++) {
+                /* v_c sits at m + 1/2 along axis c; p at nodes m-1, m, m+1, m+2 */
+                const int64_t m = idx[c];
+                double fm3 = read_axis_g(pr, n, cfg->bc, c, 1, i, j, k, m - 1, g);
+                double fm1 = read_axis_g(pr, n, cfg->bc, c, 1, i, j, k, m, g);
+                double fp1 = read_axis_g(pr, n, cfg->bc, c, 1, i, j, k, m + 1, g);
+                double fp3 = read_axis_g(pr, n, cfg->bc, c, 1, i, j, k, m + 2, g);
+                double D = stencil_w(fm3, fm1, fp1, fp3, stf, c2);
+                double inc = orc_round(mul_f(a[c][q], D, stf), af);
+                update(&v[c][q], &tv[c][q], inc, comp, af, sf);
+            }
+        }
+    }
+}
+
+/* Pressure half step: p^{n+1} = p^n + b (Dx vx + Dy vy [+ Dz vz] [+ s]) with
+ * the divergence reading vr, summed left to right, the source at global step
+ * gstep. With rowacc, each (j, k) row's energy terms (velocity, pressure). */
+static void pressure_half(const orc_acoustic_cfg *cfg, double *p, double *tp, double *const vr[3],
+                          double *const v[3], const double *const a[3], const double *b_c, double c2,
+                          int64_t src_index, int64_t src_nt, const double *src, int64_t gstep,
+                          double *rowacc, const zghost *g)
+{
+    const int64_t *n = cfg->n;
+    const int nd = cfg->ndim;
+    const int sf = cfg->store_fmt, af = cfg->arith_fmt, stf = cfg->stencil_fmt, comp = cfg->comp;
+#pragma omp parallel for schedule(static)
+    for (int64_t jk = 0; jk < n[1] * n[2]; jk++) {
+        const int64_t j = jk % n[1], k = jk / n[1];
+        acc_t ep = {0.0, 0.0}, ev = {0.0, 0.0};
+        for (int64_t i = 0; i < n[0]; i++) {
+            const int64_t q = lin(n, i, j, k);
+            const int64_t idx[3] = {i, j, k};
+            double R = 0.0;
+            for (int c = 0; c < nd; c++) {
+                /* p sits on node m along axis c; v_c at m-2, m-1, m, m+1 (+1/2) */
+                const int64_t m = idx[c];
+                double fm3 = read_axis_g(vr[c], n, cfg->bc, c, 0, i, j, k, m - 2, g);
+                double fm1 = read_axis_g(vr[c], n, cfg->bc, c, 0, i, j, k, m - 1, g);
+                double fp1 = read_axis_g(vr[c], n, cfg->bc, c, 0, i, j, k, m, g);
+                double fp3 = read_axis_g(vr[c], n, cfg->bc, c, 0, i, j, k, m + 1, g);
+                double D = stencil_w(fm3, fm1, fp1, fp3, stf, c2);
+                R = (c == 0) ? D : add_f(R, D, stf);
+            }
+            if (src && q == src_index && gstep < src_nt) R = add_f(R, src[gstep], stf);
+            double inc = orc_round(mul_f(b_c[q], R, stf), af);
+            const double p_old = p[q];
+            update(&p[q], &tp[q], inc, comp, af, sf);
+            if (rowacc) {
+                acc_add(&ep, p_old * p[q] / b_c[q]);
+                for (int c = 0; c < nd; c++) acc_add(&ev, v[c][q] * v[c][q] / a[c][q]);
+            }
+        }
+        if (rowacc) {
+            rowacc[2 * jk] = acc_val(&ev);
+            rowacc[2 * jk + 1] = acc_val(&ep);
+        }
+    }
+}
+
 /* Advance nsteps leapfrog steps. State on entry: p^n, v^{n-1/2} and their
  * compensations; on exit p^{n+nsteps}, v^{n+nsteps-1/2}.
  * Per step (Algorithm 1/2 order): all velocity components from p^n, then p
@@ -304,67 +411,34 @@ int orc_acoustic_run(const orc_acoustic_cfg *cfg, double *p, double *tp, double 
 {
     const int64_t *n = cfg->n;
     const int nd = cfg->ndim;
-    const int sf = cfg->store_fmt, af = cfg->arith_fmt, stf = cfg->stencil_fmt;
+    const int stf = cfg->stencil_fmt;
     const int comp = cfg->comp;
-    double *v[3] = {vx, vy, vz}, *tv[3] = {tvx, tvy, tvz};
-    const double *a[3] = {ax_c, ay_c, az_c};
+    const double c2 = orc_round(1.0 / 24.0, cfg->c2_override > 0 ? cfg->c2_override - 1 : stf);
+    double *const v[3] = {vx, vy, vz}, *const tv[3] = {tvx, tvy, tvz};
+    const double *const a[3] = {ax_c, ay_c, az_c};
     const int64_t npts = n[0] * n[1] * n[2];
     double *rowacc = (double *)calloc((size_t)(n[1] * n[2]) * 2, sizeof(double));
     if (!rowacc) return -1;
+    /* what the stencils read: the stored values, or RN(V + T) (pair_stencil) */
+    double *pr = p, *vr[3] = {vx, vy, vz};
+    double *pairs = NULL;
+    if (cfg->pair_stencil && comp) {
+        pairs = (double *)malloc(sizeof(double) * (size_t)npts * (size_t)(1 + nd));
+        if (!pairs) { free(rowacc); return -1; }
+        pr = pairs;
+        for (int c = 0; c < nd; c++) vr[c] = pairs + (size_t)npts * (size_t)(1 + c);
+    }
 
     for (int64_t s = 0; s < nsteps; s++) {
         const int64_t gstep = step0 + s;
-        /* velocity half step: v^{n+1/2} = v^{n-1/2} + a * D(p^n) */
-#pragma omp parallel for schedule(static)
-        for (int64_t jk = 0; jk < n[1] * n[2]; jk++) {
-            const int64_t j = jk % n[1], k = jk / n[1];
-            for (int64_t i = 0; i < n[0]; i++) {
-                const int64_t q = lin(n, i, j, k);
-                const int64_t idx[3] = {i, j, k};
-                for (int c = 0; c < nd; c++) {
-                    /* v_c sits at m + 1/2 along axis c; p at nodes m-1, m, m+1, m+2 */
-                    const int64_t m = idx[c];
-                    double fm3 = read_axis(p, n, cfg->bc, c, 1, i, j, k, m - 1);
-                    double fm1 = read_axis(p, n, cfg->bc, c, 1, i, j, k, m);
-                    double fp1 = read_axis(p, n, cfg->bc, c, 1, i, j, k, m + 1);
-                    double fp3 = read_axis(p, n, cfg->bc, c, 1, i, j, k, m + 2);
-                    double D = stencil(fm3, fm1, fp1, fp3, stf);
-                    double inc = orc_round(mul_f(a[c][q], D, stf), af);
-                    update(&v[c][q], &tv[c][q], inc, comp, af, sf);
-                }
-            }
-        }
-        /* pressure half step: p^{n+1} = p^n + b * (div v^{n+1/2} + s) */
-#pragma omp parallel for schedule(static)
-        for (int64_t jk = 0; jk < n[1] * n[2]; jk++) {
-            const int64_t j = jk % n[1], k = jk / n[1];
-            acc_t ep = {0.0, 0.0}, ev = {0.0, 0.0};
-            for (int64_t i = 0; i < n[0]; i++) {
-                const int64_t q = lin(n, i, j, k);
-                const int64_t idx[3] = {i, j, k};
-                double R = 0.0;
-                for (int c = 0; c < nd; c++) {
-                    /* p sits on node m along axis c; v_c at m-2, m-1, m, m+1 (+1/2) */
-                    const int64_t m = idx[c];
-                    double fm3 = read_axis(v[c], n, cfg->bc, c, 0, i, j, k, m - 2);
-                    double fm1 = read_axis(v[c], n, cfg->bc, c, 0, i, j, k, m - 1);
-                    double fp1 = read_axis(v[c], n, cfg->bc, c, 0, i, j, k, m);
-                    double fp3 = read_axis(v[c], n, cfg->bc, c, 0, i, j, k, m + 1);
-                    double D = stencil(fm3, fm1, fp1, fp3, stf);
-                    R = (c == 0) ? D : add_f(R, D, stf);
-                }
-                if (src && q == src_index && gstep < src_nt) R = add_f(R, src[gstep], stf);
-                double inc = orc_round(mul_f(b_c[q], R, stf), af);
-                const double p_old = p[q];
-                update(&p[q], &tp[q], inc, comp, af, sf);
-                if (energy) {
-                    acc_add(&ep, p_old * p[q] / b_c[q]);
-                    for (int c = 0; c < nd; c++) acc_add(&ev, v[c][q] * v[c][q] / a[c][q]);
-                }
-            }
-            rowacc[2 * jk] = acc_val(&ev);
-            rowacc[2 * jk + 1] = acc_val(&ep);
-        }
+        if (pairs)
+            for (int64_t q = 0; q < npts; q++) pairs[q] = add_f(p[q], tp[q], stf);
+        velocity_half(cfg, pr, v, tv, a, c2, NULL);
+        if (pairs)
+            for (int c = 0; c < nd; c++)
+                for (int64_t q = 0; q < npts; q++) vr[c][q] = add_f(v[c][q], tv[c][q], stf);
+        pressure_half(cfg, p, tp, vr, v, a, b_c, c2, src_index, src_nt, src, gstep,
+                      energy ? rowacc : NULL, NULL);
         if (energy) {
             acc_t e = {0.0, 0.0};
             for (int64_t jk = 0; jk < n[1] * n[2]; jk++) {
@@ -382,6 +456,30 @@ int orc_acoustic_run(const orc_acoustic_cfg *cfg, double *p, double *tp, double 
         }
     }
     free(rowacc);
+    free(pairs);
+    return 0;
+}
+
+/* One half step of a 3D z slab (domain decomposition along z; not in the
+ * paper): half = 0 the velocity half step (ghosts: planes of p), half = 1 the
+ * pressure half step at global step gstep (ghosts: planes of v_z), with the
+ * same operations as orc_acoustic_run. ghost_lo / ghost_hi as in zghost; the
+ * stored-value scheme only (no pair_stencil). Returns 0, or -2 for a cfg
+ * this does not cover. */
+int orc_acoustic_half_step(const orc_acoustic_cfg *cfg, int32_t half, double *p, double *tp,
+                           double *vx, double *tvx, double *vy, double *tvy, double *vz,
+                           double *tvz, const double *ax_c, const double *ay_c, const double *az_c,
+                           const double *b_c, const double *ghost_lo, const double *ghost_hi,
+                           int64_t gstep, int64_t src_index, int64_t src_nt, const double *src)
+{
+    if (cfg->ndim != 3 || cfg->pair_stencil) return -2;
+    const double c2 =
+        orc_round(1.0 / 24.0, cfg->c2_override > 0 ? cfg->c2_override - 1 : cfg->stencil_fmt);
+    double *const v[3] = {vx, vy, vz}, *const tv[3] = {tvx, tvy, tvz};
+    const double *const a[3] = {ax_c, ay_c, az_c};
+    const zghost g = {ghost_lo, ghost_hi};
+    if (half == 0) velocity_half(cfg, p, v, tv, a, c2, &g);
+    else pressure_half(cfg, p, tp, v, v, a, b_c, c2, src_index, src_nt, src, gstep, NULL, &g);
     return 0;
 }
 
