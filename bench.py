@@ -49,10 +49,42 @@ BYTES = {
 BYTES_2D = (2 + 8 + 8) + (4 + 6 + 4)
 
 # DRAM bytes per grid point of one launch (dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture on a 384^3 case, divided by the
-# points; traffic grows with the points). Kept only while the kernel is the one
-# that was captured: profiles/acoustic3d_fused_fp16_kahan_512.md.
-MEASURED_TRAFFIC_PER_POINT = {("fp16", True, "fused"): (1064.997e6 + 862.244e6) / 384 ** 3}
+# dram__bytes_write.sum of one ncu capture, divided by the points; traffic
+# grows with the points) come from profiles/dram_traffic.txt, one line per
+# capture: kernel, precision, compensation, the sha256 of the kernel's sources
+# when it was captured, bytes per point. A record whose sources have changed
+# since is not used (roofline.traffic is then null).
+KERNEL_SOURCES = {"fused": ["acoustic3d_fused.cu", "fused_common.cuh", "vec_policy.cuh", "acoustic_common.cuh",
+                            "wave_arith.cuh"],
+                  "kv": ["acoustic3d_stream.cu", "vec_policy.cuh", "acoustic_common.cuh", "wave_arith.cuh"],
+                  "kp": ["acoustic3d_stream.cu", "vec_policy.cuh", "acoustic_common.cuh", "wave_arith.cuh"]}
+
+
+def sources_sha(kernel: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2310_00236_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic_per_point(kernel: str, precision: str, comp: bool):
+    """DRAM bytes per point from the capture record of this exact kernel
+    source, else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    want = sources_sha(kernel)
+    for line in lines:
+        f = line.split()
+        if len(f) >= 5 and not line.startswith("#") and f[0] == kernel and f[1] == precision \
+                and f[2] == ("comp" if comp else "plain") and f[3] == want:
+            return float(f[4])
+    return None
+
 
 KERNEL_NAMES = {"kv": "velocity half step", "kp": "pressure half step",
                 "fused": "one-pass step (both half steps)"}
@@ -198,6 +230,75 @@ def run_variants(W, w, steps, traced=100):
     return out
 
 
+ACC_VARIANTS = (("fp16", 0), ("fp16", 3), ("fp16", 6), ("bf16", 0), ("bf16", 3), ("fp16_f32arith", 0),
+                ("fp16_f32arith", 3), ("bf16_f32arith", 3), ("fp32", 0))
+
+
+def _vname(prec_name, comp):
+    return f"{prec_name}+{comp}op" if comp else prec_name
+
+
+def run_accuracy(W):
+    """Accuracy of every variant on the GPU path: relative L2 distance of the
+    final pressure field to the binary32 run of the same problem, and the
+    largest relative energy change over the run (energy after every step).
+    Workloads: config 1 (256^2, rho = c = 1, p = 0 walls, centred Gaussian,
+    CFL 0.5, 2000 steps) and the 3D benchmark recipe at 256^3 (velocity filter
+    width 8 cells, Gaussian of 6 cells, CFL 0.4, 400 steps). The binary32 run
+    stands in for binary64 (the GPU has no binary64 path): the oracle puts its
+    own distance to binary64 at 1.5e-6 (config 1) and 5e-7 (the 3D recipe)."""
+    import torch
+    from paper_2310_00236_gb300 import inputs
+    cases = {"cfg1_256_cfl0.5_2000": (inputs.acoustic_2d_gaussian(256, 2000), 2000),
+             "cfg3_recipe_256_cfl0.4_400": (inputs.acoustic_3d_random(n=256, sigma_cells=8.0,
+                                                                      ic_sigma_cells=6.0), 400)}
+    out = {"reference": "fp32 on the GPU (oracle distance to binary64: 1.5e-6 cfg1, 5e-7 3D recipe)"}
+    stream = torch.cuda.Stream()
+    for key, (w, steps) in cases.items():
+        nd = len(w["shape"])
+        bc = [W.WAVE_BC_RIGID] * (2 * nd) + [W.WAVE_BC_PERIODIC] * (6 - 2 * nd)
+        fields, rows = {}, {}
+        for prec_name, comp in ACC_VARIANTS:
+            ctx = W.wave_create(w["shape"], w["h"], w["rho"], w["c"], w["dt"], W.PRECISIONS[prec_name], comp,
+                                bc=bc, field_scale=w["P0"], stream=stream.cuda_stream)
+            try:
+                W.wave_set_initial(ctx, W.WAVE_F_P, w["p0"])
+                en = torch.zeros(steps, dtype=torch.float64, device="cuda")
+                W.wave_set_energy_trace(ctx, en, steps)
+                W.wave_step(ctx, steps)
+                stream.synchronize()
+                e = en.cpu().numpy()
+                fields[_vname(prec_name, comp)] = W.wave_get_field(ctx, W.WAVE_F_P)
+            finally:
+                W.wave_destroy(ctx)
+            rows[_vname(prec_name, comp)] = {"energy_drift_max": float(np.max(np.abs(e - e[0])) / abs(e[0]))}
+        ref = fields["fp32"]
+        for name, f in fields.items():
+            rows[name]["rel_l2_vs_fp32"] = float(np.linalg.norm(f - ref) / np.linalg.norm(ref))
+        out[key] = rows
+    return out
+
+
+def pareto(variants, accuracy):
+    """(Gpoint-updates/s on the 512^3 benchmark, energy drift and relative L2
+    on the 3D recipe at 256^3) per variant, and whether no other variant is
+    at least as good in all three and better in one."""
+    acc = accuracy["cfg3_recipe_256_cfl0.4_400"]
+    rows = []
+    for name, v in variants.items():
+        if name not in acc:
+            continue
+        rows.append({"variant": name, "gpt_s": v["value"], "energy_drift": acc[name]["energy_drift_max"],
+                     "rel_l2_vs_fp32": acc[name]["rel_l2_vs_fp32"]})
+    for r in rows:
+        r["pareto_optimal"] = not any(
+            o is not r and o["gpt_s"] >= r["gpt_s"] and o["energy_drift"] <= r["energy_drift"]
+            and o["rel_l2_vs_fp32"] <= r["rel_l2_vs_fp32"]
+            and (o["gpt_s"] > r["gpt_s"] or o["energy_drift"] < r["energy_drift"]
+                 or o["rel_l2_vs_fp32"] < r["rel_l2_vs_fp32"]) for o in rows)
+    return rows
+
+
 def run_cfg1(W, steps=2000):
     """The 2D acoustic configuration (256^2, rho = c = 1, p = 0 walls, centred
     Gaussian, CFL 0.5), fp16 + sum_3op: L2-resident, latency-bound."""
@@ -266,8 +367,10 @@ def run_elastic(W, steps: int, warmup: int):
         z0 = float(w["rho"].max() * w["vp"].max())
         amp = 0.5 * 1e5 * w["h"] ** 2 / (w["dt"] * z0)
         W.wave_set_source(ctx, W.WAVE_F_VY, w["src_idx"], w["wavelet"] * amp)
-        # past the source window, then time
+        # past the source window, then a call of the timed length (the
+        # library's step graphs exist from then on), then time
         W.wave_step(ctx, w["src_steps"] + warmup)
+        W.wave_step(ctx, steps)
         e0 = W.wave_energy(ctx)
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
@@ -615,7 +718,7 @@ def main():
     ap.add_argument("--zchunk", type=int, default=0, help="z planes per block (0: library default)")
     ap.add_argument("--shots", type=int, default=16, help="shots of the adjoint leg")
     ap.add_argument("--leg", default="all",
-                    choices=["all", "batched", "adjoint", "elastic", "w0", "cpu_baseline"],
+                    choices=["all", "batched", "adjoint", "elastic", "w0", "accuracy", "cpu_baseline"],
                     help="run one secondary workload alone and print its JSON (profiling aid)")
     ap.add_argument("--kernel", type=int, default=0,
                     help="0 automatic, 1 one-thread-per-point, 2 two-kernel streaming")
@@ -645,6 +748,8 @@ def main():
             out = run_batched(W, args.steps, args.warmup)
         elif args.leg == "w0":
             out = run_w0(W)
+        elif args.leg == "accuracy":
+            out = run_accuracy(W)
         elif args.leg == "adjoint":
             out = run_adjoint(W, args.steps, n=args.n if args.n != 512 else 256, nshots=args.shots)
         else:
@@ -679,8 +784,8 @@ def main():
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "frac_of_nominal_7900": achieved / 7900.0,
             "peak_kind": peak_kind,
-            "traffic": (MEASURED_TRAFFIC_PER_POINT[("fp16", True, dom)] * npts
-                        if ("fp16", True, dom) in MEASURED_TRAFFIC_PER_POINT else None),
+            "traffic": (lambda t: None if t is None else t * npts)(measured_traffic_per_point(dom, "fp16", True)),
+            "traffic_sources_sha256": sources_sha(dom),
             "bytes_per_point": bpp, "ms_per_launch": kms / nl,
             "shares": {k: kt[k][1] / sum(v[1] for v in kt.values()) for k in kt}}
     drift16 = abs(r16["e1"] - r16["e0"]) / abs(r16["e0"])
@@ -698,9 +803,12 @@ def main():
     batched = None
     adjoint = None
     variants = None
+    accuracy = None
     cfg1 = None
     if not args.no_compare:
         variants = run_variants(W, w, min(args.steps, 100))
+        accuracy = run_accuracy(W)
+        accuracy["pareto"] = pareto(variants, accuracy)
         cfg1 = run_cfg1(W)
         adjoint = run_adjoint(W, min(args.steps, 1500))
         elastic = run_elastic(W, min(args.steps, 4000), args.warmup)
@@ -730,6 +838,7 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": sum(v[0] for v in kt.values()), "compare": compare,
                 "elastic": elastic, "batched": batched, "adjoint": adjoint, "variants": variants,
+                "accuracy": accuracy,
                 "cfg1": cfg1,
                 "energy_drift": drift16}
         print(json.dumps(line), flush=True)

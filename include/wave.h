@@ -122,7 +122,21 @@ typedef struct {
                             Every choice gives the same bits. */
     int32_t zchunk;      /* z planes per thread block of the 3D kernels; rows per
                             work item of the 2D row strips (0: automatic) */
-    int32_t reserved[6];
+    int32_t z_cut;       /* 3D acoustic only: the context is a z slab of a larger
+                            grid (domain decomposition along z, for a problem split
+                            over several GPUs). Bit 0: the z-lo face is a cut, bit 1:
+                            the z-hi face is a cut; a cut face reads the two ghost
+                            planes set by wave_set_z_ghosts instead of a boundary
+                            image, and the slab steps by wave_half_step. 0: the
+                            context is the whole grid. */
+    int32_t reserved[5];
+    double z0;           /* > 0: the impedance scale Z0 to use instead of
+                            max(rho) * max(vp) of this context's materials (every slab
+                            of a grid must use the grid's Z0); 0: computed */
+    const double *rho_above;  /* z_cut bit 1: the density of the grid plane just above
+                            the slab (host, n[0] * n[1], x fastest), for the z
+                            multiplier of the slab's last plane (rho averaged
+                            across the cut); else NULL */
 } wave_options;
 
 /* Optional device allocator for the context's memory (for instance a caching
@@ -362,6 +376,50 @@ wave_status wave_batch_create(int32_t nctx, wave_ctx *const *ctxs, wave_batch **
 wave_status wave_batch_step(wave_batch *batch, int64_t n);
 wave_status wave_batch_info(wave_batch *batch, int32_t *info, int32_t ninfo);
 void wave_batch_destroy(wave_batch *batch);
+
+/* Domain decomposition along z (not in the paper; the stencil radius of 2 of
+ * Section 3 fixes the ghost width). A 3D acoustic grid of nz planes is split
+ * into slabs, one context each (wave_options.z_cut, z0, rho_above), and every
+ * step is taken in two halves with an exchange of two planes per cut face in
+ * between:
+ *   wave_half_step(ctx, 0)  velocities from p (reads the p ghost planes)
+ *   exchange v_z            each slab's first two and last two planes of v_z go
+ *                           to the neighbours' ghost buffers
+ *   wave_half_step(ctx, 1)  pressure from the velocities (reads the v_z ghosts)
+ *   exchange p              likewise for p
+ * (p is exchanged once before the first step as well). Compensations are
+ * point-local and never exchanged. A slab computes exactly the values the
+ * whole grid's context computes on its planes (the same operations in the same
+ * order). The exchange is the caller's: peer copies or NCCL send/recv into the
+ * receiving GPU's own ghost buffers; the library never reads another GPU's
+ * memory.
+ *
+ * wave_set_z_ghosts -- device buffers of the ghost planes, caller owned, each
+ * two planes laid out like the context's fields (wave_get_layout): p_lo and
+ * vz_lo hold the grid planes z0-2, z0-1 below the slab, p_hi and vz_hi the
+ * planes z1, z1+1 above it. Exactly the cut faces' pointers are non-NULL, each
+ * 16-byte aligned. EINVAL otherwise or for a context that is not a slab.
+ *
+ * wave_half_step -- which = 0: the velocity half step; which = 1: the pressure
+ * half step with the source, the energy of the step (wave_energy) and the
+ * receivers; the pair advances the step count by one. For contexts that run
+ * two-kernel steps (slabs always do; others with wave_options.kernel = 1 or 2);
+ * ESTATE for a context stepping with a fused kernel, or when the halves are
+ * called out of order. wave_step is refused (ESTATE) on a slab.
+ *
+ * wave_copy_planes -- copy planes z_first .. z_first + nplanes - 1 of a field
+ * (storage format, laid out as wave_get_layout says) into device memory dst,
+ * asynchronously on the context's stream: the planes a slab sends to its
+ * neighbours. EINVAL for a range outside the context or a NULL dst.
+ *
+ * wave_get_layout -- out[0] row pitch in elements, out[1] elements per plane
+ * (pitch * n[1]), out[2] bytes per element of the storage format. */
+wave_status wave_set_z_ghosts(wave_ctx *ctx, const void *p_lo, const void *p_hi, const void *vz_lo,
+                              const void *vz_hi);
+wave_status wave_half_step(wave_ctx *ctx, int32_t which);
+wave_status wave_copy_planes(wave_ctx *ctx, wave_field field, int64_t z_first, int64_t nplanes,
+                             void *dst);
+wave_status wave_get_layout(wave_ctx *ctx, int64_t out[3]);
 
 /* wave_energy_acoustic_static -- the acoustic discrete energy (the quantity
  * wave_energy reports) computed from device arrays the caller already owns,

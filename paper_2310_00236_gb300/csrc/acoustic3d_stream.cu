@@ -22,12 +22,24 @@ namespace wave {
 
 // Load the raw vector of a field at (x, row m_y, plane m_z) applying the
 // boundary images along y and z. node_y / node_z: the field sits on nodes
-// (odd image, wall at N) or half points (even image) along that axis.
+// (odd image, wall at N) or half points (even image) along that axis. Past a
+// cut z face of a slab (prm.zg_lo / zg_hi) the plane comes from the ghost
+// planes instead (the y image still applies).
 template <class V>
 __device__ __forceinline__ typename V::Raw load_vec_img(const void *f, const AcParams &prm, int x,
                                                         int my, int mz, bool node_y, bool node_z) {
     int jy, kz;
     int sy = node_y ? img_node(my, prm.n[1], prm.bc[1], jy) : img_half(my, prm.n[1], prm.bc[1], jy);
+    if ((mz < 0 && prm.zg_lo) || (mz >= prm.n[2] && prm.zg_hi)) {
+        // ghost planes: lo holds planes -2, -1, hi holds n, n+1 (the kernels read no farther)
+        const bool lo = mz < 0;
+        const int gk = lo ? mz + 2 : mz - prm.n[2];
+        if (sy == 0 || x >= prm.n[0] || my > prm.n[1] + 2 || my < -3 || gk < 0 || gk > 1) return V::zero();
+        const typename V::Raw r = *reinterpret_cast<const typename V::Raw *>(
+            static_cast<const char *>(lo ? prm.zg_lo : prm.zg_hi) +
+            (x + prm.sy * jy + prm.sz * (int64_t)gk) * sizeof(typename V::RS));
+        return sy < 0 ? V::rneg(r) : r;
+    }
     int sz = node_z ? img_node(mz, prm.n[2], prm.bc[2], kz) : img_half(mz, prm.n[2], prm.bc[2], kz);
     if (sy == 0 || sz == 0 || x >= prm.n[0] || my > prm.n[1] + 2 || my < -3 || mz > prm.n[2] + 2 || mz < -3)
         return V::zero();

@@ -31,6 +31,12 @@ struct AcParams {
     unsigned int *e_count;     // blocks finished (reset by the last block)
     double *e_out;             // result slot (physical units)
     double e_factor;           // 0.5 h^(d-1) P0^2 dt / Z0
+    // z slab of a larger grid (3D streaming kernels): two ghost planes of the
+    // field this half step differentiates along z (p for the velocities, v_z
+    // for the pressure), pitched like the fields; zg_lo holds the grid planes
+    // z0-2, z0-1 below the slab, zg_hi the planes z1, z1+1 above it. nullptr:
+    // that face is a face of the grid and its boundary image applies.
+    const void *zg_lo, *zg_hi;
 };
 
 // Boundary images along one axis with N cells (Section 3 periodic wrap; rigid

@@ -2,13 +2,15 @@
 // with no device allocation: the reduction's scratch is a fixed-size static
 // device array of this file.
 //
-// Some callers cannot allocate device memory: a host framework that owns the
-// whole device heap and hands out only views, code running while a CUDA
-// stream is being captured into a graph (allocation calls are not allowed
-// there), or a real-time loop with a fixed memory budget that forbids any
-// allocation after start-up. wave_energy_acoustic_static serves them: they pass
-// the fields and multipliers they already hold, and the per-block partial
-// sums go to g_energy_scratch below instead of a buffer from cudaMalloc.
+// Some callers cannot allocate device memory: a host framework that reserves
+// the whole device heap at start-up and hands out only views of it (a
+// cudaMalloc of its own would fail or break the framework's accounting), or a
+// real-time loop with a fixed memory budget that forbids any allocation after
+// start-up (an allocation can block, fragment the heap or fail mid-run).
+// wave_energy_acoustic_static serves them: they pass the fields and
+// multipliers they already hold, and the per-block partial sums go to
+// g_energy_scratch below instead of a buffer from cudaMalloc.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <mutex>
 #include <stdio.h>
@@ -49,9 +51,11 @@ __device__ __forceinline__ float load_f32(const void *f, int64_t q) {
     return wave::F16::to_f32(s);
 }
 
-// Same terms as the fused energy of the pressure kernels: products in binary32
-// (exact for half / bfloat16), one correctly rounded division, a compensated
-// binary32 sum per thread, binary64 across threads and blocks.
+// The same terms as the energy of the stepping kernels, with a per-point
+// division where the fused one-pass step multiplies by rounded reciprocals of
+// a uniform a: products in binary32 (exact for half / bfloat16), one correctly
+// rounded division per term, a compensated binary32 sum per thread, binary64
+// across threads and blocks.
 template <int PREC, int NDIM>
 __global__ void __launch_bounds__(kThreads)
 energy_static_kernel(int64_t npts, const void *p_old, const void *p_new, const void *v0,
@@ -116,10 +120,43 @@ energy_static_kernel(int64_t npts, const void *p_old, const void *p_new, const v
     }
 }
 
-// Device address of g_energy_scratch, looked up once per device with that
-// device current (the host-side name is only a stand-in for the symbol).
+// Device address of g_energy_scratch, looked up with the device current (the
+// host-side name is only a stand-in for the symbol) and cached per device
+// together with the identity of the CUDA context it was looked up in: a new
+// context on the device (after cudaDeviceReset, say) loads the module afresh
+// at another address, so the lookup is repeated then.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+struct ScratchSlot {
+    unsigned long long ctx_id;
+    void *addr;
+};
 std::mutex g_scratch_mu;
-void *g_scratch_addr[256] = {nullptr};
+ScratchSlot g_scratch_slot[256] = {};
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Identity of the current context, 0 if there is none yet (or the driver
+// entry points are unavailable).
+unsigned long long current_ctx_id() {
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void *p1 = nullptr, *p2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p1, 12000, cudaEnableDefault, &q1) !=
+                cudaSuccess || q1 != cudaDriverEntryPointSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &p2, 12000, cudaEnableDefault, &q2) !=
+                cudaSuccess || q2 != cudaDriverEntryPointSuccess)
+            return 0;
+        g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(p1);
+        g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(p2);
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 wave_status scratch_address(EnergyScratch **out) {
     int dev = -1;
@@ -131,7 +168,9 @@ wave_status scratch_address(EnergyScratch **out) {
         return WAVE_ECUDA;
     }
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long id = current_ctx_id();
+    ScratchSlot &slot = g_scratch_slot[dev];
+    if (!slot.addr || id == 0 || slot.ctx_id != id) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_energy_scratch);
         if (e != cudaSuccess || !p) {
@@ -140,9 +179,10 @@ wave_status scratch_address(EnergyScratch **out) {
             set_error(g_static_err);
             return WAVE_ECUDA;
         }
-        g_scratch_addr[dev] = p;
+        slot.addr = p;
+        slot.ctx_id = current_ctx_id();  // the lookup has made the context current
     }
-    *out = static_cast<EnergyScratch *>(g_scratch_addr[dev]);
+    *out = static_cast<EnergyScratch *>(slot.addr);
     return WAVE_OK;
 }
 
@@ -172,12 +212,16 @@ extern "C" wave_status wave_energy_acoustic_static(int32_t ndim, const int64_t n
         set_error(g_static_err);
         return WAVE_EINVAL;
     }
+    const int64_t maxp = (int64_t)WAVE_ENERGY_STATIC_MAX_BLOCKS * kPointsPerBlock;
+    int64_t npts = 1;
     for (int d = 0; d < ndim; d++) {
         if (!v[d] || !a[d] || n[d] < 1) {
             snprintf(g_static_err, sizeof g_static_err, "wave_energy_acoustic_static: bad arguments");
             set_error(g_static_err);
             return WAVE_EINVAL;
         }
+        // the product of the extents, stopped at the limit before it can overflow
+        if (npts <= maxp) npts = n[d] > maxp ? maxp + 1 : npts * n[d];
     }
     if (prec != WAVE_FP32 && prec != WAVE_FP16 && prec != WAVE_BF16 && prec != WAVE_FP16_F32ARITH &&
         prec != WAVE_BF16_F32ARITH) {
@@ -186,13 +230,11 @@ extern "C" wave_status wave_energy_acoustic_static(int32_t ndim, const int64_t n
         set_error(g_static_err);
         return WAVE_EINVAL;
     }
-    const int64_t npts = n[0] * n[1] * (ndim == 3 ? n[2] : 1);
-    const int64_t maxp = (int64_t)WAVE_ENERGY_STATIC_MAX_BLOCKS * kPointsPerBlock;
     if (npts > maxp) {
         snprintf(g_static_err, sizeof g_static_err,
-                 "wave_energy_acoustic_static: %lld points exceed the static scratch limit of %lld "
-                 "points (%d blocks of %d)", (long long)npts, (long long)maxp,
-                 WAVE_ENERGY_STATIC_MAX_BLOCKS, kPointsPerBlock);
+                 "wave_energy_acoustic_static: the grid exceeds the static scratch limit of %lld "
+                 "points (%d blocks of %d)", (long long)maxp, WAVE_ENERGY_STATIC_MAX_BLOCKS,
+                 kPointsPerBlock);
         set_error(g_static_err);
         return WAVE_EINVAL;
     }

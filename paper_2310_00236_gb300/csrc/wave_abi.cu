@@ -172,7 +172,7 @@ static int fused_zchunk_for(const AcParams &prm, int prec, int sms) {
 // items, large grids long ones that re-read fewer halo rows). Measured on
 // 1024^2: 2 rows per item 50.6 (elastic) and 71.5 (acoustic) Gpt/s, 16 rows
 // 16.4 and 31.9.
-constexpr int kStripWarps = 4, kStripGraphSteps = 32;
+constexpr int kStripWarps = 4, kStripGraphLevels = 6;  // graphs of 1, 2, 4, ..., 32 steps
 static int strip_rows_for(int64_t nstrips, int64_t ny, int sms) {
     const int64_t r = nstrips * ny / (12 * (int64_t)sms);
     return (int)std::max<int64_t>(1, std::min<int64_t>(16, r));
@@ -194,7 +194,8 @@ struct wave_ctx {
     // 2D: the row-strip kernels of the batches, as a batch of one
     bool use_strips = false;
     int strip_items = 0, strip_grid = 0, strip_rows = 16;
-    cudaGraphExec_t strip_graph = nullptr;  // kStripGraphSteps plain strip steps
+    // plain strip steps replayed from captured graphs of 2^j steps (j < kStripGraphLevels)
+    cudaGraphExec_t strip_graph[kStripGraphLevels] = {};
     DevBuf strip_shot, strip_item0, strip_part;
     // second set of p, vx, vy, vz and t_vx, t_vy, t_vz for the one-pass step,
     // and the tensor maps of both sets (fset: the set the fields point to now)
@@ -202,6 +203,12 @@ struct wave_ctx {
     struct alignas(64) MapBlob { unsigned char b[2048]; } fmaps[2];
     int fset = 0;
     double h = 0, dt = 0, P0 = 1.0, Z0 = 1.0;
+    // z slab of a larger grid: cut faces (bit 0 z-lo, bit 1 z-hi), the ghost
+    // planes (p lo, p hi, v_z lo, v_z hi), whether a velocity half step awaits
+    // its pressure half
+    int z_cut = 0;
+    const void *zg[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool half_open = false;
     cudaStream_t stream = nullptr;
     bool poisoned = false;
     int64_t step = 0;
@@ -337,7 +344,8 @@ static wave_status download_packed(wave_ctx *c, const void *dev, void *host) {
 }
 
 // ------------------------------------------------------- acoustic creation
-static wave_status acoustic_coefficients(wave_ctx *c, const wave_materials *mat) {
+static wave_status acoustic_coefficients(wave_ctx *c, const wave_materials *mat, double z0_opt,
+                                         const double *rho_above) {
     const int64_t npts = c->n[0] * c->n[1] * c->n[2];
     double rho0 = 0.0, c0 = 0.0;
     for (int64_t q = 0; q < npts; q++) {
@@ -348,10 +356,14 @@ static wave_status acoustic_coefficients(wave_ctx *c, const wave_materials *mat)
         if (mat->rho[q] > rho0) rho0 = mat->rho[q];
         if (mat->vp[q] > c0) c0 = mat->vp[q];
     }
-    const double Z0 = rho0 * c0;
+    const double Z0 = z0_opt > 0.0 ? z0_opt : rho0 * c0;
     c->Z0 = Z0;
     const double h = c->h, dt = c->dt;
     const double tiny = min_normal(c->prec);
+    if (rho_above)
+        for (int64_t q = 0; q < c->n[0] * c->n[1]; q++)
+            if (!(rho_above[q] > 0.0) || !isfinite(rho_above[q]))
+                return fail(WAVE_ERANGE, "rho_above at point %lld is not positive and finite", (long long)q);
     for (int w = 0; w < 4; w++) c->coef_host[w].assign(npts, 0.0);
     c->two_over_c.resize(npts);
     for (int64_t q = 0; q < npts; q++) c->two_over_c[q] = (float)(2.0 / mat->vp[q]);
@@ -376,7 +388,9 @@ static wave_status acoustic_coefficients(wave_ctx *c, const wave_materials *mat)
             int64_t m = idx[ax] + 1;
             if (m >= c->n[ax]) m = (c->bc[2 * ax] == WAVE_BC_PERIODIC) ? 0 : idx[ax];
             const int64_t nb = q + (m - idx[ax]) * str[ax];
-            const double rho_c = (mat->rho[q] + mat->rho[nb]) * 0.5;
+            // a slab's last plane averages with the grid plane above a cut face
+            const bool across = ax == 2 && (c->z_cut & 2) && idx[2] == c->n[2] - 1;
+            const double rho_c = (mat->rho[q] + (across ? rho_above[q % (nx * ny)] : mat->rho[nb])) * 0.5;
             double av = ((dt * Z0) / h) / rho_c;
             double ar;
             uint16_t tmp16;
@@ -592,7 +606,8 @@ static void adjoint_free(wave_ctx *c) {
 
 static void destroy_ctx(wave_ctx *c) {
     if (!c) return;
-    if (c->strip_graph) cudaGraphExecDestroy(c->strip_graph);
+    for (auto g : c->strip_graph)
+        if (g) cudaGraphExecDestroy(g);
     dev_free(c, c->strip_shot);
     dev_free(c, c->strip_item0);
     dev_free(c, c->strip_part);
@@ -643,14 +658,25 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
         return fail(WAVE_EINVAL, "bad compensation %d", (int)compensated);
     if (!mat->rho || !mat->vp) return fail(WAVE_EINVAL, "material arrays are NULL");
     if (mat->kind == WAVE_ELASTIC && !mat->vs) return fail(WAVE_EINVAL, "elastic needs vs");
-    double P0 = 1.0;
-    int kchoice = 0, zchunk = 0;
+    double P0 = 1.0, z0_opt = 0.0;
+    int kchoice = 0, zchunk = 0, z_cut = 0;
+    const double *rho_above = nullptr;
     if (opt) {
         if (opt->field_scale != 0.0) P0 = opt->field_scale;
         kchoice = opt->kernel;
         zchunk = opt->zchunk;
+        z_cut = opt->z_cut;
+        z0_opt = opt->z0;
+        rho_above = opt->rho_above;
     }
     if (kchoice < 0 || kchoice > 3 || zchunk < 0) return fail(WAVE_EINVAL, "bad kernel options");
+    if (z_cut < 0 || z_cut > 3) return fail(WAVE_EINVAL, "z_cut takes bits 0 and 1 only");
+    if (z_cut && (mat->kind != WAVE_ACOUSTIC || grid->ndim != 3))
+        return fail(WAVE_EINVAL, "z slabs are 3D acoustic contexts");
+    if (z_cut && (kchoice == 1 || kchoice == 3))
+        return fail(WAVE_EINVAL, "z slabs step with the two-kernel streaming path (kernel 0 or 2)");
+    if ((z_cut & 2) && !rho_above) return fail(WAVE_EINVAL, "a cut z-hi face needs rho_above");
+    if (!(z0_opt >= 0.0) || !isfinite(z0_opt)) return fail(WAVE_EINVAL, "z0 must be >= 0 and finite");
     if (!(P0 > 0.0) || !isfinite(P0)) return fail(WAVE_EINVAL, "field_scale must be positive");
     const int64_t npts = grid->n[0] * grid->n[1] * (grid->ndim == 3 ? grid->n[2] : 1);
     if (npts > ((int64_t)1 << 31) - 1) return fail(WAVE_EINVAL, "grid too large (>= 2^31 points)");
@@ -664,6 +690,7 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
     c->prec = prec;
     c->comp = compensated;
     c->kernel_choice = kchoice;
+    c->z_cut = z_cut;
     if (zchunk > 0) { c->zchunk = zchunk; c->zchunk_set = true; }
     c->h = spacing[0];
     c->dt = dt;
@@ -685,7 +712,7 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
                             ax);
             }
         }
-        st = acoustic_coefficients(c, mat);
+        st = acoustic_coefficients(c, mat, z0_opt, (z_cut & 2) ? rho_above : nullptr);
         if (st) { delete c; return st; }
         const size_t eb = elem_bytes(prec);
         int nf = 1 + c->ndim;
@@ -697,9 +724,11 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
         AcParams prm;
         fill_acoustic_params(c, prm);
         c->e_blocks = acoustic_generic_blocks(prm, c->ndim);
-        c->use_fused = (kchoice == 0 || kchoice == 3) && acoustic_fused_supported(prm, c->ndim, c->prec);
+        c->use_fused = !z_cut && (kchoice == 0 || kchoice == 3) && acoustic_fused_supported(prm, c->ndim, c->prec);
         c->use_stream = !c->use_fused && kchoice != 1 &&
                         acoustic_stream_supported(prm, c->ndim, c->prec);
+        if (z_cut && !c->use_stream && !st)
+            st = fail(WAVE_EINVAL, "z slabs need n[0] a multiple of the 16-byte vector width");
         if (c->use_fused && !c->zchunk_set) {
             int dev = 0, sms = 1;
             cudaGetDevice(&dev);
@@ -799,6 +828,7 @@ static bool on_rigid_wall_zeroed(const wave_ctx *c, int field, const int64_t idx
     // planes of the rigid axes other than c
     for (int ax = 0; ax < c->ndim; ax++) {
         if (c->bc[2 * ax] != WAVE_BC_RIGID || idx[ax] != 0) continue;
+        if (ax == 2 && (c->z_cut & 1)) continue;  // a cut, not the grid's wall
         if (field == WAVE_F_P) return true;
         if (field - 1 != ax) return true;
     }
@@ -1046,6 +1076,46 @@ extern "C" wave_status wave_energy(wave_ctx *c, double *E) {
 
 // -------------------------------------------------------------------- step
 // energy_last: reduce the discrete energy on the last step (wave_energy reads it)
+// Run m plain steps (no energy, receivers or trace; the step index lives in
+// device memory) from captured graphs of 2^j steps: m = 32 q + (binary digits
+// of the rest), so any run length takes at most q + 5 replays. All sizes are
+// captured at the first use (63 steps' worth of launches, once), so that no
+// later call pays for a capture. one_step() queues one step on the context's
+// stream. Returns the number of steps replayed (fewer than m if a capture
+// failed; the caller takes the rest with plain launches).
+template <class F>
+static int64_t strip_graph_run(wave_ctx *c, int64_t m, F one_step, cudaError_t &err) {
+    err = cudaSuccess;
+    int64_t done = 0;
+    for (int j = kStripGraphLevels - 1; j >= 0; j--) {
+        const int64_t len = (int64_t)1 << j;
+        if (!c->strip_graph[j]) {
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                for (int64_t t = 0; t < len && e == cudaSuccess; t++) e = one_step();
+                cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+                if (e == cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&c->strip_graph[j], g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) {  // no graph: the caller launches the rest
+                cudaGetLastError();
+                c->strip_graph[j] = nullptr;
+                return done;
+            }
+        }
+        if (m - done < len) continue;
+        // the largest size as often as it fits; below it, each binary digit of the rest once
+        do {
+            err = cudaGraphLaunch(c->strip_graph[j], c->stream);
+            if (err != cudaSuccess) return done;
+            done += len;
+        } while (j == kStripGraphLevels - 1 && m - done >= len);
+    }
+    return done;
+}
+
 static wave_status acoustic_steps(wave_ctx *c, int64_t n, bool energy_last = true) {
     AcParams prm;
     fill_acoustic_params(c, prm);
@@ -1068,32 +1138,15 @@ static wave_status acoustic_steps(wave_ctx *c, int64_t n, bool energy_last = tru
         L.wpb = kStripWarps;
         L.grid = c->strip_grid;
         // plain runs (no receivers, no energy trace) on a created stream: the
-        // steps before the last are replayed from a graph of kStripGraphSteps
-        // steps (the source's step index lives in device memory)
+        // steps before the last are replayed from captured graphs (the
+        // source's step index lives in device memory)
         const bool plain = !c->nrec && !c->e_trace && c->stream != nullptr && !c->timing;
-        if (plain && n - 1 >= kStripGraphSteps) {
-            if (!c->strip_graph) {
-                cudaGraph_t g = nullptr;
-                e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-                if (e == cudaSuccess) {
-                    for (int t = 0; t < kStripGraphSteps && e == cudaSuccess; t++)
-                        e = batch_step(L, c->prec, c->comp, false, c->stream);
-                    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
-                    if (e == cudaSuccess) e = e2;
-                }
-                if (e == cudaSuccess) e = cudaGraphInstantiate(&c->strip_graph, g, 0);
-                if (g) cudaGraphDestroy(g);
-                if (e != cudaSuccess) {  // no graph: plain launches below
-                    cudaGetLastError();
-                    c->strip_graph = nullptr;
-                }
-            }
-            while (c->strip_graph && n - 1 >= kStripGraphSteps) {
-                e = cudaGraphLaunch(c->strip_graph, c->stream);
-                if (e != cudaSuccess) return cuda_check(c, e, "graph launch");
-                n -= kStripGraphSteps;
-                c->step += kStripGraphSteps;
-            }
+        if (plain && n > 1) {
+            const int64_t done = strip_graph_run(
+                c, n - 1, [&]() { return batch_step(L, c->prec, c->comp, false, c->stream); }, e);
+            if (e != cudaSuccess) return cuda_check(c, e, "graph launch");
+            n -= done;
+            c->step += done;
         }
     }
     for (int64_t s = 0; s < n; s++) {
@@ -1211,32 +1264,18 @@ static wave_status elastic_steps(wave_ctx *c, int64_t n) {
         if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
         if (err != cudaSuccess) return cuda_check(c, err, "wave_step upload");
         const bool plain = !c->nrec && !c->e_trace && c->stream != nullptr && !c->timing;
-        if (plain && n - 1 >= kStripGraphSteps) {
-            if (!c->strip_graph) {
-                cudaGraph_t g = nullptr;
-                e.energy = 0;
-                err = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-                if (err == cudaSuccess) {
-                    for (int t = 0; t < kStripGraphSteps && err == cudaSuccess; t++) {
-                        err = elastic_strip_half_step(e, c->prec, c->comp, 0, L, c->stream);
-                        if (err == cudaSuccess) err = elastic_strip_half_step(e, c->prec, c->comp, 1, L, c->stream);
-                    }
-                    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
-                    if (err == cudaSuccess) err = e2;
-                }
-                if (err == cudaSuccess) err = cudaGraphInstantiate(&c->strip_graph, g, 0);
-                if (g) cudaGraphDestroy(g);
-                if (err != cudaSuccess) {  // no graph: plain launches below
-                    cudaGetLastError();
-                    c->strip_graph = nullptr;
-                }
-            }
-            while (c->strip_graph && n - 1 >= kStripGraphSteps) {
-                err = cudaGraphLaunch(c->strip_graph, c->stream);
-                if (err != cudaSuccess) return cuda_check(c, err, "graph launch");
-                n -= kStripGraphSteps;
-                c->step += kStripGraphSteps;
-            }
+        if (plain && n > 1) {
+            e.energy = 0;
+            const int64_t done = strip_graph_run(
+                c, n - 1,
+                [&]() {
+                    cudaError_t r = elastic_strip_half_step(e, c->prec, c->comp, 0, L, c->stream);
+                    return r == cudaSuccess ? elastic_strip_half_step(e, c->prec, c->comp, 1, L, c->stream) : r;
+                },
+                err);
+            if (err != cudaSuccess) return cuda_check(c, err, "graph launch");
+            n -= done;
+            c->step += done;
         }
     }
     for (int64_t s = 0; s < n; s++) {
@@ -1271,6 +1310,8 @@ static wave_status elastic_steps(wave_ctx *c, int64_t n) {
 extern "C" wave_status wave_step(wave_ctx *c, int64_t n) {
     CHECK_CTX(c);
     if (n < 0) return fail(WAVE_EINVAL, "negative step count");
+    if (c->z_cut) return fail(WAVE_ESTATE, "a z slab steps by wave_half_step, with exchanges in between");
+    if (c->half_open) return fail(WAVE_ESTATE, "a velocity half step awaits its pressure half step");
     if (n == 0) return WAVE_OK;
     wave_status st;
     if (c->kind == WAVE_ACOUSTIC) {
@@ -1280,6 +1321,95 @@ extern "C" wave_status wave_step(wave_ctx *c, int64_t n) {
     }
     if (!st) c->have_energy = true;
     return st;
+}
+
+// ------------------------------------------------- z slabs and half steps
+extern "C" wave_status wave_set_z_ghosts(wave_ctx *c, const void *p_lo, const void *p_hi,
+                                         const void *vz_lo, const void *vz_hi) {
+    CHECK_CTX(c);
+    if (!c->z_cut) return fail(WAVE_EINVAL, "wave_set_z_ghosts: the context is not a z slab");
+    const void *g[4] = {p_lo, p_hi, vz_lo, vz_hi};
+    for (int i = 0; i < 4; i++) {
+        const bool cut = (c->z_cut >> (i & 1)) & 1;
+        if (cut != (g[i] != nullptr))
+            return fail(WAVE_EINVAL, "wave_set_z_ghosts: give the ghost buffers of exactly the cut faces");
+        if (g[i] && (reinterpret_cast<uintptr_t>(g[i]) & 15))
+            return fail(WAVE_EINVAL, "wave_set_z_ghosts: ghost buffers must be 16-byte aligned");
+    }
+    for (int i = 0; i < 4; i++) c->zg[i] = g[i];
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_half_step(wave_ctx *c, int32_t which) {
+    CHECK_CTX(c);
+    if (which != 0 && which != 1) return fail(WAVE_EINVAL, "wave_half_step: which is 0 or 1");
+    if (c->kind != WAVE_ACOUSTIC || c->use_fused || c->use_strips)
+        return fail(WAVE_ESTATE, "wave_half_step: this context steps with a fused kernel "
+                                 "(create it with kernel 1 or 2 for half steps)");
+    if ((which == 1) != c->half_open)
+        return fail(WAVE_ESTATE, "wave_half_step: the halves alternate, velocities first");
+    for (int i = 0; i < 4; i++)
+        if (((c->z_cut >> (i & 1)) & 1) && !c->zg[i])
+            return fail(WAVE_ESTATE, "wave_half_step: set the ghost buffers first");
+    AcParams prm;
+    fill_acoustic_params(c, prm);
+    prm.step = c->step;
+    prm.zg_lo = c->zg[which == 0 ? 0 : 2];
+    prm.zg_hi = c->zg[which == 0 ? 1 : 3];
+    const size_t eb = elem_bytes(c->prec);
+    cudaEvent_t m0 = mark(c);
+    cudaError_t e;
+    if (which == 0) {
+        e = c->use_stream ? acoustic_stream_half_step(prm, c->prec, c->comp, 0, c->zchunk, c->stream)
+                          : acoustic_generic_half_step(prm, c->ndim, c->prec, c->comp, 0, c->stream);
+        cudaEvent_t m1 = mark(c);
+        timed(c, 0, m0, m1);
+        if (e != cudaSuccess) return cuda_check(c, e, "wave_half_step launch");
+        c->half_open = true;
+        return WAVE_OK;
+    }
+    prm.energy = 1;
+    e = c->use_stream ? acoustic_stream_half_step(prm, c->prec, c->comp, 1, c->zchunk, c->stream)
+                      : acoustic_generic_half_step(prm, c->ndim, c->prec, c->comp, 1, c->stream);
+    cudaEvent_t m1 = mark(c);
+    timed(c, 1, m0, m1);
+    const bool trace = c->e_trace && c->e_trace_pos < c->e_trace_cap;
+    if (e == cudaSuccess && trace)
+        e = cudaMemcpyAsync(c->e_trace + c->e_trace_pos, c->e_misc.ptr, sizeof(double),
+                            cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && c->nrec && c->rec_pos < c->rec_cap)
+        e = sample_receivers(c->f[c->rec_field].ptr, (int)eb, is_bf16_storage(c->prec),
+                             static_cast<const int64_t *>(c->rec_q.ptr), (int)c->nrec,
+                             c->rec_traces + c->rec_pos * c->nrec, c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "wave_half_step launch");
+    if (trace) c->e_trace_pos++;
+    if (c->nrec && c->rec_pos < c->rec_cap) c->rec_pos++;
+    c->step++;
+    c->half_open = false;
+    c->have_energy = true;
+    return WAVE_OK;
+}
+
+extern "C" wave_status wave_copy_planes(wave_ctx *c, wave_field field, int64_t z_first, int64_t nplanes,
+                                        void *dst) {
+    CHECK_CTX(c);
+    if (!field_valid(c, field) || !dst) return fail(WAVE_EINVAL, "wave_copy_planes: bad field or NULL dst");
+    if (z_first < 0 || nplanes < 0 || z_first + nplanes > c->n[2])
+        return fail(WAVE_EINVAL, "wave_copy_planes: planes %lld..%lld outside 0..%lld", (long long)z_first,
+                    (long long)(z_first + nplanes - 1), (long long)(c->n[2] - 1));
+    const size_t eb = elem_bytes(c->prec);
+    cudaError_t e = cudaMemcpyAsync(dst, static_cast<const char *>(c->f[field].ptr) + z_first * c->plane * eb,
+                                    (size_t)(nplanes * c->plane) * eb, cudaMemcpyDeviceToDevice, c->stream);
+    return cuda_check(c, e, "wave_copy_planes");
+}
+
+extern "C" wave_status wave_get_layout(wave_ctx *c, int64_t out[3]) {
+    CHECK_CTX(c);
+    if (!out) return fail(WAVE_EINVAL, "wave_get_layout: NULL out");
+    out[0] = c->pitch;
+    out[1] = c->plane;
+    out[2] = (int64_t)elem_bytes(c->prec);
+    return WAVE_OK;
 }
 
 // Read the device error word (set by a bounded wait that expired).
@@ -1425,6 +1555,7 @@ extern "C" wave_status wave_reset(wave_ctx *c) {
     if (e != cudaSuccess) return cuda_check(c, e, "wave_reset");
     c->step = 0;
     c->have_energy = false;
+    c->half_open = false;
     c->rec_pos = 0;
     c->e_trace_pos = 0;
     c->adj.active = false;
@@ -1471,6 +1602,8 @@ static wave_status adjoint_fused_setup(wave_ctx *c);
 extern "C" wave_status wave_record(wave_ctx *c, int64_t nsteps, int64_t ncheckpoints) {
     CHECK_CTX(c);
     if (c->kind != WAVE_ACOUSTIC) return fail(WAVE_ENOTIMPL, "the adjoint covers the acoustic system");
+    if (c->z_cut) return fail(WAVE_ENOTIMPL, "the adjoint covers whole grids, not z slabs");
+    if (c->half_open) return fail(WAVE_ESTATE, "a velocity half step awaits its pressure half step");
     if (nsteps < 1) return fail(WAVE_EINVAL, "nsteps must be positive");
     if (c->nrec && c->rec_field != WAVE_F_P) return fail(WAVE_EINVAL, "adjoint receivers must record p");
     // the snapshot and replay buffers of a previous record are kept when they

@@ -36,7 +36,8 @@ EXPORTS = ["wave_set_allocator", "wave_create", "wave_set_initial", "wave_set_so
            "wave_adjoint_step", "wave_destroy", "wave_last_error", "wave_build_info",
            "wave_set_timing", "wave_get_timing", "wave_energy_acoustic_static",
            "wave_batch_create", "wave_batch_step", "wave_batch_info", "wave_batch_destroy",
-           "wave_record", "wave_get_gradient", "wave_reset", "wave_selftest_timeout"]
+           "wave_record", "wave_get_gradient", "wave_reset", "wave_selftest_timeout",
+           "wave_set_z_ghosts", "wave_half_step", "wave_copy_planes", "wave_get_layout"]
 
 
 class WaveError(RuntimeError):
@@ -57,7 +58,8 @@ class wave_materials(C.Structure):
 
 class wave_options(C.Structure):
     _fields_ = [("field_scale", C.c_double), ("kernel", C.c_int32), ("zchunk", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("z_cut", C.c_int32), ("reserved", C.c_int32 * 5), ("z0", C.c_double),
+                ("rho_above", C.POINTER(C.c_double))]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -105,6 +107,10 @@ def lib() -> C.CDLL:
         "wave_batch_create": [i32, C.POINTER(vp), C.POINTER(vp)],
         "wave_batch_step": [vp, i64],
         "wave_batch_info": [vp, C.POINTER(C.c_int32), i32],
+        "wave_set_z_ghosts": [vp, vp, vp, vp, vp],
+        "wave_half_step": [vp, i32],
+        "wave_copy_planes": [vp, C.c_int, i64, i64, vp],
+        "wave_get_layout": [vp, C.POINTER(C.c_int64)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -173,8 +179,10 @@ def _stream_handle(stream):
 
 
 def wave_create(n, spacing, rho, vp, dt, precision, comp, vs=None, bc=(WAVE_BC_RIGID,) * 6,
-                kind=WAVE_ACOUSTIC, field_scale=1.0, kernel=0, zchunk=0, stream=None) -> Context:
-    """n: cells per axis (x, y[, z]); rho, vp, vs: arrays shaped like a field."""
+                kind=WAVE_ACOUSTIC, field_scale=1.0, kernel=0, zchunk=0, stream=None,
+                z_cut=0, z0=0.0, rho_above=None) -> Context:
+    """n: cells per axis (x, y[, z]); rho, vp, vs: arrays shaped like a field.
+    z_cut, z0, rho_above: a z slab of a larger grid (wave_options in wave.h)."""
     ndim = len(n)
     g = wave_grid()
     g.ndim = ndim
@@ -198,6 +206,12 @@ def wave_create(n, spacing, rho, vp, dt, precision, comp, vs=None, bc=(WAVE_BC_R
     o.field_scale = field_scale
     o.kernel = kernel
     o.zchunk = zchunk
+    o.z_cut = z_cut
+    o.z0 = z0
+    if rho_above is not None:
+        ra, rp = _f64(rho_above)
+        keep.append(ra)
+        o.rho_above = rp
     out = C.c_void_p()
     _check(lib().wave_create(C.byref(g), sp, C.byref(m), float(dt), int(precision), int(comp),
                              C.byref(o), _stream_handle(stream), C.byref(out)))
@@ -235,6 +249,29 @@ def wave_set_receivers(ctx: Context, field: int, idx, traces=None, capacity_step
 
 def wave_step(ctx: Context, n: int):
     _check(lib().wave_step(ctx.ptr, int(n)))
+
+
+def wave_half_step(ctx: Context, which: int):
+    _check(lib().wave_half_step(ctx.ptr, int(which)))
+
+
+def wave_set_z_ghosts(ctx: Context, p_lo=None, p_hi=None, vz_lo=None, vz_hi=None):
+    """Ghost-plane buffers (device tensors of two planes each, laid out as
+    wave_get_layout says) of the cut faces; None for a face of the grid."""
+    ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+    _check(lib().wave_set_z_ghosts(ctx.ptr, ptr(p_lo), ptr(p_hi), ptr(vz_lo), ptr(vz_hi)))
+
+
+def wave_copy_planes(ctx: Context, field: int, z_first: int, nplanes: int, dst):
+    """Copy planes z_first .. z_first + nplanes - 1 of a field into the device tensor dst."""
+    _check(lib().wave_copy_planes(ctx.ptr, field, int(z_first), int(nplanes), C.c_void_p(dst.data_ptr())))
+
+
+def wave_get_layout(ctx: Context):
+    """(row pitch in elements, elements per plane, bytes per element)."""
+    out = (C.c_int64 * 3)()
+    _check(lib().wave_get_layout(ctx.ptr, out))
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def wave_set_energy_trace(ctx: Context, device_energy=None, capacity=0):
@@ -352,8 +389,36 @@ def wave_energy_acoustic_static(ndim, n, precision, p_old, p_new, v, a, b, facto
                                 stream=None):
     """The acoustic discrete energy from device tensors the caller owns, with
     no device allocation inside the library (for callers that cannot call
-    cudaMalloc). All array arguments are torch CUDA tensors (packed, storage
-    format); device_out is a one-element float64 CUDA tensor."""
+    cudaMalloc, such as a framework that reserves the whole device heap, or a
+    loop whose memory budget forbids allocating after start-up). All array
+    arguments are contiguous torch CUDA tensors in the storage format (2-byte
+    elements for the half and bfloat16 codes, 4-byte for WAVE_FP32) with at
+    least prod(n[:ndim]) elements; device_out is a float64 CUDA tensor of at
+    least one element. The library cannot check device pointers, so this
+    binding checks the tensors and raises ValueError before the call."""
+    if ndim not in (2, 3) or len(n) < ndim or len(v) != ndim or len(a) != ndim:
+        raise ValueError("ndim must be 2 or 3, with ndim extents, velocities and multipliers")
+    npts = 1
+    for d in range(ndim):
+        if int(n[d]) < 1:
+            raise ValueError(f"n[{d}] must be positive")
+        npts *= int(n[d])
+    width = 4 if int(precision) == WAVE_FP32 else 2
+    named = [("p_old", p_old), ("p_new", p_new), ("b", b)]
+    named += [(f"v[{d}]", t) for d, t in enumerate(v)] + [(f"a[{d}]", t) for d, t in enumerate(a)]
+    for name, t in named:
+        if t.element_size() != width:
+            raise ValueError(f"{name}: {t.element_size()}-byte elements, the storage format has {width}")
+        if t.numel() < npts:
+            raise ValueError(f"{name}: {t.numel()} elements, the grid has {npts}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name}: not contiguous")
+    import torch
+    if device_out.dtype != torch.float64 or device_out.numel() < 1:
+        raise ValueError("device_out must be a float64 tensor of at least one element")
+    for name, t in named + [("device_out", device_out)]:
+        if not t.is_cuda:
+            raise ValueError(f"{name}: not a CUDA tensor")
     nn = (C.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
     vv = (C.c_void_p * 3)(*([t.data_ptr() for t in v] + [None] * (3 - len(v))))
     aa = (C.c_void_p * 3)(*([t.data_ptr() for t in a] + [None] * (3 - len(a))))

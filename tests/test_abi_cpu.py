@@ -61,6 +61,12 @@ def _ones(n=(16, 16)):
     (dict(kind=W.WAVE_ELASTIC, vs=True, bc=(2, 2, 2, 1, 0, 0)), W.WAVE_EINVAL),  # free x faces
     (dict(kind=W.WAVE_ELASTIC, vs=True, bc=(1, 1, 1, 2, 0, 0)), W.WAVE_EINVAL),  # free bottom
     (dict(kind=W.WAVE_ELASTIC, vs=False), W.WAVE_EINVAL),                        # no vs
+    (dict(z_cut=1), W.WAVE_EINVAL),                          # z slabs are 3D
+    (dict(z_cut=4, n=(16, 16, 16)), W.WAVE_EINVAL),          # bits 0 and 1 only
+    (dict(z_cut=2, n=(16, 16, 16)), W.WAVE_EINVAL),          # a cut top face needs rho_above
+    (dict(z_cut=1, kernel=3, n=(16, 16, 16)), W.WAVE_EINVAL),  # slabs use the streaming step
+    (dict(z_cut=1, z0=-1.0, n=(16, 16, 16)), W.WAVE_EINVAL),
+    (dict(z_cut=1, kind=W.WAVE_ELASTIC, vs=True), W.WAVE_EINVAL),  # acoustic only
 ])
 def test_create_argument_errors(lib, kw, status):
     n = kw.pop("n", (16, 16))
@@ -68,11 +74,12 @@ def test_create_argument_errors(lib, kw, status):
                 field_scale=1.0, kind=W.WAVE_ACOUSTIC)
     rho_scale = kw.pop("rho_scale", 1.0)
     want_vs = kw.pop("vs", False)
+    slab = {k: kw.pop(k) for k in ("z_cut", "z0", "kernel") if k in kw}
     args.update(kw)
     with pytest.raises(W.WaveError) as e:
         W.wave_create(n, args["spacing"], _ones(n) * rho_scale, _ones(n), args["dt"],
                       args["precision"], args["comp"], bc=args["bc"], kind=args["kind"],
-                      field_scale=args["field_scale"], vs=_ones(n) * 0.5 if want_vs else None)
+                      field_scale=args["field_scale"], vs=_ones(n) * 0.5 if want_vs else None, **slab)
     assert e.value.status == status, str(e.value)
     assert W.wave_last_error()
 
@@ -90,3 +97,34 @@ def test_allocator_pair_required(lib):
     with pytest.raises(W.WaveError):
         W._check(lib.wave_set_allocator(W.ALLOC_FN(lambda n, s, u: None), W.FREE_FN(), None))
     W.use_default_allocator()
+
+
+def test_static_energy_binding_rejects_bad_tensors(lib):
+    """The allocation-free energy entry point takes raw device pointers the
+    library cannot check, so the binding checks every tensor first (element
+    width of the storage format, element count, layout, output dtype, device)
+    and raises before any call into the library."""
+    import torch
+    n = (16, 12)
+    ok16 = torch.zeros(16 * 12, dtype=torch.int16)
+    out = torch.zeros(1, dtype=torch.float64)
+
+    def call(prec=W.WAVE_FP16, p=ok16, b=ok16, v=None, o=out, ndim=2):
+        v = [ok16, ok16] if v is None else v
+        W.wave_energy_acoustic_static(ndim, n, prec, p, p, v, [ok16, ok16], b, 1.0, o)
+
+    cases = [
+        (dict(prec=W.WAVE_FP32), "4"),                                 # half arrays for binary32
+        (dict(p=torch.zeros(16 * 12, dtype=torch.float32)), "2"),      # binary32 array for half
+        (dict(b=torch.zeros(16 * 11, dtype=torch.int16)), "elements"),  # too few points
+        (dict(v=[ok16, torch.zeros(24, 16, dtype=torch.int16)[::2]]), "contiguous"),
+        (dict(o=torch.zeros(1, dtype=torch.float32)), "float64"),
+        (dict(o=torch.zeros(0, dtype=torch.float64)), "float64"),
+        (dict(v=[ok16]), "ndim"),
+        (dict(ndim=4), "ndim"),
+        (dict(), "CUDA"),                                              # everything right but on the host
+    ]
+    for kw, word in cases:
+        with pytest.raises(ValueError) as e:
+            call(**kw)
+        assert word in str(e.value), (kw, str(e.value))

@@ -18,3 +18,15 @@ def test_cpu_baseline_leg_per_workload(oracle_lib):
         row = d[name]
         assert set(row) == {"fp64_1t", "fp16_emulation_1t", f"fp64_{before}t", f"fp16_emulation_{before}t"}
         assert all(v > 0 for v in row.values())
+
+
+def test_pareto_marks_dominated_variants():
+    import bench
+    variants = {"a": {"value": 100.0}, "b": {"value": 90.0}, "c": {"value": 150.0}}
+    acc = {"cfg3_recipe_256_cfl0.4_400": {
+        "a": {"energy_drift_max": 1e-5, "rel_l2_vs_fp32": 1e-3},
+        "b": {"energy_drift_max": 2e-5, "rel_l2_vs_fp32": 2e-3},     # worse than a in all three
+        "c": {"energy_drift_max": 1e-3, "rel_l2_vs_fp32": 5e-3}}}
+    rows = {r["variant"]: r for r in bench.pareto(variants, acc)}
+    assert rows["a"]["pareto_optimal"] and rows["c"]["pareto_optimal"]
+    assert not rows["b"]["pareto_optimal"]
