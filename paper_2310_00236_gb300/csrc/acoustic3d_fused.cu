@@ -71,13 +71,13 @@ struct FShape {
     static constexpr int O_VZ = O_TVY + (TY + 3) * TX;
     static constexpr int O_TVZ = O_VZ + TY * TX;
     static constexpr int O_ELEMS = O_TVZ + TY * TX;
-    // new-velocity exchange inside each consumer warp (no barrier between
-    // warps): vx wide rows of the tile (each warp writes and reads only its
-    // own rows), then per warp the v_y rows it reads: 2 above its 4 rows, the
-    // 4, 1 below (the neighbouring warps' rows are recomputed, not shared)
+    // new-velocity exchange: vx wide rows of the tile (each warp writes and
+    // reads only its own rows), then two buffers (alternate planes) of the
+    // tile's new v_y rows -2 .. TY, shared by the four consumer warps (one
+    // bounded CTA sync per plane between writing and reading them)
     static constexpr int N_VY = TY * WIDE;
-    static constexpr int N_WROWS = TY / 4 + 3;
-    static constexpr int N_ELEMS = N_VY + 4 * N_WROWS * TX;
+    static constexpr int N_YROWS = TY + 3;
+    static constexpr int N_ELEMS = N_VY + 2 * N_YROWS * TX;
     static constexpr size_t RING_BYTES =
         sizeof(S) * ((size_t)SP * P_ELEMS + (size_t)SO * O_ELEMS + (size_t)N_ELEMS);
     static constexpr size_t SMEM = RING_BYTES + sizeof(uint64_t) * (2 * (SP + SO) + 1) + 128;
@@ -362,10 +362,12 @@ __global__ void __launch_bounds__(160, 4)
 
         if (k >= z0) {
             S *nvx = nbuf;
-            // this warp's v_y exchange rows: tile rows wr0 .. wr0 + N_WROWS - 1
-            const int wr0 = warp * (TY / 4) - 2;
-            S *nvy = nbuf + SH::N_VY + warp * SH::N_WROWS * TX;
-            __syncwarp();  // this warp's reads of the previous plane's exchange rows are done
+            // the tile's v_y rows -2 .. TY of this plane (buffers alternate
+            // with the planes: a buffer is rewritten only after every warp
+            // has passed the next plane's sync, i.e. finished reading it)
+            S *nvy = nbuf + SH::N_VY + (k & 1) * SH::N_YROWS * TX;
+            constexpr int wr0 = -2;
+            __syncwarp();  // this warp's reads of the previous plane's v_x rows are done
             Raw vxn = V::zero(), txn = V::zero(), vyn = V::zero(), tyn = V::zero();
             // ---- v_x^{n+1/2}: own vector, and the x halo of the tile edge lanes
             if (active) {
@@ -444,13 +446,13 @@ __global__ void __launch_bounds__(160, 4)
                 at<V>(fp.vy_out, qv) = vyn;
                 if (COMP) at<V>(fp.tvy_out, qv) = tyn;
             }
-            {
-                // this warp's halo rows wr0, wr0 + 1 (above) and wr0 + 6 (below):
-                // 3 x LANES vectors on lanes 0..23
+            if (warp == 3) {
+                // the tile's halo rows -2, -1 (above) and TY (below), for all
+                // four warps: 3 x LANES vectors on lanes 0..23 of one warp
                 const int wl = tid & 31;
                 if (wl < 3 * SH::LANES) {
                     const int hr = wl / SH::LANES, ln = wl % SH::LANES;
-                    const int lr = hr == 0 ? wr0 : (hr == 1 ? wr0 + 1 : wr0 + 2 + TY / 4);
+                    const int lr = hr == 0 ? -2 : (hr == 1 ? -1 : TY);
                     if (y0 + lr <= ny) {
                         Raw Vh, Th;
                         vy_vec(lr, ln, Vh, Th);
@@ -465,7 +467,8 @@ __global__ void __launch_bounds__(160, 4)
                 if (COMP) tpn = *reinterpret_cast<const Raw *>(static_cast<const S *>(fp.tp) + q);
                 if (prm.b) bv = __ldg(reinterpret_cast<const Raw *>(static_cast<const S *>(prm.b) + q));
             }
-            __syncwarp();
+            // every warp's v_y rows of this plane are in nvy (bounded wait)
+            if (!consumer_sync()) { ok = false; break; }
             // ---- p^{n+1}
             if (active) {
                 const S *vrow = nvx + row * WIDE + HALO - x0;
