@@ -80,7 +80,7 @@ struct FShape {
     static constexpr int N_ELEMS = N_VY + 2 * N_YROWS * TX;
     static constexpr size_t RING_BYTES =
         sizeof(S) * ((size_t)SP * P_ELEMS + (size_t)SO * O_ELEMS + (size_t)N_ELEMS);
-    static constexpr size_t SMEM = RING_BYTES + sizeof(uint64_t) * (2 * (SP + SO) + 1) + 128;
+    static constexpr size_t SMEM = RING_BYTES + sizeof(uint64_t) * (2 * (SP + SO) + 2) + 128;
     static_assert((P_ELEMS * sizeof(S)) % 128 == 0 && (O_ELEMS * sizeof(S)) % 128 == 0 &&
                       (N_ELEMS * sizeof(S)) % 128 == 0 && (O_VY * sizeof(S)) % 128 == 0 &&
                       (O_TVY * sizeof(S)) % 128 == 0 && (O_VZ * sizeof(S)) % 128 == 0 &&
@@ -109,6 +109,9 @@ __global__ void __launch_bounds__(160, 4)
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + SH::RING_BYTES);
     uint64_t *p_full = bars, *p_empty = bars + SP, *o_full = bars + 2 * SP, *o_empty = bars + 2 * SP + SO;
     uint64_t *c_bar = bars + 2 * (SP + SO);
+    // v_y rows of a plane complete: the four consumer warps' own rows and the
+    // producer warp's halo rows (160 arrivals per plane)
+    uint64_t *v_bar = bars + 2 * (SP + SO) + 1;
 
     const AcParams &prm = fp.a;
     const int nx = prm.n[0], ny = prm.n[1], nz = prm.n[2];
@@ -125,9 +128,58 @@ __global__ void __launch_bounds__(160, 4)
         for (int s = 0; s < SP; s++) { mbar_init(&p_full[s], 1); mbar_init(&p_empty[s], 4); }
         for (int s = 0; s < SO; s++) { mbar_init(&o_full[s], 1); mbar_init(&o_empty[s], 4); }
         mbar_init(c_bar, 128);
+        mbar_init(v_bar, 160);
         mbar_fence_init();
     }
     __syncthreads();
+
+    RS a_raw[3], b_raw;
+#pragma unroll
+    for (int c = 0; c < 3; c++) from_bits(prm.a_uni[c], a_raw[c]);
+    from_bits(prm.b_uni, b_raw);
+    const AV ay = V::splat(V::lds(a_raw[1]));
+    // tiles whose p rows y0-3..y0+TY+2 are all inside the grid read no images in y
+    const bool inner_y = y0 >= 3 && y0 + TY + 3 <= ny;
+    // rigid y walls: rows past the y faces were loaded as zeros; the images are
+    // read from the mirror rows, which lie inside the tile's rows (p: odd
+    // about the wall nodes 0 and ny, the wall row itself zero; v_y: even)
+    const bool rigid_y = bcy == BC_RIGID;
+    // the tile's new v_y rows -2 .. TY of plane k (two buffers alternating with
+    // the planes)
+    auto nvy_of = [&](int k) -> S * { return nbuf + SH::N_VY + (k & 1) * SH::N_YROWS * TX; };
+    // new v_y at local row lr (-2..TY), lane ln: from the p^n plane pk (rows
+    // lr-1..lr+2) and the old v_y, t_vy of the stage ost; stored into nvy
+    auto vy_new = [&](const S *pk, const S *ost, S *nvy, int lr, int ln, Raw &Vv, Raw &Tv) {
+        Raw pr[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            int l = lr - 1 + t, sg = 1;
+            if (!inner_y) {
+                int jm;
+                if (rigid_y) {
+                    sg = img_node(y0 + l, ny, bcy, jm);
+                    l = sg == 0 ? 0 : jm - y0;  // the wall row reads as zero
+                } else {
+                    sg = img_node(y0 + l, ny, bcy, jm);  // the rows hold their images
+                }
+            }
+            const S *ptr = (l >= 0 && l < TY) ? pk + l * WIDE + HALO + ln * VEC
+                                              : pk + SH::P_HALO + (l < 0 ? l + 3 : 3 + l - TY) * TX + ln * VEC;
+            const Raw r = *reinterpret_cast<const Raw *>(ptr);
+            pr[t] = inner_y ? r : signed_raw<V>(r, sg);
+        }
+        const AV D = vstencil<V>(V::ld(pr[0]), V::ld(pr[1]), V::ld(pr[2]), V::ld(pr[3]));
+        int lv = lr;
+        if (!inner_y && rigid_y) {
+            int jm;
+            img_half(y0 + lr, ny, bcy, jm);
+            lv = jm - y0;
+        }
+        Vv = *reinterpret_cast<const Raw *>(ost + SH::O_VY + (lv + 2) * TX + ln * VEC);
+        Tv = COMP ? *reinterpret_cast<const Raw *>(ost + SH::O_TVY + (lv + 2) * TX + ln * VEC) : V::zero();
+        V::template update<COMP>(Vv, Tv, V::mul(ay, D));
+        *reinterpret_cast<Raw *>(nvy + (lr + 2) * TX + ln * VEC) = Vv;
+    };
 
     if (warp == 4) {
         // ================================================= producer warp
@@ -250,12 +302,38 @@ __global__ void __launch_bounds__(160, 4)
             o_stage(k, dst, &o_full[slot], true);
             return true;
         };
+        // the tile's halo rows -2, -1 (above) and TY (below) of the new v_y of
+        // plane k, for the four consumer warps: 3 x LANES vectors on lanes
+        // 0..23, once the stages of plane k have landed and every warp has
+        // passed the v_y sync of plane k-1 (so the buffer of plane k-2,
+        // rewritten now, has been read)
+        auto halo_vy = [&](int k) -> bool {
+            // both rings count from the first warm-up plane z0 - 3
+            const int pcnt = k - (z0 - 3), ocnt = pcnt;
+            if (!wait_phase(&p_full[pcnt % SP], (pcnt / SP) & 1, fp.err)) return false;
+            if (!wait_phase(&o_full[ocnt % SO], (ocnt / SO) & 1, fp.err)) return false;
+            if (k > z0 && !wait_phase(v_bar, (k - 1 - z0) & 1, fp.err)) return false;
+            if (lane < 3 * SH::LANES) {
+                const int hr = lane / SH::LANES, ln = lane % SH::LANES;
+                const int lr = hr == 0 ? -2 : (hr == 1 ? -1 : TY);
+                if (y0 + lr <= ny) {
+                    Raw Vh, Th;
+                    vy_new(pring + (pcnt % SP) * SH::P_ELEMS, oring + (ocnt % SO) * SH::O_ELEMS, nvy_of(k), lr,
+                           ln, Vh, Th);
+                }
+            }
+            mbar_arrive(v_bar);
+            return true;
+        };
         int pc = 0, oc = 0;
         bool ok = true;
         for (int m = z0 - 3; m <= z1 + 2 && ok; m++) {
             ok = issue_p(m, pc++);
             if (ok && m >= z0) ok = issue_o(m - 3, oc++);
+            // the halo of the plane whose stages were issued an iteration ago
+            if (ok && m - 4 >= z0 && m - 4 < z1) ok = halo_vy(m - 4);
         }
+        for (int k = max(z1 + 2 - 3, z0); k < z1 && ok; k++) ok = halo_vy(k);
         if (lane == 0) {  // let the copies issued by this warp land before leaving
             for (int c = (pc > SP ? pc - SP : 0); c < pc; c++) drain_phase(&p_full[c % SP], (c / SP) & 1);
             for (int c = (oc > SO ? oc - SO : 0); c < oc; c++) drain_phase(&o_full[c % SO], (c / SO) & 1);
@@ -268,22 +346,10 @@ __global__ void __launch_bounds__(160, 4)
     const int x = x0 + lx * VEC;
     const int j = y0 + row;
     const bool active = j < ny;
-    RS a_raw[3], b_raw;
-#pragma unroll
-    for (int c = 0; c < 3; c++) from_bits(prm.a_uni[c], a_raw[c]);
-    from_bits(prm.b_uni, b_raw);
-    const AV ax = V::splat(V::lds(a_raw[0])), ay = V::splat(V::lds(a_raw[1])),
-             az = V::splat(V::lds(a_raw[2]));
+    const AV ax = V::splat(V::lds(a_raw[0])), az = V::splat(V::lds(a_raw[2]));
     const typename P::A ax_s = P::ld(a_raw[0]);
 
-    auto row_sign = [&](int my) -> int { int t; return img_node(my, ny, bcy, t); };
     auto plane_sign = [&](int m) -> int { int t; return img_node(m, nz, bcz, t); };
-    // tiles whose p rows y0-3..y0+TY+2 are all inside the grid read no images in y
-    const bool inner_y = y0 >= 3 && y0 + TY + 3 <= ny;
-    // rigid y walls: rows past the y faces were loaded as zeros; the images are
-    // read from the mirror rows, which lie inside the tile's rows (p: odd
-    // about the wall nodes 0 and ny, the wall row itself zero; v_y: even)
-    const bool rigid_y = bcy == BC_RIGID;
     // raw p vector of local row lr (-3..TY+2) at the own lane
     auto p_vec = [&](const S *pst, int lr) -> Raw {
         const S *ptr = (lr >= 0 && lr < TY) ? pst + lr * WIDE + HALO + lx * VEC
@@ -365,7 +431,7 @@ __global__ void __launch_bounds__(160, 4)
             // the tile's v_y rows -2 .. TY of this plane (buffers alternate
             // with the planes: a buffer is rewritten only after every warp
             // has passed the next plane's sync, i.e. finished reading it)
-            S *nvy = nbuf + SH::N_VY + (k & 1) * SH::N_YROWS * TX;
+            S *nvy = nvy_of(k);
             constexpr int wr0 = -2;
             __syncwarp();  // this warp's reads of the previous plane's v_x rows are done
             Raw vxn = V::zero(), txn = V::zero(), vyn = V::zero(), tyn = V::zero();
@@ -407,57 +473,13 @@ __global__ void __launch_bounds__(160, 4)
                     }
                 }
             }
-            // ---- v_y^{n+1/2} at local row lr (-2..TY), lane ln, from p rows lr-1..lr+2
-            auto vy_vec = [&](int lr, int ln, Raw &Vv, Raw &Tv) {
-                Raw pr[4];
-#pragma unroll
-                for (int t = 0; t < 4; t++) {
-                    int l = lr - 1 + t, sg = 1;
-                    if (!inner_y) {
-                        if (rigid_y) {
-                            int jm;
-                            sg = img_node(y0 + l, ny, bcy, jm);
-                            l = sg == 0 ? 0 : jm - y0;  // the wall row reads as zero
-                        } else {
-                            sg = row_sign(y0 + l);  // the rows hold their images
-                        }
-                    }
-                    const S *ptr = (l >= 0 && l < TY) ? pk + l * WIDE + HALO + ln * VEC
-                                                      : pk + SH::P_HALO + (l < 0 ? l + 3 : 3 + l - TY) * TX + ln * VEC;
-                    const Raw r = *reinterpret_cast<const Raw *>(ptr);
-                    pr[t] = inner_y ? r : signed_raw<V>(r, sg);
-                }
-                const AV D = vstencil<V>(V::ld(pr[0]), V::ld(pr[1]), V::ld(pr[2]), V::ld(pr[3]));
-                int lv = lr;
-                if (!inner_y && rigid_y) {
-                    int jm;
-                    img_half(y0 + lr, ny, bcy, jm);
-                    lv = jm - y0;
-                }
-                Vv = vec_at(ost + SH::O_VY + (lv + 2) * TX + ln * VEC);
-                Tv = COMP ? vec_at(ost + SH::O_TVY + (lv + 2) * TX + ln * VEC) : V::zero();
-                V::template update<COMP>(Vv, Tv, V::mul(ay, D));
-                *reinterpret_cast<Raw *>(nvy + (lr - wr0) * TX + ln * VEC) = Vv;
-            };
-            // own rows, and row ny (the image row the last grid row reads)
-            if (j <= ny) vy_vec(row, lx, vyn, tyn);
+            // ---- v_y^{n+1/2}: own rows, and row ny (the image row the last
+            // grid row reads); the producer warp adds the tile's halo rows
+            if (j <= ny) vy_new(pk, ost, nvy, row, lx, vyn, tyn);
             if (active) {
                 const int64_t qv = x + sy * j + sz * (int64_t)k;
                 at<V>(fp.vy_out, qv) = vyn;
                 if (COMP) at<V>(fp.tvy_out, qv) = tyn;
-            }
-            if (warp == 3) {
-                // the tile's halo rows -2, -1 (above) and TY (below), for all
-                // four warps: 3 x LANES vectors on lanes 0..23 of one warp
-                const int wl = tid & 31;
-                if (wl < 3 * SH::LANES) {
-                    const int hr = wl / SH::LANES, ln = wl % SH::LANES;
-                    const int lr = hr == 0 ? -2 : (hr == 1 ? -1 : TY);
-                    if (y0 + lr <= ny) {
-                        Raw Vh, Th;
-                        vy_vec(lr, ln, Vh, Th);
-                    }
-                }
             }
             // own t_p and b vectors from global memory, issued before the
             // exchange reads so that their latency overlaps them
@@ -467,8 +489,10 @@ __global__ void __launch_bounds__(160, 4)
                 if (COMP) tpn = *reinterpret_cast<const Raw *>(static_cast<const S *>(fp.tp) + q);
                 if (prm.b) bv = __ldg(reinterpret_cast<const Raw *>(static_cast<const S *>(prm.b) + q));
             }
-            // every warp's v_y rows of this plane are in nvy (bounded wait)
-            if (!consumer_sync()) { ok = false; break; }
+            // every warp's v_y rows and the producer's halo rows of this plane
+            // are in nvy (bounded wait)
+            mbar_arrive(v_bar);
+            if (!wait_phase(v_bar, (k - z0) & 1, fp.err)) { ok = false; break; }
             // ---- p^{n+1}
             if (active) {
                 const S *vrow = nvx + row * WIDE + HALO - x0;
