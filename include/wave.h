@@ -114,11 +114,14 @@ typedef struct {
                             the two-kernel streaming step when n[0] is a multiple of
                             the 16-byte vector width, else one thread per point;
                             2D acoustic: row strips, one warp per strip of 16-byte
-                            vectors, any size);
+                            vectors, one launch per half step, any size);
                             1: one-thread-per-point kernels only; 2: two-kernel
-                            streaming step; 3: one-pass step (both half steps in one
-                            kernel; needs n[0] a multiple of 64 (32 for binary32),
-                            rigid x faces and a uniform density, else as 0).
+                            streaming step; 3: one-pass step (3D: both half steps in
+                            one kernel; needs n[0] a multiple of 64 (32 for binary32),
+                            rigid x faces and a uniform density, else as 0; 2D
+                            acoustic: one-pass row strips, both half steps in one
+                            launch, keeping a second buffer set of p, v and t_v; a
+                            batch of such contexts also tries them in its tuner).
                             Every choice gives the same bits. */
     int32_t zchunk;      /* z planes per thread block of the 3D kernels; rows per
                             work item of the 2D row strips (0: automatic) */
@@ -368,7 +371,7 @@ wave_status wave_get_gradient(wave_ctx *ctx, float *device_out, int64_t *steps_l
  * available per context through wave_energy. Asynchronous.
  * wave_batch_info -- the launch configuration in use, written to
  * info[0 .. min(ninfo, 7) - 1]: kind (0 one thread per point, 1 one warp per
- * row strip), tile width in points, tile height in rows, threads per block,
+ * row strip, 2 one-pass row strips), tile width in points, tile height in rows, threads per block,
  * blocks, steps per graph replay (0 when no graph is in use), tuned (0/1).
  */
 typedef struct wave_batch wave_batch;

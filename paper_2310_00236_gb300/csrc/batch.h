@@ -10,14 +10,25 @@ namespace wave {
 struct BatchShot {
     AcParams prm;   // the shot's grid, fields, multipliers, source, energy slot
     int64_t step;   // index of the shot's last step taken (the next step's velocity
-                    // launch advances it before the pressure launch reads it)
+                    // launch advances it before the pressure launch reads it; the
+                    // one-pass launch reads it and a small launch advances it after)
+    // one-pass strips: the alternate buffer set of p, v_x, v_y, t_vx, t_vy
+    // (t_p is updated in place) and the number of one-pass steps taken since
+    // the parameters were uploaded: the set prm points to holds the state
+    // when it is even, the alternate set when it is odd (the other kinds
+    // update in place and leave it alone)
+    void *alt_p, *alt_v[2], *alt_tv[2];
+    int64_t fsteps;
 };
 
-// Two kinds of work item:
+// Three kinds of work item:
 //   BATCH_POINTS: a bx x by tile of points, one thread per point (one block per item);
 //   BATCH_STRIPS: a strip of 32 vectors (32 * vec_width x points) by yc rows,
-//                 one warp per item, streaming down the rows.
-enum { BATCH_POINTS = 0, BATCH_STRIPS = 1 };
+//                 one warp per item, streaming down the rows (two launches per step);
+//   BATCH_FUSED:  the same strips with both half steps in one launch (new
+//                 velocities of row j, then p of row j - 1), old state read from
+//                 one buffer set and the new state written to the other.
+enum { BATCH_POINTS = 0, BATCH_STRIPS = 1, BATCH_FUSED = 2 };
 
 struct BatchLaunch {
     BatchShot *shots;   // device array [nshots]

@@ -379,6 +379,270 @@ __global__ void __launch_bounds__(256) batch_kp_strip(const BatchShot *__restric
     }
 }
 
+// ------------------------------------------------------------------------
+// One-pass row strips: both half steps of a strip in one launch
+// ------------------------------------------------------------------------
+
+// New v_x at grid point (m, j), m inside the grid, from the old set: the
+// one-point arithmetic of the strips (stencil over p at m-1 .. m+2 with the x
+// images, the multiplier, the plain or compensated update).
+template <class V, class P, int COMP>
+__device__ __forceinline__ typename V::RS vx_new_scalar(const AcParams &prm, const void *pin, const void *vxin,
+                                                        const void *txin, int m, int j) {
+    using RS = typename V::RS;
+    const typename P::A D = stencil<P>(P::ld(x_val<V>(pin, prm, m - 1, j, true)), P::ld(x_val<V>(pin, prm, m, j, true)),
+                                       P::ld(x_val<V>(pin, prm, m + 1, j, true)),
+                                       P::ld(x_val<V>(pin, prm, m + 2, j, true)));
+    const int64_t q = m + prm.sy * (int64_t)j;
+    RS Vv = static_cast<const RS *>(vxin)[q];
+    RS Tv = COMP ? static_cast<const RS *>(txin)[q] : RS(0);
+    update<P, COMP>(Vv, Tv, P::mul(coef<P>(prm.a[0], prm.a_uni[0], q), D));
+    return Vv;
+}
+
+// One strip item per warp, walking down its rows j = y0-2 .. y1 (from row 0
+// at a rigid top face): the new v_y of row j (rows y0-2, y0-1 and y1 are the
+// halo this strip recomputes rather than reads), the new v_x of row j, then
+// p of row j-1, which reads v_y of rows j-3 .. j and v_x of row j-1 with its
+// x neighbours. Rows past a rigid y face take the images of computed rows
+// (v_y is even about the walls), as do the x neighbours past a rigid x face;
+// neighbours that belong to another strip, or that wrap around a periodic
+// face, are recomputed with the one-point arithmetic. The operations are
+// those of the two-kernel strips, in the same order, so the bits are too.
+template <class P, int COMP, bool ENERGY>
+__global__ void __launch_bounds__(128, 4) batch_fused_strip(const BatchShot *__restrict__ shots, const int *item0,
+                                                         int nshots, int nitems, int yc, double *item_part) {
+    using V = typename VecOf<P>::T;
+    using Raw = typename V::Raw;
+    using AV = typename V::AV;
+    using RS = typename V::RS;
+    constexpr int N = V::N;
+    __shared__ int s_item0[kMaxShots + 1];
+    for (int t = threadIdx.x; t <= nshots; t += blockDim.x) s_item0[t] = item0[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < nitems; item += gridDim.x * wpb) {
+        const StripItem it = strip_of<N>(s_item0, nshots, item, shots, yc);
+        const BatchShot &sh = shots[it.s];
+        const AcParams prm = sh.prm;
+        const int64_t last = sh.step;   // the index of the last step taken
+        const int64_t step = last + 1;  // this step (time index of the source)
+        const bool a_in = (sh.fsteps & 1) == 0;
+        const void *pin = a_in ? prm.p : sh.alt_p;
+        void *pout = a_in ? sh.alt_p : prm.p;
+        const void *vin0 = a_in ? prm.v[0] : sh.alt_v[0], *vin1 = a_in ? prm.v[1] : sh.alt_v[1];
+        void *vout0 = a_in ? sh.alt_v[0] : prm.v[0], *vout1 = a_in ? sh.alt_v[1] : prm.v[1];
+        const void *tin0 = a_in ? prm.tv[0] : sh.alt_tv[0], *tin1 = a_in ? prm.tv[1] : sh.alt_tv[1];
+        void *tout0 = a_in ? sh.alt_tv[0] : prm.tv[0], *tout1 = a_in ? sh.alt_tv[1] : prm.tv[1];
+        const int nx = prm.n[0], ny = prm.n[1];
+        const bool rigid_x = prm.bc[0] == BC_RIGID, rigid_y = prm.bc[1] == BC_RIGID;
+        const int x = it.x0 + lane * N;
+        const bool active = x < nx;
+        const int nvalid = active ? min(N, nx - x) : 0;
+        const bool left_edge = active && lane == 0;
+        const bool right_edge = active && (lane == 31 || x + N >= nx);
+        const int jstart = (it.y0 == 0 && rigid_y) ? 0 : it.y0 - 2;
+        // old p rows j-1, j, j+1 (row j+2 loaded in the loop)
+        Raw pq0 = row_vec<V>(pin, prm, x, jstart - 1, true, active);
+        Raw pq1 = row_vec<V>(pin, prm, x, jstart, true, active);
+        Raw pq2 = row_vec<V>(pin, prm, x, jstart + 1, true, active);
+        // new v_y rows j-3, j-2, j-1
+        Raw vq0 = V::zero(), vq1 = V::zero(), vq2 = V::zero();
+        // new v_x of row j-1 (elements past the grid replaced by their images)
+        // and its x neighbours at x-2, x-1, x+N
+        Raw vxo = V::zero();
+        RS xl1 = RS(0), xl0 = RS(0), xrr = RS(0);
+        double e_acc = 0.0;
+        for (int j = jstart; j <= it.y1; j++) {
+            const Raw pq3 = row_vec<V>(pin, prm, x, j + 2, true, active);
+            // ---- new v_y of row j (half point j + 1/2)
+            Raw vyn = V::zero();
+            if (j >= ny && rigid_y) {
+                vyn = vq2;  // the image of row ny - 1 (even about the wall)
+            } else if (active) {
+                int jm;
+                img_half(j, ny, prm.bc[1], jm);  // the row itself, or its periodic wrap
+                const int64_t qy = x + prm.sy * (int64_t)jm;
+                Raw vo = at<V>(const_cast<void *>(vin1), qy);
+                Raw to = COMP ? at<V>(const_cast<void *>(tin1), qy) : V::zero();
+                const AV Dy = vstencil<V>(V::ld(pq0), V::ld(pq1), V::ld(pq2), V::ld(pq3));
+                V::template update<COMP>(vo, to, V::mul(coef_v<V>(prm.a[1], prm.a_uni[1], qy), Dy));
+                vyn = vo;
+                if (j >= it.y0 && j < it.y1) {
+                    store_vec<V>(vout1, qy, vo, nvalid);
+                    if (COMP) store_vec<V>(tout1, qy, to, nvalid);
+                }
+            }
+            // ---- new v_x of row j (stored rows only)
+            Raw vxn = V::zero();
+            RS nl1 = RS(0), nl0 = RS(0), nrr = RS(0);
+            if (j >= it.y0 && j < it.y1) {
+                const int64_t q = x + prm.sy * (int64_t)j;
+                // strip edges inside the grid: the neighbouring vector of p, v_x,
+                // t_vx (and a_x when it varies) of this row, loaded at once
+                // (left: x-N .. x-1; right: x+N .. x+2N-1 when x+N+2 lies inside)
+                const bool lh = left_edge && x > 0;
+                const bool rh = right_edge && x + N + 2 < nx;
+                Raw hp = V::zero(), hvx = V::zero(), htx = V::zero(), ha = V::zero();
+                if (lh || rh) {
+                    const int64_t qh = q + (lh ? -N : N);
+                    hp = at<V>(const_cast<void *>(pin), qh);
+                    hvx = at<V>(const_cast<void *>(vin0), qh);
+                    if (COMP) htx = at<V>(const_cast<void *>(tin0), qh);
+                    if (prm.a[0]) ha = at<V>(const_cast<void *>(prm.a[0]), qh);
+                }
+                Raw own = pq1;
+                RS l0 = RS(0), r0 = RS(0), r1 = RS(0);
+                if (left_edge) l0 = lh ? V::get(hp, N - 1) : x_val<V>(pin, prm, x - 1, j, true);
+                if (right_edge) {
+                    r0 = rh ? V::get(hp, 0) : x_val<V>(pin, prm, x + N, j, true);
+                    r1 = rh ? V::get(hp, 1) : x_val<V>(pin, prm, x + N + 1, j, true);
+#pragma unroll
+                    for (int e = 1; e < N; e++)
+                        if (e >= nvalid) raw_set<RS, Raw>(own, e, x_val<V>(pin, prm, x + e, j, true));
+                }
+                const RS sl0 = shfl_rs(V::get(own, N - 1), 1, true);
+                const RS sr0 = shfl_rs(V::get(own, 0), 1, false);
+                const RS sr1 = shfl_rs(V::get(own, 1), 1, false);
+                if (!left_edge) l0 = sl0;
+                if (!right_edge) {
+                    r0 = sr0;
+                    r1 = sr1;
+                }
+                if (active) {
+                    const AV o = V::ld(own);
+                    const AV Dx = vstencil<V>(V::shr1(o, V::lds(l0)), o, V::shl1(o, V::lds(r0)),
+                                              V::shl2(o, V::lds(r0), V::lds(r1)));
+                    Raw vo = at<V>(const_cast<void *>(vin0), q);
+                    Raw to = COMP ? at<V>(const_cast<void *>(tin0), q) : V::zero();
+                    V::template update<COMP>(vo, to, V::mul(coef_v<V>(prm.a[0], prm.a_uni[0], q), Dx));
+                    vxn = vo;
+                    store_vec<V>(vout0, q, vo, nvalid);
+                    if (COMP) store_vec<V>(tout0, q, to, nvalid);
+                }
+                // the x neighbours of the new v_x of this row, for p of this row
+                // at the next iteration: element nvalid of a vector cut by the
+                // grid's right face holds the image of v_x(nx)
+                if (right_edge && nvalid < N) {
+                    const RS img = rigid_x ? V::get(vxn, nvalid - 1)
+                                           : vx_new_scalar<V, P, COMP>(prm, pin, vin0, tin0, 0, j);
+                    raw_set<RS, Raw>(vxn, nvalid, img);
+                }
+                nl1 = shfl_rs(V::get(vxn, N - 2), 1, true);
+                nl0 = shfl_rs(V::get(vxn, N - 1), 1, true);
+                nrr = shfl_rs(V::get(vxn, 0), 1, false);
+                // new v_x at one point from registers: p at e-1 .. e+2 of the
+                // concatenation (halo vector, own vector), the old v_x, t_vx and
+                // a_x of the halo vector's element h
+                auto edge_vx = [&](RS pm1, RS p0, RS p1, RS p2, int h) -> RS {
+                    const typename P::A D = stencil<P>(P::ld(pm1), P::ld(p0), P::ld(p1), P::ld(p2));
+                    RS Vv = V::get(hvx, h);
+                    RS Tv = COMP ? V::get(htx, h) : RS(0);
+                    RS a_s;
+                    if (prm.a[0]) a_s = V::get(ha, h);
+                    else from_bits(prm.a_uni[0], a_s);
+                    update<P, COMP>(Vv, Tv, P::mul(P::ld(a_s), D));
+                    return Vv;
+                };
+                if (left_edge) {
+                    if (lh) {
+                        // v_x at x-2: p at x-3 .. x; at x-1: p at x-2 .. x+1
+                        // (own: the row's p vector with the elements past the grid
+                        // replaced by their images)
+                        nl1 = edge_vx(V::get(hp, N - 3), V::get(hp, N - 2), V::get(hp, N - 1), V::get(own, 0), N - 2);
+                        nl0 = edge_vx(V::get(hp, N - 2), V::get(hp, N - 1), V::get(own, 0), V::get(own, 1), N - 1);
+                    } else if (x > 0) {
+                        nl1 = vx_new_scalar<V, P, COMP>(prm, pin, vin0, tin0, x - 2, j);
+                        nl0 = vx_new_scalar<V, P, COMP>(prm, pin, vin0, tin0, x - 1, j);
+                    } else if (rigid_x) {  // v_x even about the wall at -1/2
+                        nl1 = V::get(vxn, 1);
+                        nl0 = V::get(vxn, 0);
+                    } else {
+                        nl1 = vx_new_scalar<V, P, COMP>(prm, pin, vin0, tin0, nx - 2, j);
+                        nl0 = vx_new_scalar<V, P, COMP>(prm, pin, vin0, tin0, nx - 1, j);
+                    }
+                }
+                if (right_edge) {
+                    // v_x at x+N: p at x+N-1 .. x+N+2
+                    if (rh) nrr = edge_vx(V::get(own, N - 1), V::get(hp, 0), V::get(hp, 1), V::get(hp, 2), 0);
+                    else if (x + N < nx) nrr = vx_new_scalar<V, P, COMP>(prm, pin, vin0, tin0, x + N, j);
+                    else if (rigid_x) nrr = V::get(vxn, N - 1);  // v_x(nx) = v_x(nx - 1) when nvalid == N
+                    else nrr = vx_new_scalar<V, P, COMP>(prm, pin, vin0, tin0, x + N - nx, j);
+                }
+            }
+            if (j == 1 && it.y0 == 0 && rigid_y) {
+                // rows -2 and -1 are the images of rows 1 and 0
+                vq0 = vyn;
+                vq1 = vq2;
+            }
+            // ---- p of row j - 1
+            const int jp = j - 1;
+            if (jp >= it.y0 && jp < it.y1 && active) {
+                const int64_t q = x + prm.sy * (int64_t)jp;
+                const AV o = V::ld(vxo);
+                AV R = vstencil<V>(V::shr2(o, V::lds(xl1), V::lds(xl0)), V::shr1(o, V::lds(xl0)), o,
+                                   V::shl1(o, V::lds(xrr)));
+                R = V::add(R, vstencil<V>(V::ld(vq0), V::ld(vq1), V::ld(vq2), V::ld(vyn)));
+                if (jp == prm.src_j && prm.src_i >= x && prm.src_i < x + N && step < prm.src_nt) {
+                    const typename V::AS s_ = static_cast<const typename V::AS *>(prm.src)[step];
+#pragma unroll
+                    for (int e = 0; e < N; e++)
+                        if (e == prm.src_i - x) V::set(R, e, P::add(V::aget(R, e), s_));
+                }
+                Raw pv = pq0;
+                Raw tv = COMP ? at<V>(prm.tp, q) : V::zero();
+                const Raw pold = pv;
+                V::template update<COMP>(pv, tv, V::mul(coef_v<V>(prm.b, prm.b_uni, q), R));
+                store_vec<V>(pout, q, pv, nvalid);
+                if (COMP) store_vec<V>(prm.tp, q, tv, nvalid);
+                if (ENERGY) {
+                    RS bs, as0, as1;
+                    from_bits(prm.b_uni, bs);
+                    from_bits(prm.a_uni[0], as0);
+                    from_bits(prm.a_uni[1], as1);
+                    const Raw bv = prm.b ? at<V>(const_cast<void *>(prm.b), q) : V::zero();
+                    const Raw av0 = prm.a[0] ? at<V>(const_cast<void *>(prm.a[0]), q) : V::zero();
+                    const Raw av1 = prm.a[1] ? at<V>(const_cast<void *>(prm.a[1]), q) : V::zero();
+#pragma unroll
+                    for (int e = 0; e < N; e++) {
+                        if (e >= nvalid) break;
+                        const float bw = prm.b ? V::f32(bv, e) : P::to_f32(bs);
+                        const float aw0 = prm.a[0] ? V::f32(av0, e) : P::to_f32(as0);
+                        const float aw1 = prm.a[1] ? V::f32(av1, e) : P::to_f32(as1);
+                        const float fx = V::f32(vxo, e), fy = V::f32(vq2, e);
+                        e_acc += (double)e_term(V::f32(pold, e), V::f32(pv, e), bw);
+                        e_acc += (double)e_term(fx, fx, aw0);
+                        e_acc += (double)e_term(fy, fy, aw1);
+                    }
+                }
+            }
+            pq0 = pq1;
+            pq1 = pq2;
+            pq2 = pq3;
+            vq0 = vq1;
+            vq1 = vq2;
+            vq2 = vyn;
+            vxo = vxn;
+            xl1 = nl1;
+            xl0 = nl0;
+            xrr = nrr;
+        }
+        if (ENERGY) {
+            for (int off = 16; off > 0; off >>= 1) e_acc += __shfl_down_sync(0xffffffffu, e_acc, off);
+            if (lane == 0) item_part[item] = e_acc;
+        }
+    }
+}
+
+// Advance every shot's step counter and one-pass count after a one-pass launch.
+__global__ void batch_advance(BatchShot *shots, int nshots) {
+    for (int s = threadIdx.x; s < nshots; s += blockDim.x) {
+        shots[s].step++;
+        shots[s].fsteps++;
+    }
+}
+
 // Per-shot energy: the item partials of each shot summed in item order.
 __global__ void batch_energy_reduce(BatchShot *shots, const int *item0, const double *item_part) {
     const int s = blockIdx.x;
@@ -397,7 +661,16 @@ __global__ void batch_energy_reduce(BatchShot *shots, const int *item0, const do
 
 template <class P, int COMP>
 static cudaError_t launch_pc(const BatchLaunch &L, bool energy, cudaStream_t st) {
-    if (L.kind == BATCH_STRIPS) {
+    if (L.kind == BATCH_FUSED) {
+        const int threads = 32 * L.wpb;
+        if (energy)
+            batch_fused_strip<P, COMP, true><<<L.grid, threads, 0, st>>>(L.shots, L.item0, L.nshots, L.nitems,
+                                                                         L.yc, L.item_part);
+        else
+            batch_fused_strip<P, COMP, false><<<L.grid, threads, 0, st>>>(L.shots, L.item0, L.nshots, L.nitems,
+                                                                          L.yc, L.item_part);
+        batch_advance<<<1, 256, 0, st>>>(L.shots, L.nshots);
+    } else if (L.kind == BATCH_STRIPS) {
         const int threads = 32 * L.wpb;
         batch_kv_strip<P, COMP><<<L.grid, threads, 0, st>>>(L.shots, L.item0, L.nshots, L.nitems, L.yc);
         if (energy)
@@ -429,7 +702,7 @@ static cudaError_t launch_p(const BatchLaunch &L, int comp, bool energy, cudaStr
 int batch_max_shots() { return kMaxShots; }
 
 int64_t batch_items_of(int kind, int bx, int by, int yc, int prec, int64_t nx, int64_t ny) {
-    if (kind == BATCH_STRIPS) {
+    if (kind == BATCH_STRIPS || kind == BATCH_FUSED) {
         const int64_t tx = 32 * (prec == PREC_FP32 ? 4 : 8);
         return ((nx + tx - 1) / tx) * ((ny + yc - 1) / yc);
     }
@@ -437,7 +710,7 @@ int64_t batch_items_of(int kind, int bx, int by, int yc, int prec, int64_t nx, i
 }
 
 cudaError_t batch_step(const BatchLaunch &L, int prec, int comp, bool energy, cudaStream_t st) {
-    if (L.kind == BATCH_STRIPS) {
+    if (L.kind == BATCH_STRIPS || L.kind == BATCH_FUSED) {
         if (L.wpb < 1 || L.wpb > 8 || L.yc < 1) return cudaErrorInvalidValue;
     } else if (L.bx * L.by > 256 || (L.bx * L.by) % 32 != 0) {
         return cudaErrorInvalidValue;

@@ -191,8 +191,11 @@ struct wave_ctx {
     bool zchunk_set = false;
     bool use_stream = false;
     bool use_fused = false;
-    // 2D: the row-strip kernels of the batches, as a batch of one
+    // 2D: the row-strip kernels of the batches, as a batch of one; acoustic
+    // strip_fused: the one-pass strips (both half steps in one launch, the
+    // state alternating between f / t and alt_f / alt_t)
     bool use_strips = false;
+    bool strip_fused = false;
     int strip_items = 0, strip_grid = 0, strip_rows = 16;
     // plain strip steps replayed from captured graphs of 2^j steps (j < kStripGraphLevels)
     cudaGraphExec_t strip_graph[kStripGraphLevels] = {};
@@ -746,7 +749,15 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
             c->strip_items = (int)batch_items_of(BATCH_STRIPS, 0, 0, c->strip_rows, c->prec, c->n[0], c->n[1]);
             c->strip_grid = std::max(1, std::min((c->strip_items + kStripWarps - 1) / kStripWarps, 16 * sms));
             const int item0[2] = {0, c->strip_items};
-            st = dev_alloc(c, c->strip_shot, sizeof(BatchShot));
+            // kernel 3: the one-pass strips, which read the state from one
+            // buffer set and write the other (the two-launch strips are the
+            // default: faster on this hardware, see the notes on the kernels)
+            c->strip_fused = kchoice == 3;
+            for (int fi = 0; fi < 3 && c->strip_fused && !st; fi++) {
+                st = dev_alloc(c, c->alt_f[fi], c->total * eb);
+                if (!st && fi > 0 && compensated) st = dev_alloc(c, c->alt_t[fi], c->total * eb);
+            }
+            if (!st) st = dev_alloc(c, c->strip_shot, sizeof(BatchShot));
             if (!st) st = dev_alloc(c, c->strip_item0, sizeof(item0));
             if (!st) st = dev_alloc(c, c->strip_part, sizeof(double) * (size_t)c->strip_items);
             if (!st) {
@@ -1116,6 +1127,30 @@ static int64_t strip_graph_run(wave_ctx *c, int64_t m, F one_step, cudaError_t &
     return done;
 }
 
+// The current and the alternate buffer sets of p and the velocities (and their
+// compensations, t_p excepted) exchange roles after a step that wrote the new
+// state into the alternate set.
+static void swap_sets(wave_ctx *c) {
+    for (int fi = 0; fi <= c->ndim; fi++) {
+        std::swap(c->f[fi], c->alt_f[fi]);
+        if (fi > 0) std::swap(c->t[fi], c->alt_t[fi]);
+    }
+}
+
+// A shot's parameters for the strip kernels: the current set, the alternate
+// set, the index of the last step taken, no one-pass steps yet.
+static void fill_shot(wave_ctx *c, BatchShot &shot) {
+    memset(&shot, 0, sizeof shot);
+    fill_acoustic_params(c, shot.prm);
+    shot.step = c->step - 1;  // the velocity launch of the step advances it
+    shot.alt_p = c->alt_f[0].ptr;
+    for (int ax = 0; ax < 2; ax++) {
+        shot.alt_v[ax] = c->alt_f[1 + ax].ptr;
+        shot.alt_tv[ax] = c->alt_t[1 + ax].ptr;
+    }
+    shot.fsteps = 0;
+}
+
 static wave_status acoustic_steps(wave_ctx *c, int64_t n, bool energy_last = true) {
     AcParams prm;
     fill_acoustic_params(c, prm);
@@ -1123,8 +1158,7 @@ static wave_status acoustic_steps(wave_ctx *c, int64_t n, bool energy_last = tru
     BatchLaunch L;
     if (c->use_strips) {
         BatchShot shot;
-        shot.prm = prm;
-        shot.step = c->step - 1;  // the velocity launch of the step advances it
+        fill_shot(c, shot);
         cudaError_t e = cudaMemcpyAsync(c->strip_shot.ptr, &shot, sizeof shot, cudaMemcpyHostToDevice, c->stream);
         if (e != cudaSuccess) return cuda_check(c, e, "wave_step upload");
         L.shots = static_cast<BatchShot *>(c->strip_shot.ptr);
@@ -1132,7 +1166,7 @@ static wave_status acoustic_steps(wave_ctx *c, int64_t n, bool energy_last = tru
         L.item_part = static_cast<double *>(c->strip_part.ptr);
         L.nshots = 1;
         L.nitems = c->strip_items;
-        L.kind = BATCH_STRIPS;
+        L.kind = c->strip_fused ? BATCH_FUSED : BATCH_STRIPS;
         L.bx = L.by = 0;
         L.yc = c->strip_rows;
         L.wpb = kStripWarps;
@@ -1147,6 +1181,7 @@ static wave_status acoustic_steps(wave_ctx *c, int64_t n, bool energy_last = tru
             if (e != cudaSuccess) return cuda_check(c, e, "graph launch");
             n -= done;
             c->step += done;
+            if (c->strip_fused && (done & 1)) swap_sets(c);
         }
     }
     for (int64_t s = 0; s < n; s++) {
@@ -1159,6 +1194,7 @@ static wave_status acoustic_steps(wave_ctx *c, int64_t n, bool energy_last = tru
             cudaError_t e = batch_step(L, c->prec, c->comp, prm.energy != 0, c->stream);
             cudaEvent_t m1 = mark(c);
             timed(c, 3, m0, m1);
+            if (c->strip_fused) swap_sets(c);
             if (e == cudaSuccess && trace)
                 e = cudaMemcpyAsync(c->e_trace + c->e_trace_pos, c->e_misc.ptr, sizeof(double),
                                     cudaMemcpyDeviceToDevice, c->stream);
@@ -1914,6 +1950,10 @@ static const BatchShape kShapes[] = {
     {BATCH_STRIPS, 0, 0, 16, 4, 8},  {BATCH_STRIPS, 0, 0, 16, 4, 16},
     {BATCH_STRIPS, 0, 0, 32, 4, 8},  {BATCH_STRIPS, 0, 0, 32, 4, 16},
     {BATCH_STRIPS, 0, 0, 64, 4, 8},  {BATCH_STRIPS, 0, 0, 64, 4, 16},
+    // one-pass strips last (the tuner runs the candidates in this order)
+    {BATCH_FUSED, 0, 0, 16, 4, 8},   {BATCH_FUSED, 0, 0, 16, 4, 16},
+    {BATCH_FUSED, 0, 0, 32, 4, 8},   {BATCH_FUSED, 0, 0, 32, 4, 16},
+    {BATCH_FUSED, 0, 0, 64, 4, 8},   {BATCH_FUSED, 0, 0, 64, 4, 16},
 };
 constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
 constexpr int kDefaultShape = 5;
@@ -2007,15 +2047,27 @@ extern "C" wave_status wave_batch_create(int32_t nctx, wave_ctx *const *ctxs, wa
     return WAVE_OK;
 }
 
-// upload every shot's parameters and step counter
+// upload every shot's parameters, step counter and alternate set
 static cudaError_t batch_refresh(wave_batch *b) {
     b->h_shots.resize(b->ctx.size());
-    for (size_t s = 0; s < b->ctx.size(); s++) {
-        fill_acoustic_params(b->ctx[s], b->h_shots[s].prm);
-        b->h_shots[s].step = b->ctx[s]->step - 1;  // the velocity launch of a step advances it
-    }
+    for (size_t s = 0; s < b->ctx.size(); s++) fill_shot(b->ctx[s], b->h_shots[s]);
     return cudaMemcpyAsync(b->d_shots, b->h_shots.data(), sizeof(BatchShot) * b->ctx.size(),
                            cudaMemcpyHostToDevice, b->stream);
+}
+
+// The one-pass strips need every context's alternate buffer set.
+static bool batch_shape_allowed(const wave_batch *b, int shape) {
+    if (kShapes[shape].kind != BATCH_FUSED) return true;
+    for (const auto *c : b->ctx)
+        if (!c->strip_fused) return false;
+    return true;
+}
+
+// After nf one-pass steps the contexts' state lives in the alternate sets
+// when nf is odd: the host's set pointers follow.
+static void batch_follow_sets(wave_batch *b, int64_t nf) {
+    if (nf & 1)
+        for (auto *c : b->ctx) swap_sets(c);
 }
 
 static wave_status batch_fail(wave_batch *b, cudaError_t e, const char *what) {
@@ -2034,6 +2086,7 @@ extern "C" wave_status wave_batch_step(wave_batch *b, int64_t n) {
     if (e != cudaSuccess) return batch_fail(b, e, "batch upload");
     int64_t left = n;
     if (!b->tuned && left - 1 >= kNumShapes) {
+        int64_t nf = 0;  // one-pass steps among the candidates
         // autotune on real steps: every candidate computes the same bits
         float best = 1e30f;
         int bi = kDefaultShape;
@@ -2041,8 +2094,10 @@ extern "C" wave_status wave_batch_step(wave_batch *b, int64_t n) {
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         for (int si = 0; si < kNumShapes && e == cudaSuccess; si++) {
+            if (!batch_shape_allowed(b, si)) continue;
             e = batch_set_shape(b, si);
             if (e != cudaSuccess) break;
+            if (kShapes[si].kind == BATCH_FUSED) nf++;
             cudaEventRecord(e0, b->stream);
             e = batch_step(batch_launch(b), b->prec, b->comp, false, b->stream);
             cudaEventRecord(e1, b->stream);
@@ -2059,8 +2114,16 @@ extern "C" wave_status wave_batch_step(wave_batch *b, int64_t n) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (e != cudaSuccess) return batch_fail(b, e, "batch autotune");
-        e = batch_set_shape(b, bi);
+        // the candidate steps count as steps of the contexts; the one-pass
+        // ones may have moved the state to the alternate sets: follow it and
+        // upload the parameters again for the steps below
+        const int64_t tuned_steps = n - left;
+        for (auto *c : b->ctx) c->step += tuned_steps;
+        batch_follow_sets(b, nf);
+        e = batch_refresh(b);
+        if (e == cudaSuccess) e = batch_set_shape(b, bi);
         if (e != cudaSuccess) return batch_fail(b, e, "batch shape");
+        for (auto *c : b->ctx) c->step -= tuned_steps;  // added back with the rest below
         b->tuned = true;
     }
     const BatchLaunch L = batch_launch(b);
@@ -2096,6 +2159,7 @@ extern "C" wave_status wave_batch_step(wave_batch *b, int64_t n) {
     }
     e = batch_step(L, b->prec, b->comp, true, b->stream);
     if (e != cudaSuccess) return batch_fail(b, e, "batch launch");
+    if (kShapes[b->shape].kind == BATCH_FUSED) batch_follow_sets(b, left);
     for (auto *c : b->ctx) {
         c->step += n;
         c->have_energy = true;
@@ -2106,8 +2170,9 @@ extern "C" wave_status wave_batch_step(wave_batch *b, int64_t n) {
 extern "C" wave_status wave_batch_info(wave_batch *b, int32_t *info, int32_t ninfo) {
     if (!b || !info) return fail(WAVE_EINVAL, "NULL argument");
     const BatchShape &sh = kShapes[b->shape];
-    const int32_t v[7] = {sh.kind, sh.kind == BATCH_STRIPS ? 32 * (b->prec == WAVE_FP32 ? 4 : 8) : sh.bx,
-                          sh.kind == BATCH_STRIPS ? sh.yc : sh.by, sh.kind == BATCH_STRIPS ? 32 * sh.wpb : sh.bx * sh.by,
+    const bool strips = sh.kind == BATCH_STRIPS || sh.kind == BATCH_FUSED;
+    const int32_t v[7] = {sh.kind, strips ? 32 * (b->prec == WAVE_FP32 ? 4 : 8) : sh.bx,
+                          strips ? sh.yc : sh.by, strips ? 32 * sh.wpb : sh.bx * sh.by,
                           sh.grid_per_sm * b->sms, b->gexec ? b->gsteps : 0, b->tuned ? 1 : 0};
     for (int i = 0; i < ninfo && i < 7; i++) info[i] = v[i];
     return WAVE_OK;

@@ -452,7 +452,7 @@ def wave_batch_info(batch: Batch) -> dict:
     steps, tuned)."""
     v = (C.c_int32 * 7)()
     _check(lib().wave_batch_info(batch.ptr, v, 7))
-    return {"kind": ("points", "strips")[v[0]], "tile_x": v[1], "tile_y": v[2], "threads": v[3],
+    return {"kind": ("points", "strips", "one-pass strips")[v[0]], "tile_x": v[1], "tile_y": v[2], "threads": v[3],
             "blocks": v[4], "graph_steps": v[5], "tuned": bool(v[6])}
 
 

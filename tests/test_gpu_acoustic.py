@@ -58,25 +58,31 @@ def _run(shape, bc, prec, comp, steps, seed=0, variable=True, src=False, kernel=
 R, P = O.BC_RIGID, O.BC_PERIODIC
 
 
-# kernel 0: 2D row strips (the default); kernel 1: one thread per point
-@pytest.mark.parametrize("kernel", [0, 1])
+# kernel 0: 2D row strips, one launch per half step (the default); kernel 1:
+# one thread per point; kernel 3: one-pass row strips (both half steps in one
+# launch, two buffer sets)
+@pytest.mark.parametrize("kernel", [0, 1, 3])
 @pytest.mark.parametrize("prec,comp", VARIANTS)
 def test_2d_bit_exact_ragged_rigid(prec, comp, kernel):
     _run((37, 29), (R, R), prec, comp, 30, kernel=kernel)
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 3])
 @pytest.mark.parametrize("prec,comp", VARIANTS)
 def test_2d_bit_exact_periodic_source(prec, comp, kernel):
     _run((64, 40), (P, P), prec, comp, 25, src=True, kernel=kernel)
 
 
-@pytest.mark.parametrize("shape", [(257, 33), (300, 70), (8, 200), (513, 9)])
-def test_2d_strips_ragged_wide_and_tall(shape):
+@pytest.mark.parametrize("kernel", [0, 3])
+@pytest.mark.parametrize("shape", [(257, 33), (300, 70), (8, 200), (513, 9), (265, 40), (520, 17)])
+def test_2d_strips_ragged_wide_and_tall(shape, kernel):
     # strips of 256 points (128 for binary32) cut by the grid's x extent, rows
-    # cut by the 16-row items, periodic x wrapping across strip boundaries
-    _run(shape, (P, R), "fp16", 3, 12, src=True)
-    _run(shape, (R, P), "fp32", 0, 12)
+    # cut by the 16-row items, periodic x wrapping across strip boundaries;
+    # the one-pass strips also recompute the x neighbours of v_x at strip
+    # edges (from the neighbouring vectors, or point by point near the faces)
+    _run(shape, (P, R), "fp16", 3, 12, src=True, kernel=kernel)
+    _run(shape, (R, P), "fp32", 0, 12, kernel=kernel)
+    _run(shape, (R, R), "bf16", 6, 11, src=True, kernel=kernel)
 
 
 @pytest.mark.parametrize("prec,comp", [("fp16", 3), ("bf16", 6), ("fp32", 0),

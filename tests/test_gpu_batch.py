@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 R, P = W.WAVE_BC_RIGID, W.WAVE_BC_PERIODIC
 
 
-def _shot(shape, bc, prec, comp, seed, nsteps, stream=None):
+def _shot(shape, bc, prec, comp, seed, nsteps, stream=None, kernel=0):
     """One seeded shot: smooth random velocity in [1500, 4500], a Gaussian
     initial pressure and a Ricker source. Returns (ctx, oracle state)."""
     nx, ny = shape
@@ -33,7 +33,8 @@ def _shot(shape, bc, prec, comp, seed, nsteps, stream=None):
     z0 = 1000.0 * float(c.max())
     wav = 0.5 * P0 * h / z0 * inputs.ricker_table(nsteps, dt, 1.0 / (30 * dt))
     src = ([nx // 2, min(8, ny - 1)], wav)
-    return acoustic_pair(shape, bc, prec, comp, h, dt, rho, c, p0=p0, P0=P0, src=src, stream=stream)
+    return acoustic_pair(shape, bc, prec, comp, h, dt, rho, c, p0=p0, P0=P0, src=src, stream=stream,
+                         kernel=kernel)
 
 
 def _fields(ctx, comp):
@@ -45,11 +46,13 @@ def _fields(ctx, comp):
     return out
 
 
-def _run_case(shapes, bcs, prec, comp, calls, stream=None, oracle_shot=0):
+def _run_case(shapes, bcs, prec, comp, calls, stream=None, oracle_shot=0, kernel=0):
     """Batch the shots and step them by the step counts in `calls`; step twin
-    contexts one by one; compare bits and energies."""
+    contexts (default kernels) one by one; compare bits and energies.
+    kernel = 3: the batched contexts keep the second buffer set, so the tuner
+    also tries the one-pass strips."""
     total = sum(calls)
-    pairs = [_shot(s, b, prec, comp, 100 + i, total, stream) for i, (s, b) in enumerate(zip(shapes, bcs))]
+    pairs = [_shot(s, b, prec, comp, 100 + i, total, stream, kernel) for i, (s, b) in enumerate(zip(shapes, bcs))]
     twins = [_shot(s, b, prec, comp, 100 + i, total, stream)[0] for i, (s, b) in enumerate(zip(shapes, bcs))]
     ctxs = [p[0] for p in pairs]
     batch = W.wave_batch_create(ctxs)
@@ -104,6 +107,20 @@ def test_batch_autotune_and_graph_replay():
     assert info["tuned"]
     assert info["blocks"] > 0 and info["threads"] % 32 == 0
     assert info["graph_steps"] == 32
+
+
+@pytest.mark.parametrize("prec,comp", [("fp16", 3), ("fp32", 0)])
+def test_batch_one_pass_candidates_bit_exact(prec, comp):
+    """Contexts with the second buffer set: the tuner runs all 20 launch
+    shapes (the one-pass strips last), the state follows the buffer sets
+    through odd and even step counts, and every shot equals its twin stepped
+    alone by the two-launch strips."""
+    import torch
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        info = _run_case(SHAPES, BCS, prec, comp, [27, 40, 1, 7, 33], stream=stream.cuda_stream,
+                         oracle_shot=4, kernel=3)
+    assert info["tuned"]
 
 
 def test_batch_default_stream_tuned_without_graph():
