@@ -203,7 +203,7 @@ def run_variants(W, w, steps, traced=100):
     stream = torch.cuda.current_stream()
     for prec_name, comp in (("fp16", 0), ("fp16", 3), ("fp16", 6), ("bf16", 0), ("bf16", 3), ("bf16", 6),
                             ("fp16_f32arith", 0), ("fp16_f32arith", 3), ("bf16_f32arith", 0),
-                            ("bf16_f32arith", 3), ("fp32", 0)):
+                            ("bf16_f32arith", 3), ("fp16_pairs", 3), ("fp32", 0)):
         ctx = W.wave_create(w["shape"], w["h"], w["rho"], w["c"], w["dt"], W.PRECISIONS[prec_name], comp,
                             bc=[W.WAVE_BC_RIGID] * 6, field_scale=w["P0"], stream=stream.cuda_stream)
         try:
@@ -231,7 +231,7 @@ def run_variants(W, w, steps, traced=100):
 
 
 ACC_VARIANTS = (("fp16", 0), ("fp16", 3), ("fp16", 6), ("bf16", 0), ("bf16", 3), ("fp16_f32arith", 0),
-                ("fp16_f32arith", 3), ("bf16_f32arith", 3), ("fp32", 0))
+                ("fp16_f32arith", 3), ("bf16_f32arith", 3), ("fp16_pairs", 3), ("fp32", 0))
 
 
 def _vname(prec_name, comp):

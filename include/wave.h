@@ -68,6 +68,17 @@ typedef enum { WAVE_ACOUSTIC = 0, WAVE_ELASTIC = 1 } wave_physics;
  *   WAVE_FP16_F32ARITH, WAVE_BF16_F32ARITH: store in half / bfloat16, compute
  *     in binary32 registers; with compensation the update forms s = V + (T +
  *     inc) in binary32 and stores V' = RN(s), T' = RN(s - V') (not in the paper).
+ *   WAVE_FP16_PAIRS: as WAVE_FP16_F32ARITH with compensation, except that
+ *     every stencil tap reads RN32(V + T), the stored value plus its carried
+ *     compensation, instead of V (not the paper's scheme, where the stencil
+ *     reads V: the binary16 pair then acts as a ~22-bit value in the stencil,
+ *     which removes the rounding error of the stored value from the
+ *     differences); the multipliers a and b are kept in binary32 (their
+ *     rounding to binary16 is then the largest error left; per-point arrays
+ *     cost 4 bytes a point). Acoustic only; needs compensation (WAVE_EINVAL
+ *     without); wave_energy_acoustic_static does not take it; 2D steps on
+ *     the two-launch row strips, 3D on the one-thread-per-point
+ *     kernels; no z slabs, no adjoint (WAVE_ENOTIMPL).
  *   WAVE_FP64 is accepted only by the CPU oracle; wave_create returns
  *     WAVE_ENOTIMPL for it. */
 typedef enum {
@@ -76,7 +87,8 @@ typedef enum {
     WAVE_FP16 = 2,
     WAVE_BF16 = 3,
     WAVE_FP16_F32ARITH = 4,
-    WAVE_BF16_F32ARITH = 5
+    WAVE_BF16_F32ARITH = 5,
+    WAVE_FP16_PAIRS = 6
 } wave_precision;
 
 /* Solution update: plain V += inc (Algorithm 1), or the compensated update of

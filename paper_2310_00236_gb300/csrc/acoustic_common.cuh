@@ -16,9 +16,10 @@ struct AcParams {
     int64_t sy, sz;
     void *p, *tp;
     void *v[3], *tv[3];
-    const void *a[3];          // per-point multipliers (storage type) or nullptr
+    const void *a[3];          // per-point multipliers (storage type; binary32 for
+                               // the pair precision) or nullptr
     const void *b;
-    uint32_t a_uni[3], b_uni;  // uniform multipliers (storage bits / float bits)
+    uint32_t a_uni[3], b_uni;  // uniform multipliers (the same type's bits)
     // source (arithmetic-format table indexed by global step)
     int64_t src_q;             // linear pitched index of the source point, -1 none
     int src_i, src_j, src_k;   // its grid coordinates (-1 none)
@@ -60,21 +61,22 @@ __device__ __forceinline__ int img_half(int m, int N, int bc, int &out) {
 __device__ __forceinline__ void from_bits(uint32_t u, uint16_t &s) { s = static_cast<uint16_t>(u); }
 __device__ __forceinline__ void from_bits(uint32_t u, float &s) { s = __uint_as_float(u); }
 
-// Multiplier at point q: per-point array when present, else the uniform value.
+// Multiplier at point q: per-point array when present, else the uniform value
+// (both in the policy's multiplier storage, CoefOf<P>).
 template <class P>
 __device__ __forceinline__ typename P::A coef(const void *arr, uint32_t uni, int64_t q) {
-    typename P::S s;
-    if (arr) s = static_cast<const typename P::S *>(arr)[q];
+    typename CoefOf<P>::S s;
+    if (arr) s = static_cast<const typename CoefOf<P>::S *>(arr)[q];
     else from_bits(uni, s);
-    return P::ld(s);
+    return CoefOf<P>::ld(s);
 }
 
 template <class P>
 __device__ __forceinline__ float coef_f32(const void *arr, uint32_t uni, int64_t q) {
-    typename P::S s;
-    if (arr) s = static_cast<const typename P::S *>(arr)[q];
+    typename CoefOf<P>::S s;
+    if (arr) s = static_cast<const typename CoefOf<P>::S *>(arr)[q];
     else from_bits(uni, s);
-    return P::to_f32(s);
+    return CoefOf<P>::f32(s);
 }
 
 // Energy term helpers: products in binary32 (exact for half / bfloat16

@@ -62,6 +62,7 @@ static cudaError_t launch_p(const AcParams &prm, int prec, int comp, int half_st
     case PREC_BF16: return launch_c<BF16, NDIM>(prm, comp, half_step, st);
     case PREC_FP16_F32ARITH: return launch_c<F16W, NDIM>(prm, comp ? 3 : 0, half_step, st);
     case PREC_BF16_F32ARITH: return launch_c<BF16W, NDIM>(prm, comp ? 3 : 0, half_step, st);
+    case PREC_FP16_PAIRS: return launch_t<F16WP, 3, NDIM>(prm, half_step, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -13,6 +13,17 @@ __device__ __forceinline__ typename P::A read_signed(const typename P::S *f, int
     return sign > 0 ? v : P::neg(v);
 }
 
+// A stencil tap: the stored value, or for the pair policies RN(V + T) (the
+// image's sign applied to the sum, which negation commutes with).
+template <class P>
+__device__ __forceinline__ typename P::A read_tap(const typename P::S *f, const typename P::S *t, int64_t q,
+                                                  int sign) {
+    if (!IsPairs<P>::value) return read_signed<P>(f, q, sign);
+    if (sign == 0) return P::zero();
+    const typename P::A v = P::add(P::ld(f[q]), P::ld(t[q]));
+    return sign > 0 ? v : P::neg(v);
+}
+
 // Velocity half step at point (i, j, k): for each axis c, v_c at m + 1/2
 // reads p at nodes m-1, m, m+1, m+2 along c.
 template <class P, int COMP, int NDIM>
@@ -23,6 +34,7 @@ __device__ __forceinline__ void kv_point(const AcParams &prm, int i, int j, int 
     const int64_t str[3] = {1, prm.sy, prm.sz};
     const int64_t q = i + prm.sy * j + prm.sz * k;
     const S *p = static_cast<const S *>(prm.p);
+    const S *tp = static_cast<const S *>(prm.tp);
 #pragma unroll
     for (int c = 0; c < NDIM; c++) {
         const int m = idx[c];
@@ -32,7 +44,7 @@ __device__ __forceinline__ void kv_point(const AcParams &prm, int i, int j, int 
         for (int t = 0; t < 4; t++) {
             int mm;
             int sg = img_node(m - 1 + t, prm.n[c], prm.bc[c], mm);
-            f[t] = read_signed<P>(p, base + str[c] * mm, sg);
+            f[t] = read_tap<P>(p, tp, base + str[c] * mm, sg);
         }
         A D = stencil<P>(f[0], f[1], f[2], f[3]);
         A inc = P::mul(coef<P>(prm.a[c], prm.a_uni[c], q), D);
@@ -63,12 +75,13 @@ __device__ __forceinline__ double kp_point(const AcParams &prm, int i, int j, in
         const int m = idx[c];
         const int64_t base = q - str[c] * m;
         const S *v = static_cast<const S *>(prm.v[c]);
+        const S *tv = static_cast<const S *>(prm.tv[c]);
         A f[4];
 #pragma unroll
         for (int t = 0; t < 4; t++) {
             int mm;
             img_half(m - 2 + t, prm.n[c], prm.bc[c], mm);
-            f[t] = P::ld(v[base + str[c] * mm]);
+            f[t] = read_tap<P>(v, tv, base + str[c] * mm, 1);
         }
         A D = stencil<P>(f[0], f[1], f[2], f[3]);
         R = (c == 0) ? D : P::add(R, D);

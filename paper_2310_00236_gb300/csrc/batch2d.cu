@@ -145,13 +145,27 @@ __device__ __forceinline__ void raw_set<float, float4>(float4 &r, int e, float s
     if (e == 0) r.x = s; else if (e == 1) r.y = s; else if (e == 2) r.z = s; else r.w = s;
 }
 
+// Multipliers of the vector at q (per-point array or uniform value); the pair
+// precision keeps them in binary32 (two 16-byte loads per vector of 8).
 template <class V>
 __device__ __forceinline__ typename V::AV coef_v(const void *arr, uint32_t uni, int64_t q) {
-    if (arr) return V::ld(*reinterpret_cast<const typename V::Raw *>(
-                 static_cast<const char *>(arr) + q * sizeof(typename V::RS)));
-    typename V::RS s;
-    from_bits(uni, s);
-    return V::splat(V::lds(s));
+    if constexpr (VPairs<V>::value) {
+        typename V::AV a;
+        if (arr) {
+            const float4 *f = reinterpret_cast<const float4 *>(static_cast<const float *>(arr) + q);
+            const float4 lo = f[0], hi = f[1];
+            a.f[0] = lo.x; a.f[1] = lo.y; a.f[2] = lo.z; a.f[3] = lo.w;
+            a.f[4] = hi.x; a.f[5] = hi.y; a.f[6] = hi.z; a.f[7] = hi.w;
+            return a;
+        }
+        return V::splat(__uint_as_float(uni));
+    } else {
+        if (arr) return V::ld(*reinterpret_cast<const typename V::Raw *>(
+                     static_cast<const char *>(arr) + q * sizeof(typename V::RS)));
+        typename V::RS s;
+        from_bits(uni, s);
+        return V::splat(V::lds(s));
+    }
 }
 
 // Store the first nvalid elements of a vector (all of it when nvalid == N).
@@ -209,12 +223,22 @@ __global__ void __launch_bounds__(256) batch_kv_strip(BatchShot *shots, const in
         const int nvalid = active ? min(N, nx - x) : 0;
         const bool left_edge = active && lane == 0;
         const bool right_edge = active && (lane == 31 || x + N >= nx);
-        // row queue of the own p vector: rows j-1, j, j+1 (j+2 loaded in the loop)
+        // row queue of the own p vector: rows j-1, j, j+1 (j+2 loaded in the
+        // loop); with the pair policies the same queue of t_p (the taps read
+        // RN(p + t_p))
+        constexpr bool PAIRS = IsPairs<P>::value;
         Raw q0 = row_vec<V>(prm.p, prm, x, it.y0 - 1, true, active);
         Raw q1 = row_vec<V>(prm.p, prm, x, it.y0, true, active);
         Raw q2 = row_vec<V>(prm.p, prm, x, it.y0 + 1, true, active);
+        Raw u0 = V::zero(), u1 = V::zero(), u2 = V::zero();
+        if (PAIRS) {
+            u0 = row_vec<V>(prm.tp, prm, x, it.y0 - 1, true, active);
+            u1 = row_vec<V>(prm.tp, prm, x, it.y0, true, active);
+            u2 = row_vec<V>(prm.tp, prm, x, it.y0 + 1, true, active);
+        }
         for (int j = it.y0; j < it.y1; j++) {
             const Raw q3 = row_vec<V>(prm.p, prm, x, j + 2, true, active);
+            const Raw u3 = PAIRS ? row_vec<V>(prm.tp, prm, x, j + 2, true, active) : V::zero();
             const int64_t q = x + prm.sy * (int64_t)j;
             Raw vx = V::zero(), vy = V::zero(), tx = V::zero(), ty = V::zero();
             if (active) {
@@ -225,36 +249,47 @@ __global__ void __launch_bounds__(256) batch_kv_strip(BatchShot *shots, const in
                     ty = at<V>(prm.tv[1], q);
                 }
             }
-            // x neighbours p[x-1], p[x+N], p[x+N+1]; at strip and grid edges
-            // from memory with the x image, and the own vector's elements past
-            // the grid replaced by their images
-            Raw own = q1;
-            RS l0 = RS(0), r0 = RS(0), r1 = RS(0);
-            if (left_edge) l0 = x_val<V>(prm.p, prm, x - 1, j, true);
-            if (right_edge) {
-                r0 = x_val<V>(prm.p, prm, x + N, j, true);
-                r1 = x_val<V>(prm.p, prm, x + N + 1, j, true);
+            // x neighbours p[x-1], p[x+N], p[x+N+1] of a row of field f (p, or
+            // t_p for the pairs); at strip and grid edges from memory with the
+            // x image, and the own vector's elements past the grid replaced by
+            // their images
+            auto xnb = [&](const void *f, Raw &own, RS &l0, RS &r0, RS &r1) {
+                l0 = r0 = r1 = RS(0);
+                if (left_edge) l0 = x_val<V>(f, prm, x - 1, j, true);
+                if (right_edge) {
+                    r0 = x_val<V>(f, prm, x + N, j, true);
+                    r1 = x_val<V>(f, prm, x + N + 1, j, true);
 #pragma unroll
-                for (int e = 1; e < N; e++)
-                    if (e >= nvalid) raw_set<RS, Raw>(own, e, x_val<V>(prm.p, prm, x + e, j, true));
-            }
-            // (from the fixed-up vector: the lane left of a partial vector
-            // reads its element 1, which may lie past the grid)
-            const RS sl0 = shfl_rs(V::get(own, N - 1), 1, true);
-            const RS sr0 = shfl_rs(V::get(own, 0), 1, false);
-            const RS sr1 = shfl_rs(V::get(own, 1), 1, false);
-            if (!left_edge) l0 = sl0;
-            if (!right_edge) {
-                r0 = sr0;
-                r1 = sr1;
-            }
+                    for (int e = 1; e < N; e++)
+                        if (e >= nvalid) raw_set<RS, Raw>(own, e, x_val<V>(f, prm, x + e, j, true));
+                }
+                // (from the fixed-up vector: the lane left of a partial vector
+                // reads its element 1, which may lie past the grid)
+                const RS sl0 = shfl_rs(V::get(own, N - 1), 1, true);
+                const RS sr0 = shfl_rs(V::get(own, 0), 1, false);
+                const RS sr1 = shfl_rs(V::get(own, 1), 1, false);
+                if (!left_edge) l0 = sl0;
+                if (!right_edge) {
+                    r0 = sr0;
+                    r1 = sr1;
+                }
+            };
+            Raw own = q1, ownt = u1;
+            RS l0, r0, r1, l0t = RS(0), r0t = RS(0), r1t = RS(0);
+            xnb(prm.p, own, l0, r0, r1);
+            if (PAIRS) xnb(prm.tp, ownt, l0t, r0t, r1t);
             if (active) {
-                const AV o = V::ld(own);
+                // taps: the stored values, or RN(V + T) for the pairs
+                auto tap = [&](const Raw &v, const Raw &t) -> AV { return PAIRS ? V::add(V::ld(v), V::ld(t)) : V::ld(v); };
+                auto tap_s = [&](RS v, RS t) -> typename V::AS {
+                    return PAIRS ? P::add(V::lds(v), V::lds(t)) : V::lds(v);
+                };
+                const AV o = tap(own, ownt);
+                const typename V::AS a_l0 = tap_s(l0, l0t), a_r0 = tap_s(r0, r0t), a_r1 = tap_s(r1, r1t);
                 // v_x at i + 1/2: p[i-1], p[i], p[i+1], p[i+2]
-                const AV Dx = vstencil<V>(V::shr1(o, V::lds(l0)), o, V::shl1(o, V::lds(r0)),
-                                          V::shl2(o, V::lds(r0), V::lds(r1)));
+                const AV Dx = vstencil<V>(V::shr1(o, a_l0), o, V::shl1(o, a_r0), V::shl2(o, a_r0, a_r1));
                 // v_y at j + 1/2: rows j-1, j, j+1, j+2
-                const AV Dy = vstencil<V>(V::ld(q0), V::ld(q1), V::ld(q2), V::ld(q3));
+                const AV Dy = vstencil<V>(tap(q0, u0), tap(q1, u1), tap(q2, u2), tap(q3, u3));
                 V::template update<COMP>(vx, tx, V::mul(coef_v<V>(prm.a[0], prm.a_uni[0], q), Dx));
                 V::template update<COMP>(vy, ty, V::mul(coef_v<V>(prm.a[1], prm.a_uni[1], q), Dy));
                 store_vec<V>(prm.v[0], q, vx, nvalid);
@@ -267,6 +302,9 @@ __global__ void __launch_bounds__(256) batch_kv_strip(BatchShot *shots, const in
             q0 = q1;
             q1 = q2;
             q2 = q3;
+            u0 = u1;
+            u1 = u2;
+            u2 = u3;
         }
     }
 }
@@ -296,47 +334,70 @@ __global__ void __launch_bounds__(256) batch_kp_strip(const BatchShot *__restric
         const int nvalid = active ? min(N, nx - x) : 0;
         const bool left_edge = active && lane == 0;
         const bool right_edge = active && (lane == 31 || x + N >= nx);
-        // row queue of the own v_y vector: rows j-2, j-1, j (j+1 loaded in the loop)
+        // row queue of the own v_y vector: rows j-2, j-1, j (j+1 loaded in
+        // the loop); with the pair policies the same queue of t_vy (the taps
+        // read RN(v + t_v))
+        constexpr bool PAIRS = IsPairs<P>::value;
         Raw r0 = row_vec<V>(prm.v[1], prm, x, it.y0 - 2, false, active);
         Raw r1 = row_vec<V>(prm.v[1], prm, x, it.y0 - 1, false, active);
         Raw r2 = row_vec<V>(prm.v[1], prm, x, it.y0, false, active);
+        Raw u0 = V::zero(), u1 = V::zero(), u2 = V::zero();
+        if (PAIRS) {
+            u0 = row_vec<V>(prm.tv[1], prm, x, it.y0 - 2, false, active);
+            u1 = row_vec<V>(prm.tv[1], prm, x, it.y0 - 1, false, active);
+            u2 = row_vec<V>(prm.tv[1], prm, x, it.y0, false, active);
+        }
         double e_acc = 0.0;
         for (int j = it.y0; j < it.y1; j++) {
             const Raw r3 = row_vec<V>(prm.v[1], prm, x, j + 1, false, active);
+            const Raw u3 = PAIRS ? row_vec<V>(prm.tv[1], prm, x, j + 1, false, active) : V::zero();
             const int64_t q = x + prm.sy * (int64_t)j;
-            Raw vx = V::zero(), pv = V::zero(), tv = V::zero();
+            Raw vx = V::zero(), pv = V::zero(), tv = V::zero(), tx = V::zero();
             if (active) {
                 vx = at<V>(prm.v[0], q);
                 pv = at<V>(prm.p, q);
                 if (COMP) tv = at<V>(prm.tp, q);
+                if (PAIRS) tx = at<V>(prm.tv[0], q);
             }
-            // x neighbours v_x[x-2], v_x[x-1], v_x[x+N] (half-point images)
-            Raw own = vx;
-            RS l1 = RS(0), l0 = RS(0), rr = RS(0);
-            if (left_edge) {
-                l1 = x_val<V>(prm.v[0], prm, x - 2, j, false);
-                l0 = x_val<V>(prm.v[0], prm, x - 1, j, false);
-            }
-            if (right_edge) {
-                rr = x_val<V>(prm.v[0], prm, x + N, j, false);
+            // x neighbours v_x[x-2], v_x[x-1], v_x[x+N] (half-point images) of
+            // a row of field f (v_x, or t_vx for the pairs)
+            auto xnb = [&](const void *f, const Raw &row, Raw &own, RS &l1, RS &l0, RS &rr) {
+                own = row;
+                l1 = l0 = rr = RS(0);
+                if (left_edge) {
+                    l1 = x_val<V>(f, prm, x - 2, j, false);
+                    l0 = x_val<V>(f, prm, x - 1, j, false);
+                }
+                if (right_edge) {
+                    rr = x_val<V>(f, prm, x + N, j, false);
 #pragma unroll
-                for (int e = 1; e < N; e++)
-                    if (e >= nvalid) raw_set<RS, Raw>(own, e, x_val<V>(prm.v[0], prm, x + e, j, false));
-            }
-            const RS sl1 = shfl_rs(V::get(vx, N - 2), 1, true);
-            const RS sl0 = shfl_rs(V::get(vx, N - 1), 1, true);
-            const RS srr = shfl_rs(V::get(vx, 0), 1, false);
-            if (!left_edge) {
-                l1 = sl1;
-                l0 = sl0;
-            }
-            if (!right_edge) rr = srr;
+                    for (int e = 1; e < N; e++)
+                        if (e >= nvalid) raw_set<RS, Raw>(own, e, x_val<V>(f, prm, x + e, j, false));
+                }
+                const RS sl1 = shfl_rs(V::get(row, N - 2), 1, true);
+                const RS sl0 = shfl_rs(V::get(row, N - 1), 1, true);
+                const RS srr = shfl_rs(V::get(row, 0), 1, false);
+                if (!left_edge) {
+                    l1 = sl1;
+                    l0 = sl0;
+                }
+                if (!right_edge) rr = srr;
+            };
+            Raw own, ownt = V::zero();
+            RS l1, l0, rr, l1t = RS(0), l0t = RS(0), rrt = RS(0);
+            xnb(prm.v[0], vx, own, l1, l0, rr);
+            if (PAIRS) xnb(prm.tv[0], tx, ownt, l1t, l0t, rrt);
             if (active) {
-                const AV o = V::ld(own);
+                // taps: the stored values, or RN(V + T) for the pairs
+                auto tap = [&](const Raw &v, const Raw &t) -> AV { return PAIRS ? V::add(V::ld(v), V::ld(t)) : V::ld(v); };
+                auto tap_s = [&](RS v, RS t) -> typename V::AS {
+                    return PAIRS ? P::add(V::lds(v), V::lds(t)) : V::lds(v);
+                };
+                const AV o = tap(own, ownt);
+                const typename V::AS a_l1 = tap_s(l1, l1t), a_l0 = tap_s(l0, l0t), a_rr = tap_s(rr, rrt);
                 // node i reads v_x at i-2, i-1, i, i+1 (+1/2)
-                AV R = vstencil<V>(V::shr2(o, V::lds(l1), V::lds(l0)), V::shr1(o, V::lds(l0)), o,
-                                   V::shl1(o, V::lds(rr)));
-                R = V::add(R, vstencil<V>(V::ld(r0), V::ld(r1), V::ld(r2), V::ld(r3)));
+                AV R = vstencil<V>(V::shr2(o, a_l1, a_l0), V::shr1(o, a_l0), o, V::shl1(o, a_rr));
+                R = V::add(R, vstencil<V>(tap(r0, u0), tap(r1, u1), tap(r2, u2), tap(r3, u3)));
                 if (j == prm.src_j && prm.src_i >= x && prm.src_i < x + N && step < prm.src_nt) {
                     const typename V::AS s_ = static_cast<const typename V::AS *>(prm.src)[step];
 #pragma unroll
@@ -347,7 +408,17 @@ __global__ void __launch_bounds__(256) batch_kp_strip(const BatchShot *__restric
                 V::template update<COMP>(pv, tv, V::mul(coef_v<V>(prm.b, prm.b_uni, q), R));
                 store_vec<V>(prm.p, q, pv, nvalid);
                 if (COMP) store_vec<V>(prm.tp, q, tv, nvalid);
-                if (ENERGY) {
+                if constexpr (ENERGY && PAIRS) {
+                    // (binary32 multipliers, CoefOf)
+#pragma unroll
+                    for (int e = 0; e < N; e++) {
+                        if (e >= nvalid) break;
+                        const float fx = V::f32(vx, e), fy = V::f32(r2, e);
+                        e_acc += (double)e_term(V::f32(pold, e), V::f32(pv, e), coef_f32<P>(prm.b, prm.b_uni, q + e));
+                        e_acc += (double)e_term(fx, fx, coef_f32<P>(prm.a[0], prm.a_uni[0], q + e));
+                        e_acc += (double)e_term(fy, fy, coef_f32<P>(prm.a[1], prm.a_uni[1], q + e));
+                    }
+                } else if constexpr (ENERGY) {
                     RS bs, as0, as1;
                     from_bits(prm.b_uni, bs);
                     from_bits(prm.a_uni[0], as0);
@@ -371,6 +442,9 @@ __global__ void __launch_bounds__(256) batch_kp_strip(const BatchShot *__restric
             r0 = r1;
             r1 = r2;
             r2 = r3;
+            u0 = u1;
+            u1 = u2;
+            u2 = u3;
         }
         if (ENERGY) {
             for (int off = 16; off > 0; off >>= 1) e_acc += __shfl_down_sync(0xffffffffu, e_acc, off);
@@ -662,14 +736,19 @@ __global__ void batch_energy_reduce(BatchShot *shots, const int *item0, const do
 template <class P, int COMP>
 static cudaError_t launch_pc(const BatchLaunch &L, bool energy, cudaStream_t st) {
     if (L.kind == BATCH_FUSED) {
-        const int threads = 32 * L.wpb;
-        if (energy)
-            batch_fused_strip<P, COMP, true><<<L.grid, threads, 0, st>>>(L.shots, L.item0, L.nshots, L.nitems,
-                                                                         L.yc, L.item_part);
-        else
-            batch_fused_strip<P, COMP, false><<<L.grid, threads, 0, st>>>(L.shots, L.item0, L.nshots, L.nitems,
-                                                                          L.yc, L.item_part);
-        batch_advance<<<1, 256, 0, st>>>(L.shots, L.nshots);
+        // (the one-pass strips read the stored values only)
+        if constexpr (IsPairs<P>::value) {
+            return cudaErrorInvalidValue;
+        } else {
+            const int threads = 32 * L.wpb;
+            if (energy)
+                batch_fused_strip<P, COMP, true><<<L.grid, threads, 0, st>>>(L.shots, L.item0, L.nshots,
+                                                                             L.nitems, L.yc, L.item_part);
+            else
+                batch_fused_strip<P, COMP, false><<<L.grid, threads, 0, st>>>(L.shots, L.item0, L.nshots,
+                                                                              L.nitems, L.yc, L.item_part);
+            batch_advance<<<1, 256, 0, st>>>(L.shots, L.nshots);
+        }
     } else if (L.kind == BATCH_STRIPS) {
         const int threads = 32 * L.wpb;
         batch_kv_strip<P, COMP><<<L.grid, threads, 0, st>>>(L.shots, L.item0, L.nshots, L.nitems, L.yc);
@@ -721,6 +800,7 @@ cudaError_t batch_step(const BatchLaunch &L, int prec, int comp, bool energy, cu
     case PREC_BF16: return launch_p<BF16>(L, comp, energy, st);
     case PREC_FP16_F32ARITH: return launch_p<F16W>(L, comp ? 3 : 0, energy, st);
     case PREC_BF16_F32ARITH: return launch_p<BF16W>(L, comp ? 3 : 0, energy, st);
+    case PREC_FP16_PAIRS: return comp ? launch_pc<F16WP, 3>(L, energy, st) : cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }

@@ -217,6 +217,11 @@ template <> struct VecOf<BF16> { using T = VPacked<BF16>; };
 template <> struct VecOf<F32> { using T = VF32; };
 template <> struct VecOf<F16W> { using T = VWide<F16W, F16>; };
 template <> struct VecOf<BF16W> { using T = VWide<BF16W, BF16>; };
+template <> struct VecOf<F16WP> { using T = VWide<F16WP, F16>; };
+
+// Vector policies of the pair precision (binary32 multipliers, CoefOf).
+template <class V> struct VPairs { static constexpr bool value = false; };
+template <class Store> struct VPairs<VWide<PairArith<Store>, Store>> { static constexpr bool value = true; };
 
 template <class V>
 __device__ __forceinline__ typename V::AV vstencil(const typename V::AV &fm3, const typename V::AV &fm1,

@@ -111,8 +111,14 @@ static double bf16_to_double(uint16_t b) {
 static int elem_bytes(int prec) { return prec == PREC_FP32 ? 4 : 2; }
 static bool is_bf16_storage(int prec) { return prec == PREC_BF16 || prec == PREC_BF16_F32ARITH; }
 static bool arith_is_f32(int prec) {
-    return prec == PREC_FP32 || prec == PREC_FP16_F32ARITH || prec == PREC_BF16_F32ARITH;
+    return prec == PREC_FP32 || prec == PREC_FP16_F32ARITH || prec == PREC_BF16_F32ARITH ||
+           prec == PREC_FP16_PAIRS;
 }
+
+// Format of the multipliers a and b: the storage format, except binary32 for
+// the pair precision (whose stencils read V + T; the multipliers' rounding to
+// binary16 would then be the largest error left).
+static int coef_prec(int prec) { return prec == PREC_FP16_PAIRS ? PREC_FP32 : prec; }
 
 // value -> storage bits (uint16 or float bits) ; returns false if not finite
 static inline void store_value(int prec, double x, void *dst, int64_t i) {
@@ -133,7 +139,8 @@ static inline double load_value(int prec, const void *src, int64_t i) {
 
 // Smallest positive normal number of the storage format.
 static double min_normal(int prec) {
-    return (prec == PREC_FP16 || prec == PREC_FP16_F32ARITH) ? ldexp(1.0, -14) : ldexp(1.0, -126);
+    return (prec == PREC_FP16 || prec == PREC_FP16_F32ARITH || prec == PREC_FP16_PAIRS) ? ldexp(1.0, -14)
+                                                                                           : ldexp(1.0, -126);
 }
 
 // Parallel loop over [0, n) on the host.
@@ -330,8 +337,8 @@ static wave_status check_device_error(wave_ctx *c);
     } while (0)
 
 // Copy a packed host array (n[0]*n[1]*n[2] elements) into a pitched field.
-static wave_status upload_packed(wave_ctx *c, void *dev, const void *host) {
-    const size_t eb = elem_bytes(c->prec);
+static wave_status upload_packed(wave_ctx *c, void *dev, const void *host, size_t eb = 0) {
+    if (!eb) eb = elem_bytes(c->prec);
     cudaError_t e = cudaMemcpy2DAsync(dev, c->pitch * eb, host, c->n[0] * eb, c->n[0] * eb,
                                       c->n[1] * c->n[2], cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -362,7 +369,8 @@ static wave_status acoustic_coefficients(wave_ctx *c, const wave_materials *mat,
     const double Z0 = z0_opt > 0.0 ? z0_opt : rho0 * c0;
     c->Z0 = Z0;
     const double h = c->h, dt = c->dt;
-    const double tiny = min_normal(c->prec);
+    const int cp = coef_prec(c->prec);
+    const double tiny = min_normal(cp);
     if (rho_above)
         for (int64_t q = 0; q < c->n[0] * c->n[1]; q++)
             if (!(rho_above[q] > 0.0) || !isfinite(rho_above[q]))
@@ -382,8 +390,8 @@ static wave_status acoustic_coefficients(wave_ctx *c, const wave_materials *mat,
         {
             uint16_t tmp16;
             float tmp32;
-            if (c->prec == PREC_FP32) { tmp32 = (float)v; r = tmp32; }
-            else { store_value(c->prec, v, &tmp16, 0); r = load_value(c->prec, &tmp16, 0); }
+            if (cp == PREC_FP32) { tmp32 = (float)v; r = tmp32; }
+            else { store_value(cp, v, &tmp16, 0); r = load_value(cp, &tmp16, 0); }
         }
         b[q] = r;
         if (!(r >= tiny) || !isfinite(r)) { bad = true; bad_q = q; }
@@ -398,8 +406,8 @@ static wave_status acoustic_coefficients(wave_ctx *c, const wave_materials *mat,
             double ar;
             uint16_t tmp16;
             float tmp32;
-            if (c->prec == PREC_FP32) { tmp32 = (float)av; ar = tmp32; }
-            else { store_value(c->prec, av, &tmp16, 0); ar = load_value(c->prec, &tmp16, 0); }
+            if (cp == PREC_FP32) { tmp32 = (float)av; ar = tmp32; }
+            else { store_value(cp, av, &tmp16, 0); ar = load_value(cp, &tmp16, 0); }
             c->coef_host[1 + ax][q] = ar;
             if (!(ar >= tiny) || !isfinite(ar)) { bad = true; bad_q = q; }
         }
@@ -496,23 +504,24 @@ static wave_status upload_coef(wave_ctx *c, int w) {
     bool uni = true;
     for (int64_t q = 1; q < npts && uni; q++) uni = (v[q] == v[0]);
     c->coef_is_uniform[w] = uni;
+    const int cp = coef_prec(c->prec);
     if (uni) {
-        if (c->prec == PREC_FP32) {
+        if (cp == PREC_FP32) {
             float f = (float)v[0];
             memcpy(&c->coef_uni[w], &f, 4);
         } else {
             uint16_t hb;
-            store_value(c->prec, v[0], &hb, 0);
+            store_value(cp, v[0], &hb, 0);
             c->coef_uni[w] = hb;
         }
         return WAVE_OK;
     }
-    const size_t eb = elem_bytes(c->prec);
+    const size_t eb = elem_bytes(cp);
     wave_status st = dev_alloc(c, c->coef[w], c->total * eb);
     if (st) return st;
     std::vector<unsigned char> tmp(npts * eb);
-    for (int64_t q = 0; q < npts; q++) store_value(c->prec, v[q], tmp.data(), q);
-    return upload_packed(c, c->coef[w].ptr, tmp.data());
+    for (int64_t q = 0; q < npts; q++) store_value(cp, v[q], tmp.data(), q);
+    return upload_packed(c, c->coef[w].ptr, tmp.data(), eb);
 }
 
 static void fill_acoustic_params(wave_ctx *c, AcParams &prm) {
@@ -655,10 +664,15 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
     }
     if (!(dt > 0.0) || !isfinite(dt)) return fail(WAVE_EINVAL, "dt must be positive and finite");
     if (prec == WAVE_FP64) return fail(WAVE_ENOTIMPL, "WAVE_FP64 runs only in the CPU oracle");
-    if (prec < WAVE_FP32 || prec > WAVE_BF16_F32ARITH) return fail(WAVE_EINVAL, "bad precision");
+    if (prec < WAVE_FP32 || prec > WAVE_FP16_PAIRS) return fail(WAVE_EINVAL, "bad precision");
     if (compensated != WAVE_COMP_NONE && compensated != WAVE_COMP_3OP &&
         compensated != WAVE_COMP_6OP)
         return fail(WAVE_EINVAL, "bad compensation %d", (int)compensated);
+    if (prec == WAVE_FP16_PAIRS) {
+        // the stencils read V + T: nothing to read without the compensation
+        if (compensated == WAVE_COMP_NONE) return fail(WAVE_EINVAL, "WAVE_FP16_PAIRS needs a compensation");
+        if (mat->kind != WAVE_ACOUSTIC) return fail(WAVE_ENOTIMPL, "WAVE_FP16_PAIRS covers the acoustic system");
+    }
     if (!mat->rho || !mat->vp) return fail(WAVE_EINVAL, "material arrays are NULL");
     if (mat->kind == WAVE_ELASTIC && !mat->vs) return fail(WAVE_EINVAL, "elastic needs vs");
     double P0 = 1.0, z0_opt = 0.0;
@@ -679,6 +693,9 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
     if (z_cut && (kchoice == 1 || kchoice == 3))
         return fail(WAVE_EINVAL, "z slabs step with the two-kernel streaming path (kernel 0 or 2)");
     if ((z_cut & 2) && !rho_above) return fail(WAVE_EINVAL, "a cut z-hi face needs rho_above");
+    if (prec == WAVE_FP16_PAIRS && z_cut) return fail(WAVE_ENOTIMPL, "WAVE_FP16_PAIRS covers whole grids");
+    if (prec == WAVE_FP16_PAIRS && grid->ndim == 2 && kchoice == 3)
+        return fail(WAVE_ENOTIMPL, "WAVE_FP16_PAIRS steps 2D grids with the two-launch strips");
     if (!(z0_opt >= 0.0) || !isfinite(z0_opt)) return fail(WAVE_EINVAL, "z0 must be >= 0 and finite");
     if (!(P0 > 0.0) || !isfinite(P0)) return fail(WAVE_EINVAL, "field_scale must be positive");
     const int64_t npts = grid->n[0] * grid->n[1] * (grid->ndim == 3 ? grid->n[2] : 1);
@@ -727,8 +744,11 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
         AcParams prm;
         fill_acoustic_params(c, prm);
         c->e_blocks = acoustic_generic_blocks(prm, c->ndim);
-        c->use_fused = !z_cut && (kchoice == 0 || kchoice == 3) && acoustic_fused_supported(prm, c->ndim, c->prec);
-        c->use_stream = !c->use_fused && kchoice != 1 &&
+        // (3D grids of WAVE_FP16_PAIRS step with the one-thread-per-point kernels)
+        const bool pairs = prec == WAVE_FP16_PAIRS;
+        c->use_fused = !pairs && !z_cut && (kchoice == 0 || kchoice == 3) &&
+                       acoustic_fused_supported(prm, c->ndim, c->prec);
+        c->use_stream = !pairs && !c->use_fused && kchoice != 1 &&
                         acoustic_stream_supported(prm, c->ndim, c->prec);
         if (z_cut && !c->use_stream && !st)
             st = fail(WAVE_EINVAL, "z slabs need n[0] a multiple of the 16-byte vector width");
@@ -1639,6 +1659,7 @@ extern "C" wave_status wave_record(wave_ctx *c, int64_t nsteps, int64_t ncheckpo
     CHECK_CTX(c);
     if (c->kind != WAVE_ACOUSTIC) return fail(WAVE_ENOTIMPL, "the adjoint covers the acoustic system");
     if (c->z_cut) return fail(WAVE_ENOTIMPL, "the adjoint covers whole grids, not z slabs");
+    if (c->prec == PREC_FP16_PAIRS) return fail(WAVE_ENOTIMPL, "the adjoint covers the stored-value stencils");
     if (c->half_open) return fail(WAVE_ESTATE, "a velocity half step awaits its pressure half step");
     if (nsteps < 1) return fail(WAVE_EINVAL, "nsteps must be positive");
     if (c->nrec && c->rec_field != WAVE_F_P) return fail(WAVE_EINVAL, "adjoint receivers must record p");

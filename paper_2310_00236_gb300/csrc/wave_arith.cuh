@@ -122,6 +122,34 @@ __device__ __forceinline__ uint16_t WideArith<BF16>::st(float a) {
 using F16W = WideArith<F16>;
 using BF16W = WideArith<BF16>;
 
+// The binary32-register arithmetic with stencils that read the stored pair:
+// every stencil tap is RN32(V + T), the stored value plus its carried
+// compensation, instead of V (not the paper's scheme, where the stencil reads
+// V: reading the pair removes the error of the rounded stored value; the
+// update is WideArith's compensated one).
+template <class Store>
+struct PairArith : WideArith<Store> {};
+using F16WP = PairArith<F16>;
+
+template <class P> struct IsPairs { static constexpr bool value = false; };
+template <class Store> struct IsPairs<PairArith<Store>> { static constexpr bool value = true; };
+
+// Storage of the multipliers a and b: the field storage type, except for the
+// pair policies, which keep them in binary32 (their rounding to binary16 is
+// the error the pair stencil does not remove).
+template <class P>
+struct CoefOf {
+    using S = typename P::S;
+    static __device__ __forceinline__ typename P::A ld(S s) { return P::ld(s); }
+    static __device__ __forceinline__ float f32(S s) { return P::to_f32(s); }
+};
+template <class Store>
+struct CoefOf<PairArith<Store>> {
+    using S = float;
+    static __device__ __forceinline__ float ld(float s) { return s; }
+    static __device__ __forceinline__ float f32(float s) { return s; }
+};
+
 // ------------------------------------------------------------ the method's ops
 // Fourth-order staggered difference (Section 3):
 //   D = C1 * (f[+1/2] - f[-1/2]) - C2 * (f[+3/2] - f[-3/2])

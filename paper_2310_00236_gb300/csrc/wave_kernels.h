@@ -7,7 +7,7 @@ namespace wave {
 
 // Same values as wave_precision in include/wave.h.
 enum { PREC_FP64 = 0, PREC_FP32 = 1, PREC_FP16 = 2, PREC_BF16 = 3,
-       PREC_FP16_F32ARITH = 4, PREC_BF16_F32ARITH = 5 };
+       PREC_FP16_F32ARITH = 4, PREC_BF16_F32ARITH = 5, PREC_FP16_PAIRS = 6 };
 
 struct AcParams;
 

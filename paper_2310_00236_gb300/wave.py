@@ -19,13 +19,14 @@ WAVE_OK, WAVE_EINVAL, WAVE_ENOMEM, WAVE_ERANGE, WAVE_ECUDA, WAVE_ETIMEOUT, WAVE_
     WAVE_ENOTIMPL = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ERANGE", "ECUDA", "ETIMEOUT", "ESTATE", "ENOTIMPL"]
 WAVE_ACOUSTIC, WAVE_ELASTIC = 0, 1
-WAVE_FP64, WAVE_FP32, WAVE_FP16, WAVE_BF16, WAVE_FP16_F32ARITH, WAVE_BF16_F32ARITH = range(6)
+WAVE_FP64, WAVE_FP32, WAVE_FP16, WAVE_BF16, WAVE_FP16_F32ARITH, WAVE_BF16_F32ARITH, WAVE_FP16_PAIRS = range(7)
 WAVE_COMP_NONE, WAVE_COMP_3OP, WAVE_COMP_6OP = 0, 3, 6
 WAVE_BC_PERIODIC, WAVE_BC_RIGID, WAVE_BC_FREE = 0, 1, 2
 WAVE_F_P, WAVE_F_VX, WAVE_F_VY, WAVE_F_VZ, WAVE_F_SXX, WAVE_F_SYY, WAVE_F_SXY = range(7)
 
 PRECISIONS = {"fp32": WAVE_FP32, "fp16": WAVE_FP16, "bf16": WAVE_BF16,
               "fp16_f32arith": WAVE_FP16_F32ARITH, "bf16_f32arith": WAVE_BF16_F32ARITH,
+              "fp16_pairs": WAVE_FP16_PAIRS,
               "fp64": WAVE_FP64}
 
 # Every symbol include/wave.h declares.

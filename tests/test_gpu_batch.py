@@ -93,7 +93,7 @@ BCS = [(R, R), (P, R), (R, P), (R, R), (P, P)]
 
 
 @pytest.mark.parametrize("prec,comp", [("fp16", 3), ("fp16", 0), ("bf16", 6), ("fp32", 0),
-                                       ("fp16_f32arith", 3)])
+                                       ("fp16_f32arith", 3), ("fp16_pairs", 3)])
 def test_batch_bit_exact_ragged_shots(prec, comp):
     _run_case(SHAPES, BCS, prec, comp, [12])
 

@@ -22,6 +22,7 @@ pytestmark = pytest.mark.gpu
 R = W.WAVE_BC_RIGID
 VARIANTS = [("fp16", 0), ("fp16", 3), ("fp16", 6), ("bf16", 0), ("bf16", 3), ("bf16", 6),
             ("fp16_f32arith", 0), ("fp16_f32arith", 3), ("bf16_f32arith", 3), ("fp32", 0)]
+VARIANTS_3D = VARIANTS + [("fp16_pairs", 3)]
 
 
 def _rel(a, b):
@@ -35,7 +36,7 @@ def test_precision_ladder_3d_acoustic():
     ref = O.acoustic_setup(shape, (1, 1, 1), w["h"], w["dt"], w["rho"], w["c"], O.FP64, 0, p0=w["p0"])
     _, E = ref.run(steps, energy=True)
     rows = {}
-    for prec, comp in VARIANTS:
+    for prec, comp in VARIANTS_3D:
         code = PREC[prec][0]
         ctx = W.wave_create(shape, w["h"], w["rho"], w["c"], w["dt"], code, comp, bc=[R] * 6)
         try:
@@ -62,6 +63,10 @@ def test_precision_ladder_3d_acoustic():
         assert abs(rows[(s, 3)][1]) < abs(rows[(s, 0)][1])
         assert _close(rows[(s, 3)], rows[(s, 6)], rows[(s, 0)])
     assert abs(rows[("fp16_f32arith", 3)][1]) < abs(rows[("fp16_f32arith", 0)][1])
+    # reading the pair V + T (and binary32 multipliers) removes the stored
+    # value's and the multipliers' rounding: under the 2e-3 bar, an order of
+    # magnitude below the stored-value stencil
+    assert rows[("fp16_pairs", 3)][0] < min(2e-3, 0.2 * rows[("fp16_f32arith", 3)][0])
     assert abs(rows[("fp16+fp64 stencil", 3)][1]) < abs(rows[("fp16+fp64 stencil", 0)][1])
     for k, (err, _) in rows.items():
         if k != ("fp32", 0):

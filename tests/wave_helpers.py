@@ -15,7 +15,11 @@ PREC = {
     "fp32": (W.WAVE_FP32, O.FP32, O.FP32),
     "fp16_f32arith": (W.WAVE_FP16_F32ARITH, O.FP16, O.FP32),
     "bf16_f32arith": (W.WAVE_BF16_F32ARITH, O.BF16, O.FP32),
+    # stencils read RN32(V + T), multipliers in binary32: the oracle's
+    # pair_stencil and coef_fmt readings
+    "fp16_pairs": (W.WAVE_FP16_PAIRS, O.FP16, O.FP32),
 }
+PAIRS = {"fp16_pairs"}
 
 
 def to_bits(values: np.ndarray, fmt: int) -> np.ndarray:
@@ -47,8 +51,10 @@ def acoustic_pair(shape, bc, prec, comp, h, dt, rho, c, p0=None, v0=None, P0=1.0
         bcw += [b, b]
     ctx = W.wave_create(shape, h, rho, c, dt, code, comp, bc=bcw, field_scale=P0, kernel=kernel,
                         zchunk=zchunk, stream=stream)
+    # the pair precision: stencils read RN32(V + T), multipliers in binary32
+    pairs = prec in PAIRS
     st = O.acoustic_setup(shape, bc, h, dt, rho, c, sfmt, comp, P0=P0, arith_fmt=afmt,
-                          p0=p0, v0=v0)
+                          p0=p0, v0=v0, pair_stencil=pairs, coef_fmt=O.FP32 if pairs else None)
     if p0 is not None:
         W.wave_set_initial(ctx, W.WAVE_F_P, p0)
     if v0 is not None:
