@@ -125,16 +125,26 @@ typedef struct {
     int32_t kernel;      /* 0: automatic (3D: the one-pass step where it applies, else
                             the two-kernel streaming step when n[0] is a multiple of
                             the 16-byte vector width, else one thread per point;
-                            2D acoustic: row strips, one warp per strip of 16-byte
-                            vectors, one launch per half step, any size);
+                            2D acoustic: the cluster-resident steps of kernel 4
+                            when the state fits, else the row strips of kernel 2);
                             1: one-thread-per-point kernels only; 2: two-kernel
-                            streaming step; 3: one-pass step (3D: both half steps in
+                            streaming step (2D acoustic: row strips, one warp per
+                            strip of 16-byte vectors, one launch per half step,
+                            any size); 3: one-pass step (3D: both half steps in
                             one kernel; needs n[0] a multiple of 64 (32 for binary32),
                             rigid x faces and a uniform density, else as 0; 2D
                             acoustic: one-pass row strips, both half steps in one
                             launch, keeping a second buffer set of p, v and t_v; a
-                            batch of such contexts also tries them in its tuner).
-                            Every choice gives the same bits. */
+                            batch of such contexts also tries them in its tuner);
+                            4: 2D acoustic only, cluster-resident steps: the rows
+                            cut into bands over one thread-block cluster of up to
+                            16 CTAs, the whole state in their shared memory, rows
+                            past a band's edge read from the neighbouring CTA's
+                            shared memory, a cluster barrier after each half step,
+                            and every step of a wave_step call (energies, receivers
+                            and source included) in one launch; WAVE_EINVAL if the
+                            state does not fit (about 3.6 MB: 300k points at 12
+                            bytes a point). Every choice gives the same bits. */
     int32_t zchunk;      /* z planes per thread block of the 3D kernels; rows per
                             work item of the 2D row strips (0: automatic) */
     int32_t z_cut;       /* 3D acoustic only: the context is a z slab of a larger
@@ -307,7 +317,8 @@ wave_status wave_steps_done(wave_ctx *ctx, int64_t *steps);
  * kernel kind, the launches and their summed device time (milliseconds) since
  * timing was last enabled. Kinds: 0 velocity half step, 1 pressure (or stress)
  * half step including source and energy, 2 receiver sampling, 3 a whole step
- * in one launch sequence (3D one-pass kernel, 2D row strips). Enabling resets
+ * in one launch sequence (3D one-pass kernel, 2D row strips; for the 2D
+ * cluster-resident steps, every step of one wave_step call). Enabling resets
  * the totals. Not part of the method; a measurement aid. */
 wave_status wave_set_timing(wave_ctx *ctx, int32_t enable);
 wave_status wave_get_timing(wave_ctx *ctx, int32_t kind, int64_t *launches, double *ms);

@@ -203,6 +203,10 @@ struct wave_ctx {
     // state alternating between f / t and alt_f / alt_t)
     bool use_strips = false;
     bool strip_fused = false;
+    // 2D acoustic: the cluster-resident steps (the whole state in the shared
+    // memory of one cluster, one launch per wave_step call)
+    bool use_cluster = false;
+    ClusterPlan cplan;
     int strip_items = 0, strip_grid = 0, strip_rows = 16;
     // plain strip steps replayed from captured graphs of 2^j steps (j < kStripGraphLevels)
     cudaGraphExec_t strip_graph[kStripGraphLevels] = {};
@@ -686,7 +690,9 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
         z0_opt = opt->z0;
         rho_above = opt->rho_above;
     }
-    if (kchoice < 0 || kchoice > 3 || zchunk < 0) return fail(WAVE_EINVAL, "bad kernel options");
+    if (kchoice < 0 || kchoice > 4 || zchunk < 0) return fail(WAVE_EINVAL, "bad kernel options");
+    if (kchoice == 4 && (mat->kind != WAVE_ACOUSTIC || grid->ndim != 2))
+        return fail(WAVE_EINVAL, "kernel 4 (cluster-resident steps) takes 2D acoustic grids");
     if (z_cut < 0 || z_cut > 3) return fail(WAVE_EINVAL, "z_cut takes bits 0 and 1 only");
     if (z_cut && (mat->kind != WAVE_ACOUSTIC || grid->ndim != 3))
         return fail(WAVE_EINVAL, "z slabs are 3D acoustic contexts");
@@ -773,6 +779,15 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
             // buffer set and write the other (the two-launch strips are the
             // default: faster on this hardware, see the notes on the kernels)
             c->strip_fused = kchoice == 3;
+            // kernel 0 (the default) and 4: the cluster-resident steps when the
+            // state fits the shared memory of one cluster (the strips stay set
+            // up: batches step the context with them)
+            if ((kchoice == 0 || kchoice == 4) && !st) {
+                c->use_cluster = acoustic_cluster_plan(prm, c->prec, compensated, c->cplan);
+                cudaGetLastError();
+                if (kchoice == 4 && !c->use_cluster)
+                    st = fail(WAVE_EINVAL, "kernel 4: the grid's state does not fit one cluster's shared memory");
+            }
             for (int fi = 0; fi < 3 && c->strip_fused && !st; fi++) {
                 st = dev_alloc(c, c->alt_f[fi], c->total * eb);
                 if (!st && fi > 0 && compensated) st = dev_alloc(c, c->alt_t[fi], c->total * eb);
@@ -1176,6 +1191,34 @@ static wave_status acoustic_steps(wave_ctx *c, int64_t n, bool energy_last = tru
     fill_acoustic_params(c, prm);
     const size_t eb = elem_bytes(c->prec);
     BatchLaunch L;
+    if (c->use_cluster) {
+        // all n steps in one launch: energies, receivers and the source's
+        // step index handled inside it
+        ClusterRun run;
+        memset(&run, 0, sizeof run);
+        run.prm = prm;
+        run.prm.step = c->step;
+        run.nsteps = n;
+        const int64_t tn = c->e_trace ? std::min<int64_t>(n, c->e_trace_cap - c->e_trace_pos) : 0;
+        run.e_trace = tn > 0 ? c->e_trace + c->e_trace_pos : nullptr;
+        run.e_trace_n = std::max<int64_t>(tn, 0);
+        run.e_last = energy_last ? static_cast<double *>(c->e_misc.ptr) : nullptr;
+        const int64_t rn = c->nrec ? std::min<int64_t>(n, c->rec_cap - c->rec_pos) : 0;
+        run.rec_q = static_cast<const int64_t *>(c->rec_q.ptr);
+        run.nrec = (int)c->nrec;
+        run.rec_field = c->rec_field;
+        run.traces = rn > 0 ? c->rec_traces + c->rec_pos * c->nrec : nullptr;
+        run.rec_n = std::max<int64_t>(rn, 0);
+        cudaEvent_t m0 = mark(c);
+        cudaError_t e = acoustic_cluster_steps(run, c->cplan, c->prec, c->comp, c->stream);
+        cudaEvent_t m1 = mark(c);
+        timed(c, 3, m0, m1);
+        if (e != cudaSuccess) return cuda_check(c, e, "wave_step launch");
+        c->e_trace_pos += run.e_trace_n;
+        c->rec_pos += run.rec_n;
+        c->step += n;
+        return WAVE_OK;
+    }
     if (c->use_strips) {
         BatchShot shot;
         fill_shot(c, shot);

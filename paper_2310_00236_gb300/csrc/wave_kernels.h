@@ -37,6 +37,30 @@ cudaError_t acoustic_fused_step(const AcParams &prm, const void *maps, const voi
                                 void *const out[7], void *tp, int prec, int comp, int zchunk, int *err,
                                 cudaStream_t st);
 
+// Cluster-resident 2D steps (acoustic2d_cluster.cu): the whole state of a
+// small 2D grid in the shared memory of one cluster of up to 16 CTAs, any
+// number of steps per launch.
+struct ClusterRun {
+    AcParams prm;           // global arrays (pitch prm.sy); prm.step: global index of the first step
+    int64_t nsteps;
+    double *e_trace;        // energies after steps 0 .. e_trace_n - 1 (physical units), or nullptr
+    int64_t e_trace_n;
+    double *e_last;         // energy after the last step, or nullptr
+    const int64_t *rec_q;   // receivers: pitched linear indices of field rec_field (0 p, 1 v_x, 2 v_y)
+    int nrec, rec_field;
+    float *traces;          // traces[s * nrec + r] for steps s < rec_n
+    int64_t rec_n;
+};
+struct ClusterPlan {
+    int ctas = 0, rows = 0, rpi = 1;  // CTAs (= bands), rows per band, rows per work item
+    size_t smem = 0;                  // dynamic shared memory per CTA
+};
+// A cluster shape that holds the grid's state and that the device can run;
+// false if none (the grid is too large, or the precision has no such kernel).
+bool acoustic_cluster_plan(const AcParams &prm, int prec, int comp, ClusterPlan &pl);
+cudaError_t acoustic_cluster_steps(const ClusterRun &run, const ClusterPlan &pl, int prec, int comp,
+                                   cudaStream_t st);
+
 // A bounded mbarrier wait that nothing completes (polls iterations), setting
 // *err to 1 when it expires: the self-test of the device error path.
 cudaError_t selftest_wait(int *err, uint32_t polls, cudaStream_t st);

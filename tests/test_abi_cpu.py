@@ -72,6 +72,9 @@ def _ones(n=(16, 16)):
     (dict(precision=W.WAVE_FP16_PAIRS, kind=W.WAVE_ELASTIC, vs=True), W.WAVE_ENOTIMPL),
     (dict(precision=W.WAVE_FP16_PAIRS, z_cut=1, n=(16, 16, 16)), W.WAVE_ENOTIMPL),
     (dict(precision=W.WAVE_FP16_PAIRS, kernel=3), W.WAVE_ENOTIMPL),    # one-pass strips
+    (dict(kernel=4, n=(16, 16, 16)), W.WAVE_EINVAL),                   # cluster steps are 2D
+    (dict(kernel=4, kind=W.WAVE_ELASTIC, vs=True), W.WAVE_EINVAL),     # and acoustic
+    (dict(kernel=5), W.WAVE_EINVAL),
 ])
 def test_create_argument_errors(lib, kw, status):
     n = kw.pop("n", (16, 16))

@@ -19,7 +19,7 @@ VARIANTS = [("fp16", 0), ("fp16", 3), ("fp16", 6), ("bf16", 0), ("bf16", 3), ("b
             ("fp32", 0), ("fp32", 3), ("fp16_f32arith", 0), ("fp16_f32arith", 3),
             ("bf16_f32arith", 3), ("fp16_pairs", 3)]
 # (kernel, precision, compensation); the one-pass strips read stored values only
-KVARIANTS = [(k, p, c) for k in (0, 1, 3) for p, c in VARIANTS if not (k == 3 and p in PAIRS)]
+KVARIANTS = [(k, p, c) for k in (0, 1, 2, 3) for p, c in VARIANTS if not (k == 3 and p in PAIRS)]
 
 
 def _media(shape, seed, h):
@@ -60,9 +60,11 @@ def _run(shape, bc, prec, comp, steps, seed=0, variable=True, src=False, kernel=
 R, P = O.BC_RIGID, O.BC_PERIODIC
 
 
-# kernel 0: 2D row strips, one launch per half step (the default); kernel 1:
-# one thread per point; kernel 3: one-pass row strips (both half steps in one
-# launch, two buffer sets)
+# kernel 0 (the default): for these sizes the cluster-resident steps (the whole
+# state in one cluster's shared memory, bands of rows per CTA, rows past a band
+# read from the neighbouring CTA); kernel 1: one thread per point; kernel 2:
+# row strips, one launch per half step; kernel 3: one-pass row strips (both
+# half steps in one launch, two buffer sets)
 @pytest.mark.parametrize("kernel,prec,comp", KVARIANTS)
 def test_2d_bit_exact_ragged_rigid(prec, comp, kernel):
     _run((37, 29), (R, R), prec, comp, 30, kernel=kernel)
@@ -73,7 +75,7 @@ def test_2d_bit_exact_periodic_source(prec, comp, kernel):
     _run((64, 40), (P, P), prec, comp, 25, src=True, kernel=kernel)
 
 
-@pytest.mark.parametrize("kernel", [0, 3])
+@pytest.mark.parametrize("kernel", [0, 2, 3])
 @pytest.mark.parametrize("shape", [(257, 33), (300, 70), (8, 200), (513, 9), (265, 40), (520, 17)])
 def test_2d_strips_ragged_wide_and_tall(shape, kernel):
     # strips of 256 points (128 for binary32) cut by the grid's x extent, rows
@@ -83,7 +85,7 @@ def test_2d_strips_ragged_wide_and_tall(shape, kernel):
     _run(shape, (P, R), "fp16", 3, 12, src=True, kernel=kernel)
     _run(shape, (R, P), "fp32", 0, 12, kernel=kernel)
     _run(shape, (R, R), "bf16", 6, 11, src=True, kernel=kernel)
-    if kernel == 0:
+    if kernel != 3:
         # pair taps: the t queues and x neighbours of t follow the same paths
         _run(shape, (P, R), "fp16_pairs", 3, 12, src=True, kernel=kernel)
 
@@ -289,7 +291,8 @@ def test_2d_graph_replay_on_side_stream_bit_exact():
     wav = inputs.ricker_table(sum(steps), dt, 40.0) * 0.5 * h / z0
     stream = torch.cuda.Stream()
     ctx, st = acoustic_pair(shape, (R, P), "fp16", 3, h, dt, rho, c,
-                            p0=inputs.gaussian(shape, h, 2.5 * h), src=([30, 20], wav), stream=stream.cuda_stream)
+                            p0=inputs.gaussian(shape, h, 2.5 * h), src=([30, 20], wav), stream=stream.cuda_stream,
+                            kernel=2)
     try:
         for n in steps:
             W.wave_step(ctx, n)
@@ -301,6 +304,86 @@ def test_2d_graph_replay_on_side_stream_bit_exact():
     finally:
         W.wave_destroy(ctx)
     assert not bad, bad
+
+
+@pytest.mark.parametrize("prec,comp", [("fp16", 3), ("fp32", 0), ("fp16_pairs", 3)])
+def test_2d_cluster_receivers_and_energy_trace_across_calls(prec, comp):
+    """Cluster-resident steps over several wave_step calls: the source's step
+    index, the v_x receiver traces and the per-step energies continue across
+    calls and stop at their capacities; fields, traces and energies equal the
+    oracle's (energies to the binary32 terms' rounding)."""
+    import torch
+    shape = (150, 70)
+    h = 10.0
+    rho, c = _media(shape, 11, h)
+    dt = 0.4 * h / 4500.0
+    calls = [17, 1, 30]
+    total = sum(calls)
+    z0 = float(np.max(rho) * np.max(c))
+    wav = inputs.ricker_table(total, dt, 40.0) * 0.5 * h / z0
+    recs = [(5, 7), (75, 34), (149, 69), (0, 0), (140, 35)]
+    cap_rec, cap_e = 40, 45
+    ctx, st = acoustic_pair(shape, (R, P), prec, comp, h, dt, rho, c, p0=inputs.gaussian(shape, h, 3 * h),
+                            src=([50, 35], wav), kernel=4)
+    try:
+        tr = torch.full((cap_rec * len(recs),), -7.0, dtype=torch.float32, device="cuda")
+        en = torch.full((cap_e,), -7.0, dtype=torch.float64, device="cuda")
+        W.wave_set_receivers(ctx, W.WAVE_F_VX, recs, tr, cap_rec)
+        W.wave_set_energy_trace(ctx, en, cap_e)
+        for n in calls:
+            W.wave_step(ctx, n)
+        ridx = [int(np.ravel_multi_index((j, i), st.shape)) for i, j in recs]
+        traces, E = st.run(total, energy=True, rec_field=1, rec_index=ridx)
+        bad = compare_acoustic(ctx, st, prec, comp)
+        got = tr.cpu().numpy().reshape(cap_rec, len(recs)).astype(np.float64)
+        if not np.array_equal(got, traces[:cap_rec]):
+            bad.append("receiver traces differ")
+        fac = O.energy_factor(h, dt, 1.0, st.Z0, 2)
+        np.testing.assert_allclose(en.cpu().numpy(), E[:cap_e] * fac, rtol=2e-6)
+        assert abs(W.wave_energy(ctx) - E[-1] * fac) <= 2e-6 * abs(E[-1] * fac)
+        assert np.any(got != 0)
+    finally:
+        W.wave_destroy(ctx)
+    assert not bad, bad
+
+
+def test_2d_cluster_largest_grid_and_fit_limit():
+    """512 x 448 binary16 + compensation (about 2.75 MB of state, 28 rows per
+    band over 16 CTAs): bit-exact to the oracle and to the row strips; a grid
+    whose state does not fit is refused by kernel 4 and stepped by the strips
+    under kernel 0."""
+    shape = (512, 448)
+    h = 10.0
+    rho, c = _media(shape, 12, h)
+    dt = 0.4 * h / 4500.0
+    p0 = inputs.gaussian(shape, h, 20 * h)
+    ctx, st = acoustic_pair(shape, (R, R), "fp16", 3, h, dt, rho, c, p0=p0, kernel=4)
+    twin, _ = acoustic_pair(shape, (R, R), "fp16", 3, h, dt, rho, c, p0=p0, kernel=2)
+    try:
+        W.wave_step(ctx, 30)
+        W.wave_step(twin, 30)
+        st.run(30)
+        bad = compare_acoustic(ctx, st, "fp16", 3)
+        for f in (W.WAVE_F_P, W.WAVE_F_VX, W.WAVE_F_VY):
+            for cf in (0, 1):
+                if not np.array_equal(W.wave_get_raw(ctx, f, cf), W.wave_get_raw(twin, f, cf)):
+                    bad.append(f"field {f} comp {cf}: cluster and strips differ")
+    finally:
+        W.wave_destroy(ctx)
+        W.wave_destroy(twin)
+    assert not bad, bad
+    big = (1024, 1024)
+    ones = np.ones(big[::-1])
+    with pytest.raises(W.WaveError) as e:
+        W.wave_create(big, 1.0, ones, ones, 0.4, W.WAVE_FP16, 3, bc=[1] * 6, kernel=4)
+    assert e.value.status == W.WAVE_EINVAL
+    ctx = W.wave_create(big, 1.0, ones, ones, 0.4, W.WAVE_FP16, 3, bc=[1] * 6)
+    try:
+        W.wave_set_initial(ctx, W.WAVE_F_P, inputs.gaussian(big, 1.0, 30.0))
+        W.wave_step(ctx, 3)
+        assert np.isfinite(W.wave_energy(ctx))
+    finally:
+        W.wave_destroy(ctx)
 
 
 def test_bounded_wait_expiry_reports_timeout_and_leaves_gpu_usable():
