@@ -126,7 +126,8 @@ typedef struct {
                             the two-kernel streaming step when n[0] is a multiple of
                             the 16-byte vector width, else one thread per point;
                             2D acoustic: the cluster-resident steps of kernel 4
-                            when the state fits, else the row strips of kernel 2);
+                            for small grids (a band of at most 5120 points, e.g.
+                            256^2), else the row strips of kernel 2);
                             1: one-thread-per-point kernels only; 2: two-kernel
                             streaming step (2D acoustic: row strips, one warp per
                             strip of 16-byte vectors, one launch per half step,

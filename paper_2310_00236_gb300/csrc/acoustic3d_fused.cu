@@ -48,6 +48,10 @@ namespace wave {
 template <class P>
 struct FShape {
     using S = typename P::S;
+    // the pair precision: every p slot also holds the t_p tile (at P_ELEMS),
+    // and the exchange buffers hold the new velocities' T beside them (at
+    // N_ELEMS); the stencil taps are RN32(V + T)
+    static constexpr bool PAIRS = IsPairs<P>::value;
     static constexpr int VEC = 16 / sizeof(S);
     static constexpr int LANES = 8;
     static constexpr int TX = LANES * VEC;
@@ -78,8 +82,10 @@ struct FShape {
     static constexpr int N_VY = TY * WIDE;
     static constexpr int N_YROWS = TY + 3;
     static constexpr int N_ELEMS = N_VY + 2 * N_YROWS * TX;
+    static constexpr int P_SLOT = PAIRS ? 2 * P_ELEMS : P_ELEMS;
+    static constexpr int N_TOT = PAIRS ? 2 * N_ELEMS : N_ELEMS;
     static constexpr size_t RING_BYTES =
-        sizeof(S) * ((size_t)SP * P_ELEMS + (size_t)SO * O_ELEMS + (size_t)N_ELEMS);
+        sizeof(S) * ((size_t)SP * P_SLOT + (size_t)SO * O_ELEMS + (size_t)N_TOT);
     static constexpr size_t SMEM = RING_BYTES + sizeof(uint64_t) * (2 * (SP + SO) + 2) + 128;
     static_assert((P_ELEMS * sizeof(S)) % 128 == 0 && (O_ELEMS * sizeof(S)) % 128 == 0 &&
                       (N_ELEMS * sizeof(S)) % 128 == 0 && (O_VY * sizeof(S)) % 128 == 0 &&
@@ -89,9 +95,10 @@ struct FShape {
 };
 
 template <class P, int COMP, bool ENERGY>
-__global__ void __launch_bounds__(160, 4)
+__global__ void __launch_bounds__(160, IsPairs<P>::value ? 2 : 4)
     fused_step(const __grid_constant__ FusedParams fp, const __grid_constant__ FusedMaps maps) {
     using SH = FShape<P>;
+    constexpr bool PAIRS = SH::PAIRS;
     using S = typename P::S;
     using V = typename VecOf<P>::T;
     using Raw = typename V::Raw;
@@ -104,7 +111,7 @@ __global__ void __launch_bounds__(160, 4)
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
     S *pring = reinterpret_cast<S *>(base);
-    S *oring = pring + SP * SH::P_ELEMS;
+    S *oring = pring + SP * SH::P_SLOT;
     S *nbuf = oring + SO * SH::O_ELEMS;
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + SH::RING_BYTES);
     uint64_t *p_full = bars, *p_empty = bars + SP, *o_full = bars + 2 * SP, *o_empty = bars + 2 * SP + SO;
@@ -133,11 +140,16 @@ __global__ void __launch_bounds__(160, 4)
     }
     __syncthreads();
 
-    RS a_raw[3], b_raw;
+    // uniform multipliers in their storage (CoefOf: binary32 for the pairs)
+    using CS = typename CoefOf<P>::S;
+    CS a_raw[3], b_raw;
 #pragma unroll
     for (int c = 0; c < 3; c++) from_bits(prm.a_uni[c], a_raw[c]);
     from_bits(prm.b_uni, b_raw);
-    const AV ay = V::splat(V::lds(a_raw[1]));
+    const AV ay = V::splat(CoefOf<P>::ld(a_raw[1]));
+    // a stencil tap: the stored value, or RN(V + T) for the pairs
+    auto tap = [&](const Raw &v, const Raw &t) -> AV { return PAIRS ? V::add(V::ld(v), V::ld(t)) : V::ld(v); };
+    auto tap_s = [&](RS v, RS t) -> typename V::AS { return PAIRS ? P::add(V::lds(v), V::lds(t)) : V::lds(v); };
     // tiles whose p rows y0-3..y0+TY+2 are all inside the grid read no images in y
     const bool inner_y = y0 >= 3 && y0 + TY + 3 <= ny;
     // rigid y walls: rows past the y faces were loaded as zeros; the images are
@@ -150,7 +162,7 @@ __global__ void __launch_bounds__(160, 4)
     // new v_y at local row lr (-2..TY), lane ln: from the p^n plane pk (rows
     // lr-1..lr+2) and the old v_y, t_vy of the stage ost; stored into nvy
     auto vy_new = [&](const S *pk, const S *ost, S *nvy, int lr, int ln, Raw &Vv, Raw &Tv) {
-        Raw pr[4];
+        Raw pr[4], tr[4];
 #pragma unroll
         for (int t = 0; t < 4; t++) {
             int l = lr - 1 + t, sg = 1;
@@ -167,8 +179,13 @@ __global__ void __launch_bounds__(160, 4)
                                               : pk + SH::P_HALO + (l < 0 ? l + 3 : 3 + l - TY) * TX + ln * VEC;
             const Raw r = *reinterpret_cast<const Raw *>(ptr);
             pr[t] = inner_y ? r : signed_raw<V>(r, sg);
+            tr[t] = V::zero();
+            if (PAIRS) {
+                const Raw rt = *reinterpret_cast<const Raw *>(ptr + SH::P_ELEMS);
+                tr[t] = inner_y ? rt : signed_raw<V>(rt, sg);
+            }
         }
-        const AV D = vstencil<V>(V::ld(pr[0]), V::ld(pr[1]), V::ld(pr[2]), V::ld(pr[3]));
+        const AV D = vstencil<V>(tap(pr[0], tr[0]), tap(pr[1], tr[1]), tap(pr[2], tr[2]), tap(pr[3], tr[3]));
         int lv = lr;
         if (!inner_y && rigid_y) {
             int jm;
@@ -179,6 +196,7 @@ __global__ void __launch_bounds__(160, 4)
         Tv = COMP ? *reinterpret_cast<const Raw *>(ost + SH::O_TVY + (lv + 2) * TX + ln * VEC) : V::zero();
         V::template update<COMP>(Vv, Tv, V::mul(ay, D));
         *reinterpret_cast<Raw *>(nvy + (lr + 2) * TX + ln * VEC) = Vv;
+        if (PAIRS) *reinterpret_cast<Raw *>(nvy + SH::N_ELEMS + (lr + 2) * TX + ln * VEC) = Tv;
     };
 
     if (warp == 4) {
@@ -225,12 +243,13 @@ __global__ void __launch_bounds__(160, 4)
         const bool bot_box = rigid_y || y0 + TY + 3 <= ny;        // p rows y0+TY..y0+TY+2 inside
         const bool vy_box = rigid_y || (y0 >= 2 && y0 + TY + 1 <= ny);  // v_y rows y0-2..y0+TY inside
         // one p plane: the boxes (lane 0) and the row-by-row groups (spread over lanes)
-        auto p_plane = [&](int m, S *dst, uint64_t *bar, bool issue) -> uint32_t {
-            const S *pin = static_cast<const S *>(fp.p_in);
+        auto p_plane1 = [&](int m, S *dst, uint64_t *bar, bool issue, const void *src_arr, const CUtensorMap *m_own,
+                            const CUtensorMap *m_halo) -> uint32_t {
+            const S *pin = static_cast<const S *>(src_arr);
             const int mz = plane_of(m, true);
             uint32_t bytes = 0;
             if (own_box) {
-                if (issue && lane == 0) tma_box(dst, &maps.p_own, x0 - HALO, y0, mz, bar);
+                if (issue && lane == 0) tma_box(dst, m_own, x0 - HALO, y0, mz, bar);
                 bytes += TY * WIDE * eb;
             } else {
                 for (int r = 0; r < TY; r++)
@@ -241,7 +260,7 @@ __global__ void __launch_bounds__(160, 4)
                 S *hd = dst + SH::P_HALO + side * 3 * TX;
                 const int ybase = side == 0 ? y0 - 3 : y0 + TY;
                 if (side == 0 ? top_box : bot_box) {
-                    if (issue && lane == 0) tma_box(hd, &maps.p_halo, x0, ybase, mz, bar);
+                    if (issue && lane == 0) tma_box(hd, m_halo, x0, ybase, mz, bar);
                 } else {
                     for (int h = 0; h < 3; h++)
                         if (issue && lane == 16 + side * 3 + h)
@@ -249,6 +268,11 @@ __global__ void __launch_bounds__(160, 4)
                 }
                 bytes += 3 * TX * eb;
             }
+            return bytes;
+        };
+        auto p_plane = [&](int m, S *dst, uint64_t *bar, bool issue) -> uint32_t {
+            uint32_t bytes = p_plane1(m, dst, bar, issue, fp.p_in, &maps.p_own, &maps.p_halo);
+            if (PAIRS) bytes += p_plane1(m, dst + SH::P_ELEMS, bar, issue, fp.tp, &maps.tp_own, &maps.tp_halo);
             return bytes;
         };
         // the other arrays of iteration k (warm-up iterations k < z0: v_z, t_vz only)
@@ -285,7 +309,7 @@ __global__ void __launch_bounds__(160, 4)
         auto issue_p = [&](int m, int cnt) -> bool {
             const int slot = cnt % SP;
             if (cnt >= SP && !wait_phase(&p_empty[slot], ((cnt / SP) - 1) & 1, fp.err)) return false;
-            S *dst = pring + slot * SH::P_ELEMS;
+            S *dst = pring + slot * SH::P_SLOT;
             const uint32_t total = p_plane(m, dst, nullptr, false);
             if (lane == 0) mbar_expect_tx(&p_full[slot], total);
             __syncwarp();
@@ -318,7 +342,7 @@ __global__ void __launch_bounds__(160, 4)
                 const int lr = hr == 0 ? -2 : (hr == 1 ? -1 : TY);
                 if (y0 + lr <= ny) {
                     Raw Vh, Th;
-                    vy_new(pring + (pcnt % SP) * SH::P_ELEMS, oring + (ocnt % SO) * SH::O_ELEMS, nvy_of(k), lr,
+                    vy_new(pring + (pcnt % SP) * SH::P_SLOT, oring + (ocnt % SO) * SH::O_ELEMS, nvy_of(k), lr,
                            ln, Vh, Th);
                 }
             }
@@ -346,8 +370,8 @@ __global__ void __launch_bounds__(160, 4)
     const int x = x0 + lx * VEC;
     const int j = y0 + row;
     const bool active = j < ny;
-    const AV ax = V::splat(V::lds(a_raw[0])), az = V::splat(V::lds(a_raw[2]));
-    const typename P::A ax_s = P::ld(a_raw[0]);
+    const AV ax = V::splat(CoefOf<P>::ld(a_raw[0])), az = V::splat(CoefOf<P>::ld(a_raw[2]));
+    const typename P::A ax_s = CoefOf<P>::ld(a_raw[0]);
 
     auto plane_sign = [&](int m) -> int { int t; return img_node(m, nz, bcz, t); };
     // raw p vector of local row lr (-3..TY+2) at the own lane
@@ -368,6 +392,9 @@ __global__ void __launch_bounds__(160, 4)
     };
 
     Raw vzq0 = V::zero(), vzq1 = V::zero(), vzq2 = V::zero(), vzq3 = V::zero();
+    // the pairs: T of the new v_z queue and of the p planes
+    Raw tzq0 = V::zero(), tzq1 = V::zero(), tzq2 = V::zero(), tzq3 = V::zero();
+    Raw tq0 = V::zero(), tq1 = V::zero(), tq2 = V::zero();
     int oc = 0, p_waited = 0;
     // ring positions kept incrementally (no division by the ring depth):
     // the next p stage to wait for and its phase, the slot of plane k
@@ -395,26 +422,33 @@ __global__ void __launch_bounds__(160, 4)
         const int oslot = oc % SO;
         if (!wait_phase(&o_full[oslot], (oc / SO) & 1, fp.err)) { ok = false; break; }
         const S *ost = oring + oslot * SH::O_ELEMS;
-        const S *pk = pring + pk_slot * SH::P_ELEMS;
+        const S *pk = pring + pk_slot * SH::P_SLOT;
 
         // ---- v_z^{n+1/2} at plane k+1 of the own vector (p^n planes k..k+3)
         Raw vzn = V::zero(), tzn = V::zero();
         const bool inner_z = k >= 0 && k + 3 < nz;  // planes k..k+3 inside the grid
-        Raw pq3 = V::zero();
+        Raw pq3 = V::zero(), tq3 = V::zero();
         if (active) {
-            auto plane = [&](int t) -> Raw {
+            // plane k + t of p (off = 0) or t_p (off = P_ELEMS)
+            auto plane = [&](int t, int off) -> Raw {
                 int sl = pk_slot + t;
                 if (sl >= SP) sl -= SP;
-                const Raw r = p_vec(pring + sl * SH::P_ELEMS, row);
+                const Raw r = p_vec(pring + sl * SH::P_SLOT + off, row);
                 return inner_z ? r : signed_raw<V>(r, plane_sign(k + t));
             };
             if (k == z0 - 3) {
-                pq0 = plane(0);
-                pq1 = plane(1);
-                pq2 = plane(2);
+                pq0 = plane(0, 0);
+                pq1 = plane(1, 0);
+                pq2 = plane(2, 0);
+                if (PAIRS) {
+                    tq0 = plane(0, SH::P_ELEMS);
+                    tq1 = plane(1, SH::P_ELEMS);
+                    tq2 = plane(2, SH::P_ELEMS);
+                }
             }
-            pq3 = plane(3);
-            const AV D = vstencil<V>(V::ld(pq0), V::ld(pq1), V::ld(pq2), V::ld(pq3));
+            pq3 = plane(3, 0);
+            if (PAIRS) tq3 = plane(3, SH::P_ELEMS);
+            const AV D = vstencil<V>(tap(pq0, tq0), tap(pq1, tq1), tap(pq2, tq2), tap(pq3, tq3));
             vzn = vec_at(ost + SH::O_VZ + row * TX + lx * VEC);
             tzn = COMP ? vec_at(ost + SH::O_TVZ + row * TX + lx * VEC) : V::zero();
             V::template update<COMP>(vzn, tzn, V::mul(az, D));
@@ -425,6 +459,7 @@ __global__ void __launch_bounds__(160, 4)
             }
         }
         vzq3 = vzn;
+        tzq3 = tzn;
 
         if (k >= z0) {
             S *nvx = nbuf;
@@ -438,20 +473,27 @@ __global__ void __launch_bounds__(160, 4)
             // ---- v_x^{n+1/2}: own vector, and the x halo of the tile edge lanes
             if (active) {
                 const S *prow = pk + row * WIDE + HALO - x0;  // indexed by global x
-                const Raw own_p = pq0;  // plane k is inside the grid: no image
-                RS l0, r0, r1;
-                if (x == 0) l0 = V::rneg_s(prow[1]);               // p[-1] = -p[1]
-                else l0 = prow[x - 1];
-                if (x + VEC == nx) { r0 = RS(0); r1 = V::rneg_s(prow[nx - 1]); }  // wall node, image
-                else { r0 = prow[x + VEC]; r1 = prow[x + VEC + 1]; }
-                const AV own = V::ld(own_p);
-                const AV D = vstencil<V>(V::shr1(own, V::lds(l0)), own, V::shl1(own, V::lds(r0)),
-                                         V::shl2(own, V::lds(r0), V::lds(r1)));
+                const S *trow = prow + SH::P_ELEMS;             // t_p (the pairs)
+                // plane k is inside the grid: no image; p[-1] = -p[1] and the
+                // wall node and its image at the x faces
+                auto xn = [&](const S *r, RS &l0, RS &r0, RS &r1) {
+                    if (x == 0) l0 = V::rneg_s(r[1]);
+                    else l0 = r[x - 1];
+                    if (x + VEC == nx) { r0 = RS(0); r1 = V::rneg_s(r[nx - 1]); }
+                    else { r0 = r[x + VEC]; r1 = r[x + VEC + 1]; }
+                };
+                RS l0, r0, r1, l0t = RS(0), r0t = RS(0), r1t = RS(0);
+                xn(prow, l0, r0, r1);
+                if (PAIRS) xn(trow, l0t, r0t, r1t);
+                const AV own = tap(pq0, tq0);
+                const typename V::AS al0 = tap_s(l0, l0t), ar0 = tap_s(r0, r0t), ar1 = tap_s(r1, r1t);
+                const AV D = vstencil<V>(V::shr1(own, al0), own, V::shl1(own, ar0), V::shl2(own, ar0, ar1));
                 vxn = vec_at(ost + SH::O_VX + row * WIDE + HALO + lx * VEC);
                 txn = COMP ? vec_at(ost + SH::O_TVX + row * WIDE + HALO + lx * VEC) : V::zero();
                 V::template update<COMP>(vxn, txn, V::mul(ax, D));
                 S *nrow = nvx + row * WIDE + HALO - x0;
                 *reinterpret_cast<Raw *>(nrow + x) = vxn;
+                if (PAIRS) *reinterpret_cast<Raw *>(nrow + SH::N_ELEMS + x) = txn;
                 // final: store now, so that the registers are free for the rest of the plane
                 const int64_t qv = x + sy * j + sz * (int64_t)k;
                 at<V>(fp.vx_out, qv) = vxn;
@@ -464,12 +506,15 @@ __global__ void __launch_bounds__(160, 4)
                     if (ix >= 0 && ix < nx) {
                         const S *vxr = ost + SH::O_VX + row * WIDE + HALO - x0;
                         const S *txr = ost + SH::O_TVX + row * WIDE + HALO - x0;
-                        const typename P::A D1 = stencil<P>(P::ld(prow[ix - 1]), P::ld(prow[ix]),
-                                                            P::ld(prow[ix + 1]), P::ld(prow[ix + 2]));
+                        auto tp1 = [&](int m) -> typename P::A {
+                            return PAIRS ? P::add(P::ld(prow[m]), P::ld(trow[m])) : P::ld(prow[m]);
+                        };
+                        const typename P::A D1 = stencil<P>(tp1(ix - 1), tp1(ix), tp1(ix + 1), tp1(ix + 2));
                         S Vv = vxr[ix];
                         S Tv = COMP ? txr[ix] : S(0);
                         update<P, COMP>(Vv, Tv, P::mul(ax_s, D1));
                         nrow[ix] = Vv;
+                        if (PAIRS) nrow[SH::N_ELEMS + ix] = Tv;
                     }
                 }
             }
@@ -485,9 +530,18 @@ __global__ void __launch_bounds__(160, 4)
             // exchange reads so that their latency overlaps them
             const int64_t q = x + sy * j + sz * (int64_t)k;
             Raw tpn = V::zero(), bv = V::zero();
+            float4 bf0 = make_float4(0.f, 0.f, 0.f, 0.f), bf1 = bf0;  // the pairs: binary32 b
             if (active) {
                 if (COMP) tpn = *reinterpret_cast<const Raw *>(static_cast<const S *>(fp.tp) + q);
-                if (prm.b) bv = __ldg(reinterpret_cast<const Raw *>(static_cast<const S *>(prm.b) + q));
+                if (prm.b) {
+                    if (PAIRS) {
+                        const float4 *bp = reinterpret_cast<const float4 *>(static_cast<const float *>(prm.b) + q);
+                        bf0 = __ldg(bp);
+                        bf1 = __ldg(bp + 1);
+                    } else {
+                        bv = __ldg(reinterpret_cast<const Raw *>(static_cast<const S *>(prm.b) + q));
+                    }
+                }
             }
             // every warp's v_y rows and the producer's halo rows of this plane
             // are in nvy (bounded wait)
@@ -496,18 +550,22 @@ __global__ void __launch_bounds__(160, 4)
             // ---- p^{n+1}
             if (active) {
                 const S *vrow = nvx + row * WIDE + HALO - x0;
-                const AV ownx = V::ld(*reinterpret_cast<const Raw *>(vrow + x));
+                const S *tvrow = vrow + SH::N_ELEMS;  // the pairs: T of the new v_x
+                const AV ownx = tap(*reinterpret_cast<const Raw *>(vrow + x),
+                                    PAIRS ? *reinterpret_cast<const Raw *>(tvrow + x) : V::zero());
                 // v_x at x-2, x-1, x+VEC; at the x faces the even images (v_x at 1, 0; nx-1)
-                const RS l1 = x == 0 ? vrow[1] : vrow[x - 2];
-                const RS l0 = x == 0 ? vrow[0] : vrow[x - 1];
-                const RS rr = x + VEC == nx ? vrow[nx - 1] : vrow[x + VEC];
-                AV R = vstencil<V>(V::shr2(ownx, V::lds(l1), V::lds(l0)), V::shr1(ownx, V::lds(l0)),
-                                   ownx, V::shl1(ownx, V::lds(rr)));
+                const int il1 = x == 0 ? 1 : x - 2, il0 = x == 0 ? 0 : x - 1, irr = x + VEC == nx ? nx - 1 : x + VEC;
+                const typename V::AS l1 = tap_s(vrow[il1], PAIRS ? tvrow[il1] : RS(0));
+                const typename V::AS l0 = tap_s(vrow[il0], PAIRS ? tvrow[il0] : RS(0));
+                const typename V::AS rr = tap_s(vrow[irr], PAIRS ? tvrow[irr] : RS(0));
+                AV R = vstencil<V>(V::shr2(ownx, l1, l0), V::shr1(ownx, l0), ownx, V::shl1(ownx, rr));
                 const S *vyc = nvy + (row - 2 - wr0) * TX + lx * VEC;  // rows row-2 .. row+1
-                const AV Dy = vstencil<V>(V::ld(vec_at(vyc)), V::ld(vec_at(vyc + TX)),
-                                          V::ld(vec_at(vyc + 2 * TX)), V::ld(vec_at(vyc + 3 * TX)));
+                auto vy_tap = [&](int r) -> AV {
+                    return tap(vec_at(vyc + r * TX), PAIRS ? vec_at(vyc + SH::N_ELEMS + r * TX) : V::zero());
+                };
+                const AV Dy = vstencil<V>(vy_tap(0), vy_tap(1), vy_tap(2), vy_tap(3));
                 R = V::add(R, Dy);
-                const AV Dz = vstencil<V>(V::ld(vzq0), V::ld(vzq1), V::ld(vzq2), V::ld(vzq3));
+                const AV Dz = vstencil<V>(tap(vzq0, tzq0), tap(vzq1, tzq1), tap(vzq2, tzq2), tap(vzq3, tzq3));
                 R = V::add(R, Dz);
                 if (k == prm.src_k && j == prm.src_j && prm.src_i >= x && prm.src_i < x + VEC &&
                     prm.step < prm.src_nt) {
@@ -517,21 +575,34 @@ __global__ void __launch_bounds__(160, 4)
                     for (int e = 0; e < VEC; e++)
                         if (e == prm.src_i - x) V::set(R, e, P::add(V::aget(R, e), sv_));
                 }
-                const AV bc = prm.b ? V::ld(bv) : V::splat(V::lds(b_raw));
+                AV bc;
+                if constexpr (PAIRS) {
+                    if (prm.b) {
+                        const float bb[8] = {bf0.x, bf0.y, bf0.z, bf0.w, bf1.x, bf1.y, bf1.z, bf1.w};
+#pragma unroll
+                        for (int e = 0; e < VEC; e++) V::set(bc, e, bb[e]);
+                    } else {
+                        bc = V::splat(CoefOf<P>::ld(b_raw));
+                    }
+                } else {
+                    bc = prm.b ? V::ld(bv) : V::splat(V::lds(b_raw));
+                }
                 const Raw pold = pq0;
                 Raw pn = pold;
                 V::template update<COMP>(pn, tpn, V::mul(bc, R));
                 at<V>(fp.p_out, q) = pn;
-                if (COMP) at<V>(fp.tp, q) = tpn;
+                if (COMP) at<V>(fp.tp_out, q) = tpn;
                 if (ENERGY) {
                     // v^2 / a with the uniform a as a product by its reciprocal;
                     // the four terms of a point summed in binary32, then added
                     // to the compensated accumulator
-                    const float ia0 = __frcp_rn(P::to_f32(a_raw[0])), ia1 = __frcp_rn(P::to_f32(a_raw[1])),
-                                ia2 = __frcp_rn(P::to_f32(a_raw[2]));
+                    const float ia0 = __frcp_rn(CoefOf<P>::f32(a_raw[0])), ia1 = __frcp_rn(CoefOf<P>::f32(a_raw[1])),
+                                ia2 = __frcp_rn(CoefOf<P>::f32(a_raw[2]));
 #pragma unroll
                     for (int e = 0; e < VEC; e++) {
-                        const float bw = prm.b ? V::f32(bv, e) : P::to_f32(b_raw);
+                        float bw;
+                        if constexpr (PAIRS) bw = V::aget(bc, e);
+                        else bw = prm.b ? V::f32(bv, e) : P::to_f32(b_raw);
                         const float fx = V::f32(vxn, e), fy = V::f32(vyn, e), fz = V::f32(vzq2, e);
                         float t = e_term(V::f32(pold, e), V::f32(pn, e), bw);
                         t = __fadd_rn(t, __fmul_rn(__fmul_rn(fx, fx), ia0));
@@ -553,9 +624,15 @@ __global__ void __launch_bounds__(160, 4)
         vzq0 = vzq1;
         vzq1 = vzq2;
         vzq2 = vzq3;
+        tzq0 = tzq1;
+        tzq1 = tzq2;
+        tzq2 = tzq3;
         pq0 = pq1;
         pq1 = pq2;
         pq2 = pq3;
+        tq0 = tq1;
+        tq1 = tq2;
+        tq2 = tq3;
     }
     if (ENERGY) {
         double val = ok ? (double)e_s + (double)e_c : 0.0;
@@ -684,14 +761,16 @@ bool acoustic_fused_encode(void *out_maps, const AcParams &prm, const void *cons
         ok = encode(&mp.tvx, in[4], prm.n, prm.sy, eb, wide, ty) &&
              encode(&mp.tvy, in[5], prm.n, prm.sy, eb, tx, ty + 3) &&
              encode(&mp.tvz, in[6], prm.n, prm.sy, eb, tx, ty);
-    (void)tp;
+    // the pairs read t_p tiles like p's (tp: the input set's t_p)
+    if (ok && prec == PREC_FP16_PAIRS)
+        ok = encode(&mp.tp_own, tp, prm.n, prm.sy, eb, wide, ty) && encode(&mp.tp_halo, tp, prm.n, prm.sy, eb, tx, 3);
     if (ok) memcpy(out_maps, &mp, sizeof mp);
     return ok;
 }
 
 cudaError_t acoustic_fused_step(const AcParams &prm, const void *maps, const void *const in[7],
-                                void *const out[7], void *tp, int prec, int comp, int zchunk, int *err,
-                                cudaStream_t st) {
+                                void *const out[7], void *tp, void *tp_out, int prec, int comp, int zchunk,
+                                int *err, cudaStream_t st) {
     FusedParams fp;
     fp.a = prm;
     fp.p_in = in[0]; fp.vx_in = in[1]; fp.vy_in = in[2]; fp.vz_in = in[3];
@@ -699,6 +778,7 @@ cudaError_t acoustic_fused_step(const AcParams &prm, const void *maps, const voi
     fp.p_out = out[0]; fp.vx_out = out[1]; fp.vy_out = out[2]; fp.vz_out = out[3];
     fp.tvx_out = out[4]; fp.tvy_out = out[5]; fp.tvz_out = out[6];
     fp.tp = tp;
+    fp.tp_out = tp_out;
     fp.zchunk = zchunk;
     fp.err = err;
     const FusedMaps &mp = *static_cast<const FusedMaps *>(maps);
@@ -709,6 +789,7 @@ cudaError_t acoustic_fused_step(const AcParams &prm, const void *maps, const voi
     case PREC_BF16: return launch_c<BF16>(fp, mp, comp, energy, st);
     case PREC_FP16_F32ARITH: return launch_c<F16W>(fp, mp, comp ? 3 : 0, energy, st);
     case PREC_BF16_F32ARITH: return launch_c<BF16W>(fp, mp, comp ? 3 : 0, energy, st);
+    case PREC_FP16_PAIRS: return comp ? launch_t<F16WP, 3>(fp, mp, energy, st) : cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }

@@ -78,13 +78,16 @@ __device__ __forceinline__ void drain_phase(uint64_t *bar, uint32_t parity) {
 
 struct FusedMaps {
     CUtensorMap p_own, p_halo, vx, tvx, vy, tvy, vz, tvz;
+    CUtensorMap tp_own, tp_halo;  // the pair precision: t_p tiles like p's
 };
 
 struct FusedParams {
     AcParams a;  // grid, boundaries, strides, multipliers, source, energy
     const void *p_in, *vx_in, *vy_in, *vz_in, *tvx_in, *tvy_in, *tvz_in;
     void *p_out, *vx_out, *vy_out, *vz_out, *tvx_out, *tvy_out, *tvz_out;
-    void *tp;    // in place
+    void *tp;       // t_p read (own point; the pair precision: also the stencil taps)
+    void *tp_out;   // t_p written: tp itself (in place), except for the pair
+                    // precision, whose neighbours read the old t_p in their halos
     int zchunk;
     int *err;    // set to 1 when a bounded wait expires
 };

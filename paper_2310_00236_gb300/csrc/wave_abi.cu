@@ -750,9 +750,10 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
         AcParams prm;
         fill_acoustic_params(c, prm);
         c->e_blocks = acoustic_generic_blocks(prm, c->ndim);
-        // (3D grids of WAVE_FP16_PAIRS step with the one-thread-per-point kernels)
+        // (3D grids of WAVE_FP16_PAIRS: the one-pass step where it applies, else
+        // one thread per point; no streaming kernels)
         const bool pairs = prec == WAVE_FP16_PAIRS;
-        c->use_fused = !pairs && !z_cut && (kchoice == 0 || kchoice == 3) &&
+        c->use_fused = !z_cut && (kchoice == 0 || kchoice == 3) &&
                        acoustic_fused_supported(prm, c->ndim, c->prec);
         c->use_stream = !pairs && !c->use_fused && kchoice != 1 &&
                         acoustic_stream_supported(prm, c->ndim, c->prec);
@@ -779,11 +780,16 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
             // buffer set and write the other (the two-launch strips are the
             // default: faster on this hardware, see the notes on the kernels)
             c->strip_fused = kchoice == 3;
-            // kernel 0 (the default) and 4: the cluster-resident steps when the
-            // state fits the shared memory of one cluster (the strips stay set
-            // up: batches step the context with them)
+            // kernel 4: the cluster-resident steps (the state in the shared
+            // memory of one cluster); kernel 0 (the default) takes them while
+            // a band holds at most 5120 points: a warp walks a row in about
+            // 2500 cycles, so a step costs about 3 us plus 0.85 us per 1000
+            // points of a band, against about 6.3 us for the two strip
+            // launches (256^2: 4.9 against 6.2 us; 384^2: 9.2 against 6.2).
+            // The strips stay set up: batches step the context with them.
             if ((kchoice == 0 || kchoice == 4) && !st) {
-                c->use_cluster = acoustic_cluster_plan(prm, c->prec, compensated, c->cplan);
+                c->use_cluster = acoustic_cluster_plan(prm, c->prec, compensated, c->cplan) &&
+                                 (kchoice == 4 || (int64_t)c->cplan.rows * c->n[0] <= 5120);
                 cudaGetLastError();
                 if (kchoice == 4 && !c->use_cluster)
                     st = fail(WAVE_EINVAL, "kernel 4: the grid's state does not fit one cluster's shared memory");
@@ -806,9 +812,10 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
             c->e_blocks = std::max(c->e_blocks, acoustic_stream_blocks(prm, c->prec, c->zchunk));
         if (c->use_fused) {
             c->e_blocks = std::max(c->e_blocks, acoustic_fused_blocks(prm, c->prec, c->zchunk));
+            // (the pair precision alternates t_p between the sets too)
             for (int fi = 0; fi < 4 && !st; fi++) {
                 st = dev_alloc(c, c->alt_f[fi], c->total * eb);
-                if (!st && fi > 0 && compensated) st = dev_alloc(c, c->alt_t[fi], c->total * eb);
+                if (!st && (fi > 0 || pairs) && compensated) st = dev_alloc(c, c->alt_t[fi], c->total * eb);
             }
             if (!st && fused_maps_bytes() > sizeof(c->fmaps[0].b))
                 st = fail(WAVE_ECUDA, "tensor map block too large");
@@ -816,7 +823,8 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
                 DevBuf *F = set == 0 ? c->f : c->alt_f;
                 DevBuf *T = set == 0 ? c->t : c->alt_t;
                 const void *in[7] = {F[0].ptr, F[1].ptr, F[2].ptr, F[3].ptr, T[1].ptr, T[2].ptr, T[3].ptr};
-                if (!acoustic_fused_encode(c->fmaps[set].b, prm, in, c->t[0].ptr, c->prec, compensated))
+                if (!acoustic_fused_encode(c->fmaps[set].b, prm, in, pairs ? T[0].ptr : c->t[0].ptr, c->prec,
+                                           compensated))
                     st = fail(WAVE_ECUDA, "cuTensorMapEncodeTiled failed for the one-pass step");
             }
         }
@@ -1278,14 +1286,16 @@ static wave_status acoustic_steps(wave_ctx *c, int64_t n, bool energy_last = tru
                             c->alt_t[1].ptr, c->alt_t[2].ptr, c->alt_t[3].ptr};
             int *err = reinterpret_cast<int *>(static_cast<char *>(c->e_misc.ptr) + 16);
             cudaEvent_t m0 = mark(c);
+            const bool pairs = c->prec == PREC_FP16_PAIRS;
             cudaError_t e = acoustic_fused_step(prm, c->fmaps[c->fset].b, in, out, c->t[0].ptr,
-                                                c->prec, c->comp, c->zchunk, err, c->stream);
+                                                pairs ? c->alt_t[0].ptr : c->t[0].ptr, c->prec, c->comp,
+                                                c->zchunk, err, c->stream);
             c->fset ^= 1;
             cudaEvent_t m1 = mark(c);
             timed(c, 3, m0, m1);
             for (int fi = 0; fi < 4; fi++) {
                 std::swap(c->f[fi], c->alt_f[fi]);
-                if (fi > 0) std::swap(c->t[fi], c->alt_t[fi]);
+                if (fi > 0 || pairs) std::swap(c->t[fi], c->alt_t[fi]);
             }
             if (e == cudaSuccess && trace)
                 e = cudaMemcpyAsync(c->e_trace + c->e_trace_pos, c->e_misc.ptr, sizeof(double),
@@ -1952,8 +1962,8 @@ extern "C" wave_status wave_adjoint_step(wave_ctx *c, int64_t n, const float *re
             prm.p = A.mu.ptr;
             for (int ax = 0; ax < 3; ax++) prm.v[ax] = A.nu[ax].ptr;
             if (e == cudaSuccess)
-                e = acoustic_fused_step(prm, A.fm[A.fset].b, in, out, nullptr, PREC_FP32, 0, c->zchunk, err,
-                                        c->stream);
+                e = acoustic_fused_step(prm, A.fm[A.fset].b, in, out, nullptr, nullptr, PREC_FP32, 0, c->zchunk,
+                                        err, c->stream);
             A.fset ^= 1;
             std::swap(A.mu, A.mu_alt);
             for (int ax = 0; ax < 3; ax++) std::swap(A.nu[ax], A.nu_alt[ax]);

@@ -25,17 +25,19 @@ cudaError_t acoustic_stream_half_step(const AcParams &prm, int prec, int comp, i
                                       int zchunk, cudaStream_t st);
 
 // One-pass 3D step (fused velocity and pressure half steps) with a TMA
-// shared-memory pipeline; reads in[] (p, vx, vy, vz, tvx, tvy, tvz), writes
-// out[], t_p in place. maps: the tensor maps of the input set (from
-// acoustic_fused_encode). err: device word set to 1 if a bounded wait expires.
+// shared-memory pipeline; reads in[] (p, vx, vy, vz, tvx, tvy, tvz) and tp,
+// writes out[] and tp_out (= tp: t_p in place; the pair precision, whose
+// stencils read t_p in the halos, gives the other set's t_p). maps: the tensor
+// maps of the input set (from acoustic_fused_encode, with that set's t_p). err:
+// device word set to 1 if a bounded wait expires.
 bool acoustic_fused_supported(const AcParams &prm, int ndim, int prec);
 unsigned acoustic_fused_blocks(const AcParams &prm, int prec, int zchunk);
 size_t fused_maps_bytes();
 bool acoustic_fused_encode(void *out_maps, const AcParams &prm, const void *const in[7], const void *tp,
                            int prec, int comp);
 cudaError_t acoustic_fused_step(const AcParams &prm, const void *maps, const void *const in[7],
-                                void *const out[7], void *tp, int prec, int comp, int zchunk, int *err,
-                                cudaStream_t st);
+                                void *const out[7], void *tp, void *tp_out, int prec, int comp, int zchunk,
+                                int *err, cudaStream_t st);
 
 // Cluster-resident 2D steps (acoustic2d_cluster.cu): the whole state of a
 // small 2D grid in the shared memory of one cluster of up to 16 CTAs, any

@@ -19,7 +19,7 @@ VARIANTS = [("fp16", 0), ("fp16", 3), ("fp16", 6), ("bf16", 0), ("bf16", 3), ("b
             ("fp32", 0), ("fp32", 3), ("fp16_f32arith", 0), ("fp16_f32arith", 3),
             ("bf16_f32arith", 3), ("fp16_pairs", 3)]
 # (kernel, precision, compensation); the one-pass strips read stored values only
-KVARIANTS = [(k, p, c) for k in (0, 1, 2, 3) for p, c in VARIANTS if not (k == 3 and p in PAIRS)]
+KVARIANTS = [(k, p, c) for k in (4, 1, 2, 3) for p, c in VARIANTS if not (k == 3 and p in PAIRS)]
 
 
 def _media(shape, seed, h):
@@ -60,7 +60,7 @@ def _run(shape, bc, prec, comp, steps, seed=0, variable=True, src=False, kernel=
 R, P = O.BC_RIGID, O.BC_PERIODIC
 
 
-# kernel 0 (the default): for these sizes the cluster-resident steps (the whole
+# kernel 4 (the default for small grids): cluster-resident steps (the whole
 # state in one cluster's shared memory, bands of rows per CTA, rows past a band
 # read from the neighbouring CTA); kernel 1: one thread per point; kernel 2:
 # row strips, one launch per half step; kernel 3: one-pass row strips (both
@@ -75,7 +75,7 @@ def test_2d_bit_exact_periodic_source(prec, comp, kernel):
     _run((64, 40), (P, P), prec, comp, 25, src=True, kernel=kernel)
 
 
-@pytest.mark.parametrize("kernel", [0, 2, 3])
+@pytest.mark.parametrize("kernel", [4, 2, 3])
 @pytest.mark.parametrize("shape", [(257, 33), (300, 70), (8, 200), (513, 9), (265, 40), (520, 17)])
 def test_2d_strips_ragged_wide_and_tall(shape, kernel):
     # strips of 256 points (128 for binary32) cut by the grid's x extent, rows
@@ -384,6 +384,23 @@ def test_2d_cluster_largest_grid_and_fit_limit():
         assert np.isfinite(W.wave_energy(ctx))
     finally:
         W.wave_destroy(ctx)
+
+
+def test_2d_default_kernel_choice():
+    """Kernel 0 takes the cluster-resident steps (one launch per call) for a
+    256^2 grid and the row strips (one launch sequence per step) for 384^2."""
+    for side, launches in ((256, 1), (384, 10)):
+        shape = (side, side)
+        ones = np.ones(shape)
+        ctx = W.wave_create(shape, 1.0 / side, ones, ones, 0.5 / side, W.WAVE_FP16, 3, bc=[1] * 6)
+        try:
+            W.wave_set_initial(ctx, W.WAVE_F_P, inputs.gaussian(shape, 1.0 / side, 0.05))
+            W.wave_set_timing(ctx, True)
+            W.wave_step(ctx, 10)
+            n, _ = W.wave_get_timing(ctx, 3)
+            assert n == launches, (side, n)
+        finally:
+            W.wave_destroy(ctx)
 
 
 def test_bounded_wait_expiry_reports_timeout_and_leaves_gpu_usable():

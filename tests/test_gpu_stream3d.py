@@ -14,7 +14,7 @@ import pytest
 import oracle as O
 from paper_2310_00236_gb300 import inputs
 from paper_2310_00236_gb300 import wave as W
-from wave_helpers import PREC, acoustic_pair, compare_acoustic, gpu_bits, to_bits
+from wave_helpers import PAIRS, PREC, acoustic_pair, compare_acoustic, gpu_bits, to_bits
 
 pytestmark = pytest.mark.gpu
 R, P = O.BC_RIGID, O.BC_PERIODIC
@@ -90,7 +90,7 @@ def _subbox_expect(w, st_full, prec, comp, steps, points):
         hi = [min(n, c + M + 1) for c in (i, j, k)]
         sl = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
         shape = (hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2])
-        cfg = O.acoustic_cfg(shape, (R, R, R), sfmt, comp, afmt)
+        cfg = O.acoustic_cfg(shape, (R, R, R), sfmt, comp, afmt, pair_stencil=prec in PAIRS)
         st = O.AcousticState(cfg)
         st.a = [np.ascontiguousarray(st_full["a"][ax][sl]) for ax in range(3)]
         st.b = np.ascontiguousarray(st_full["b"][sl])
@@ -108,7 +108,7 @@ def _subbox_expect(w, st_full, prec, comp, steps, points):
     return out
 
 
-@pytest.mark.parametrize("prec,comp,kernel", [("fp16", 3, 0), ("fp32", 0, 0), ("fp16", 3, 3)])
+@pytest.mark.parametrize("prec,comp,kernel", [("fp16", 3, 0), ("fp32", 0, 0), ("fp16", 3, 3), ("fp16_pairs", 3, 0)])
 def test_full_size_512_sampled_bit_exact(prec, comp, kernel):
     """The benchmark workload's grid and media (512^3, smooth random velocity,
     rho = 1000, p = 0 walls, CFL 0.4) in the benchmark's launch configuration,
@@ -138,8 +138,9 @@ def test_full_size_512_sampled_bit_exact(prec, comp, kernel):
                 got["tv%d" % ax] = gpu_bits(W.wave_get_raw(ctx, W.WAVE_F_VX + ax, 1))
     finally:
         W.wave_destroy(ctx)
-    # full-grid coefficients and scaled initial pressure from the oracle
-    cfg = O.acoustic_cfg(w["shape"], (R, R, R), sfmt, comp, afmt)
+    # full-grid coefficients (binary32 for the pair precision) and scaled
+    # initial pressure from the oracle
+    cfg = O.acoustic_cfg(w["shape"], (R, R, R), O.FP32 if prec in PAIRS else sfmt, comp, afmt)
     a, b, Z0, ok = O.acoustic_coefficients(cfg, w["h"], w["dt"], w["P0"], w["rho"], w["c"])
     assert ok
     p = O.scale_pressure(w["p0"], w["P0"], sfmt).reshape(w["p0"].shape)
@@ -168,7 +169,7 @@ def test_full_size_512_sampled_bit_exact(prec, comp, kernel):
 
 
 # ------------------------------------------------------ one-pass step (fused)
-FUSED_VARIANTS = VARIANTS
+FUSED_VARIANTS = VARIANTS + [("fp16_pairs", 3)]
 
 
 def _uniform_rho_run(shape, bc, prec, comp, steps, zchunk, src=False, energy=True, seed=0):
@@ -219,9 +220,11 @@ def test_fused_rigid_y_faces_every_tail(ny):
     tile spanning both faces."""
     _uniform_rho_run((64, ny, 11), (R, R, R), "fp16", 3, 9, zchunk=4, src=True)
     _uniform_rho_run((32, ny, 9), (R, R, P), "fp32", 0, 6, zchunk=3)
+    _uniform_rho_run((64, ny, 10), (R, R, P), "fp16_pairs", 3, 7, zchunk=3, src=True)
 
 
-@pytest.mark.parametrize("prec,comp", [("fp16", 3), ("bf16", 6), ("fp32", 0), ("fp16_f32arith", 3)])
+@pytest.mark.parametrize("prec,comp", [("fp16", 3), ("bf16", 6), ("fp32", 0), ("fp16_f32arith", 3),
+                                       ("fp16_pairs", 3)])
 def test_fused_periodic_mixed_source(prec, comp):
     """Periodic y and z, rigid x (the one-pass step reads rigid x images)."""
     nx = 192 if prec != "fp32" else 96
