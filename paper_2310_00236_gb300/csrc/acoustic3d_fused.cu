@@ -95,7 +95,9 @@ struct FShape {
 };
 
 template <class P, int COMP, bool ENERGY>
-__global__ void __launch_bounds__(160, IsPairs<P>::value ? 2 : 4)
+// (the pair kernel: three CTAs per SM at 128 registers; its energy variant,
+// launched on a call's last step, two, to stay free of spills)
+__global__ void __launch_bounds__(160, IsPairs<P>::value ? (ENERGY ? 2 : 3) : 4)
     fused_step(const __grid_constant__ FusedParams fp, const __grid_constant__ FusedMaps maps) {
     using SH = FShape<P>;
     constexpr bool PAIRS = SH::PAIRS;
@@ -392,9 +394,9 @@ __global__ void __launch_bounds__(160, IsPairs<P>::value ? 2 : 4)
     };
 
     Raw vzq0 = V::zero(), vzq1 = V::zero(), vzq2 = V::zero(), vzq3 = V::zero();
-    // the pairs: T of the new v_z queue and of the p planes
-    Raw tzq0 = V::zero(), tzq1 = V::zero(), tzq2 = V::zero(), tzq3 = V::zero();
-    Raw tq0 = V::zero(), tq1 = V::zero(), tq2 = V::zero();
+    // the pairs: queues of the taps RN(V + T) themselves (each formed once):
+    // p of planes k .. k+3 and the new v_z of planes k-2 .. k+1
+    AV ps0{}, ps1{}, ps2{}, ps3{}, zs0{}, zs1{}, zs2{}, zs3{};
     int oc = 0, p_waited = 0;
     // ring positions kept incrementally (no division by the ring depth):
     // the next p stage to wait for and its phase, the slot of plane k
@@ -427,7 +429,7 @@ __global__ void __launch_bounds__(160, IsPairs<P>::value ? 2 : 4)
         // ---- v_z^{n+1/2} at plane k+1 of the own vector (p^n planes k..k+3)
         Raw vzn = V::zero(), tzn = V::zero();
         const bool inner_z = k >= 0 && k + 3 < nz;  // planes k..k+3 inside the grid
-        Raw pq3 = V::zero(), tq3 = V::zero();
+        Raw pq3 = V::zero();
         if (active) {
             // plane k + t of p (off = 0) or t_p (off = P_ELEMS)
             auto plane = [&](int t, int off) -> Raw {
@@ -436,19 +438,24 @@ __global__ void __launch_bounds__(160, IsPairs<P>::value ? 2 : 4)
                 const Raw r = p_vec(pring + sl * SH::P_SLOT + off, row);
                 return inner_z ? r : signed_raw<V>(r, plane_sign(k + t));
             };
-            if (k == z0 - 3) {
-                pq0 = plane(0, 0);
-                pq1 = plane(1, 0);
-                pq2 = plane(2, 0);
-                if (PAIRS) {
-                    tq0 = plane(0, SH::P_ELEMS);
-                    tq1 = plane(1, SH::P_ELEMS);
-                    tq2 = plane(2, SH::P_ELEMS);
+            AV D;
+            if constexpr (PAIRS) {
+                if (k == z0 - 3) {
+                    ps0 = tap(plane(0, 0), plane(0, SH::P_ELEMS));
+                    ps1 = tap(plane(1, 0), plane(1, SH::P_ELEMS));
+                    ps2 = tap(plane(2, 0), plane(2, SH::P_ELEMS));
                 }
+                ps3 = tap(plane(3, 0), plane(3, SH::P_ELEMS));
+                D = vstencil<V>(ps0, ps1, ps2, ps3);
+            } else {
+                if (k == z0 - 3) {
+                    pq0 = plane(0, 0);
+                    pq1 = plane(1, 0);
+                    pq2 = plane(2, 0);
+                }
+                pq3 = plane(3, 0);
+                D = vstencil<V>(V::ld(pq0), V::ld(pq1), V::ld(pq2), V::ld(pq3));
             }
-            pq3 = plane(3, 0);
-            if (PAIRS) tq3 = plane(3, SH::P_ELEMS);
-            const AV D = vstencil<V>(tap(pq0, tq0), tap(pq1, tq1), tap(pq2, tq2), tap(pq3, tq3));
             vzn = vec_at(ost + SH::O_VZ + row * TX + lx * VEC);
             tzn = COMP ? vec_at(ost + SH::O_TVZ + row * TX + lx * VEC) : V::zero();
             V::template update<COMP>(vzn, tzn, V::mul(az, D));
@@ -459,7 +466,7 @@ __global__ void __launch_bounds__(160, IsPairs<P>::value ? 2 : 4)
             }
         }
         vzq3 = vzn;
-        tzq3 = tzn;
+        if constexpr (PAIRS) zs3 = tap(vzn, tzn);
 
         if (k >= z0) {
             S *nvx = nbuf;
@@ -485,7 +492,9 @@ __global__ void __launch_bounds__(160, IsPairs<P>::value ? 2 : 4)
                 RS l0, r0, r1, l0t = RS(0), r0t = RS(0), r1t = RS(0);
                 xn(prow, l0, r0, r1);
                 if (PAIRS) xn(trow, l0t, r0t, r1t);
-                const AV own = tap(pq0, tq0);
+                AV own;
+                if constexpr (PAIRS) own = ps0;
+                else own = V::ld(pq0);
                 const typename V::AS al0 = tap_s(l0, l0t), ar0 = tap_s(r0, r0t), ar1 = tap_s(r1, r1t);
                 const AV D = vstencil<V>(V::shr1(own, al0), own, V::shl1(own, ar0), V::shl2(own, ar0, ar1));
                 vxn = vec_at(ost + SH::O_VX + row * WIDE + HALO + lx * VEC);
@@ -565,7 +574,9 @@ __global__ void __launch_bounds__(160, IsPairs<P>::value ? 2 : 4)
                 };
                 const AV Dy = vstencil<V>(vy_tap(0), vy_tap(1), vy_tap(2), vy_tap(3));
                 R = V::add(R, Dy);
-                const AV Dz = vstencil<V>(tap(vzq0, tzq0), tap(vzq1, tzq1), tap(vzq2, tzq2), tap(vzq3, tzq3));
+                AV Dz;
+                if constexpr (PAIRS) Dz = vstencil<V>(zs0, zs1, zs2, zs3);
+                else Dz = vstencil<V>(V::ld(vzq0), V::ld(vzq1), V::ld(vzq2), V::ld(vzq3));
                 R = V::add(R, Dz);
                 if (k == prm.src_k && j == prm.src_j && prm.src_i >= x && prm.src_i < x + VEC &&
                     prm.step < prm.src_nt) {
@@ -587,7 +598,11 @@ __global__ void __launch_bounds__(160, IsPairs<P>::value ? 2 : 4)
                 } else {
                     bc = prm.b ? V::ld(bv) : V::splat(V::lds(b_raw));
                 }
-                const Raw pold = pq0;
+                // p^n of the own vector (the pairs keep only the taps in
+                // registers: p from the ring's plane k, inside the grid)
+                Raw pold;
+                if constexpr (PAIRS) pold = p_vec(pk, row);
+                else pold = pq0;
                 Raw pn = pold;
                 V::template update<COMP>(pn, tpn, V::mul(bc, R));
                 at<V>(fp.p_out, q) = pn;
@@ -603,7 +618,11 @@ __global__ void __launch_bounds__(160, IsPairs<P>::value ? 2 : 4)
                         float bw;
                         if constexpr (PAIRS) bw = V::aget(bc, e);
                         else bw = prm.b ? V::f32(bv, e) : P::to_f32(b_raw);
-                        const float fx = V::f32(vxn, e), fy = V::f32(vyn, e), fz = V::f32(vzq2, e);
+                        // (the pairs keep only the v_z taps in registers: the
+                        // stored v_z of plane k, written by this thread one
+                        // plane ago)
+                        const float fx = V::f32(vxn, e), fy = V::f32(vyn, e),
+                                    fz = V::f32(PAIRS ? at<V>(fp.vz_out, q) : vzq2, e);
                         float t = e_term(V::f32(pold, e), V::f32(pn, e), bw);
                         t = __fadd_rn(t, __fmul_rn(__fmul_rn(fx, fx), ia0));
                         t = __fadd_rn(t, __fmul_rn(__fmul_rn(fy, fy), ia1));
@@ -624,15 +643,15 @@ __global__ void __launch_bounds__(160, IsPairs<P>::value ? 2 : 4)
         vzq0 = vzq1;
         vzq1 = vzq2;
         vzq2 = vzq3;
-        tzq0 = tzq1;
-        tzq1 = tzq2;
-        tzq2 = tzq3;
+        zs0 = zs1;
+        zs1 = zs2;
+        zs2 = zs3;
         pq0 = pq1;
         pq1 = pq2;
         pq2 = pq3;
-        tq0 = tq1;
-        tq1 = tq2;
-        tq2 = tq3;
+        ps0 = ps1;
+        ps1 = ps2;
+        ps2 = ps3;
     }
     if (ENERGY) {
         double val = ok ? (double)e_s + (double)e_c : 0.0;
@@ -672,13 +691,22 @@ static cudaError_t launch_t(const FusedParams &fp, const FusedMaps &maps, bool e
     dim3 grid(fp.a.n[0] / SH::TX, (fp.a.n[1] + SH::TY - 1) / SH::TY,
               (fp.a.n[2] + fp.zchunk - 1) / fp.zchunk);
     const int smem = (int)SH::SMEM;
+    // the pair kernel (74.75 KiB, at most 128 registers) fits three CTAs per SM
+    // only with the whole shared-memory carveout (3 x 75.75 of 228 KiB)
+    const int carveout = SH::PAIRS ? 100 : -1;
     cudaError_t e;
     if (energy) {
         e = cudaFuncSetAttribute(fused_step<P, COMP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess && carveout >= 0)
+            e = cudaFuncSetAttribute(fused_step<P, COMP, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     carveout);
         if (e != cudaSuccess) return e;
         fused_step<P, COMP, true><<<grid, 160, smem, st>>>(fp, maps);
     } else {
         e = cudaFuncSetAttribute(fused_step<P, COMP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess && carveout >= 0)
+            e = cudaFuncSetAttribute(fused_step<P, COMP, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     carveout);
         if (e != cudaSuccess) return e;
         fused_step<P, COMP, false><<<grid, 160, smem, st>>>(fp, maps);
     }
