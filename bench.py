@@ -42,6 +42,9 @@ BYTES = {
     ("fp32", False): {"kv": 4 + 12 + 12, "kp": 12 + 4 + 4 + 4, "fused": (4 + 12 + 4) + (4 + 12)},
     ("fp32", True): {"kv": 4 + 12 + 12 + 12 + 12, "kp": 12 + 4 + 4 + 4 + 4 + 4,
                      "fused": (4 + 4 + 12 + 12 + 4) + (4 + 4 + 12 + 12)},
+    # the pair precision on the one-pass step (its only fast 3D kernel): b in
+    # binary32, t_p read from one buffer set and written to the other
+    ("fp16_pairs", True): {"fused": (2 + 2 + 6 + 6 + 4) + (2 + 2 + 6 + 6)},
 }
 # Acoustic 2D fp16 + compensation, uniform a, per-point b, both half steps:
 #   velocity: read p + v(2) + t_v(2), write v(2) + t_v(2)   = 2 + 8 + 8
@@ -744,6 +747,9 @@ def main():
                     help="run one secondary workload alone and print its JSON (profiling aid)")
     ap.add_argument("--kernel", type=int, default=0,
                     help="0 automatic, 1 one-thread-per-point, 2 two-kernel streaming")
+    ap.add_argument("--precision", default="fp16", choices=["fp16", "fp16_pairs"],
+                    help="precision of the timed workload (compensated): fp16 + sum_3op, the configured "
+                         "one, or the pair precision (profiling aid)")
     args = ap.parse_args()
     global ZCHUNK, KERNEL
     ZCHUNK = args.zchunk
@@ -791,7 +797,7 @@ def main():
         gpu_id = str(local)
     sampler = ClockSampler(gpu_id)
     sampler.start()
-    r16 = run_variant(W, w, "fp16", 3, args.steps, args.warmup)
+    r16 = run_variant(W, w, args.precision, 3, args.steps, args.warmup)
     clocks = sampler.stop()
     t_max = max_over_ranks(r16["ms"], ws, device="cuda")
     value = npts * args.steps * ws / (t_max * 1e-3) / 1e9
@@ -800,13 +806,15 @@ def main():
     kt = r16["kt"]
     dom = max(kt, key=lambda k: kt[k][1])
     nl, kms = kt[dom]
-    bpp = BYTES[("fp16", True)][dom]
+    if dom not in BYTES[(args.precision, True)]:
+        raise SystemExit(f"no algorithmic byte count for {args.precision} on the {dom} kernel")
+    bpp = BYTES[(args.precision, True)][dom]
     achieved = bpp * npts / (kms / nl * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": KERNEL_NAMES[dom],
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "frac_of_nominal_7900": achieved / 7900.0,
             "peak_kind": peak_kind,
-            "traffic": (lambda t: None if t is None else t * npts)(measured_traffic_per_point(dom, "fp16", True)),
+            "traffic": (lambda t: None if t is None else t * npts)(measured_traffic_per_point(dom, args.precision, True)),
             "traffic_sources_sha256": sources_sha(dom),
             "bytes_per_point": bpp, "ms_per_launch": kms / nl,
             "shares": {k: kt[k][1] / sum(v[1] for v in kt.values()) for k in kt}}
@@ -855,7 +863,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
                 "config": {"workload": "3d_acoustic_random_velocity_rigid_gaussian",
                            "n": args.n, "cells": npts, "h_m": w["h"], "cfl": 0.4,
-                           "precision": "fp16", "compensation": "sum_3op",
+                           "precision": args.precision, "compensation": "sum_3op",
                            "l2": "working set 2.4 GB > L2 (no flush needed)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": sum(v[0] for v in kt.values()), "compare": compare,
