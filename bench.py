@@ -409,9 +409,17 @@ def run_elastic(W, steps: int, warmup: int):
     finally:
         W.wave_destroy(ctx)
     npts = w["shape"][0] * w["shape"][1]
+    gpts = npts * steps / (ms * 1e-3) / 1e9
+    # algorithmic state traffic per point and step (the layered media give
+    # per-point multipliers): velocity launch reads v, t_v, the three
+    # stresses, b_x, b_y (18 B) and writes v, t_v (8 B); stress launch reads
+    # the stresses, their t, v, l2m, lam, mu (22 B) and writes the stresses
+    # and their t (12 B). The ~31 MB state stays in L2.
+    bpp = (18 + 8) + (22 + 12)
     return {"workload": "2d_elastic_1024_three_layers_free_top", "precision": "fp16",
-            "compensation": "sum_6op", "value": npts * steps / (ms * 1e-3) / 1e9, "unit": UNIT,
-            "ms_per_step": ms / steps, "energy_drift_after_source": abs(e1 - e0) / abs(e0)}
+            "compensation": "sum_6op", "value": gpts, "unit": UNIT,
+            "ms_per_step": ms / steps, "energy_drift_after_source": abs(e1 - e0) / abs(e0),
+            "state_bytes_per_point_step": bpp, "state_gbs": bpp * gpts, "resident": "L2"}
 
 
 def run_batched(W, steps: int, warmup: int, nshots: int = 64):
