@@ -49,18 +49,21 @@ struct Band {
     using Raw = typename V::Raw;
     using RS = typename V::RS;
     RS *base;      // this CTA's slots
-    int64_t slot;  // elements per slot (R * pitch)
-    int64_t sp;    // row pitch (elements), that of the global arrays
+    int slot;      // elements per slot (R * pitch; a band fits in shared memory)
+    int sp;        // row pitch (elements), that of the global arrays
     int R;         // rows per band
     int r0, r1;    // this band's rows [r0, r1)
     int rank;
 
-    __device__ __forceinline__ RS *own_row(int a, int j) const { return base + a * slot + (int64_t)(j - r0) * sp; }
-    // Row jy of slot a (0 <= jy < ny), in whichever band holds it.
+    __device__ __forceinline__ RS *own_row(int a, int j) const { return base + (a * slot + (j - r0) * sp); }
+    // Row jy of slot a (0 <= jy < ny), in whichever band holds it. A row
+    // less than one band height above or below this band is in the
+    // neighbouring band (bands start at multiples of R); others (the images
+    // of periodic y walls wrap across the grid) take the division.
     __device__ __forceinline__ const RS *row(int a, int jy) const {
-        const int owner = jy / R;
-        RS *p = base + a * slot + (int64_t)(jy - owner * R) * sp;
-        if (owner == rank) return p;
+        if (jy >= r0 && jy < r1) return own_row(a, jy);
+        const int owner = (jy >= r0 - R && jy < r0 + 2 * R) ? (jy < r0 ? rank - 1 : rank + 1) : jy / R;
+        RS *p = base + (a * slot + (jy - owner * R) * sp);
         return cg::this_cluster().map_shared_rank(p, (unsigned)owner);
     }
     // Row my at x (a whole vector) with the y boundary image (as row_vec of
@@ -296,13 +299,13 @@ __global__ void __launch_bounds__(kWarps * 32, 1) cluster_steps(ClusterRun run, 
     extern __shared__ __align__(16) unsigned char smem[];
     Band<V> B;
     B.base = reinterpret_cast<RS *>(smem);
-    B.sp = prm.sy;
-    B.slot = (int64_t)R * prm.sy;
+    B.sp = (int)prm.sy;
+    B.slot = R * (int)prm.sy;
     B.R = R;
     B.r0 = min(rank * R, ny);
     B.r1 = min(B.r0 + R, ny);
     B.rank = rank;
-    double *e_part = reinterpret_cast<double *>(smem + (size_t)NA * B.slot * sizeof(RS));  // kWarps + 1
+    double *e_part = reinterpret_cast<double *>(smem + (size_t)NA * (size_t)B.slot * sizeof(RS));  // kWarps + 1
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     // this band of every array into shared memory (16-byte copies: the pitch
