@@ -140,8 +140,12 @@ __device__ __forceinline__ StripItem strip_of(const int *s_item0, int nshots, in
 }
 
 // Velocity half step of one strip: v_x += a_x Dx(p), v_y += a_y Dy(p), row by row.
+// (Both strip kernels are bounded to 80 registers, three blocks of 256 threads
+// per SM: the strips wait on global loads, and 24 warps per SM instead of 16
+// hide more of it: 64 shots 136 -> 152 Gpt/s, 8192^2 171 -> 183, at a few
+// bytes of spills.)
 template <class P, int COMP>
-__global__ void __launch_bounds__(256) batch_kv_strip(BatchShot *shots, const int *item0,
+__global__ void __launch_bounds__(256, 3) batch_kv_strip(BatchShot *shots, const int *item0,
                                                       int nshots, int nitems, int yc) {
     advance_counters(shots, nshots);
     using V = typename VecOf<P>::T;
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(256) batch_kv_strip(BatchShot *shots, const in
 // Pressure half step of one strip: p += b (Dx v_x + Dy v_y [+ s]), with the
 // item's energy terms p^n p^{n+1} / b + v_x^2 / a_x + v_y^2 / a_y.
 template <class P, int COMP, bool ENERGY>
-__global__ void __launch_bounds__(256) batch_kp_strip(const BatchShot *__restrict__ shots, const int *item0,
+__global__ void __launch_bounds__(256, 3) batch_kp_strip(const BatchShot *__restrict__ shots, const int *item0,
                                                       int nshots, int nitems, int yc, double *item_part) {
     using V = typename VecOf<P>::T;
     using Raw = typename V::Raw;
