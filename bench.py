@@ -751,7 +751,7 @@ def main():
     ap.add_argument("--zchunk", type=int, default=0, help="z planes per block (0: library default)")
     ap.add_argument("--shots", type=int, default=16, help="shots of the adjoint leg")
     ap.add_argument("--leg", default="all",
-                    choices=["all", "batched", "adjoint", "elastic", "w0", "accuracy", "cpu_baseline"],
+                    choices=["all", "batched", "adjoint", "elastic", "w0", "accuracy", "cfg1", "cpu_baseline"],
                     help="run one secondary workload alone and print its JSON (profiling aid)")
     ap.add_argument("--kernel", type=int, default=0,
                     help="0 automatic, 1 one-thread-per-point, 2 two-kernel streaming")
@@ -786,6 +786,8 @@ def main():
             out = run_w0(W)
         elif args.leg == "accuracy":
             out = run_accuracy(W)
+        elif args.leg == "cfg1":
+            out = run_cfg1(W)
         elif args.leg == "adjoint":
             out = run_adjoint(W, args.steps, n=args.n if args.n != 512 else 256, nshots=args.shots)
         else:
