@@ -245,17 +245,17 @@ def run_accuracy(W):
     """Accuracy of every variant on the GPU path: relative L2 distance of the
     final pressure field to the binary32 run of the same problem, and the
     largest relative energy change over the run (energy after every step).
-    Workloads: config 1 (256^2, rho = c = 1, p = 0 walls, centred Gaussian,
+    Workloads: the 2D acoustic 256^2 problem (rho = c = 1, p = 0 walls, centred Gaussian,
     CFL 0.5, 2000 steps) and the 3D benchmark recipe at 256^3 (velocity filter
     width 8 cells, Gaussian of 6 cells, CFL 0.4, 400 steps). The binary32 run
     stands in for binary64 (the GPU has no binary64 path): the oracle puts its
-    own distance to binary64 at 1.5e-6 (config 1) and 5e-7 (the 3D recipe)."""
+    own distance to binary64 at 1.5e-6 (2D 256^2) and 5e-7 (the 3D recipe)."""
     import torch
     from paper_2310_00236_gb300 import inputs
-    cases = {"cfg1_256_cfl0.5_2000": (inputs.acoustic_2d_gaussian(256, 2000), 2000),
-             "cfg3_recipe_256_cfl0.4_400": (inputs.acoustic_3d_random(n=256, sigma_cells=8.0,
+    cases = {"acoustic2d_256_cfl0.5_2000": (inputs.acoustic_2d_gaussian(256, 2000), 2000),
+             "acoustic3d_recipe_256_cfl0.4_400": (inputs.acoustic_3d_random(n=256, sigma_cells=8.0,
                                                                       ic_sigma_cells=6.0), 400)}
-    out = {"reference": "fp32 on the GPU (oracle distance to binary64: 1.5e-6 cfg1, 5e-7 3D recipe)"}
+    out = {"reference": "fp32 on the GPU (oracle distance to binary64: 1.5e-6 2D 256^2, 5e-7 3D recipe)"}
     stream = torch.cuda.Stream()
     for key, (w, steps) in cases.items():
         nd = len(w["shape"])
@@ -286,7 +286,7 @@ def pareto(variants, accuracy):
     """(Gpoint-updates/s on the 512^3 benchmark, energy drift and relative L2
     on the 3D recipe at 256^3) per variant, and whether no other variant is
     at least as good in all three and better in one."""
-    acc = accuracy["cfg3_recipe_256_cfl0.4_400"]
+    acc = accuracy["acoustic3d_recipe_256_cfl0.4_400"]
     rows = []
     for name, v in variants.items():
         if name not in acc:
@@ -302,7 +302,7 @@ def pareto(variants, accuracy):
     return rows
 
 
-def _cfg1_time(W, w, steps, kernel, prec=None, comp=None):
+def _acoustic2d_256_time(W, w, steps, kernel, prec=None, comp=None):
     import torch
     stream = torch.cuda.Stream()  # a created stream: the row strips replay step graphs on it
     prec = W.WAVE_FP16 if prec is None else prec
@@ -328,7 +328,7 @@ def _cfg1_time(W, w, steps, kernel, prec=None, comp=None):
     return ms, abs(e1 - e0) / abs(e0)
 
 
-def run_cfg1(W, steps=2000):
+def run_acoustic2d_256(W, steps=2000):
     """The 2D acoustic configuration (256^2, rho = c = 1, p = 0 walls, centred
     Gaussian, CFL 0.5), fp16 + sum_3op, 2000 steps in one wave_step call: the
     cluster-resident steps (the default for this size: the whole state in the
@@ -342,10 +342,10 @@ def run_cfg1(W, steps=2000):
     out = {"workload": "2d_acoustic_256_gaussian_rigid_cfl0.5", "precision": "fp16", "compensation": "sum_3op",
            "steps": steps, "unit": UNIT, "state_bytes_per_point_step": 24}
     for name, kernel in (("cluster", 4), ("strips", 2)):
-        ms, drift = _cfg1_time(W, w, steps, kernel)
+        ms, drift = _acoustic2d_256_time(W, w, steps, kernel)
         out[name] = {"value": npts * steps / (ms * 1e-3) / 1e9, "us_per_step": ms * 1e3 / steps,
                      "state_gbs": 24 * npts * steps / (ms * 1e-3) / 1e9, "energy_drift": drift}
-    ms, drift = _cfg1_time(W, w, steps, 4, W.WAVE_FP32, 0)
+    ms, drift = _acoustic2d_256_time(W, w, steps, 4, W.WAVE_FP32, 0)
     out["cluster_fp32"] = {"value": npts * steps / (ms * 1e-3) / 1e9, "us_per_step": ms * 1e3 / steps,
                            "energy_drift": drift}
     out["value"] = out["cluster"]["value"]
@@ -641,8 +641,8 @@ def oracle_sample(target_s: float = 12.0, n: int = 64):
 def oracle_per_config(budget: float = 2.0):
     """CPU baseline per workload: the oracle's binary64 solver and its fp16
     emulation (sum_3op acoustic, sum_6op elastic), on one thread and on every
-    host core, in Mpoint-updates/s: config 1 (2D acoustic 256^2), a 64^3
-    sample of the 3D recipe, config 2 (2D elastic 1024^2). Each figure times
+    host core, in Mpoint-updates/s: the 2D acoustic 256^2 problem, a 64^3
+    sample of the 3D recipe, the 2D elastic 1024^2 problem. Each figure times
     about `budget` seconds of steps after one untimed step."""
     import oracle as O
     from paper_2310_00236_gb300 import inputs
@@ -675,9 +675,9 @@ def oracle_per_config(budget: float = 2.0):
 
     cores = O.set_threads()
     out = {"kind": "oracle", "unit": "Mpoint-updates/s", "cores": cores, "nproc": os.cpu_count()}
-    cases = [("cfg1_2d_acoustic_256", 256 * 256, acoustic(w1, O.FP64, 0), acoustic(w1, O.FP16, 3)),
-             ("cfg3_3d_acoustic_sample_64", 64 ** 3, acoustic(w3, O.FP64, 0), acoustic(w3, O.FP16, 3)),
-             ("cfg2_2d_elastic_1024", 1024 * 1024, elastic(O.FP64, 0), elastic(O.FP16, 6))]
+    cases = [("acoustic2d_256", 256 * 256, acoustic(w1, O.FP64, 0), acoustic(w1, O.FP16, 3)),
+             ("acoustic3d_sample_64", 64 ** 3, acoustic(w3, O.FP64, 0), acoustic(w3, O.FP16, 3)),
+             ("elastic2d_1024", 1024 * 1024, elastic(O.FP64, 0), elastic(O.FP16, 6))]
     try:
         for name, pts, m64, m16 in cases:
             row = {}
@@ -761,7 +761,7 @@ def main():
     ap.add_argument("--zchunk", type=int, default=0, help="z planes per block (0: library default)")
     ap.add_argument("--shots", type=int, default=16, help="shots of the adjoint leg")
     ap.add_argument("--leg", default="all",
-                    choices=["all", "batched", "adjoint", "elastic", "w0", "accuracy", "cfg1", "cpu_baseline"],
+                    choices=["all", "batched", "adjoint", "elastic", "w0", "accuracy", "acoustic2d_256", "cpu_baseline"],
                     help="run one secondary workload alone and print its JSON (profiling aid)")
     ap.add_argument("--kernel", type=int, default=0,
                     help="0 automatic, 1 one-thread-per-point, 2 two-kernel streaming")
@@ -796,8 +796,8 @@ def main():
             out = run_w0(W)
         elif args.leg == "accuracy":
             out = run_accuracy(W)
-        elif args.leg == "cfg1":
-            out = run_cfg1(W)
+        elif args.leg == "acoustic2d_256":
+            out = run_acoustic2d_256(W)
         elif args.leg == "adjoint":
             out = run_adjoint(W, args.steps, n=args.n if args.n != 512 else 256, nshots=args.shots)
         else:
@@ -854,12 +854,12 @@ def main():
     adjoint = None
     variants = None
     accuracy = None
-    cfg1 = None
+    acoustic2d_256 = None
     if not args.no_compare:
         variants = run_variants(W, w, min(args.steps, 100))
         accuracy = run_accuracy(W)
         accuracy["pareto"] = pareto(variants, accuracy)
-        cfg1 = run_cfg1(W)
+        acoustic2d_256 = run_acoustic2d_256(W)
         adjoint = run_adjoint(W, min(args.steps, 1500))
         elastic = run_elastic(W, min(args.steps, 4000), args.warmup)
         batched = run_batched(W, min(args.steps, 3000), args.warmup)
@@ -889,7 +889,7 @@ def main():
                 "gpu_launches": sum(v[0] for v in kt.values()), "compare": compare,
                 "elastic": elastic, "batched": batched, "adjoint": adjoint, "variants": variants,
                 "accuracy": accuracy,
-                "cfg1": cfg1,
+                "acoustic2d_256": acoustic2d_256,
                 "energy_drift": drift16}
         print(json.dumps(line), flush=True)
 

@@ -14,7 +14,7 @@ from the paper's method (half storage and arithmetic, plain or sum_3op), the
 binary32-register variant, and a stencil that reads the stored pair V + T
 (not the paper's scheme) with binary32 weight and multipliers.
 
-Usage: python tests/accuracy_split.py [cfg1] [w0] [cfg3] [--small]
+Usage: python tests/accuracy_split.py [acoustic2d_256] [w0] [acoustic3d_recipe] [--small]
 """
 from __future__ import annotations
 
@@ -45,13 +45,13 @@ VARIANTS = [
 ]
 
 
-def cfg1(small=False):
+def acoustic2d_256(small=False):
     """2D, rho = c = 1, p = 0 walls, centred Gaussian (sigma 0.05), CFL 0.5."""
     n, steps = (128, 1000) if small else (256, 2000)
     h = 1.0 / n
     x = np.arange(n) * h
     X, Y = np.meshgrid(x, x)
-    return dict(name=f"cfg1 {n}^2, CFL 0.5, {steps} steps", shape=(n, n), bc=(1, 1), h=h, dt=0.5 * h,
+    return dict(name=f"2D acoustic {n}^2, CFL 0.5, {steps} steps", shape=(n, n), bc=(1, 1), h=h, dt=0.5 * h,
                 rho=np.ones((n, n)), c=np.ones((n, n)),
                 p0=np.exp(-((X - 0.5) ** 2 + (Y - 0.5) ** 2) / (2 * 0.05 ** 2)), steps=steps)
 
@@ -70,14 +70,14 @@ def w0(small=False):
                 src=(n // 3, n // 3, wav * 0.5 * h), rec=(2 * n // 3, 2 * n // 3))
 
 
-def cfg3(small=False):
+def acoustic3d_recipe(small=False):
     """The 3D benchmark recipe on an n^3 sample (velocity filter width scaled
     by n / 512, the Gaussian initial pressure kept at 6 cells), p = 0 walls,
     CFL 0.4."""
     n, steps = (32, 100) if small else (64, 400)
     w = inputs.acoustic_3d_random(n=n, sigma_cells=16.0 * n / 512, ic_sigma_cells=6.0,
                                   smooth_dtype=np.float64)
-    return dict(name=f"cfg3 recipe {n}^3, CFL 0.4, {steps} steps", shape=w["shape"], bc=(1, 1, 1),
+    return dict(name=f"3D recipe {n}^3, CFL 0.4, {steps} steps", shape=w["shape"], bc=(1, 1, 1),
                 h=w["h"], dt=w["dt"], rho=w["rho"], c=w["c"], p0=w["p0"], steps=steps)
 
 
@@ -108,9 +108,9 @@ def split(case):
 
 def main(argv):
     small = "--small" in argv
-    which = [a for a in argv if not a.startswith("--")] or ["cfg1", "w0", "cfg3"]
+    which = [a for a in argv if not a.startswith("--")] or ["acoustic2d_256", "w0", "acoustic3d_recipe"]
     for key in which:
-        case = {"cfg1": cfg1, "w0": w0, "cfg3": cfg3}[key](small)
+        case = {"acoustic2d_256": acoustic2d_256, "w0": w0, "acoustic3d_recipe": acoustic3d_recipe}[key](small)
         t0 = time.time()
         rows = split(case)
         print(f"\n{case['name']} ({time.time() - t0:.0f} s, {O.set_threads()} threads)\n")

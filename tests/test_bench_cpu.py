@@ -14,7 +14,7 @@ def test_cpu_baseline_leg_per_workload(oracle_lib):
     d = bench.oracle_per_config(budget=0.02)
     assert O.set_threads() == before  # the thread count is restored
     assert d["kind"] == "oracle" and d["unit"] == "Mpoint-updates/s" and d["cores"] == before
-    for name in ("cfg1_2d_acoustic_256", "cfg3_3d_acoustic_sample_64", "cfg2_2d_elastic_1024"):
+    for name in ("acoustic2d_256", "acoustic3d_sample_64", "elastic2d_1024"):
         row = d[name]
         assert set(row) == {"fp64_1t", "fp16_emulation_1t", f"fp64_{before}t", f"fp16_emulation_{before}t"}
         assert all(v > 0 for v in row.values())
@@ -23,7 +23,7 @@ def test_cpu_baseline_leg_per_workload(oracle_lib):
 def test_pareto_marks_dominated_variants():
     import bench
     variants = {"a": {"value": 100.0}, "b": {"value": 90.0}, "c": {"value": 150.0}}
-    acc = {"cfg3_recipe_256_cfl0.4_400": {
+    acc = {"acoustic3d_recipe_256_cfl0.4_400": {
         "a": {"energy_drift_max": 1e-5, "rel_l2_vs_fp32": 1e-3},
         "b": {"energy_drift_max": 2e-5, "rel_l2_vs_fp32": 2e-3},     # worse than a in all three
         "c": {"energy_drift_max": 1e-3, "rel_l2_vs_fp32": 5e-3}}}

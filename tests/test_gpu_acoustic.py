@@ -212,7 +212,7 @@ def test_runs_are_deterministic():
         assert outs[0][1] == outs[1][1]
 
 
-def test_cfg1_full_size_2000_steps_bit_exact():
+def test_acoustic2d_256_full_size_2000_steps_bit_exact():
     """2D acoustic 256^2, rho = c = 1, p = 0 walls, Gaussian, CFL 0.5, 2000
     steps, fp16 + sum_3op: every stored bit equals the oracle's."""
     w = inputs.acoustic_2d_gaussian(256, 2000)
@@ -227,7 +227,7 @@ def test_cfg1_full_size_2000_steps_bit_exact():
     assert not bad, bad
 
 
-def test_cfg1_pairs_full_size_bit_exact_and_within_2e3():
+def test_acoustic2d_256_pairs_full_size_bit_exact_and_within_2e3():
     """The same problem with the pair stencils (binary16 V and T, binary32
     registers, every tap RN32(V + T)): every stored bit equals the oracle's
     pair_stencil run, and the pressure is within 2e-3 relative L2 of the

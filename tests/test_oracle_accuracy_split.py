@@ -2,7 +2,7 @@
 "Range"), checked at reduced size with the CPU oracle (tests/accuracy_split.py
 prints the full-size tables).
 
-* cfg1 (rho = c = 1, CFL 0.5): the multipliers a = b = 1/2 are exact in
+* the 2D acoustic 256^2 problem (rho = c = 1, CFL 0.5): the multipliers a = b = 1/2 are exact in
   binary16, so their rounding costs nothing; rounding the weight 1/24 alone
   costs about a third of the method's error; half storage with the
   compensation carried and every other operation and coefficient in binary64
@@ -24,8 +24,8 @@ def _err(case, ref, **kw):
     return float(np.linalg.norm(out - ref) / np.linalg.norm(ref))
 
 
-def test_split_cfg1(oracle_lib):
-    case = A.cfg1(small=True)
+def test_split_acoustic2d_256(oracle_lib):
+    case = A.acoustic2d_256(small=True)
     ref, _ = A.run(case, store_fmt=O.FP64, comp=0)
     method = _err(case, ref, store_fmt=O.FP16, comp=3)
     coef = _err(case, ref, store_fmt=O.FP64, comp=0, coef_fmt=O.FP16)
