@@ -404,11 +404,14 @@ EBC_ZERO = 3
 
 class ElasticCfg(C.Structure):
     _fields_ = [("n", C.c_int64 * 2), ("bc", C.c_int32 * 4), ("store_fmt", C.c_int32),
-                ("arith_fmt", C.c_int32), ("stencil_fmt", C.c_int32), ("comp", C.c_int32)]
+                ("arith_fmt", C.c_int32), ("stencil_fmt", C.c_int32), ("comp", C.c_int32),
+                ("pair_stencil", C.c_int32)]
 
 
-def elastic_cfg(shape, bc, store_fmt, comp, arith_fmt=None, stencil_fmt=None) -> ElasticCfg:
-    """shape (nx, ny); bc per face (x-lo, x-hi, y-lo, y-hi)."""
+def elastic_cfg(shape, bc, store_fmt, comp, arith_fmt=None, stencil_fmt=None,
+                pair_stencil=False) -> ElasticCfg:
+    """shape (nx, ny); bc per face (x-lo, x-hi, y-lo, y-hi). pair_stencil: the
+    stencils read RN(V + T) (with compensation; not the paper's scheme)."""
     cfg = ElasticCfg()
     cfg.n[0], cfg.n[1] = shape
     for i in range(4):
@@ -417,6 +420,7 @@ def elastic_cfg(shape, bc, store_fmt, comp, arith_fmt=None, stencil_fmt=None) ->
     cfg.arith_fmt = store_fmt if arith_fmt is None else arith_fmt
     cfg.stencil_fmt = cfg.arith_fmt if stencil_fmt is None else stencil_fmt
     cfg.comp = comp
+    cfg.pair_stencil = 1 if pair_stencil else 0
     return cfg
 
 
@@ -506,12 +510,14 @@ def elastic_scale_source(w, dt, Z0, P0, h, fmt):
 
 
 def elastic_setup(shape, bc, h, dt, rho, vp, vs, store_fmt, comp, P0=1.0, arith_fmt=None,
-                  stencil_fmt=None, init=None):
+                  stencil_fmt=None, init=None, coef_fmt=None, pair_stencil=False):
     """Ready-to-run ElasticState from physical inputs. init: dict field -> array
-    (velocities in m/s, stresses in Pa)."""
-    cfg = elastic_cfg(shape, bc, store_fmt, comp, arith_fmt, stencil_fmt)
+    (velocities in m/s, stresses in Pa). coef_fmt: round the multipliers to
+    this format instead of the storage format; pair_stencil: see elastic_cfg."""
+    cfg = elastic_cfg(shape, bc, store_fmt, comp, arith_fmt, stencil_fmt, pair_stencil)
     st = ElasticState(cfg)
-    coef, Z0, ok = elastic_coefficients(cfg, h, dt, rho, vp, vs)
+    ccfg = cfg if coef_fmt is None else elastic_cfg(shape, bc, coef_fmt, comp)
+    coef, Z0, ok = elastic_coefficients(ccfg, h, dt, rho, vp, vs)
     if not ok:
         raise ValueError("elastic multiplier outside the storage format's range")
     st.coef, st.Z0, st.P0, st.h, st.dt = coef, Z0, P0, h, dt

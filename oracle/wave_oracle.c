@@ -761,6 +761,7 @@ typedef struct {
     int64_t n[2];
     int32_t bc[4];
     int32_t store_fmt, arith_fmt, stencil_fmt, comp;
+    int32_t pair_stencil;  /* with comp: the stencils read RN(V + T) (not the paper) */
 } orc_elastic_cfg;
 
 /* Image of index m along an axis of N points for a field that is node-type
@@ -848,7 +849,10 @@ static double e_stencil(const double *f, const orc_elastic_cfg *c, int ax, int n
  *     + sum over nodes w (l2m (sxx sxx' + syy syy') - lam (sxx syy' + syy sxx')) / (l2m^2 - lam^2)
  *     + sum sxy sxy' / mu              (primes: after the step)
  * with w = 1/2 on the row of a free surface (there lam = 0 and syy = 0, so the
- * node term is sxx sxx' / l2m with the reduced modulus) and w = 1 elsewhere. */
+ * node term is sxx sxx' / l2m with the reduced modulus) and w = 1 elsewhere.
+ * With pair_stencil (and comp) the stencils read RN(V + T) in the stencil
+ * format, formed for the stresses before the velocity half step and for the
+ * velocities before the stress half step; the energy reads the stored V. */
 int orc_elastic_run(const orc_elastic_cfg *c, double *vx, double *tvx, double *vy, double *tvy,
                     double *sxx, double *tsxx, double *syy, double *tsyy, double *sxy,
                     double *tsxy, const double *bx, const double *by, const double *l2m,
@@ -856,29 +860,48 @@ int orc_elastic_run(const orc_elastic_cfg *c, double *vx, double *tvx, double *v
                     int64_t src_index, int64_t src_nt, const double *src, int32_t rec_field,
                     int64_t nrec, const int64_t *rec_index, double *traces, double *energy)
 {
-    const int64_t nx = c->n[0], ny = c->n[1];
+    const int64_t nx = c->n[0], ny = c->n[1], npts = nx * ny;
     const int sf = c->store_fmt, af = c->arith_fmt, stf = c->stencil_fmt, comp = c->comp;
     double *rowacc = (double *)calloc((size_t)ny, sizeof(double));
     if (!rowacc) return -1;
+    /* what the stencils read: the stored values, or RN(V + T) (pair_stencil) */
+    const double *rxx = sxx, *ryy = syy, *rxy = sxy, *rvx = vx, *rvy = vy;
+    double *pairs = NULL;
+    if (c->pair_stencil && comp) {
+        pairs = (double *)malloc(sizeof(double) * (size_t)npts * 5);
+        if (!pairs) { free(rowacc); return -1; }
+        rxx = pairs; ryy = pairs + npts; rxy = pairs + 2 * npts; rvx = pairs + 3 * npts; rvy = pairs + 4 * npts;
+    }
     for (int64_t s = 0; s < nsteps; s++) {
         const int64_t gstep = step0 + s;
+        if (pairs)
+            for (int64_t q = 0; q < npts; q++) {
+                pairs[q] = add_f(sxx[q], tsxx[q], stf);
+                pairs[npts + q] = add_f(syy[q], tsyy[q], stf);
+                pairs[2 * npts + q] = add_f(sxy[q], tsxy[q], stf);
+            }
 #pragma omp parallel for schedule(static)
         for (int64_t j = 0; j < ny; j++)
             for (int64_t i = 0; i < nx; i++) {
                 const int64_t q = i + nx * j;
                 /* vx at (i+1/2, j): sxx node-type in x (even); sxy half-type in y (odd at
                  * rigid walls and at the free surface) */
-                double R = add_f(e_stencil(sxx, c, 0, 1, 0, 1, i, j, stf),
-                                 e_stencil(sxy, c, 1, 0, 1, 1, i, j, stf), stf);
+                double R = add_f(e_stencil(rxx, c, 0, 1, 0, 1, i, j, stf),
+                                 e_stencil(rxy, c, 1, 0, 1, 1, i, j, stf), stf);
                 double inc = orc_round(mul_f(bx[q], R, stf), af);
                 update(&vx[q], &tvx[q], inc, comp, af, sf);
                 /* vy at (i, j+1/2): sxy half-type in x (odd); syy node-type in y (even at
                  * rigid walls, odd at the free surface) */
-                R = add_f(e_stencil(sxy, c, 0, 0, 1, 1, i, j, stf),
-                          e_stencil(syy, c, 1, 1, 0, 1, i, j, stf), stf);
+                R = add_f(e_stencil(rxy, c, 0, 0, 1, 1, i, j, stf),
+                          e_stencil(ryy, c, 1, 1, 0, 1, i, j, stf), stf);
                 inc = orc_round(mul_f(by[q], R, stf), af);
                 if (src && q == src_index && gstep < src_nt) inc = add_f(inc, src[gstep], af);
                 update(&vy[q], &tvy[q], inc, comp, af, sf);
+            }
+        if (pairs)
+            for (int64_t q = 0; q < npts; q++) {
+                pairs[3 * npts + q] = add_f(vx[q], tvx[q], stf);
+                pairs[4 * npts + q] = add_f(vy[q], tvy[q], stf);
             }
 #pragma omp parallel for schedule(static)
         for (int64_t j = 0; j < ny; j++) {
@@ -887,16 +910,16 @@ int orc_elastic_run(const orc_elastic_cfg *c, double *vx, double *tvx, double *v
                 const int64_t q = i + nx * j;
                 /* nodes: vx half-type in x (odd), vy half-type in y (odd at rigid walls,
                  * even at the free surface) */
-                const double dxvx = e_stencil(vx, c, 0, 0, 1, 0, i, j, stf);
-                const double dyvy = e_stencil(vy, c, 1, 0, 1, 0, i, j, stf);
+                const double dxvx = e_stencil(rvx, c, 0, 0, 1, 0, i, j, stf);
+                const double dyvy = e_stencil(rvy, c, 1, 0, 1, 0, i, j, stf);
                 const double sxx0 = sxx[q], syy0 = syy[q], sxy0 = sxy[q];
                 double inc = orc_round(add_f(mul_f(l2m[q], dxvx, stf), mul_f(lam[q], dyvy, stf), stf), af);
                 update(&sxx[q], &tsxx[q], inc, comp, af, sf);
                 inc = orc_round(add_f(mul_f(lam[q], dxvx, stf), mul_f(l2m[q], dyvy, stf), stf), af);
                 update(&syy[q], &tsyy[q], inc, comp, af, sf);
                 /* sxy at (i+1/2, j+1/2): vy node-type in x (even), vx node-type in y (even) */
-                double R = add_f(e_stencil(vy, c, 0, 1, 0, 0, i, j, stf),
-                                 e_stencil(vx, c, 1, 1, 0, 0, i, j, stf), stf);
+                double R = add_f(e_stencil(rvy, c, 0, 1, 0, 0, i, j, stf),
+                                 e_stencil(rvx, c, 1, 1, 0, 0, i, j, stf), stf);
                 inc = orc_round(mul_f(mu[q], R, stf), af);
                 update(&sxy[q], &tsxy[q], inc, comp, af, sf);
                 if (energy) {
@@ -923,6 +946,7 @@ int orc_elastic_run(const orc_elastic_cfg *c, double *vx, double *tvx, double *v
         }
     }
     free(rowacc);
+    free(pairs);
     return 0;
 }
 
