@@ -73,12 +73,14 @@ typedef enum { WAVE_ACOUSTIC = 0, WAVE_ELASTIC = 1 } wave_physics;
  *     compensation, instead of V (not the paper's scheme, where the stencil
  *     reads V: the binary16 pair then acts as a ~22-bit value in the stencil,
  *     which removes the rounding error of the stored value from the
- *     differences); the multipliers a and b are kept in binary32 (their
- *     rounding to binary16 is then the largest error left; per-point arrays
- *     cost 4 bytes a point). Acoustic only; needs compensation (WAVE_EINVAL
- *     without); wave_energy_acoustic_static does not take it; 2D steps on
- *     the two-launch row strips, 3D on the one-thread-per-point
- *     kernels; no z slabs, no adjoint (WAVE_ENOTIMPL).
+ *     differences); the multipliers (acoustic a, b; elastic bx, by, l2m, lam,
+ *     mu) are kept in binary32 (their rounding to binary16 would then be the
+ *     largest error left; per-point arrays cost 4 bytes a point). Needs
+ *     compensation (WAVE_EINVAL without). Acoustic 3D: the one-pass step
+ *     where it applies (t_p then alternates between two buffers), else one
+ *     thread per point; 2D: the cluster-resident steps or the two-launch row
+ *     strips (not kernel 3). No z slabs and no adjoint (WAVE_ENOTIMPL);
+ *     wave_energy_acoustic_static does not take it (WAVE_EINVAL).
  *   WAVE_FP64 is accepted only by the CPU oracle; wave_create returns
  *     WAVE_ENOTIMPL for it. */
 typedef enum {

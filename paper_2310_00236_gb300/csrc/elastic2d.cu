@@ -18,14 +18,16 @@
 
 namespace wave {
 
-// Stencil of field f along axis ax at point (i, j): f node-type along ax read at
-// indices m-1..m+2, half-type at m-2..m+1.
+// Stencil of field fi along axis ax at point (i, j): f node-type along ax read at
+// indices m-1..m+2, half-type at m-2..m+1. Taps: the stored values, or for the
+// pair policies RN(V + T) (the image's sign applied to the sum).
 template <class P>
-__device__ __forceinline__ typename P::A estencil(const void *fv, const ElParams &e, int ax, bool node,
+__device__ __forceinline__ typename P::A estencil(int fi, const ElParams &e, int ax, bool node,
                                                   bool odd, bool odd_free, int i, int j) {
     using S = typename P::S;
     using A = typename P::A;
-    const S *f = static_cast<const S *>(fv);
+    const S *f = static_cast<const S *>(e.f[fi]);
+    const S *tf = static_cast<const S *>(e.t[fi]);
     const int m = ax == 0 ? i : j;
     const int first = node ? m - 1 : m - 2;
     A v[4];
@@ -37,7 +39,7 @@ __device__ __forceinline__ typename P::A estencil(const void *fv, const ElParams
             v[t] = P::zero();
         } else {
             const int64_t q = ax == 0 ? (mm + e.sy * (int64_t)j) : (i + e.sy * (int64_t)mm);
-            const A x = P::ld(f[q]);
+            const A x = IsPairs<P>::value ? P::add(P::ld(f[q]), P::ld(tf[q])) : P::ld(f[q]);
             v[t] = sg > 0 ? x : P::neg(x);
         }
     }
@@ -54,8 +56,8 @@ __global__ void __launch_bounds__(128) el_v(ElParams e) {
     if (i >= e.n[0] || j >= e.n[1]) return;
     const int64_t q = i + e.sy * (int64_t)j;
     // vx: sxx node-type in x (even), sxy half-type in y (odd at walls and surface)
-    A R = P::add(estencil<P>(e.f[F_SXX], e, 0, true, false, true, i, j),
-                 estencil<P>(e.f[F_SXY], e, 1, false, true, true, i, j));
+    A R = P::add(estencil<P>(F_SXX, e, 0, true, false, true, i, j),
+                 estencil<P>(F_SXY, e, 1, false, true, true, i, j));
     A inc = P::mul(coef<P>(e.c[C_BX], e.c_uni[C_BX], q), R);
     S *vx = static_cast<S *>(e.f[F_VX]), *tvx = static_cast<S *>(e.t[F_VX]);
     S V = vx[q], T = COMP ? tvx[q] : S(0);
@@ -63,8 +65,8 @@ __global__ void __launch_bounds__(128) el_v(ElParams e) {
     vx[q] = V;
     if (COMP) tvx[q] = T;
     // vy: sxy half-type in x (odd), syy node-type in y (even at walls, odd at the surface)
-    R = P::add(estencil<P>(e.f[F_SXY], e, 0, false, true, true, i, j),
-               estencil<P>(e.f[F_SYY], e, 1, true, false, true, i, j));
+    R = P::add(estencil<P>(F_SXY, e, 0, false, true, true, i, j),
+               estencil<P>(F_SYY, e, 1, true, false, true, i, j));
     inc = P::mul(coef<P>(e.c[C_BY], e.c_uni[C_BY], q), R);
     if (q == e.src_q && e.step < e.src_nt) inc = P::add(inc, static_cast<const A *>(e.src)[e.step]);
     S *vy = static_cast<S *>(e.f[F_VY]), *tvy = static_cast<S *>(e.t[F_VY]);
@@ -85,8 +87,8 @@ __global__ void __launch_bounds__(128) el_s(ElParams e) {
     if (i < e.n[0] && j < e.n[1]) {
         const int64_t q = i + e.sy * (int64_t)j;
         // nodes: vx half-type in x (odd), vy half-type in y (odd at walls, even at the surface)
-        const A dxvx = estencil<P>(e.f[F_VX], e, 0, false, true, false, i, j);
-        const A dyvy = estencil<P>(e.f[F_VY], e, 1, false, true, false, i, j);
+        const A dxvx = estencil<P>(F_VX, e, 0, false, true, false, i, j);
+        const A dyvy = estencil<P>(F_VY, e, 1, false, true, false, i, j);
         const A l2m = coef<P>(e.c[C_L2M], e.c_uni[C_L2M], q);
         const A lam = coef<P>(e.c[C_LAM], e.c_uni[C_LAM], q);
         S *sxx = static_cast<S *>(e.f[F_SXX]), *tsxx = static_cast<S *>(e.t[F_SXX]);
@@ -107,8 +109,8 @@ __global__ void __launch_bounds__(128) el_s(ElParams e) {
         if (COMP) tsyy[q] = T;
         const S syy1 = V;
         // sxy: vy node-type in x (even), vx node-type in y (even)
-        const A R = P::add(estencil<P>(e.f[F_VY], e, 0, true, false, false, i, j),
-                           estencil<P>(e.f[F_VX], e, 1, true, false, false, i, j));
+        const A R = P::add(estencil<P>(F_VY, e, 0, true, false, false, i, j),
+                           estencil<P>(F_VX, e, 1, true, false, false, i, j));
         inc = P::mul(coef<P>(e.c[C_MU], e.c_uni[C_MU], q), R);
         V = sxy0;
         T = COMP ? tsxy[q] : S(0);
@@ -161,6 +163,7 @@ cudaError_t elastic_half_step(const ElParams &e, int prec, int comp, int half, c
     case PREC_BF16: return launch_c<BF16>(e, comp, half, st);
     case PREC_FP16_F32ARITH: return launch_c<F16W>(e, comp ? 3 : 0, half, st);
     case PREC_BF16_F32ARITH: return launch_c<BF16W>(e, comp ? 3 : 0, half, st);
+    case PREC_FP16_PAIRS: return comp ? launch_t<F16WP, 3>(e, half, st) : cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }

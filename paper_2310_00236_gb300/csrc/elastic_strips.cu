@@ -18,6 +18,7 @@
 #include "acoustic_common.cuh"
 #include "elastic.h"
 #include "elastic_common.cuh"
+#include "strip_common.cuh"
 #include "vec_policy.cuh"
 #include "wave_kernels.h"
 
@@ -72,35 +73,70 @@ struct ElStrip {
             if (k >= nvalid) set_raw(own, k, xval(f, e, x + k, j, node, odd));
         return own;
     }
-    // D_x of a field that sits on the x nodes: reads x-1 .. x+N+1.
-    static __device__ __forceinline__ AV dx_node(const Raw &own, const void *f, const ElParams &e, int x, int j,
-                                                 bool odd, bool left_edge, bool right_edge) {
+    // x neighbours x-1, x+N, x+N+1 of a node-type row (lanes, or the x images)
+    static __device__ __forceinline__ void nb_node(const Raw &own, const void *f, const ElParams &e, int x, int j,
+                                                   bool odd, bool left_edge, bool right_edge, RS &l0, RS &r0,
+                                                   RS &r1) {
         const RS sl0 = shfl(V::get(own, N - 1), true);
         const RS sr0 = shfl(V::get(own, 0), false);
         const RS sr1 = shfl(V::get(own, 1), false);
-        const RS l0 = left_edge ? xval(f, e, x - 1, j, true, odd) : sl0;
-        const RS r0 = right_edge ? xval(f, e, x + N, j, true, odd) : sr0;
-        const RS r1 = right_edge ? xval(f, e, x + N + 1, j, true, odd) : sr1;
-        const AV o = V::ld(own);
-        return vstencil<V>(V::shr1(o, V::lds(l0)), o, V::shl1(o, V::lds(r0)), V::shl2(o, V::lds(r0), V::lds(r1)));
+        l0 = left_edge ? xval(f, e, x - 1, j, true, odd) : sl0;
+        r0 = right_edge ? xval(f, e, x + N, j, true, odd) : sr0;
+        r1 = right_edge ? xval(f, e, x + N + 1, j, true, odd) : sr1;
     }
-    // D_x of a field that sits on the x half points: reads x-2 .. x+N.
-    static __device__ __forceinline__ AV dx_half(const Raw &own, const void *f, const ElParams &e, int x, int j,
-                                                 bool odd, bool left_edge, bool right_edge) {
+    // x neighbours x-2, x-1, x+N of a half-type row
+    static __device__ __forceinline__ void nb_half(const Raw &own, const void *f, const ElParams &e, int x, int j,
+                                                   bool odd, bool left_edge, bool right_edge, RS &l1, RS &l0,
+                                                   RS &rr) {
         const RS sl1 = shfl(V::get(own, N - 2), true);
         const RS sl0 = shfl(V::get(own, N - 1), true);
         const RS srr = shfl(V::get(own, 0), false);
-        const RS l1 = left_edge ? xval(f, e, x - 2, j, false, odd) : sl1;
-        const RS l0 = left_edge ? xval(f, e, x - 1, j, false, odd) : sl0;
-        const RS rr = right_edge ? xval(f, e, x + N, j, false, odd) : srr;
-        const AV o = V::ld(own);
-        return vstencil<V>(V::shr2(o, V::lds(l1), V::lds(l0)), V::shr1(o, V::lds(l0)), o, V::shl1(o, V::lds(rr)));
+        l1 = left_edge ? xval(f, e, x - 2, j, false, odd) : sl1;
+        l0 = left_edge ? xval(f, e, x - 1, j, false, odd) : sl0;
+        rr = right_edge ? xval(f, e, x + N, j, false, odd) : srr;
     }
+    // D_x of a field that sits on the x nodes: reads x-1 .. x+N+1. With PAIRS
+    // the taps are RN(V + T) (own_t, ft: the field's compensation).
+    template <class P, bool PAIRS>
+    static __device__ __forceinline__ AV dx_node(const Raw &own, const Raw &own_t, const void *f, const void *ft,
+                                                 const ElParams &e, int x, int j, bool odd, bool left_edge,
+                                                 bool right_edge) {
+        RS l0, r0, r1;
+        nb_node(own, f, e, x, j, odd, left_edge, right_edge, l0, r0, r1);
+        AV o = V::ld(own);
+        typename V::AS al0 = V::lds(l0), ar0 = V::lds(r0), ar1 = V::lds(r1);
+        if constexpr (PAIRS) {
+            RS t0, t1, t2;
+            nb_node(own_t, ft, e, x, j, odd, left_edge, right_edge, t0, t1, t2);
+            o = V::add(o, V::ld(own_t));
+            al0 = P::add(al0, V::lds(t0));
+            ar0 = P::add(ar0, V::lds(t1));
+            ar1 = P::add(ar1, V::lds(t2));
+        }
+        return vstencil<V>(V::shr1(o, al0), o, V::shl1(o, ar0), V::shl2(o, ar0, ar1));
+    }
+    // D_x of a field that sits on the x half points: reads x-2 .. x+N.
+    template <class P, bool PAIRS>
+    static __device__ __forceinline__ AV dx_half(const Raw &own, const Raw &own_t, const void *f, const void *ft,
+                                                 const ElParams &e, int x, int j, bool odd, bool left_edge,
+                                                 bool right_edge) {
+        RS l1, l0, rr;
+        nb_half(own, f, e, x, j, odd, left_edge, right_edge, l1, l0, rr);
+        AV o = V::ld(own);
+        typename V::AS al1 = V::lds(l1), al0 = V::lds(l0), arr = V::lds(rr);
+        if constexpr (PAIRS) {
+            RS t0, t1, t2;
+            nb_half(own_t, ft, e, x, j, odd, left_edge, right_edge, t0, t1, t2);
+            o = V::add(o, V::ld(own_t));
+            al1 = P::add(al1, V::lds(t0));
+            al0 = P::add(al0, V::lds(t1));
+            arr = P::add(arr, V::lds(t2));
+        }
+        return vstencil<V>(V::shr2(o, al1, al0), V::shr1(o, al0), o, V::shl1(o, arr));
+    }
+    // multipliers of the vector at q (binary32 for the pair precision)
     static __device__ __forceinline__ AV coefv(const void *arr, uint32_t uni, int64_t q) {
-        if (arr) return V::ld(*reinterpret_cast<const Raw *>(static_cast<const char *>(arr) + q * sizeof(RS)));
-        RS s;
-        from_bits(uni, s);
-        return V::splat(V::lds(s));
+        return coef_v<V>(arr, uni, q);
     }
     static __device__ __forceinline__ void store(void *f, int64_t q, const Raw &r, int nvalid) {
         if (nvalid >= N) {
@@ -163,19 +199,34 @@ __global__ void __launch_bounds__(256) el_v_strip(const ElParams e, int nitems, 
         const bool le = active && lane == 0;
         const bool re = active && (lane == 31 || x + N >= e.n[0]);
         // sxy rows j-2 .. j+1 (half points in y; odd at walls and surface); syy rows
-        // j-1 .. j+2 (nodes; even at walls, odd at the surface)
+        // j-1 .. j+2 (nodes; even at walls, odd at the surface); with the pair
+        // policies the same queues of their compensations (taps RN(S + T))
+        constexpr bool PAIRS = IsPairs<P>::value;
         Raw a0 = X::row(e.f[F_SXY], e, x, it.y0 - 2, false, true, true, active);
         Raw a1 = X::row(e.f[F_SXY], e, x, it.y0 - 1, false, true, true, active);
         Raw a2 = X::row(e.f[F_SXY], e, x, it.y0, false, true, true, active);
         Raw b0 = X::row(e.f[F_SYY], e, x, it.y0 - 1, true, false, true, active);
         Raw b1 = X::row(e.f[F_SYY], e, x, it.y0, true, false, true, active);
         Raw b2 = X::row(e.f[F_SYY], e, x, it.y0 + 1, true, false, true, active);
+        Raw ta0 = V::zero(), ta1 = V::zero(), ta2 = V::zero(), tb0 = V::zero(), tb1 = V::zero(), tb2 = V::zero();
+        if (PAIRS) {
+            ta0 = X::row(e.t[F_SXY], e, x, it.y0 - 2, false, true, true, active);
+            ta1 = X::row(e.t[F_SXY], e, x, it.y0 - 1, false, true, true, active);
+            ta2 = X::row(e.t[F_SXY], e, x, it.y0, false, true, true, active);
+            tb0 = X::row(e.t[F_SYY], e, x, it.y0 - 1, true, false, true, active);
+            tb1 = X::row(e.t[F_SYY], e, x, it.y0, true, false, true, active);
+            tb2 = X::row(e.t[F_SYY], e, x, it.y0 + 1, true, false, true, active);
+        }
+        auto tap = [&](const Raw &v, const Raw &t) -> AV { return PAIRS ? V::add(V::ld(v), V::ld(t)) : V::ld(v); };
         for (int j = it.y0; j < it.y1; j++) {
             const Raw a3 = X::row(e.f[F_SXY], e, x, j + 1, false, true, true, active);
             const Raw b3 = X::row(e.f[F_SYY], e, x, j + 2, true, false, true, active);
+            const Raw ta3 = PAIRS ? X::row(e.t[F_SXY], e, x, j + 1, false, true, true, active) : V::zero();
+            const Raw tb3 = PAIRS ? X::row(e.t[F_SYY], e, x, j + 2, true, false, true, active) : V::zero();
             const int64_t q = x + e.sy * (int64_t)j;
-            Raw sxx = V::zero(), vx = V::zero(), vy = V::zero(), tx = V::zero(), ty = V::zero();
+            Raw sxx = V::zero(), vx = V::zero(), vy = V::zero(), tx = V::zero(), ty = V::zero(), tsxx = V::zero();
             if (active) {
+                if (PAIRS) tsxx = X::load(e.t[F_SXX], q);
                 sxx = X::load(e.f[F_SXX], q);
                 vx = X::load(e.f[F_VX], q);
                 vy = X::load(e.f[F_VY], q);
@@ -184,19 +235,25 @@ __global__ void __launch_bounds__(256) el_v_strip(const ElParams e, int nitems, 
                     ty = X::load(e.t[F_VY], q);
                 }
             }
-            Raw sxx_f = sxx, sxy_f = a2;
+            Raw sxx_f = sxx, sxy_f = a2, tsxx_f = tsxx, tsxy_f = ta2;
             if (re) {
                 sxx_f = X::fix(sxx, e.f[F_SXX], e, x, j, nvalid, true, false);
                 sxy_f = X::fix(a2, e.f[F_SXY], e, x, j, nvalid, false, true);
+                if (PAIRS) {
+                    tsxx_f = X::fix(tsxx, e.t[F_SXX], e, x, j, nvalid, true, false);
+                    tsxy_f = X::fix(ta2, e.t[F_SXY], e, x, j, nvalid, false, true);
+                }
             }
-            const AV dxsxx = X::dx_node(sxx_f, e.f[F_SXX], e, x, j, false, le, re);
-            const AV dxsxy = X::dx_half(sxy_f, e.f[F_SXY], e, x, j, true, le, re);
+            const AV dxsxx =
+                X::template dx_node<P, PAIRS>(sxx_f, tsxx_f, e.f[F_SXX], e.t[F_SXX], e, x, j, false, le, re);
+            const AV dxsxy =
+                X::template dx_half<P, PAIRS>(sxy_f, tsxy_f, e.f[F_SXY], e.t[F_SXY], e, x, j, true, le, re);
             if (active) {
                 // vx: Dx sxx + Dy sxy
-                AV R = V::add(dxsxx, vstencil<V>(V::ld(a0), V::ld(a1), V::ld(a2), V::ld(a3)));
+                AV R = V::add(dxsxx, vstencil<V>(tap(a0, ta0), tap(a1, ta1), tap(a2, ta2), tap(a3, ta3)));
                 V::template update<COMP>(vx, tx, V::mul(X::coefv(e.c[C_BX], e.c_uni[C_BX], q), R));
                 // vy: Dx sxy + Dy syy [+ s]
-                R = V::add(dxsxy, vstencil<V>(V::ld(b0), V::ld(b1), V::ld(b2), V::ld(b3)));
+                R = V::add(dxsxy, vstencil<V>(tap(b0, tb0), tap(b1, tb1), tap(b2, tb2), tap(b3, tb3)));
                 AV inc = V::mul(X::coefv(e.c[C_BY], e.c_uni[C_BY], q), R);
                 if (j == src_j && src_i >= x && src_i < x + N && step < e.src_nt) {
                     const typename V::AS sv = static_cast<const typename V::AS *>(e.src)[step];
@@ -214,6 +271,8 @@ __global__ void __launch_bounds__(256) el_v_strip(const ElParams e, int nitems, 
             }
             a0 = a1; a1 = a2; a2 = a3;
             b0 = b1; b1 = b2; b2 = b3;
+            ta0 = ta1; ta1 = ta2; ta2 = ta3;
+            tb0 = tb1; tb1 = tb2; tb2 = tb3;
         }
     }
 }
@@ -239,17 +298,31 @@ __global__ void __launch_bounds__(256) el_s_strip(const ElParams e, int nitems, 
         const bool le = active && lane == 0;
         const bool re = active && (lane == 31 || x + N >= e.n[0]);
         // vy rows j-2 .. j+1 (half points in y; odd at walls, even at the surface); vx
-        // rows j-1 .. j+2 (nodes, even)
+        // rows j-1 .. j+2 (nodes, even); with the pair policies the same queues
+        // of their compensations (taps RN(V + T))
+        constexpr bool PAIRS = IsPairs<P>::value;
         Raw c0 = X::row(e.f[F_VY], e, x, it.y0 - 2, false, true, false, active);
         Raw c1 = X::row(e.f[F_VY], e, x, it.y0 - 1, false, true, false, active);
         Raw c2 = X::row(e.f[F_VY], e, x, it.y0, false, true, false, active);
         Raw d0 = X::row(e.f[F_VX], e, x, it.y0 - 1, true, false, false, active);
         Raw d1 = X::row(e.f[F_VX], e, x, it.y0, true, false, false, active);
         Raw d2 = X::row(e.f[F_VX], e, x, it.y0 + 1, true, false, false, active);
+        Raw tc0 = V::zero(), tc1 = V::zero(), tc2 = V::zero(), td0 = V::zero(), td1 = V::zero(), td2 = V::zero();
+        if (PAIRS) {
+            tc0 = X::row(e.t[F_VY], e, x, it.y0 - 2, false, true, false, active);
+            tc1 = X::row(e.t[F_VY], e, x, it.y0 - 1, false, true, false, active);
+            tc2 = X::row(e.t[F_VY], e, x, it.y0, false, true, false, active);
+            td0 = X::row(e.t[F_VX], e, x, it.y0 - 1, true, false, false, active);
+            td1 = X::row(e.t[F_VX], e, x, it.y0, true, false, false, active);
+            td2 = X::row(e.t[F_VX], e, x, it.y0 + 1, true, false, false, active);
+        }
+        auto tap = [&](const Raw &v, const Raw &t) -> AV { return PAIRS ? V::add(V::ld(v), V::ld(t)) : V::ld(v); };
         double en = 0.0;
         for (int j = it.y0; j < it.y1; j++) {
             const Raw c3 = X::row(e.f[F_VY], e, x, j + 1, false, true, false, active);
             const Raw d3 = X::row(e.f[F_VX], e, x, j + 2, true, false, false, active);
+            const Raw tc3 = PAIRS ? X::row(e.t[F_VY], e, x, j + 1, false, true, false, active) : V::zero();
+            const Raw td3 = PAIRS ? X::row(e.t[F_VX], e, x, j + 2, true, false, false, active) : V::zero();
             const int64_t q = x + e.sy * (int64_t)j;
             Raw sxx = V::zero(), syy = V::zero(), sxy = V::zero();
             Raw txx = V::zero(), tyy = V::zero(), txy = V::zero();
@@ -263,21 +336,25 @@ __global__ void __launch_bounds__(256) el_s_strip(const ElParams e, int nitems, 
                     txy = X::load(e.t[F_SXY], q);
                 }
             }
-            Raw vx_f = d1, vy_f = c2;
+            Raw vx_f = d1, vy_f = c2, tvx_f = td1, tvy_f = tc2;
             if (re) {
                 vx_f = X::fix(d1, e.f[F_VX], e, x, j, nvalid, false, true);
                 vy_f = X::fix(c2, e.f[F_VY], e, x, j, nvalid, true, false);
+                if (PAIRS) {
+                    tvx_f = X::fix(td1, e.t[F_VX], e, x, j, nvalid, false, true);
+                    tvy_f = X::fix(tc2, e.t[F_VY], e, x, j, nvalid, true, false);
+                }
             }
-            const AV dxvx = X::dx_half(vx_f, e.f[F_VX], e, x, j, true, le, re);
-            const AV dxvy = X::dx_node(vy_f, e.f[F_VY], e, x, j, false, le, re);
+            const AV dxvx = X::template dx_half<P, PAIRS>(vx_f, tvx_f, e.f[F_VX], e.t[F_VX], e, x, j, true, le, re);
+            const AV dxvy = X::template dx_node<P, PAIRS>(vy_f, tvy_f, e.f[F_VY], e.t[F_VY], e, x, j, false, le, re);
             if (active) {
-                const AV dyvy = vstencil<V>(V::ld(c0), V::ld(c1), V::ld(c2), V::ld(c3));
+                const AV dyvy = vstencil<V>(tap(c0, tc0), tap(c1, tc1), tap(c2, tc2), tap(c3, tc3));
                 const AV l2m = X::coefv(e.c[C_L2M], e.c_uni[C_L2M], q);
                 const AV lam = X::coefv(e.c[C_LAM], e.c_uni[C_LAM], q);
                 const Raw sxx0 = sxx, syy0 = syy, sxy0 = sxy;
                 V::template update<COMP>(sxx, txx, V::add(V::mul(l2m, dxvx), V::mul(lam, dyvy)));
                 V::template update<COMP>(syy, tyy, V::add(V::mul(lam, dxvx), V::mul(l2m, dyvy)));
-                const AV R = V::add(dxvy, vstencil<V>(V::ld(d0), V::ld(d1), V::ld(d2), V::ld(d3)));
+                const AV R = V::add(dxvy, vstencil<V>(tap(d0, td0), tap(d1, td1), tap(d2, td2), tap(d3, td3)));
                 V::template update<COMP>(sxy, txy, V::mul(X::coefv(e.c[C_MU], e.c_uni[C_MU], q), R));
                 X::store(e.f[F_SXX], q, sxx, nvalid);
                 X::store(e.f[F_SYY], q, syy, nvalid);
@@ -287,7 +364,27 @@ __global__ void __launch_bounds__(256) el_s_strip(const ElParams e, int nitems, 
                     X::store(e.t[F_SYY], q, tyy, nvalid);
                     X::store(e.t[F_SXY], q, txy, nvalid);
                 }
-                if (ENERGY) {
+                if (ENERGY && PAIRS) {
+                    // binary64 terms with the binary32 multipliers (CoefOf)
+                    const double wrow = (e.bc[2] == EBC_FREE && j == 0) ? 0.5 : 1.0;
+#pragma unroll
+                    for (int k = 0; k < N; k++) {
+                        if (k < nvalid) {
+                            const double bx = coef_f32<P>(e.c[0], e.c_uni[0], q + k);
+                            const double by = coef_f32<P>(e.c[1], e.c_uni[1], q + k);
+                            const double L = coef_f32<P>(e.c[2], e.c_uni[2], q + k);
+                            const double M = coef_f32<P>(e.c[3], e.c_uni[3], q + k);
+                            const double mu = coef_f32<P>(e.c[4], e.c_uni[4], q + k);
+                            const double vxv = V::f32(d1, k), vyv = V::f32(c2, k);
+                            const double a0 = V::f32(sxx0, k), a1 = V::f32(sxx, k);
+                            const double b0 = V::f32(syy0, k), b1 = V::f32(syy, k);
+                            double t = wrow * (vxv * vxv / bx) + vyv * vyv / by;
+                            t += wrow * ((L * (a0 * a1 + b0 * b1) - M * (a0 * b1 + b0 * a1)) / (L * L - M * M));
+                            if (mu > 0.0) t += (double)V::f32(sxy0, k) * (double)V::f32(sxy, k) / mu;
+                            en += t;
+                        }
+                    }
+                } else if (ENERGY) {
                     // binary64 terms, as in the one-thread-per-point kernel
                     const Raw cb[5] = {e.c[0] ? X::load(e.c[0], q) : V::zero(), e.c[1] ? X::load(e.c[1], q) : V::zero(),
                                        e.c[2] ? X::load(e.c[2], q) : V::zero(), e.c[3] ? X::load(e.c[3], q) : V::zero(),
@@ -318,6 +415,8 @@ __global__ void __launch_bounds__(256) el_s_strip(const ElParams e, int nitems, 
             }
             c0 = c1; c1 = c2; c2 = c3;
             d0 = d1; d1 = d2; d2 = d3;
+            tc0 = tc1; tc1 = tc2; tc2 = tc3;
+            td0 = td1; td1 = td2; td2 = td3;
         }
         if (ENERGY) {
             for (int off = 16; off > 0; off >>= 1) en += __shfl_down_sync(0xffffffffu, en, off);
@@ -378,6 +477,7 @@ cudaError_t elastic_strip_half_step(const ElParams &e, int prec, int comp, int h
     case PREC_BF16: return launch_c<BF16>(e, comp, half, L, st);
     case PREC_FP16_F32ARITH: return launch_c<F16W>(e, comp ? 3 : 0, half, L, st);
     case PREC_BF16_F32ARITH: return launch_c<BF16W>(e, comp ? 3 : 0, half, L, st);
+    case PREC_FP16_PAIRS: return comp ? launch_t<F16WP, 3>(e, half, L, st) : cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }

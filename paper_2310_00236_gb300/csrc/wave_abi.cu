@@ -455,7 +455,8 @@ static wave_status elastic_coefficients(wave_ctx *c, const wave_materials *mat) 
     }
     const double Z0 = rho0 * c0, h = c->h, dt = c->dt;
     c->Z0 = Z0;
-    const double tiny = min_normal(c->prec);
+    const int cp = coef_prec(c->prec);  // binary32 for the pair precision
+    const double tiny = min_normal(cp);
     for (int w = 0; w < 5; w++) c->coef_host[w].assign(npts, 0.0);
     auto lame = [&](int64_t q, double &m, double &l) {
         m = (mat->rho[q] * mat->vs[q]) * mat->vs[q];
@@ -468,8 +469,8 @@ static wave_status elastic_coefficients(wave_ctx *c, const wave_materials *mat) 
             const int64_t j1 = j + 1 < ny ? j + 1 : (c->bc[3] == WAVE_BC_PERIODIC ? 0 : j);
             const double rx = (mat->rho[q] + mat->rho[i1 + nx * j]) * 0.5;
             const double ry = (mat->rho[q] + mat->rho[i + nx * j1]) * 0.5;
-            const double bx = round_store(c->prec, ((dt * Z0) / h) / rx);
-            const double by = round_store(c->prec, ((dt * Z0) / h) / ry);
+            const double bx = round_store(cp, ((dt * Z0) / h) / rx);
+            const double by = round_store(cp, ((dt * Z0) / h) / ry);
             double m00, l00, m10, l10, m01, l01, m11, l11;
             lame(q, m00, l00);
             lame(i1 + nx * j, m10, l10);
@@ -477,12 +478,12 @@ static wave_status elastic_coefficients(wave_ctx *c, const wave_materials *mat) 
             lame(i1 + nx * j1, m11, l11);
             const bool surface = c->bc[2] == WAVE_BC_FREE && j == 0;
             const double msurf = ((4.0 * m00) * (l00 + m00)) / (l00 + 2.0 * m00);
-            const double l2m = round_store(c->prec, ((dt * (surface ? msurf : l00 + 2.0 * m00)) / Z0) / h);
-            const double lam = surface ? 0.0 : round_store(c->prec, ((dt * l00) / Z0) / h);
+            const double l2m = round_store(cp, ((dt * (surface ? msurf : l00 + 2.0 * m00)) / Z0) / h);
+            const double lam = surface ? 0.0 : round_store(cp, ((dt * l00) / Z0) / h);
             double mh = 0.0;
             if (m00 > 0.0 && m10 > 0.0 && m01 > 0.0 && m11 > 0.0)
                 mh = 4.0 / (1.0 / m00 + 1.0 / m10 + 1.0 / m01 + 1.0 / m11);
-            const double mu = round_store(c->prec, ((dt * mh) / Z0) / h);
+            const double mu = round_store(cp, ((dt * mh) / Z0) / h);
             c->coef_host[0][q] = bx;
             c->coef_host[1][q] = by;
             c->coef_host[2][q] = l2m;
@@ -675,7 +676,6 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
     if (prec == WAVE_FP16_PAIRS) {
         // the stencils read V + T: nothing to read without the compensation
         if (compensated == WAVE_COMP_NONE) return fail(WAVE_EINVAL, "WAVE_FP16_PAIRS needs a compensation");
-        if (mat->kind != WAVE_ACOUSTIC) return fail(WAVE_ENOTIMPL, "WAVE_FP16_PAIRS covers the acoustic system");
     }
     if (!mat->rho || !mat->vp) return fail(WAVE_EINVAL, "material arrays are NULL");
     if (mat->kind == WAVE_ELASTIC && !mat->vs) return fail(WAVE_EINVAL, "elastic needs vs");

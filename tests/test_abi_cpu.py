@@ -69,7 +69,6 @@ def _ones(n=(16, 16)):
     (dict(z_cut=1, kind=W.WAVE_ELASTIC, vs=True), W.WAVE_EINVAL),  # acoustic only
     (dict(precision=7), W.WAVE_EINVAL),
     (dict(precision=W.WAVE_FP16_PAIRS, comp=0), W.WAVE_EINVAL),        # pairs need T
-    (dict(precision=W.WAVE_FP16_PAIRS, kind=W.WAVE_ELASTIC, vs=True), W.WAVE_ENOTIMPL),
     (dict(precision=W.WAVE_FP16_PAIRS, z_cut=1, n=(16, 16, 16)), W.WAVE_ENOTIMPL),
     (dict(precision=W.WAVE_FP16_PAIRS, kernel=3), W.WAVE_ENOTIMPL),    # one-pass strips
     (dict(kernel=4, n=(16, 16, 16)), W.WAVE_EINVAL),                   # cluster steps are 2D

@@ -12,7 +12,7 @@ import pytest
 
 import oracle as O
 from paper_2310_00236_gb300 import wave as W
-from wave_helpers import PREC, gpu_bits, to_bits
+from wave_helpers import PAIRS, PREC, gpu_bits, to_bits
 
 pytestmark = pytest.mark.gpu
 PER, RIG, FREE = W.WAVE_BC_PERIODIC, W.WAVE_BC_RIGID, W.WAVE_BC_FREE
@@ -40,8 +40,10 @@ def elastic_pair(shape, bc, prec, comp, h, dt, rho, vp, vs, init, P0, src=None, 
     code, sfmt, afmt = PREC[prec]
     ctx = W.wave_create(shape, h, rho, vp, dt, code, comp, vs=vs, bc=list(bc) + [0, 0],
                         kind=W.WAVE_ELASTIC, field_scale=P0, kernel=kernel)
+    # the pair precision: stencil taps RN32(V + T), multipliers in binary32
+    pairs = prec in PAIRS
     st = O.elastic_setup(shape, bc, h, dt, rho, vp, vs, sfmt, comp, P0=P0, arith_fmt=afmt,
-                         init=init)
+                         init=init, pair_stencil=pairs, coef_fmt=O.FP32 if pairs else None)
     for name, fid in FIELDS:
         if name in init:
             W.wave_set_initial(ctx, fid, init[name])
@@ -111,7 +113,7 @@ def _run(shape, bc, prec, comp, steps, src=False, energy=False, seed=0, kernel=0
 
 
 VARIANTS = [("fp16", 0), ("fp16", 3), ("fp16", 6), ("bf16", 3), ("bf16", 6), ("fp32", 0),
-            ("fp32", 3), ("fp16_f32arith", 3), ("bf16_f32arith", 0)]
+            ("fp32", 3), ("fp16_f32arith", 3), ("bf16_f32arith", 0), ("fp16_pairs", 3)]
 BCS = [(RIG, RIG, FREE, RIG), (PER, PER, FREE, RIG), (PER, PER, PER, PER), (RIG, RIG, RIG, RIG)]
 
 

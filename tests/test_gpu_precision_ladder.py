@@ -22,7 +22,8 @@ pytestmark = pytest.mark.gpu
 R = W.WAVE_BC_RIGID
 VARIANTS = [("fp16", 0), ("fp16", 3), ("fp16", 6), ("bf16", 0), ("bf16", 3), ("bf16", 6),
             ("fp16_f32arith", 0), ("fp16_f32arith", 3), ("bf16_f32arith", 3), ("fp32", 0)]
-VARIANTS_3D = VARIANTS + [("fp16_pairs", 3)]
+# the paper's variants and the pair precision (not the paper's scheme)
+LADDER = VARIANTS + [("fp16_pairs", 3)]
 
 
 def _rel(a, b):
@@ -36,7 +37,7 @@ def test_precision_ladder_3d_acoustic():
     ref = O.acoustic_setup(shape, (1, 1, 1), w["h"], w["dt"], w["rho"], w["c"], O.FP64, 0, p0=w["p0"])
     _, E = ref.run(steps, energy=True)
     rows = {}
-    for prec, comp in VARIANTS_3D:
+    for prec, comp in LADDER:
         code = PREC[prec][0]
         ctx = W.wave_create(shape, w["h"], w["rho"], w["c"], w["dt"], code, comp, bc=[R] * 6)
         try:
@@ -96,7 +97,7 @@ def test_precision_ladder_2d_elastic():
     fids = (W.WAVE_F_VX, W.WAVE_F_VY, W.WAVE_F_SXX, W.WAVE_F_SYY, W.WAVE_F_SXY)
     refv = np.concatenate([ref.f[k].ravel() for k in names])
     rows = {}
-    for prec, comp in VARIANTS:
+    for prec, comp in LADDER:
         code = PREC[prec][0]
         ctx = W.wave_create(shape, w["h"], w["rho"], w["vp"], w["dt"], code, comp, vs=w["vs"],
                             bc=[1, 1, 2, 1, 0, 0], kind=W.WAVE_ELASTIC, field_scale=P0)
@@ -119,6 +120,8 @@ def test_precision_ladder_2d_elastic():
     for s in ("fp16", "bf16"):
         assert abs(rows[(s, 3)][1]) < abs(rows[(s, 0)][1])
         assert _close(rows[(s, 3)], rows[(s, 6)], rows[(s, 0)])
+    # the pair precision reads V + T in its stencils (and binary32 multipliers)
+    assert rows[("fp16_pairs", 3)][0] < 0.2 * rows[("fp16_f32arith", 3)][0]
     for k, (err, _) in rows.items():
         if k != ("fp32", 0):
             assert err > 10 * rows[("fp32", 0)][0]
