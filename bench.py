@@ -377,15 +377,18 @@ def run_e2e(W, w, prec_name, comp, steps):
             "finite": bool(np.isfinite(p).all())}
 
 
-def run_elastic(W, steps: int, warmup: int):
+def run_elastic(W, steps: int, warmup: int, precision=None, comp=None, pairs_too=True):
     """2D elastic three-layer workload (1024^2, free top, rigid sides, Ricker
-    15 Hz vertical force for 0.1 s), fp16 + sum_6op. L2-resident (~31 MB)."""
+    15 Hz vertical force for 0.1 s), fp16 + sum_6op (and, beside it, the pair
+    precision). L2-resident (~31 MB)."""
     import torch
     from paper_2310_00236_gb300 import inputs
     w = inputs.elastic_2d_layered()
     stream = torch.cuda.Stream()  # a created stream: the library replays step graphs on it
-    ctx = W.wave_create(w["shape"], w["h"], w["rho"], w["vp"], w["dt"], W.WAVE_FP16,
-                        W.WAVE_COMP_6OP, vs=w["vs"], bc=[1, 1, 2, 1, 0, 0], kind=W.WAVE_ELASTIC,
+    precision = W.WAVE_FP16 if precision is None else precision
+    comp = W.WAVE_COMP_6OP if comp is None else comp
+    ctx = W.wave_create(w["shape"], w["h"], w["rho"], w["vp"], w["dt"], precision,
+                        comp, vs=w["vs"], bc=[1, 1, 2, 1, 0, 0], kind=W.WAVE_ELASTIC,
                         field_scale=1e5, stream=stream.cuda_stream)
     try:
         # amplitude: the scaled peak increment w dt Z0 / (P0 h^2) is 0.5
@@ -416,10 +419,19 @@ def run_elastic(W, steps: int, warmup: int):
     # the stresses, their t, v, l2m, lam, mu (22 B) and writes the stresses
     # and their t (12 B). The ~31 MB state stays in L2.
     bpp = (18 + 8) + (22 + 12)
-    return {"workload": "2d_elastic_1024_three_layers_free_top", "precision": "fp16",
-            "compensation": "sum_6op", "value": gpts, "unit": UNIT,
-            "ms_per_step": ms / steps, "energy_drift_after_source": abs(e1 - e0) / abs(e0),
-            "state_bytes_per_point_step": bpp, "state_gbs": bpp * gpts, "resident": "L2"}
+    out = {"workload": "2d_elastic_1024_three_layers_free_top", "precision": "fp16",
+           "compensation": "sum_6op", "value": gpts, "unit": UNIT,
+           "ms_per_step": ms / steps, "energy_drift_after_source": abs(e1 - e0) / abs(e0),
+           "state_bytes_per_point_step": bpp, "state_gbs": bpp * gpts, "resident": "L2"}
+    if precision == W.WAVE_FP16_PAIRS:
+        out["precision"], out["compensation"] = "fp16_pairs", "f32 registers"
+        # binary32 multipliers: 10 more bytes per point and step
+        out["state_bytes_per_point_step"] = bpp + 10
+        out["state_gbs"] = (bpp + 10) * gpts
+    elif pairs_too:
+        p = run_elastic(W, steps, warmup, W.WAVE_FP16_PAIRS, W.WAVE_COMP_3OP, pairs_too=False)
+        out["pairs"] = {k: p[k] for k in ("value", "ms_per_step", "energy_drift_after_source", "state_gbs")}
+    return out
 
 
 def run_batched(W, steps: int, warmup: int, nshots: int = 64):
