@@ -163,12 +163,13 @@ static void parallel_for(int64_t n, F f) {
     for (auto &x : th) x.join();
 }
 
-// z planes per block of the one-pass 3D step: 24 (each block recomputes 3
-// warm-up planes, so longer chunks waste less; 20 to 32 measured within 0.5 %
-// of each other at 512^3, 16 was 3 % slower), halved while the grid would
-// have fewer blocks than the GPU runs at once (4 per SM), down to 6.
+// z planes per block of the one-pass 3D step: 32 (each block recomputes 3
+// warm-up planes, so longer chunks waste less; at 512^3 16 / 20 / 24 / 28 /
+// 32 / 40 planes gave 152.6 / 158.2 / 160.6 / 161.8 / 162.5 / 161.9 Gpt/s),
+// halved while the grid would have fewer blocks than the GPU runs at once
+// (4 per SM), down to 6.
 static int fused_zchunk_for(const AcParams &prm, int prec, int sms) {
-    int zc = 24;
+    int zc = 32;
     while (zc > 6 && (int64_t)acoustic_fused_blocks(prm, prec, zc) < 4 * (int64_t)sms) zc /= 2;
     return zc;
 }
