@@ -467,6 +467,17 @@ def run_batched(W, steps: int, warmup: int, nshots: int = 64):
         ms = ev0.elapsed_time(ev1)
         e1 = [W.wave_energy(c) for c in ctxs]
         info = W.wave_batch_info(batch)
+        # beside the tuned choice: every step of a call in one cooperative
+        # launch (launch shapes 14 and 16: rows of 16, 8 and 4 warps per block)
+        persistent = {}
+        for shape in (14, 16):
+            W.wave_batch_set_shape(batch, shape)
+            W.wave_batch_step(batch, 8)
+            ev0.record(stream)
+            W.wave_batch_step(batch, steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            persistent[shape] = ev0.elapsed_time(ev1)
     finally:
         if batch is not None:
             W.wave_batch_destroy(batch)
@@ -474,13 +485,16 @@ def run_batched(W, steps: int, warmup: int, nshots: int = 64):
             W.wave_destroy(c)
     cells = int(np.sum(sides.astype(np.int64) ** 2))
     gpts = cells * steps / (ms * 1e-3) / 1e9
+    pbest = min(persistent, key=persistent.get)
     launches_per_step = 2  # velocity and pressure half steps (the first advances the step counters)
     return {"workload": "2d_acoustic_64_shots_sides_256_2048", "shots": int(nshots), "cells": cells,
             "precision": "fp16", "compensation": "sum_3op", "value": gpts, "unit": UNIT,
             "ms_per_step": ms / steps, "launch": info,
             "hbm_gbs_algorithmic": BYTES_2D * gpts, "bytes_per_point": BYTES_2D,
             "gpu_launches": launches_per_step * steps + 1,
-            "finite": bool(np.all(np.isfinite(e1))), "energy_min": float(min(e1))}
+            "finite": bool(np.all(np.isfinite(e1))), "energy_min": float(min(e1)),
+            "persistent": {"value": cells * steps / (persistent[pbest] * 1e-3) / 1e9, "shape": pbest,
+                           "ms_per_step": persistent[pbest] / steps, "launches": 2}}
 
 
 def run_adjoint(W, steps: int, n: int = 256, nshots: int = 16):

@@ -387,22 +387,35 @@ wave_status wave_get_gradient(wave_ctx *ctx, float *device_out, int64_t *steps_l
  * receivers set. The contexts stay valid and owned by the caller; they must
  * outlive the batch. Errors: EINVAL (mixed contexts, nctx outside 1..1024),
  * ENOMEM, ECUDA.
- * wave_batch_step -- advance every context of the batch n steps: each step is
- * two launches over one work list of (shot, tile) items, with each shot's
- * arithmetic identical to wave_step on that context alone (the same bits).
- * The first call with enough steps times the candidate tile shapes and grid
- * sizes on its first steps (real steps of the problems) and keeps the
- * fastest; runs of steps are then replayed from a captured CUDA graph when the
+ * wave_batch_step -- advance every context of the batch n steps over one work
+ * list of (shot, tile) items, with each shot's arithmetic identical to
+ * wave_step on that context alone (the same bits). Launch kinds: two launches
+ * per step (tiles of points, or row strips), one launch per step (one-pass
+ * row strips), or every step of the call in one cooperative launch (row
+ * strips with a grid barrier between the half steps; every block resident;
+ * a barrier wait is bounded, about a second, and on expiry every context's
+ * error word is set: wave_energy then returns ETIMEOUT). The first call with
+ * enough steps (25) times the candidate launch shapes on its first steps
+ * (real steps of the problems) and keeps the fastest; runs of steps of the
+ * two-launch kinds are then replayed from a captured CUDA graph when the
  * stream is not the legacy default stream. The energy of the last step is
  * available per context through wave_energy. Asynchronous.
+ * wave_batch_set_shape -- use candidate launch shape `shape` (0 .. 23, the
+ * tuner's list: 0-1 tiles of points, 2-13 two-launch strips, 14-17 the
+ * persistent cooperative launch, 18-23 one-pass strips) instead of tuning.
+ * Errors: EINVAL (index out of range; a one-pass shape without every
+ * context's second buffer set, or with WAVE_FP16_PAIRS).
  * wave_batch_info -- the launch configuration in use, written to
  * info[0 .. min(ninfo, 7) - 1]: kind (0 one thread per point, 1 one warp per
- * row strip, 2 one-pass row strips), tile width in points, tile height in rows, threads per block,
- * blocks, steps per graph replay (0 when no graph is in use), tuned (0/1).
+ * row strip, 2 one-pass row strips, 3 persistent row strips), tile width in
+ * points, tile height in rows, threads per block, blocks (0 for kind 3: as
+ * many as are resident at once), steps per graph replay (0 when no graph is
+ * in use), tuned (0/1).
  */
 typedef struct wave_batch wave_batch;
 wave_status wave_batch_create(int32_t nctx, wave_ctx *const *ctxs, wave_batch **out);
 wave_status wave_batch_step(wave_batch *batch, int64_t n);
+wave_status wave_batch_set_shape(wave_batch *batch, int32_t shape);
 wave_status wave_batch_info(wave_batch *batch, int32_t *info, int32_t ninfo);
 void wave_batch_destroy(wave_batch *batch);
 

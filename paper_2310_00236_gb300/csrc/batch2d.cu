@@ -18,6 +18,8 @@
 // each array is read about once. Both give the same bits.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "acoustic_point.cuh"
 #include "batch.h"
 #include "strip_common.cuh"
@@ -145,22 +147,13 @@ __device__ __forceinline__ StripItem strip_of(const int *s_item0, int nshots, in
 // hide more of it: 64 shots 136 -> 152 Gpt/s, 8192^2 171 -> 183, at a few
 // bytes of spills.)
 template <class P, int COMP>
-__global__ void __launch_bounds__(256, 3) batch_kv_strip(BatchShot *shots, const int *item0,
-                                                      int nshots, int nitems, int yc) {
-    advance_counters(shots, nshots);
+__device__ __forceinline__ void kv_strip_item(const AcParams &prm, const StripItem &it, int lane) {
     using V = typename VecOf<P>::T;
     using Raw = typename V::Raw;
     using AV = typename V::AV;
     using RS = typename V::RS;
     constexpr int N = V::N;
-    __shared__ int s_item0[kMaxShots + 1];
-    for (int t = threadIdx.x; t <= nshots; t += blockDim.x) s_item0[t] = item0[t];
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
-    for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < nitems; item += gridDim.x * wpb) {
-        const StripItem it = strip_of<N>(s_item0, nshots, item, shots, yc);
-        const AcParams prm = shots[it.s].prm;
+    {
         const int nx = prm.n[0];
         const int x = it.x0 + lane * N;
         const bool active = x < nx;
@@ -253,16 +246,11 @@ __global__ void __launch_bounds__(256, 3) batch_kv_strip(BatchShot *shots, const
     }
 }
 
-// Pressure half step of one strip: p += b (Dx v_x + Dy v_y [+ s]), with the
-// item's energy terms p^n p^{n+1} / b + v_x^2 / a_x + v_y^2 / a_y.
-template <class P, int COMP, bool ENERGY>
-__global__ void __launch_bounds__(256, 3) batch_kp_strip(const BatchShot *__restrict__ shots, const int *item0,
-                                                      int nshots, int nitems, int yc, double *item_part) {
-    using V = typename VecOf<P>::T;
-    using Raw = typename V::Raw;
-    using AV = typename V::AV;
-    using RS = typename V::RS;
-    constexpr int N = V::N;
+template <class P, int COMP>
+__global__ void __launch_bounds__(256, 3) batch_kv_strip(BatchShot *shots, const int *item0,
+                                                      int nshots, int nitems, int yc) {
+    advance_counters(shots, nshots);
+    constexpr int N = VecOf<P>::T::N;
     __shared__ int s_item0[kMaxShots + 1];
     for (int t = threadIdx.x; t <= nshots; t += blockDim.x) s_item0[t] = item0[t];
     __syncthreads();
@@ -271,7 +259,20 @@ __global__ void __launch_bounds__(256, 3) batch_kp_strip(const BatchShot *__rest
     for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < nitems; item += gridDim.x * wpb) {
         const StripItem it = strip_of<N>(s_item0, nshots, item, shots, yc);
         const AcParams prm = shots[it.s].prm;
-        const int64_t step = shots[it.s].step;
+        kv_strip_item<P, COMP>(prm, it, lane);
+    }
+}
+
+// Pressure half step of one strip: p += b (Dx v_x + Dy v_y [+ s]), with the
+// item's energy terms p^n p^{n+1} / b + v_x^2 / a_x + v_y^2 / a_y.
+template <class P, int COMP, bool ENERGY>
+__device__ __forceinline__ double kp_strip_item(const AcParams &prm, int64_t step, const StripItem &it, int lane) {
+    using V = typename VecOf<P>::T;
+    using Raw = typename V::Raw;
+    using AV = typename V::AV;
+    using RS = typename V::RS;
+    constexpr int N = V::N;
+    {
         const int nx = prm.n[0];
         const int x = it.x0 + lane * N;
         const bool active = x < nx;
@@ -390,6 +391,24 @@ __global__ void __launch_bounds__(256, 3) batch_kp_strip(const BatchShot *__rest
             u1 = u2;
             u2 = u3;
         }
+        return e_acc;
+    }
+}
+
+template <class P, int COMP, bool ENERGY>
+__global__ void __launch_bounds__(256, 3) batch_kp_strip(const BatchShot *__restrict__ shots, const int *item0,
+                                                      int nshots, int nitems, int yc, double *item_part) {
+    constexpr int N = VecOf<P>::T::N;
+    __shared__ int s_item0[kMaxShots + 1];
+    for (int t = threadIdx.x; t <= nshots; t += blockDim.x) s_item0[t] = item0[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < nitems; item += gridDim.x * wpb) {
+        const StripItem it = strip_of<N>(s_item0, nshots, item, shots, yc);
+        const AcParams prm = shots[it.s].prm;
+        const int64_t step = shots[it.s].step;
+        double e_acc = kp_strip_item<P, COMP, ENERGY>(prm, step, it, lane);
         if (ENERGY) {
             for (int off = 16; off > 0; off >>= 1) e_acc += __shfl_down_sync(0xffffffffu, e_acc, off);
             if (lane == 0) item_part[item] = e_acc;
@@ -677,6 +696,172 @@ __global__ void batch_energy_reduce(BatchShot *shots, const int *item0, const do
     }
 }
 
+// ------------------------------------------------------------------------
+// Every step of a call in one cooperative launch (BATCH_PERSIST)
+// ------------------------------------------------------------------------
+
+// Grid-wide barrier on a counter that only grows within a launch (zeroed
+// before it): each block's thread 0 adds one and waits until every block has
+// arrived at this and the earlier barriers. The fences order the blocks'
+// writes before the barrier with the reads after it. The wait is bounded
+// (2^24 polls of about 64 ns): on expiry it sets *err, and every block leaves
+// at its next check (the others then expire in turn).
+__device__ __forceinline__ bool grid_barrier(unsigned int *bar, int *err, unsigned int &gen) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        const unsigned int target = (gen + 1u) * gridDim.x;
+        for (uint32_t polls = 0;; polls++) {
+            unsigned int v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if (v >= target) break;
+            if (polls > (1u << 24)) {
+                atomicExch(err, 1);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    gen++;
+    __syncthreads();
+    return *reinterpret_cast<volatile int *>(err) == 0;
+}
+
+// nsteps steps of every shot: velocity strips, barrier, pressure strips,
+// barrier; block 0 advances the step counters at the start of each step (the
+// pressure phase reads them after the barrier); with energy_last the last
+// step's item partials and then each shot's energy (items summed in order).
+template <class P, int COMP>
+__global__ void __launch_bounds__(256, 3) batch_persist_strips(BatchShot *shots, const int *item0, int nshots,
+                                                            int nitems, int yc, int64_t nsteps, int energy_last,
+                                                            double *item_part, unsigned int *bar, int *err) {
+    constexpr int N = VecOf<P>::T::N;
+    __shared__ int s_item0[kMaxShots + 1];
+    __shared__ double warp_sums[8];
+    for (int t = threadIdx.x; t <= nshots; t += blockDim.x) s_item0[t] = item0[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int w0 = blockIdx.x * wpb + (threadIdx.x >> 5), gw = gridDim.x * wpb;
+    unsigned int gen = 0;
+    for (int64_t s = 0; s < nsteps; s++) {
+        if (blockIdx.x == 0)
+            for (int t = threadIdx.x; t < nshots; t += blockDim.x) shots[t].step++;
+        for (int item = w0; item < nitems; item += gw) {
+            const StripItem it = strip_of<N>(s_item0, nshots, item, shots, yc);
+            const AcParams prm = shots[it.s].prm;
+            kv_strip_item<P, COMP>(prm, it, lane);
+        }
+        if (!grid_barrier(bar, err, gen)) return;
+        const bool energy = energy_last && s == nsteps - 1;
+        for (int item = w0; item < nitems; item += gw) {
+            const StripItem it = strip_of<N>(s_item0, nshots, item, shots, yc);
+            const AcParams prm = shots[it.s].prm;
+            const int64_t step = shots[it.s].step;
+            if (energy) {
+                double e = kp_strip_item<P, COMP, true>(prm, step, it, lane);
+                for (int off = 16; off > 0; off >>= 1) e += __shfl_down_sync(0xffffffffu, e, off);
+                if (lane == 0) item_part[item] = e;
+            } else {
+                kp_strip_item<P, COMP, false>(prm, step, it, lane);
+            }
+        }
+        if (!grid_barrier(bar, err, gen)) return;
+    }
+    if (energy_last) {
+        for (int sh = blockIdx.x; sh < nshots; sh += gridDim.x) {
+            double e = 0.0;
+            for (int it = s_item0[sh] + threadIdx.x; it < s_item0[sh + 1]; it += blockDim.x) e += item_part[it];
+            for (int off = 16; off > 0; off >>= 1) e += __shfl_down_sync(0xffffffffu, e, off);
+            if (lane == 0) warp_sums[threadIdx.x >> 5] = e;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double t = 0.0;
+                for (int w = 0; w < wpb; w++) t += warp_sums[w];
+                *shots[sh].prm.e_out = t * shots[sh].prm.e_factor;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// After a persistent launch: an expired barrier marks every shot's context.
+__global__ void batch_err_propagate(BatchShot *shots, int nshots, const int *err) {
+    if (*err == 0) return;
+    for (int s = threadIdx.x; s < nshots; s += blockDim.x)
+        if (shots[s].err) *shots[s].err = 1;
+}
+
+template <class P, int COMP>
+static cudaError_t persist_pc(const BatchLaunch &L, int64_t nsteps, bool energy_last, cudaStream_t st) {
+    void *fn = reinterpret_cast<void *>(&batch_persist_strips<P, COMP>);
+    const int threads = 32 * L.wpb;
+    int dev = 0, sms = 1, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    // every block resident at once (a cooperative launch refuses more)
+    const int grid = std::max(1, std::min((L.nitems + L.wpb - 1) / L.wpb, per_sm * sms));
+    // the barrier counter grows by grid per barrier, two barriers a step: keep
+    // it below 2^31 within a launch
+    const int64_t chunk = std::max<int64_t>(1, ((int64_t)1 << 30) / grid);
+    e = cudaMemsetAsync(L.err, 0, sizeof(int), st);
+    for (int64_t done = 0; done < nsteps && e == cudaSuccess;) {
+        const int64_t n = std::min(chunk, nsteps - done);
+        const int el = (energy_last && done + n == nsteps) ? 1 : 0;
+        e = cudaMemsetAsync(L.bar, 0, sizeof(unsigned int), st);
+        if (e != cudaSuccess) break;
+        BatchShot *shots = L.shots;
+        const int *item0 = L.item0;
+        int nshots = L.nshots, nitems = L.nitems, yc = L.yc;
+        int64_t ns = n;
+        double *part = L.item_part;
+        unsigned int *bar = L.bar;
+        int *err = L.err;
+        void *args[] = {&shots, &item0, &nshots, &nitems, &yc, &ns, const_cast<int *>(&el), &part, &bar, &err};
+        e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, 0, st);
+        done += n;
+    }
+    if (e == cudaSuccess) {
+        batch_err_propagate<<<1, 256, 0, st>>>(L.shots, L.nshots, L.err);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+cudaError_t batch_persist(const BatchLaunch &L, int prec, int comp, int64_t nsteps, bool energy_last,
+                          cudaStream_t st) {
+    if (L.kind != BATCH_PERSIST || L.wpb < 1 || L.wpb > 8 || L.yc < 1 || !L.bar || !L.err)
+        return cudaErrorInvalidValue;
+    if (nsteps < 1) return cudaSuccess;
+    switch (prec) {
+    case PREC_FP32:
+        return comp == 0 ? persist_pc<F32, 0>(L, nsteps, energy_last, st)
+                         : comp == 3 ? persist_pc<F32, 3>(L, nsteps, energy_last, st)
+                                     : persist_pc<F32, 6>(L, nsteps, energy_last, st);
+    case PREC_FP16:
+        return comp == 0 ? persist_pc<F16, 0>(L, nsteps, energy_last, st)
+                         : comp == 3 ? persist_pc<F16, 3>(L, nsteps, energy_last, st)
+                                     : persist_pc<F16, 6>(L, nsteps, energy_last, st);
+    case PREC_BF16:
+        return comp == 0 ? persist_pc<BF16, 0>(L, nsteps, energy_last, st)
+                         : comp == 3 ? persist_pc<BF16, 3>(L, nsteps, energy_last, st)
+                                     : persist_pc<BF16, 6>(L, nsteps, energy_last, st);
+    case PREC_FP16_F32ARITH:
+        return comp ? persist_pc<F16W, 3>(L, nsteps, energy_last, st) : persist_pc<F16W, 0>(L, nsteps, energy_last, st);
+    case PREC_BF16_F32ARITH:
+        return comp ? persist_pc<BF16W, 3>(L, nsteps, energy_last, st)
+                    : persist_pc<BF16W, 0>(L, nsteps, energy_last, st);
+    case PREC_FP16_PAIRS:
+        return comp ? persist_pc<F16WP, 3>(L, nsteps, energy_last, st) : cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 template <class P, int COMP>
 static cudaError_t launch_pc(const BatchLaunch &L, bool energy, cudaStream_t st) {
     if (L.kind == BATCH_FUSED) {
@@ -725,7 +910,7 @@ static cudaError_t launch_p(const BatchLaunch &L, int comp, bool energy, cudaStr
 int batch_max_shots() { return kMaxShots; }
 
 int64_t batch_items_of(int kind, int bx, int by, int yc, int prec, int64_t nx, int64_t ny) {
-    if (kind == BATCH_STRIPS || kind == BATCH_FUSED) {
+    if (kind == BATCH_STRIPS || kind == BATCH_FUSED || kind == BATCH_PERSIST) {
         const int64_t tx = 32 * (prec == PREC_FP32 ? 4 : 8);
         return ((nx + tx - 1) / tx) * ((ny + yc - 1) / yc);
     }
@@ -733,6 +918,7 @@ int64_t batch_items_of(int kind, int bx, int by, int yc, int prec, int64_t nx, i
 }
 
 cudaError_t batch_step(const BatchLaunch &L, int prec, int comp, bool energy, cudaStream_t st) {
+    if (L.kind == BATCH_PERSIST) return batch_persist(L, prec, comp, 1, energy, st);
     if (L.kind == BATCH_STRIPS || L.kind == BATCH_FUSED) {
         if (L.wpb < 1 || L.wpb > 8 || L.yc < 1) return cudaErrorInvalidValue;
     } else if (L.bx * L.by > 256 || (L.bx * L.by) % 32 != 0) {

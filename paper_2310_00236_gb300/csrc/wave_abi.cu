@@ -1193,6 +1193,7 @@ static void fill_shot(wave_ctx *c, BatchShot &shot) {
         shot.alt_tv[ax] = c->alt_t[1 + ax].ptr;
     }
     shot.fsteps = 0;
+    shot.err = reinterpret_cast<int *>(static_cast<char *>(c->e_misc.ptr) + 16);
 }
 
 static wave_status acoustic_steps(wave_ctx *c, int64_t n, bool energy_last = true) {
@@ -2006,6 +2007,7 @@ struct wave_batch {
     BatchShot *d_shots = nullptr;
     int *d_item0 = nullptr;
     double *d_part = nullptr;
+    unsigned int *d_sync = nullptr;  // [barrier counter][error word] of the persistent launches
     std::vector<BatchShot> h_shots;
     int shape = 0, nitems = 0, sms = 1;
     bool tuned = false;
@@ -2025,6 +2027,10 @@ static const BatchShape kShapes[] = {
     {BATCH_STRIPS, 0, 0, 16, 4, 8},  {BATCH_STRIPS, 0, 0, 16, 4, 16},
     {BATCH_STRIPS, 0, 0, 32, 4, 8},  {BATCH_STRIPS, 0, 0, 32, 4, 16},
     {BATCH_STRIPS, 0, 0, 64, 4, 8},  {BATCH_STRIPS, 0, 0, 64, 4, 16},
+    // every step of a call in one cooperative launch (grid: as many blocks as
+    // are resident at once)
+    {BATCH_PERSIST, 0, 0, 16, 8, 0}, {BATCH_PERSIST, 0, 0, 32, 8, 0},
+    {BATCH_PERSIST, 0, 0, 16, 4, 0}, {BATCH_PERSIST, 0, 0, 32, 4, 0},
     // one-pass strips last (the tuner runs the candidates in this order)
     {BATCH_FUSED, 0, 0, 16, 4, 8},   {BATCH_FUSED, 0, 0, 16, 4, 16},
     {BATCH_FUSED, 0, 0, 32, 4, 8},   {BATCH_FUSED, 0, 0, 32, 4, 16},
@@ -2066,6 +2072,8 @@ static BatchLaunch batch_launch(wave_batch *b) {
     L.yc = sh.yc;
     L.wpb = sh.wpb;
     L.grid = sh.grid_per_sm * b->sms;
+    L.bar = b->d_sync;
+    L.err = reinterpret_cast<int *>(b->d_sync + 1);
     return L;
 }
 
@@ -2076,6 +2084,7 @@ extern "C" void wave_batch_destroy(wave_batch *b) {
     if (b->d_shots) cudaFree(b->d_shots);
     if (b->d_item0) cudaFree(b->d_item0);
     if (b->d_part) cudaFree(b->d_part);
+    if (b->d_sync) cudaFree(b->d_sync);
     delete b;
 }
 
@@ -2111,6 +2120,7 @@ extern "C" wave_status wave_batch_create(int32_t nctx, wave_ctx *const *ctxs, wa
     cudaError_t e = cudaMalloc(&b->d_shots, sizeof(BatchShot) * nctx);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_item0, sizeof(int) * (nctx + 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_part, sizeof(double) * (size_t)max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sync, 2 * sizeof(unsigned int));
     if (e == cudaSuccess) e = batch_set_shape(b, kDefaultShape);
     if (e != cudaSuccess) {
         wave_batch_destroy(b);
@@ -2202,6 +2212,16 @@ extern "C" wave_status wave_batch_step(wave_batch *b, int64_t n) {
         b->tuned = true;
     }
     const BatchLaunch L = batch_launch(b);
+    if (kShapes[b->shape].kind == BATCH_PERSIST) {
+        // every remaining step in one cooperative launch (the last with the energy)
+        e = batch_persist(L, b->prec, b->comp, left, true, b->stream);
+        if (e != cudaSuccess) return batch_fail(b, e, "batch persistent launch");
+        for (auto *c : b->ctx) {
+            c->step += n;
+            c->have_energy = true;
+        }
+        return WAVE_OK;
+    }
     int64_t plain = left - 1;  // steps without energy; the last step reduces it
     const int G = 32;
     if (b->tuned && b->stream != nullptr && plain >= G) {
@@ -2242,10 +2262,28 @@ extern "C" wave_status wave_batch_step(wave_batch *b, int64_t n) {
     return WAVE_OK;
 }
 
+extern "C" wave_status wave_batch_set_shape(wave_batch *b, int32_t shape) {
+    if (!b) return fail(WAVE_EINVAL, "wave_batch_set_shape: NULL batch");
+    if (shape < 0 || shape >= kNumShapes) return fail(WAVE_EINVAL, "launch shape %d not in 0..%d", shape, kNumShapes - 1);
+    if (!batch_shape_allowed(b, shape))
+        return fail(WAVE_EINVAL, "launch shape %d needs every context's second buffer set (kernel 3)", shape);
+    if (b->prec == WAVE_FP16_PAIRS && kShapes[shape].kind == BATCH_FUSED)
+        return fail(WAVE_EINVAL, "the one-pass strips read the stored values only");
+    cudaError_t e = batch_set_shape(b, shape);
+    if (e != cudaSuccess) return batch_fail(b, e, "batch shape");
+    if (b->gexec) {  // the captured graph belongs to the previous shape
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+        b->gsteps = 0;
+    }
+    b->tuned = true;
+    return WAVE_OK;
+}
+
 extern "C" wave_status wave_batch_info(wave_batch *b, int32_t *info, int32_t ninfo) {
     if (!b || !info) return fail(WAVE_EINVAL, "NULL argument");
     const BatchShape &sh = kShapes[b->shape];
-    const bool strips = sh.kind == BATCH_STRIPS || sh.kind == BATCH_FUSED;
+    const bool strips = sh.kind == BATCH_STRIPS || sh.kind == BATCH_FUSED || sh.kind == BATCH_PERSIST;
     const int32_t v[7] = {sh.kind, strips ? 32 * (b->prec == WAVE_FP32 ? 4 : 8) : sh.bx,
                           strips ? sh.yc : sh.by, strips ? 32 * sh.wpb : sh.bx * sh.by,
                           sh.grid_per_sm * b->sms, b->gexec ? b->gsteps : 0, b->tuned ? 1 : 0};

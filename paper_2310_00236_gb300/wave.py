@@ -36,7 +36,7 @@ EXPORTS = ["wave_set_allocator", "wave_create", "wave_set_initial", "wave_set_so
            "wave_get_state", "wave_set_state", "wave_sync", "wave_steps_done",
            "wave_adjoint_step", "wave_destroy", "wave_last_error", "wave_build_info",
            "wave_set_timing", "wave_get_timing", "wave_energy_acoustic_static",
-           "wave_batch_create", "wave_batch_step", "wave_batch_info", "wave_batch_destroy",
+           "wave_batch_create", "wave_batch_step", "wave_batch_set_shape", "wave_batch_info", "wave_batch_destroy",
            "wave_record", "wave_get_gradient", "wave_reset", "wave_selftest_timeout",
            "wave_set_z_ghosts", "wave_half_step", "wave_copy_planes", "wave_get_layout"]
 
@@ -107,6 +107,7 @@ def lib() -> C.CDLL:
         "wave_get_gradient": [vp, vp, C.POINTER(C.c_int64)],
         "wave_batch_create": [i32, C.POINTER(vp), C.POINTER(vp)],
         "wave_batch_step": [vp, i64],
+        "wave_batch_set_shape": [vp, i32],
         "wave_batch_info": [vp, C.POINTER(C.c_int32), i32],
         "wave_set_z_ghosts": [vp, vp, vp, vp, vp],
         "wave_half_step": [vp, i32],
@@ -453,8 +454,15 @@ def wave_batch_info(batch: Batch) -> dict:
     steps, tuned)."""
     v = (C.c_int32 * 7)()
     _check(lib().wave_batch_info(batch.ptr, v, 7))
-    return {"kind": ("points", "strips", "one-pass strips")[v[0]], "tile_x": v[1], "tile_y": v[2], "threads": v[3],
+    return {"kind": ("points", "strips", "one-pass strips", "persistent strips")[v[0]], "tile_x": v[1], "tile_y": v[2], "threads": v[3],
             "blocks": v[4], "graph_steps": v[5], "tuned": bool(v[6])}
+
+
+def wave_batch_set_shape(batch: Batch, shape: int):
+    """Use candidate launch shape `shape` of the tuner's list instead of tuning
+    (0-1 tiles of points, 2-13 two-launch strips, 14-17 persistent strips,
+    18-23 one-pass strips)."""
+    _check(lib().wave_batch_set_shape(batch.ptr, int(shape)))
 
 
 def wave_batch_destroy(batch: Batch):

@@ -46,7 +46,7 @@ def _fields(ctx, comp):
     return out
 
 
-def _run_case(shapes, bcs, prec, comp, calls, stream=None, oracle_shot=0, kernel=0):
+def _run_case(shapes, bcs, prec, comp, calls, stream=None, oracle_shot=0, kernel=0, shape=None):
     """Batch the shots and step them by the step counts in `calls`; step twin
     contexts (default kernels) one by one; compare bits and energies.
     kernel = 3: the batched contexts keep the second buffer set, so the tuner
@@ -56,6 +56,8 @@ def _run_case(shapes, bcs, prec, comp, calls, stream=None, oracle_shot=0, kernel
     twins = [_shot(s, b, prec, comp, 100 + i, total, stream)[0] for i, (s, b) in enumerate(zip(shapes, bcs))]
     ctxs = [p[0] for p in pairs]
     batch = W.wave_batch_create(ctxs)
+    if shape is not None:
+        W.wave_batch_set_shape(batch, shape)
     try:
         for n in calls:
             W.wave_batch_step(batch, n)
@@ -105,13 +107,18 @@ def test_batch_autotune_and_graph_replay():
         info = _run_case(SHAPES[:3], BCS[:3], "fp16", 3, [100, 40, 1, 7], stream=stream.cuda_stream,
                          oracle_shot=2)
     assert info["tuned"]
-    assert info["blocks"] > 0 and info["threads"] % 32 == 0
-    assert info["graph_steps"] == 32
+    assert info["threads"] % 32 == 0
+    # the two-launch kinds replay graphs of 32 steps; the persistent kind runs
+    # every step of a call in one cooperative launch
+    if info["kind"] == "persistent strips":
+        assert info["graph_steps"] == 0
+    else:
+        assert info["blocks"] > 0 and info["graph_steps"] == 32
 
 
 @pytest.mark.parametrize("prec,comp", [("fp16", 3), ("fp32", 0)])
 def test_batch_one_pass_candidates_bit_exact(prec, comp):
-    """Contexts with the second buffer set: the tuner runs all 20 launch
+    """Contexts with the second buffer set: the tuner runs all 24 launch
     shapes (the one-pass strips last), the state follows the buffer sets
     through odd and even step counts, and every shot equals its twin stepped
     alone by the two-launch strips."""
@@ -144,3 +151,18 @@ def test_batch_rejects_mixed_contexts():
     finally:
         for c in (a, b, c3):
             W.wave_destroy(c)
+
+
+@pytest.mark.parametrize("prec,comp", [("fp16", 3), ("fp32", 0), ("bf16", 6), ("fp16_pairs", 3)])
+@pytest.mark.parametrize("shape", [14, 17])
+def test_batch_persistent_launch_bit_exact(prec, comp, shape):
+    """The persistent kind (every step of a call in one cooperative launch,
+    grid barriers between the half steps): every shot equals its twin stepped
+    alone, over calls of several lengths, one shot equals the oracle, and the
+    per-shot energies agree."""
+    import torch
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        info = _run_case(SHAPES, BCS, prec, comp, [30, 1, 7, 64], stream=stream.cuda_stream, oracle_shot=3,
+                         shape=shape)
+    assert info["kind"] == "persistent strips" and info["graph_steps"] == 0
