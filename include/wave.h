@@ -391,8 +391,9 @@ wave_status wave_get_gradient(wave_ctx *ctx, float *device_out, int64_t *steps_l
  * list of (shot, tile) items, with each shot's arithmetic identical to
  * wave_step on that context alone (the same bits). Launch kinds: two launches
  * per step (tiles of points, or row strips), one launch per step (one-pass
- * row strips), or every step of the call in one cooperative launch (row
- * strips with a grid barrier between the half steps; every block resident;
+ * row strips), or every step of the call but the last in one cooperative
+ * launch (row strips with a grid barrier between the half steps; every block
+ * resident; the last step, which reduces the energy, on the row strips;
  * a barrier wait is bounded, about a second, and on expiry every context's
  * error word is set: wave_energy then returns ETIMEOUT). The first call with
  * enough steps (25) times the candidate launch shapes on its first steps

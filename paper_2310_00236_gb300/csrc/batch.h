@@ -30,8 +30,9 @@ struct BatchShot {
 //   BATCH_FUSED:   the same strips with both half steps in one launch (new
 //                  velocities of row j, then p of row j - 1), old state read from
 //                  one buffer set and the new state written to the other;
-//   BATCH_PERSIST: the same strips, every step of a call in one cooperative
-//                  launch (grid barriers between the half steps).
+//   BATCH_PERSIST: the same strips, every step of a call but the last (which
+//                  reduces the energy, on the two-launch strips) in one
+//                  cooperative launch (grid barriers between the half steps).
 enum { BATCH_POINTS = 0, BATCH_STRIPS = 1, BATCH_FUSED = 2, BATCH_PERSIST = 3 };
 
 struct BatchLaunch {

@@ -729,17 +729,17 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *bar, int *err, unsign
     return *reinterpret_cast<volatile int *>(err) == 0;
 }
 
-// nsteps steps of every shot: velocity strips, barrier, pressure strips,
-// barrier; block 0 advances the step counters at the start of each step (the
-// pressure phase reads them after the barrier); with energy_last the last
-// step's item partials and then each shot's energy (items summed in order).
+// nsteps plain steps of every shot: velocity strips, barrier, pressure
+// strips, barrier; block 0 advances the step counters at the start of each
+// step (the pressure phase reads them after the barrier). (The step that
+// reduces the energy runs on the two-launch strips: with the energy terms
+// inlined too, this kernel would spill at its 80-register bound.)
 template <class P, int COMP>
 __global__ void __launch_bounds__(256, 3) batch_persist_strips(BatchShot *shots, const int *item0, int nshots,
-                                                            int nitems, int yc, int64_t nsteps, int energy_last,
-                                                            double *item_part, unsigned int *bar, int *err) {
+                                                            int nitems, int yc, int64_t nsteps,
+                                                            unsigned int *bar, int *err) {
     constexpr int N = VecOf<P>::T::N;
     __shared__ int s_item0[kMaxShots + 1];
-    __shared__ double warp_sums[8];
     for (int t = threadIdx.x; t <= nshots; t += blockDim.x) s_item0[t] = item0[t];
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -755,35 +755,13 @@ __global__ void __launch_bounds__(256, 3) batch_persist_strips(BatchShot *shots,
             kv_strip_item<P, COMP>(prm, it, lane);
         }
         if (!grid_barrier(bar, err, gen)) return;
-        const bool energy = energy_last && s == nsteps - 1;
         for (int item = w0; item < nitems; item += gw) {
             const StripItem it = strip_of<N>(s_item0, nshots, item, shots, yc);
             const AcParams prm = shots[it.s].prm;
             const int64_t step = shots[it.s].step;
-            if (energy) {
-                double e = kp_strip_item<P, COMP, true>(prm, step, it, lane);
-                for (int off = 16; off > 0; off >>= 1) e += __shfl_down_sync(0xffffffffu, e, off);
-                if (lane == 0) item_part[item] = e;
-            } else {
-                kp_strip_item<P, COMP, false>(prm, step, it, lane);
-            }
+            kp_strip_item<P, COMP, false>(prm, step, it, lane);
         }
         if (!grid_barrier(bar, err, gen)) return;
-    }
-    if (energy_last) {
-        for (int sh = blockIdx.x; sh < nshots; sh += gridDim.x) {
-            double e = 0.0;
-            for (int it = s_item0[sh] + threadIdx.x; it < s_item0[sh + 1]; it += blockDim.x) e += item_part[it];
-            for (int off = 16; off > 0; off >>= 1) e += __shfl_down_sync(0xffffffffu, e, off);
-            if (lane == 0) warp_sums[threadIdx.x >> 5] = e;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double t = 0.0;
-                for (int w = 0; w < wpb; w++) t += warp_sums[w];
-                *shots[sh].prm.e_out = t * shots[sh].prm.e_factor;
-            }
-            __syncthreads();
-        }
     }
 }
 
@@ -793,6 +771,9 @@ __global__ void batch_err_propagate(BatchShot *shots, int nshots, const int *err
     for (int s = threadIdx.x; s < nshots; s += blockDim.x)
         if (shots[s].err) *shots[s].err = 1;
 }
+
+template <class P, int COMP>
+static cudaError_t launch_pc(const BatchLaunch &L, bool energy, cudaStream_t st);
 
 template <class P, int COMP>
 static cudaError_t persist_pc(const BatchLaunch &L, int64_t nsteps, bool energy_last, cudaStream_t st) {
@@ -809,26 +790,33 @@ static cudaError_t persist_pc(const BatchLaunch &L, int64_t nsteps, bool energy_
     // the barrier counter grows by grid per barrier, two barriers a step: keep
     // it below 2^31 within a launch
     const int64_t chunk = std::max<int64_t>(1, ((int64_t)1 << 30) / grid);
+    // the plain steps in cooperative launches; the last step, which reduces
+    // the energy, on the two-launch strips of the same rows and warps
+    const int64_t plain = energy_last ? nsteps - 1 : nsteps;
     e = cudaMemsetAsync(L.err, 0, sizeof(int), st);
-    for (int64_t done = 0; done < nsteps && e == cudaSuccess;) {
-        const int64_t n = std::min(chunk, nsteps - done);
-        const int el = (energy_last && done + n == nsteps) ? 1 : 0;
+    for (int64_t done = 0; done < plain && e == cudaSuccess;) {
+        const int64_t n = std::min(chunk, plain - done);
         e = cudaMemsetAsync(L.bar, 0, sizeof(unsigned int), st);
         if (e != cudaSuccess) break;
         BatchShot *shots = L.shots;
         const int *item0 = L.item0;
         int nshots = L.nshots, nitems = L.nitems, yc = L.yc;
         int64_t ns = n;
-        double *part = L.item_part;
         unsigned int *bar = L.bar;
         int *err = L.err;
-        void *args[] = {&shots, &item0, &nshots, &nitems, &yc, &ns, const_cast<int *>(&el), &part, &bar, &err};
+        void *args[] = {&shots, &item0, &nshots, &nitems, &yc, &ns, &bar, &err};
         e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, 0, st);
         done += n;
     }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && plain > 0) {
         batch_err_propagate<<<1, 256, 0, st>>>(L.shots, L.nshots, L.err);
         e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && energy_last) {
+        BatchLaunch S = L;
+        S.kind = BATCH_STRIPS;
+        S.grid = 16 * sms * 4 / L.wpb;  // a grid-stride loop: any size works
+        e = launch_pc<P, COMP>(S, true, st);
     }
     return e;
 }
