@@ -77,8 +77,9 @@ typedef enum { WAVE_ACOUSTIC = 0, WAVE_ELASTIC = 1 } wave_physics;
  *     mu) are kept in binary32 (their rounding to binary16 would then be the
  *     largest error left; per-point arrays cost 4 bytes a point). Needs
  *     compensation (WAVE_EINVAL without). Acoustic 3D: the one-pass step
- *     where it applies (t_p then alternates between two buffers), else one
- *     thread per point; 2D: the cluster-resident steps or the two-launch row
+ *     where it applies (t_p then alternates between two buffers), else the
+ *     two-kernel streaming step, else one thread per point (the same choice
+ *     as the other precisions); 2D: the cluster-resident steps or the two-launch row
  *     strips (not kernel 3). No z slabs and no adjoint (WAVE_ENOTIMPL);
  *     wave_energy_acoustic_static does not take it (WAVE_EINVAL).
  *   WAVE_FP64 is accepted only by the CPU oracle; wave_create returns

@@ -15,6 +15,7 @@
 // odd / even images of the p = 0 walls) are applied on every halo load.
 #include <cuda_runtime.h>
 #include "acoustic_common.cuh"
+#include "strip_common.cuh"
 #include "vec_policy.cuh"
 #include "wave_kernels.h"
 
@@ -60,26 +61,7 @@ __device__ __forceinline__ typename V::RS load_x_img(const void *f, const AcPara
     return s < 0 ? V::rneg_s(v) : v;
 }
 
-template <class RS>
-__device__ __forceinline__ RS shfl_rs(RS v, int delta, bool up) {
-    uint32_t u;
-    if (sizeof(RS) == 2) u = (uint32_t)(*reinterpret_cast<const uint16_t *>(&v));
-    else u = *reinterpret_cast<const uint32_t *>(&v);
-    u = up ? __shfl_up_sync(0xffffffffu, u, delta) : __shfl_down_sync(0xffffffffu, u, delta);
-    RS r;
-    if (sizeof(RS) == 2) *reinterpret_cast<uint16_t *>(&r) = (uint16_t)u;
-    else *reinterpret_cast<uint32_t *>(&r) = u;
-    return r;
-}
-
-template <class V>
-__device__ __forceinline__ typename V::AV coef_vec(const void *arr, uint32_t uni, int64_t q) {
-    if (arr) return V::ld(*reinterpret_cast<const typename V::Raw *>(
-                 static_cast<const char *>(arr) + q * sizeof(typename V::RS)));
-    typename V::RS s;
-    from_bits(uni, s);
-    return V::splat(V::lds(s));
-}
+// (multipliers: coef_v of strip_common.cuh, binary32 for the pair precision)
 
 
 constexpr int TXV = 8;  // threads per tile row
@@ -91,14 +73,19 @@ template <class P, int COMP, int TY>
 // (bounded to 64 registers: eight blocks of 128 threads per SM; the kernels
 // wait on global loads, and 32 warps per SM hide more of it than the 20 of the
 // unbounded 96 registers: 512^3 fp16 + sum_3op 92.5 -> 112.3 Gpt/s)
-__global__ void __launch_bounds__(TXV *TY, 8) kv_stream(AcParams prm, int zchunk) {
+// (the pair precision, with the T queues, planes and neighbours beside each
+// field's, at four blocks per SM)
+__global__ void __launch_bounds__(TXV *TY, IsPairs<P>::value ? 4 : 8) kv_stream(AcParams prm, int zchunk) {
     using V = typename VecOf<P>::T;
     using Raw = typename V::Raw;
     using AV = typename V::AV;
     using RS = typename V::RS;
+    using AS = typename V::AS;
     constexpr int N = V::N;
     constexpr int TX = TXV * N;
+    constexpr bool PAIRS = IsPairs<P>::value;
     __shared__ Raw sp[2][TY + 3][TXV];  // local row r <-> global row y0 - 1 + r
+    __shared__ Raw stp[PAIRS ? 2 : 1][PAIRS ? TY + 3 : 1][TXV];  // the pairs: t_p likewise
 
     const int tid = threadIdx.x;
     const int lx = tid % TXV, row = tid / TXV;
@@ -115,15 +102,28 @@ __global__ void __launch_bounds__(TXV *TY, 8) kv_stream(AcParams prm, int zchunk
     const int h_row = y0 - 1 + h_local;
     const int h_x = x0 + (tid % TXV) * N;
 
-    // z queue of the own p vector: planes k-1, k, k+1 (k+2 loaded in the loop)
+    // z queue of the own p vector: planes k-1, k, k+1 (k+2 loaded in the
+    // loop); the pairs: the same queue of t_p (taps RN(p + t_p))
     Raw q0 = load_vec_img<V>(prm.p, prm, x, j, z0 - 1, true, true);
     Raw q1 = load_vec_img<V>(prm.p, prm, x, j, z0, true, true);
     Raw q2 = load_vec_img<V>(prm.p, prm, x, j, z0 + 1, true, true);
+    Raw u0 = V::zero(), u1 = V::zero(), u2 = V::zero();
+    if (PAIRS) {
+        u0 = load_vec_img<V>(prm.tp, prm, x, j, z0 - 1, true, true);
+        u1 = load_vec_img<V>(prm.tp, prm, x, j, z0, true, true);
+        u2 = load_vec_img<V>(prm.tp, prm, x, j, z0 + 1, true, true);
+    }
+    auto tap = [&](const Raw &v, const Raw &t) -> AV { return PAIRS ? V::add(V::ld(v), V::ld(t)) : V::ld(v); };
+    auto tap_s = [&](RS v, RS t) -> AS { return PAIRS ? P::add(V::lds(v), V::lds(t)) : V::lds(v); };
     int buf = 0;
     for (int k = z0; k < z1; k++) {
         Raw q3 = load_vec_img<V>(prm.p, prm, x, j, k + 2, true, true);
-        Raw hv;
-        if (halo_loader) hv = load_vec_img<V>(prm.p, prm, h_x, h_row, k, true, true);
+        Raw u3 = PAIRS ? load_vec_img<V>(prm.tp, prm, x, j, k + 2, true, true) : V::zero();
+        Raw hv, hu = V::zero();
+        if (halo_loader) {
+            hv = load_vec_img<V>(prm.p, prm, h_x, h_row, k, true, true);
+            if (PAIRS) hu = load_vec_img<V>(prm.tp, prm, h_x, h_row, k, true, true);
+        }
         const int64_t q = x + prm.sy * j + prm.sz * (int64_t)k;
         Raw vv[3], tt[3];
         if (active) {
@@ -134,33 +134,45 @@ __global__ void __launch_bounds__(TXV *TY, 8) kv_stream(AcParams prm, int zchunk
             }
         }
         // x neighbours of the own plane-k vector: p[x-1], p[x+N], p[x+N+1]
-        RS l0 = shfl_rs(V::get(q1, N - 1), 1, true);
-        RS r0 = shfl_rs(V::get(q1, 0), 1, false);
-        RS r1 = shfl_rs(V::get(q1, 1), 1, false);
+        // (of t_p too for the pairs)
+        auto xnb = [&](const void *f, const Raw &own_r, RS &l0, RS &r0, RS &r1) {
+            l0 = shfl_rs(V::get(own_r, N - 1), 1, true);
+            r0 = shfl_rs(V::get(own_r, 0), 1, false);
+            r1 = shfl_rs(V::get(own_r, 1), 1, false);
+            if (active) {
+                if (lx == 0) l0 = load_x_img<V>(f, prm, x - 1, j, k, true);
+                if (lx == TXV - 1 || x + N >= prm.n[0]) {
+                    r0 = load_x_img<V>(f, prm, x + N, j, k, true);
+                    r1 = load_x_img<V>(f, prm, x + N + 1, j, k, true);
+                }
+            }
+        };
+        RS l0, r0, r1, l0t = RS(0), r0t = RS(0), r1t = RS(0);
+        xnb(prm.p, q1, l0, r0, r1);
+        if (PAIRS) xnb(prm.tp, u1, l0t, r0t, r1t);
         sp[buf][row + 1][lx] = q1;
         if (halo_loader) sp[buf][h_local][tid % TXV] = hv;
-        if (active) {
-            if (lx == 0) l0 = load_x_img<V>(prm.p, prm, x - 1, j, k, true);
-            if (lx == TXV - 1 || x + N >= prm.n[0]) {
-                r0 = load_x_img<V>(prm.p, prm, x + N, j, k, true);
-                r1 = load_x_img<V>(prm.p, prm, x + N + 1, j, k, true);
-            }
+        if (PAIRS) {
+            stp[buf][row + 1][lx] = u1;
+            if (halo_loader) stp[buf][h_local][tid % TXV] = hu;
         }
         __syncthreads();
         if (active) {
-            const AV own = V::ld(q1);
+            const AV own = tap(q1, u1);
+            const AS a_l0 = tap_s(l0, l0t), a_r0 = tap_s(r0, r0t), a_r1 = tap_s(r1, r1t);
             // v_x at i + 1/2: p[i-1], p[i], p[i+1], p[i+2]
-            AV Dx = vstencil<V>(V::shr1(own, V::lds(l0)), own, V::shl1(own, V::lds(r0)),
-                                V::shl2(own, V::lds(r0), V::lds(r1)));
+            AV Dx = vstencil<V>(V::shr1(own, a_l0), own, V::shl1(own, a_r0), V::shl2(own, a_r0, a_r1));
             // v_y at j + 1/2: rows j-1, j, j+1, j+2 (local rows row, row+1, row+2, row+3)
-            AV Dy = vstencil<V>(V::ld(sp[buf][row][lx]), own, V::ld(sp[buf][row + 2][lx]),
-                                V::ld(sp[buf][row + 3][lx]));
+            auto prow = [&](int r) -> AV {
+                return PAIRS ? tap(sp[buf][r][lx], stp[PAIRS ? buf : 0][PAIRS ? r : 0][lx]) : V::ld(sp[buf][r][lx]);
+            };
+            AV Dy = vstencil<V>(prow(row), own, prow(row + 2), prow(row + 3));
             // v_z at k + 1/2: planes k-1, k, k+1, k+2
-            AV Dz = vstencil<V>(V::ld(q0), own, V::ld(q2), V::ld(q3));
+            AV Dz = vstencil<V>(tap(q0, u0), own, tap(q2, u2), tap(q3, u3));
             AV D[3] = {Dx, Dy, Dz};
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                AV inc = V::mul(coef_vec<V>(prm.a[c], prm.a_uni[c], q), D[c]);
+                AV inc = V::mul(coef_v<V>(prm.a[c], prm.a_uni[c], q), D[c]);
                 V::template update<COMP>(vv[c], tt[c], inc);
                 at<V>(prm.v[c], q) = vv[c];
                 if (COMP) at<V>(prm.tv[c], q) = tt[c];
@@ -169,6 +181,9 @@ __global__ void __launch_bounds__(TXV *TY, 8) kv_stream(AcParams prm, int zchunk
         q0 = q1;
         q1 = q2;
         q2 = q3;
+        u0 = u1;
+        u1 = u2;
+        u2 = u3;
         buf ^= 1;
     }
 }
@@ -191,15 +206,20 @@ struct KSum {
 // Pressure half step: p += b * (Dx vx + Dy vy + Dz vz [+ s]), optional energy.
 // ------------------------------------------------------------------------
 template <class P, int COMP, int TY, bool ENERGY>
-// (64 registers as kv_stream; the energy variant, a call's last step, unbounded)
-__global__ void __launch_bounds__(TXV *TY, ENERGY ? 1 : 8) kp_stream(AcParams prm, int zchunk) {
+// (64 registers as kv_stream, the pairs four blocks per SM; the energy variant,
+// a call's last step, unbounded)
+__global__ void __launch_bounds__(TXV *TY, ENERGY ? 1 : (IsPairs<P>::value ? 4 : 8))
+    kp_stream(AcParams prm, int zchunk) {
     using V = typename VecOf<P>::T;
     using Raw = typename V::Raw;
     using AV = typename V::AV;
     using RS = typename V::RS;
+    using AS = typename V::AS;
     constexpr int N = V::N;
     constexpr int TX = TXV * N;
+    constexpr bool PAIRS = IsPairs<P>::value;
     __shared__ Raw sv[2][TY + 3][TXV];  // v_y, local row r <-> global row y0 - 2 + r
+    __shared__ Raw stv[PAIRS ? 2 : 1][PAIRS ? TY + 3 : 1][TXV];  // the pairs: t_vy likewise
 
     const int tid = threadIdx.x;
     const int lx = tid % TXV, row = tid / TXV;
@@ -215,19 +235,36 @@ __global__ void __launch_bounds__(TXV *TY, ENERGY ? 1 : 8) kp_stream(AcParams pr
     const int h_row = y0 - 2 + h_local;
     const int h_x = x0 + (tid % TXV) * N;
 
-    // z queue of the own v_z vector: planes k-2, k-1, k (k+1 loaded in the loop)
+    // z queue of the own v_z vector: planes k-2, k-1, k (k+1 loaded in the
+    // loop); the pairs: the same queue of t_vz (taps RN(v + t_v))
     Raw r0 = load_vec_img<V>(prm.v[2], prm, x, j, z0 - 2, true, false);
     Raw r1 = load_vec_img<V>(prm.v[2], prm, x, j, z0 - 1, true, false);
     Raw r2 = load_vec_img<V>(prm.v[2], prm, x, j, z0, true, false);
+    Raw u0 = V::zero(), u1 = V::zero(), u2 = V::zero();
+    if (PAIRS) {
+        u0 = load_vec_img<V>(prm.tv[2], prm, x, j, z0 - 2, true, false);
+        u1 = load_vec_img<V>(prm.tv[2], prm, x, j, z0 - 1, true, false);
+        u2 = load_vec_img<V>(prm.tv[2], prm, x, j, z0, true, false);
+    }
+    auto tap = [&](const Raw &v, const Raw &t) -> AV { return PAIRS ? V::add(V::ld(v), V::ld(t)) : V::ld(v); };
+    auto tap_s = [&](RS v, RS t) -> AS { return PAIRS ? P::add(V::lds(v), V::lds(t)) : V::lds(v); };
     KSum acc;
     int buf = 0;
     for (int k = z0; k < z1; k++) {
         Raw r3 = load_vec_img<V>(prm.v[2], prm, x, j, k + 1, true, false);
+        Raw u3 = PAIRS ? load_vec_img<V>(prm.tv[2], prm, x, j, k + 1, true, false) : V::zero();
         // own v_x and v_y (rows beyond the grid take the even image)
         Raw vx = load_vec_img<V>(prm.v[0], prm, x, j, k, true, true);
         Raw vy = load_vec_img<V>(prm.v[1], prm, x, j, k, false, true);
-        Raw hv;
-        if (halo_loader) hv = load_vec_img<V>(prm.v[1], prm, h_x, h_row, k, false, true);
+        Raw tx = V::zero(), ty = V::zero(), hv, hu = V::zero();
+        if (PAIRS) {
+            tx = load_vec_img<V>(prm.tv[0], prm, x, j, k, true, true);
+            ty = load_vec_img<V>(prm.tv[1], prm, x, j, k, false, true);
+        }
+        if (halo_loader) {
+            hv = load_vec_img<V>(prm.v[1], prm, h_x, h_row, k, false, true);
+            if (PAIRS) hu = load_vec_img<V>(prm.tv[1], prm, h_x, h_row, k, false, true);
+        }
         const int64_t q = x + prm.sy * j + prm.sz * (int64_t)k;
         Raw pv, tv;
         if (active) {
@@ -237,31 +274,43 @@ __global__ void __launch_bounds__(TXV *TY, ENERGY ? 1 : 8) kp_stream(AcParams pr
         // x neighbours of v_x: vx[x-2], vx[x-1], vx[x+N]. The tile-edge lanes
         // load theirs from global memory before the shuffles, so those loads
         // overlap the vector loads above instead of waiting for them.
+        // (of t_vx too for the pairs)
         const bool left_edge = active && lx == 0;
         const bool right_edge = active && (lx == TXV - 1 || x + N >= prm.n[0]);
-        RS el1 = RS(0), el0 = RS(0), err = RS(0);
-        if (left_edge) {
-            el1 = load_x_img<V>(prm.v[0], prm, x - 2, j, k, false);
-            el0 = load_x_img<V>(prm.v[0], prm, x - 1, j, k, false);
-        }
-        if (right_edge) err = load_x_img<V>(prm.v[0], prm, x + N, j, k, false);
-        RS l1 = shfl_rs(V::get(vx, N - 2), 1, true);
-        RS l0 = shfl_rs(V::get(vx, N - 1), 1, true);
-        RS rr = shfl_rs(V::get(vx, 0), 1, false);
-        if (left_edge) { l1 = el1; l0 = el0; }
-        if (right_edge) rr = err;
+        auto xnb = [&](const void *f, const Raw &own_r, RS &l1, RS &l0, RS &rr) {
+            RS el1 = RS(0), el0 = RS(0), err = RS(0);
+            if (left_edge) {
+                el1 = load_x_img<V>(f, prm, x - 2, j, k, false);
+                el0 = load_x_img<V>(f, prm, x - 1, j, k, false);
+            }
+            if (right_edge) err = load_x_img<V>(f, prm, x + N, j, k, false);
+            l1 = shfl_rs(V::get(own_r, N - 2), 1, true);
+            l0 = shfl_rs(V::get(own_r, N - 1), 1, true);
+            rr = shfl_rs(V::get(own_r, 0), 1, false);
+            if (left_edge) { l1 = el1; l0 = el0; }
+            if (right_edge) rr = err;
+        };
+        RS l1, l0, rr, l1t = RS(0), l0t = RS(0), rrt = RS(0);
+        xnb(prm.v[0], vx, l1, l0, rr);
+        if (PAIRS) xnb(prm.tv[0], tx, l1t, l0t, rrt);
         sv[buf][row + 2][lx] = vy;
         if (halo_loader) sv[buf][h_local][tid % TXV] = hv;
+        if (PAIRS) {
+            stv[buf][row + 2][lx] = ty;
+            if (halo_loader) stv[buf][h_local][tid % TXV] = hu;
+        }
         __syncthreads();
         if (active) {
-            const AV ownx = V::ld(vx);
+            const AV ownx = tap(vx, tx);
+            const AS a_l1 = tap_s(l1, l1t), a_l0 = tap_s(l0, l0t), a_rr = tap_s(rr, rrt);
             // node i reads v_x at i-2, i-1, i, i+1 (+1/2)
-            AV R = vstencil<V>(V::shr2(ownx, V::lds(l1), V::lds(l0)), V::shr1(ownx, V::lds(l0)), ownx,
-                               V::shl1(ownx, V::lds(rr)));
-            AV Dy = vstencil<V>(V::ld(sv[buf][row][lx]), V::ld(sv[buf][row + 1][lx]), V::ld(vy),
-                                V::ld(sv[buf][row + 3][lx]));
+            AV R = vstencil<V>(V::shr2(ownx, a_l1, a_l0), V::shr1(ownx, a_l0), ownx, V::shl1(ownx, a_rr));
+            auto vrow = [&](int r) -> AV {
+                return PAIRS ? tap(sv[buf][r][lx], stv[PAIRS ? buf : 0][PAIRS ? r : 0][lx]) : V::ld(sv[buf][r][lx]);
+            };
+            AV Dy = vstencil<V>(vrow(row), vrow(row + 1), tap(vy, ty), vrow(row + 3));
             R = V::add(R, Dy);
-            AV Dz = vstencil<V>(V::ld(r0), V::ld(r1), V::ld(r2), V::ld(r3));
+            AV Dz = vstencil<V>(tap(r0, u0), tap(r1, u1), tap(r2, u2), tap(r3, u3));
             R = V::add(R, Dz);
             if (k == prm.src_k && j == prm.src_j && prm.src_i >= x && prm.src_i < x + N &&
                 prm.step < prm.src_nt) {
@@ -271,12 +320,24 @@ __global__ void __launch_bounds__(TXV *TY, ENERGY ? 1 : 8) kp_stream(AcParams pr
                 for (int e = 0; e < N; e++)
                     if (e == prm.src_i - x) V::set(R, e, P::add(V::aget(R, e), sv_));
             }
-            AV inc = V::mul(coef_vec<V>(prm.b, prm.b_uni, q), R);
+            AV inc = V::mul(coef_v<V>(prm.b, prm.b_uni, q), R);
             Raw pold = pv;
             V::template update<COMP>(pv, tv, inc);
             at<V>(prm.p, q) = pv;
             if (COMP) at<V>(prm.tp, q) = tv;
-            if (ENERGY) {
+            if constexpr (ENERGY && PAIRS) {
+                // (binary32 multipliers, CoefOf)
+                const Raw vc[3] = {vx, vy, r2};
+#pragma unroll
+                for (int e = 0; e < N; e++) {
+                    acc.add(e_term(V::f32(pold, e), V::f32(pv, e), coef_f32<P>(prm.b, prm.b_uni, q + e)));
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        const float vf = V::f32(vc[c], e);
+                        acc.add(e_term(vf, vf, coef_f32<P>(prm.a[c], prm.a_uni[c], q + e)));
+                    }
+                }
+            } else if constexpr (ENERGY) {
                 typename V::RS bs, as[3];
                 const Raw *bvec = prm.b ? reinterpret_cast<const Raw *>(
                                               static_cast<const char *>(prm.b) + q * sizeof(RS)) : nullptr;
@@ -307,6 +368,9 @@ __global__ void __launch_bounds__(TXV *TY, ENERGY ? 1 : 8) kp_stream(AcParams pr
         r0 = r1;
         r1 = r2;
         r2 = r3;
+        u0 = u1;
+        u1 = u2;
+        u2 = u3;
         buf ^= 1;
     }
     if (ENERGY) energy_reduce((double)acc.s + (double)acc.c, prm);
@@ -357,6 +421,8 @@ cudaError_t acoustic_stream_half_step(const AcParams &prm, int prec, int comp, i
     case PREC_BF16: return launch_c<BF16>(prm, comp, half_step, zchunk, energy, st);
     case PREC_FP16_F32ARITH: return launch_c<F16W>(prm, comp ? 3 : 0, half_step, zchunk, energy, st);
     case PREC_BF16_F32ARITH: return launch_c<BF16W>(prm, comp ? 3 : 0, half_step, zchunk, energy, st);
+    case PREC_FP16_PAIRS:
+        return comp ? launch_t<F16WP, 3, 16>(prm, half_step, zchunk, energy, st) : cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }

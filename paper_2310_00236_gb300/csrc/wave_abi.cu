@@ -751,12 +751,13 @@ extern "C" wave_status wave_create(const wave_grid *grid, const double spacing[3
         AcParams prm;
         fill_acoustic_params(c, prm);
         c->e_blocks = acoustic_generic_blocks(prm, c->ndim);
-        // (3D grids of WAVE_FP16_PAIRS: the one-pass step where it applies, else
-        // one thread per point; no streaming kernels)
+        // (3D grids of WAVE_FP16_PAIRS take the same kernels as the stored-value
+        // precisions: the one-pass step, else the streaming kernels, else one
+        // thread per point)
         const bool pairs = prec == WAVE_FP16_PAIRS;
         c->use_fused = !z_cut && (kchoice == 0 || kchoice == 3) &&
                        acoustic_fused_supported(prm, c->ndim, c->prec);
-        c->use_stream = !pairs && !c->use_fused && kchoice != 1 &&
+        c->use_stream = !c->use_fused && kchoice != 1 &&
                         acoustic_stream_supported(prm, c->ndim, c->prec);
         if (z_cut && !c->use_stream && !st)
             st = fail(WAVE_EINVAL, "z slabs need n[0] a multiple of the 16-byte vector width");

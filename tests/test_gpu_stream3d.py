@@ -20,7 +20,8 @@ pytestmark = pytest.mark.gpu
 R, P = O.BC_RIGID, O.BC_PERIODIC
 
 VARIANTS = [("fp16", 0), ("fp16", 3), ("fp16", 6), ("bf16", 3), ("bf16", 0), ("fp32", 0),
-            ("fp32", 3), ("fp16_f32arith", 3), ("fp16_f32arith", 0), ("bf16_f32arith", 3)]
+            ("fp32", 3), ("fp16_f32arith", 3), ("fp16_f32arith", 0), ("bf16_f32arith", 3),
+            ("fp16_pairs", 3)]
 
 
 def _media(shape, seed):
@@ -64,7 +65,8 @@ def test_stream_ragged_tiles_rigid(prec, comp):
     _run((nx, 37, 29), (R, R, R), prec, comp, 6, zchunk=8, energy=True)
 
 
-@pytest.mark.parametrize("prec,comp", [("fp16", 3), ("bf16", 6), ("fp32", 0), ("fp16_f32arith", 3)])
+@pytest.mark.parametrize("prec,comp", [("fp16", 3), ("bf16", 6), ("fp32", 0), ("fp16_f32arith", 3),
+                                       ("fp16_pairs", 3)])
 def test_stream_periodic_and_mixed_with_source(prec, comp):
     nx = 128 if prec != "fp32" else 64
     _run((nx, 20, 17), (P, P, P), prec, comp, 7, zchunk=5, src=True)
@@ -74,6 +76,7 @@ def test_stream_periodic_and_mixed_with_source(prec, comp):
 
 def test_stream_minimum_sizes():
     _run((8, 8, 8), (R, R, R), "fp16", 3, 9, zchunk=2, energy=True)
+    _run((8, 9, 8), (P, R, P), "fp16_pairs", 3, 9, zchunk=1, energy=True)
     _run((8, 9, 8), (P, R, P), "fp16", 6, 9, zchunk=1)
     _run((12, 8, 9), (R, P, R), "fp32", 3, 9, zchunk=4, energy=True)
 
@@ -108,7 +111,8 @@ def _subbox_expect(w, st_full, prec, comp, steps, points):
     return out
 
 
-@pytest.mark.parametrize("prec,comp,kernel", [("fp16", 3, 0), ("fp32", 0, 0), ("fp16", 3, 3), ("fp16_pairs", 3, 0)])
+@pytest.mark.parametrize("prec,comp,kernel", [("fp16", 3, 0), ("fp32", 0, 0), ("fp16", 3, 3), ("fp16_pairs", 3, 0),
+                                              ("fp16_pairs", 3, 2)])
 def test_full_size_512_sampled_bit_exact(prec, comp, kernel):
     """The benchmark workload's grid and media (512^3, smooth random velocity,
     rho = 1000, p = 0 walls, CFL 0.4) in the benchmark's launch configuration,
@@ -169,7 +173,7 @@ def test_full_size_512_sampled_bit_exact(prec, comp, kernel):
 
 
 # ------------------------------------------------------ one-pass step (fused)
-FUSED_VARIANTS = VARIANTS + [("fp16_pairs", 3)]
+FUSED_VARIANTS = VARIANTS
 
 
 def _uniform_rho_run(shape, bc, prec, comp, steps, zchunk, src=False, energy=True, seed=0):
