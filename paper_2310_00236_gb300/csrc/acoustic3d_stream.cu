@@ -267,9 +267,11 @@ __global__ void __launch_bounds__(TXV *TY, ENERGY ? 1 : (IsPairs<P>::value ? 4 :
         }
         const int64_t q = x + prm.sy * j + prm.sz * (int64_t)k;
         Raw pv, tv;
+        AV bco;  // the multiplier b, loaded with the fields (not after the barrier)
         if (active) {
             pv = at<V>(prm.p, q);
             tv = COMP ? at<V>(prm.tp, q) : V::zero();
+            bco = coef_v<V>(prm.b, prm.b_uni, q);
         }
         // x neighbours of v_x: vx[x-2], vx[x-1], vx[x+N]. The tile-edge lanes
         // load theirs from global memory before the shuffles, so those loads
@@ -320,7 +322,7 @@ __global__ void __launch_bounds__(TXV *TY, ENERGY ? 1 : (IsPairs<P>::value ? 4 :
                 for (int e = 0; e < N; e++)
                     if (e == prm.src_i - x) V::set(R, e, P::add(V::aget(R, e), sv_));
             }
-            AV inc = V::mul(coef_v<V>(prm.b, prm.b_uni, q), R);
+            AV inc = V::mul(bco, R);
             Raw pold = pv;
             V::template update<COMP>(pv, tv, inc);
             at<V>(prm.p, q) = pv;
