@@ -63,6 +63,18 @@ __device__ __forceinline__ typename V::RS load_x_img(const void *f, const AcPara
 
 // (multipliers: coef_v of strip_common.cuh, binary32 for the pair precision)
 
+// 16-byte asynchronous copy global -> shared (cp.async, cached in L2 only);
+// src_bytes 0 reads nothing and writes zeros. Completion: cp_wait_all by the
+// issuing thread, then a barrier before other threads read the bytes.
+__device__ __forceinline__ void cp16(void *smem, const void *gmem, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+                 "l"(gmem), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 
 constexpr int TXV = 8;  // threads per tile row
 
@@ -218,8 +230,14 @@ __global__ void __launch_bounds__(TXV *TY, ENERGY ? 1 : (IsPairs<P>::value ? 4 :
     constexpr int N = V::N;
     constexpr int TX = TXV * N;
     constexpr bool PAIRS = IsPairs<P>::value;
+    static_assert(sizeof(Raw) == 16, "one 16-byte vector per thread");
+    // v_x and v_y planes, filled by cp.async one plane ahead (the copies of
+    // plane k + 1 run while plane k is computed, so the plane's barrier waits
+    // on no fresh load); the pairs: t_vx, t_vy likewise
     __shared__ Raw sv[2][TY + 3][TXV];  // v_y, local row r <-> global row y0 - 2 + r
-    __shared__ Raw stv[PAIRS ? 2 : 1][PAIRS ? TY + 3 : 1][TXV];  // the pairs: t_vy likewise
+    __shared__ Raw sx[2][TY][TXV];      // v_x of the own rows
+    __shared__ Raw stv[PAIRS ? 2 : 1][PAIRS ? TY + 3 : 1][TXV];
+    __shared__ Raw stx[PAIRS ? 2 : 1][PAIRS ? TY : 1][TXV];
 
     const int tid = threadIdx.x;
     const int lx = tid % TXV, row = tid / TXV;
@@ -248,23 +266,41 @@ __global__ void __launch_bounds__(TXV *TY, ENERGY ? 1 : (IsPairs<P>::value ? 4 :
     }
     auto tap = [&](const Raw &v, const Raw &t) -> AV { return PAIRS ? V::add(V::ld(v), V::ld(t)) : V::ld(v); };
     auto tap_s = [&](RS v, RS t) -> AS { return PAIRS ? P::add(V::lds(v), V::lds(t)) : V::lds(v); };
+    auto gptr = [&](const void *f, int64_t qq) -> const void * {
+        return static_cast<const char *>(f) + qq * (int64_t)sizeof(RS);
+    };
+    // Copies of plane kk (inside the grid or slab: no z image) into buffer bb:
+    // the own v_x vector (zeros outside the grid: those lanes' results are not
+    // kept and no kept lane reads them), the own and halo v_y rows (rows past
+    // the y faces take the even image, which has sign +1; zeros past x or past
+    // the image range, as load_vec_img gives).
+    auto issue_plane = [&](int kk, int bb) {
+        const int64_t zoff = prm.sz * (int64_t)kk;
+        const int64_t qo = x + prm.sy * j + zoff;
+        cp16(&sx[bb][row][lx], active ? gptr(prm.v[0], qo) : prm.v[0], active ? 16 : 0);
+        if (PAIRS)
+            cp16(&stx[PAIRS ? bb : 0][PAIRS ? row : 0][lx], active ? gptr(prm.tv[0], qo) : prm.tv[0],
+                 active ? 16 : 0);
+        auto vy_row = [&](int xx, int my, int lrow, int lcol) {
+            int jy;
+            img_half(my, prm.n[1], prm.bc[1], jy);
+            const bool ok = xx < prm.n[0] && my >= -3 && my <= prm.n[1] + 2;
+            const int64_t qq = xx + prm.sy * jy + zoff;
+            cp16(&sv[bb][lrow][lcol], ok ? gptr(prm.v[1], qq) : prm.v[1], ok ? 16 : 0);
+            if (PAIRS)
+                cp16(&stv[PAIRS ? bb : 0][PAIRS ? lrow : 0][lcol], ok ? gptr(prm.tv[1], qq) : prm.tv[1],
+                     ok ? 16 : 0);
+        };
+        vy_row(x, j, row + 2, lx);
+        if (halo_loader) vy_row(h_x, h_row, h_local, tid % TXV);
+        cp_commit();
+    };
+    issue_plane(z0, 0);
     KSum acc;
     int buf = 0;
     for (int k = z0; k < z1; k++) {
         Raw r3 = load_vec_img<V>(prm.v[2], prm, x, j, k + 1, true, false);
         Raw u3 = PAIRS ? load_vec_img<V>(prm.tv[2], prm, x, j, k + 1, true, false) : V::zero();
-        // own v_x and v_y (rows beyond the grid take the even image)
-        Raw vx = load_vec_img<V>(prm.v[0], prm, x, j, k, true, true);
-        Raw vy = load_vec_img<V>(prm.v[1], prm, x, j, k, false, true);
-        Raw tx = V::zero(), ty = V::zero(), hv, hu = V::zero();
-        if (PAIRS) {
-            tx = load_vec_img<V>(prm.tv[0], prm, x, j, k, true, true);
-            ty = load_vec_img<V>(prm.tv[1], prm, x, j, k, false, true);
-        }
-        if (halo_loader) {
-            hv = load_vec_img<V>(prm.v[1], prm, h_x, h_row, k, false, true);
-            if (PAIRS) hu = load_vec_img<V>(prm.tv[1], prm, h_x, h_row, k, false, true);
-        }
         const int64_t q = x + prm.sy * j + prm.sz * (int64_t)k;
         Raw pv, tv;
         AV bco;  // the multiplier b, loaded with the fields (not after the barrier)
@@ -273,35 +309,43 @@ __global__ void __launch_bounds__(TXV *TY, ENERGY ? 1 : (IsPairs<P>::value ? 4 :
             tv = COMP ? at<V>(prm.tp, q) : V::zero();
             bco = coef_v<V>(prm.b, prm.b_uni, q);
         }
-        // x neighbours of v_x: vx[x-2], vx[x-1], vx[x+N]. The tile-edge lanes
-        // load theirs from global memory before the shuffles, so those loads
-        // overlap the vector loads above instead of waiting for them.
-        // (of t_vx too for the pairs)
+        // x neighbours of v_x: vx[x-2], vx[x-1], vx[x+N]: the tile-edge lanes
+        // load theirs from global memory here, the others take them from the
+        // adjacent lanes after the barrier (of t_vx too for the pairs)
         const bool left_edge = active && lx == 0;
         const bool right_edge = active && (lx == TXV - 1 || x + N >= prm.n[0]);
-        auto xnb = [&](const void *f, const Raw &own_r, RS &l1, RS &l0, RS &rr) {
-            RS el1 = RS(0), el0 = RS(0), err = RS(0);
-            if (left_edge) {
-                el1 = load_x_img<V>(f, prm, x - 2, j, k, false);
-                el0 = load_x_img<V>(f, prm, x - 1, j, k, false);
+        RS el1 = RS(0), el0 = RS(0), err = RS(0), el1t = RS(0), el0t = RS(0), errt = RS(0);
+        if (left_edge) {
+            el1 = load_x_img<V>(prm.v[0], prm, x - 2, j, k, false);
+            el0 = load_x_img<V>(prm.v[0], prm, x - 1, j, k, false);
+            if (PAIRS) {
+                el1t = load_x_img<V>(prm.tv[0], prm, x - 2, j, k, false);
+                el0t = load_x_img<V>(prm.tv[0], prm, x - 1, j, k, false);
             }
-            if (right_edge) err = load_x_img<V>(f, prm, x + N, j, k, false);
+        }
+        if (right_edge) {
+            err = load_x_img<V>(prm.v[0], prm, x + N, j, k, false);
+            if (PAIRS) errt = load_x_img<V>(prm.tv[0], prm, x + N, j, k, false);
+        }
+        // plane k's copies (issued one plane earlier) are in; once every
+        // thread is past the barrier, buffer buf ^ 1 (plane k - 1) is free
+        cp_wait_all();
+        __syncthreads();
+        if (k + 1 < z1) issue_plane(k + 1, buf ^ 1);
+        const Raw vx = sx[buf][row][lx];
+        const Raw vy = sv[buf][row + 2][lx];
+        const Raw tx = PAIRS ? stx[PAIRS ? buf : 0][PAIRS ? row : 0][lx] : V::zero();
+        const Raw ty = PAIRS ? stv[PAIRS ? buf : 0][PAIRS ? row + 2 : 0][lx] : V::zero();
+        auto xnb = [&](const Raw &own_r, RS e1, RS e0, RS er, RS &l1, RS &l0, RS &rr) {
             l1 = shfl_rs(V::get(own_r, N - 2), 1, true);
             l0 = shfl_rs(V::get(own_r, N - 1), 1, true);
             rr = shfl_rs(V::get(own_r, 0), 1, false);
-            if (left_edge) { l1 = el1; l0 = el0; }
-            if (right_edge) rr = err;
+            if (left_edge) { l1 = e1; l0 = e0; }
+            if (right_edge) rr = er;
         };
         RS l1, l0, rr, l1t = RS(0), l0t = RS(0), rrt = RS(0);
-        xnb(prm.v[0], vx, l1, l0, rr);
-        if (PAIRS) xnb(prm.tv[0], tx, l1t, l0t, rrt);
-        sv[buf][row + 2][lx] = vy;
-        if (halo_loader) sv[buf][h_local][tid % TXV] = hv;
-        if (PAIRS) {
-            stv[buf][row + 2][lx] = ty;
-            if (halo_loader) stv[buf][h_local][tid % TXV] = hu;
-        }
-        __syncthreads();
+        xnb(vx, el1, el0, err, l1, l0, rr);
+        if (PAIRS) xnb(tx, el1t, el0t, errt, l1t, l0t, rrt);
         if (active) {
             const AV ownx = tap(vx, tx);
             const AS a_l1 = tap_s(l1, l1t), a_l0 = tap_s(l0, l0t), a_rr = tap_s(rr, rrt);
