@@ -127,15 +127,28 @@ __global__ void __launch_bounds__(TXV *TY, IsPairs<P>::value ? 4 : 8) kv_stream(
     }
     auto tap = [&](const Raw &v, const Raw &t) -> AV { return PAIRS ? V::add(V::ld(v), V::ld(t)) : V::ld(v); };
     auto tap_s = [&](RS v, RS t) -> AS { return PAIRS ? P::add(V::lds(v), V::lds(t)) : V::lds(v); };
+    // Halo rows of the shared plane by cp.async one plane ahead (planes inside
+    // the grid or slab: only the y image applies, the same on every plane; the
+    // odd image's sign is applied in shared memory after the copy lands, zeros
+    // at the wall node and past x or the image range, as load_vec_img gives)
+    int h_jy = 0;
+    const int h_sg = halo_loader ? img_node(h_row, prm.n[1], prm.bc[1], h_jy) : 0;
+    const bool h_ok = halo_loader && h_sg != 0 && h_x < prm.n[0] && h_row >= -3 && h_row <= prm.n[1] + 2;
+    auto issue_halo = [&](int kk, int bb) {
+        if (!halo_loader) return;
+        const int64_t qq = h_x + prm.sy * (int64_t)h_jy + prm.sz * (int64_t)kk;
+        cp16(&sp[bb][h_local][tid % TXV], h_ok ? static_cast<const char *>(prm.p) + qq * (int64_t)sizeof(RS) : prm.p,
+             h_ok ? 16 : 0);
+        if (PAIRS)
+            cp16(&stp[PAIRS ? bb : 0][PAIRS ? h_local : 0][tid % TXV],
+                 h_ok ? static_cast<const char *>(prm.tp) + qq * (int64_t)sizeof(RS) : prm.tp, h_ok ? 16 : 0);
+        cp_commit();
+    };
+    issue_halo(z0, 0);
     int buf = 0;
     for (int k = z0; k < z1; k++) {
         Raw q3 = load_vec_img<V>(prm.p, prm, x, j, k + 2, true, true);
         Raw u3 = PAIRS ? load_vec_img<V>(prm.tp, prm, x, j, k + 2, true, true) : V::zero();
-        Raw hv, hu = V::zero();
-        if (halo_loader) {
-            hv = load_vec_img<V>(prm.p, prm, h_x, h_row, k, true, true);
-            if (PAIRS) hu = load_vec_img<V>(prm.tp, prm, h_x, h_row, k, true, true);
-        }
         const int64_t q = x + prm.sy * j + prm.sz * (int64_t)k;
         Raw vv[3], tt[3];
         if (active) {
@@ -163,12 +176,18 @@ __global__ void __launch_bounds__(TXV *TY, IsPairs<P>::value ? 4 : 8) kv_stream(
         xnb(prm.p, q1, l0, r0, r1);
         if (PAIRS) xnb(prm.tp, u1, l0t, r0t, r1t);
         sp[buf][row + 1][lx] = q1;
-        if (halo_loader) sp[buf][h_local][tid % TXV] = hv;
-        if (PAIRS) {
-            stp[buf][row + 1][lx] = u1;
-            if (halo_loader) stp[buf][h_local][tid % TXV] = hu;
+        if (PAIRS) stp[PAIRS ? buf : 0][PAIRS ? row + 1 : 0][lx] = u1;
+        cp_wait_all();
+        if (h_ok && h_sg < 0) {
+            sp[buf][h_local][tid % TXV] = V::rneg(sp[buf][h_local][tid % TXV]);
+            if (PAIRS)
+                stp[PAIRS ? buf : 0][PAIRS ? h_local : 0][tid % TXV] =
+                    V::rneg(stp[PAIRS ? buf : 0][PAIRS ? h_local : 0][tid % TXV]);
         }
+        // past the barrier every thread is done with plane k - 1: buffer
+        // buf ^ 1 takes plane k + 1's halo rows
         __syncthreads();
+        if (k + 1 < z1) issue_halo(k + 1, buf ^ 1);
         if (active) {
             const AV own = tap(q1, u1);
             const AS a_l0 = tap_s(l0, l0t), a_r0 = tap_s(r0, r0t), a_r1 = tap_s(r1, r1t);
