@@ -59,8 +59,8 @@ BYTES_2D = (2 + 8 + 8) + (4 + 6 + 4)
 # since is not used (roofline.traffic is then null).
 KERNEL_SOURCES = {"fused": ["acoustic3d_fused.cu", "fused_common.cuh", "vec_policy.cuh", "acoustic_common.cuh",
                             "wave_arith.cuh"],
-                  "kv": ["acoustic3d_stream.cu", "vec_policy.cuh", "acoustic_common.cuh", "wave_arith.cuh"],
-                  "kp": ["acoustic3d_stream.cu", "vec_policy.cuh", "acoustic_common.cuh", "wave_arith.cuh"]}
+                  "kv": ["acoustic3d_stream.cu", "strip_common.cuh", "vec_policy.cuh", "acoustic_common.cuh", "wave_arith.cuh"],
+                  "kp": ["acoustic3d_stream.cu", "strip_common.cuh", "vec_policy.cuh", "acoustic_common.cuh", "wave_arith.cuh"]}
 
 
 def sources_sha(kernel: str) -> str:
