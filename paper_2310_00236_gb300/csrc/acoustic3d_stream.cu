@@ -390,17 +390,26 @@ __global__ void __launch_bounds__(TXV *TY, ENERGY ? 1 : (IsPairs<P>::value ? 4 :
             V::template update<COMP>(pv, tv, inc);
             at<V>(prm.p, q) = pv;
             if (COMP) at<V>(prm.tp, q) = tv;
+            // Energy terms as the one-pass step forms them: v^2 / a with a
+            // uniform a as a product by its reciprocal (a per-point a: the
+            // division), the four terms of a point summed in binary32, then
+            // added to the compensated accumulator
             if constexpr (ENERGY && PAIRS) {
                 // (binary32 multipliers, CoefOf)
                 const Raw vc[3] = {vx, vy, r2};
+                float ia[3];
+#pragma unroll
+                for (int c = 0; c < 3; c++) ia[c] = __frcp_rn(coef_f32<P>(nullptr, prm.a_uni[c], 0));
 #pragma unroll
                 for (int e = 0; e < N; e++) {
-                    acc.add(e_term(V::f32(pold, e), V::f32(pv, e), coef_f32<P>(prm.b, prm.b_uni, q + e)));
+                    float t = e_term(V::f32(pold, e), V::f32(pv, e), coef_f32<P>(prm.b, prm.b_uni, q + e));
 #pragma unroll
                     for (int c = 0; c < 3; c++) {
                         const float vf = V::f32(vc[c], e);
-                        acc.add(e_term(vf, vf, coef_f32<P>(prm.a[c], prm.a_uni[c], q + e)));
+                        t = __fadd_rn(t, prm.a[c] ? e_term(vf, vf, coef_f32<P>(prm.a[c], prm.a_uni[c], q + e))
+                                                  : __fmul_rn(__fmul_rn(vf, vf), ia[c]));
                     }
+                    acc.add(t);
                 }
             } else if constexpr (ENERGY) {
                 typename V::RS bs, as[3];
@@ -413,20 +422,25 @@ __global__ void __launch_bounds__(TXV *TY, ENERGY ? 1 : (IsPairs<P>::value ? 4 :
                     avv[c] = prm.a[c] ? *reinterpret_cast<const Raw *>(static_cast<const char *>(prm.a[c]) +
                                                                       q * sizeof(RS)) : V::zero();
                 from_bits(prm.b_uni, bs);
+                float ia[3];
 #pragma unroll
-                for (int c = 0; c < 3; c++) from_bits(prm.a_uni[c], as[c]);
+                for (int c = 0; c < 3; c++) {
+                    from_bits(prm.a_uni[c], as[c]);
+                    ia[c] = __frcp_rn(P::to_f32(as[c]));
+                }
                 const Raw vz_own = r2;
 #pragma unroll
                 for (int e = 0; e < N; e++) {
                     const float bw = prm.b ? V::f32(bv, e) : P::to_f32(bs);
-                    acc.add(e_term(V::f32(pold, e), V::f32(pv, e), bw));
+                    float t = e_term(V::f32(pold, e), V::f32(pv, e), bw);
                     const Raw vc[3] = {vx, vy, vz_own};
 #pragma unroll
                     for (int c = 0; c < 3; c++) {
-                        const float aw = prm.a[c] ? V::f32(avv[c], e) : P::to_f32(as[c]);
                         const float vf = V::f32(vc[c], e);
-                        acc.add(e_term(vf, vf, aw));
+                        t = __fadd_rn(t, prm.a[c] ? e_term(vf, vf, V::f32(avv[c], e))
+                                                  : __fmul_rn(__fmul_rn(vf, vf), ia[c]));
                     }
+                    acc.add(t);
                 }
             }
         }
