@@ -10,7 +10,11 @@
 //   * x neighbours come from the adjacent lanes by warp shuffle (global loads
 //     only at tile edges), y neighbours from a double-buffered shared-memory
 //     plane (one __syncthreads per plane);
-//   * half and bfloat16 arithmetic is done on packed pairs (f16x2 / bf16x2).
+//   * what a plane's barrier would otherwise wait for (the velocity kernel's
+//     halo rows, the pressure kernel's v_x and v_y planes) is copied into
+//     shared memory by cp.async one plane ahead;
+//   * half and bfloat16 arithmetic is done on packed pairs (f16x2 / bf16x2);
+//     the pair precision adds a T queue, plane and x neighbours per field.
 // Requirements: 3D, n[0] a multiple of VEC. Boundary images (periodic, or the
 // odd / even images of the p = 0 walls) are applied on every halo load.
 #include <cuda_runtime.h>
