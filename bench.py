@@ -863,6 +863,7 @@ def main():
             "traffic": (lambda t: None if t is None else t * npts)(measured_traffic_per_point(dom, args.precision, True)),
             "traffic_sources_sha256": sources_sha(dom),
             "bytes_per_point": bpp, "ms_per_launch": kms / nl,
+            "ms_per_launch_by_kernel": {k: kt[k][1] / kt[k][0] for k in kt},
             "shares": {k: kt[k][1] / sum(v[1] for v in kt.values()) for k in kt}}
     drift16 = abs(r16["e1"] - r16["e0"]) / abs(r16["e0"])
 
