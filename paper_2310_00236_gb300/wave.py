@@ -160,6 +160,8 @@ class Context:
         self.n = tuple(n)
         self.prec = prec
         self.kind = kind
+        self.nrec = 0           # receivers set (wave_set_receivers)
+        self.recorded_steps = 0  # steps of the recorded run (wave_record)
 
     @property
     def shape(self):
@@ -169,6 +171,27 @@ class Context:
     @property
     def npts(self):
         return int(np.prod(self.n[: self.ndim]))
+
+
+def _device_buffer(t, name, min_bytes, dtype=None):
+    """Check a caller's device tensor before its pointer goes to the library,
+    which cannot check device pointers (a short or misplaced buffer would be
+    read or written past its end on the device): a torch tensor of `dtype`
+    (any element type when None), at least min_bytes long, contiguous, on a
+    CUDA device. Raises TypeError / ValueError."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: a torch tensor is required, got {type(t).__name__}")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name}: {t.dtype}, the library writes {dtype}")
+    nbytes = t.numel() * t.element_size()
+    if nbytes < min_bytes:
+        raise ValueError(f"{name}: {nbytes} bytes, the call needs {min_bytes}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: not contiguous")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: not a CUDA tensor")
+    return C.c_void_p(t.data_ptr())
 
 
 def _stream_handle(stream):
@@ -239,14 +262,19 @@ def wave_set_source(ctx: Context, field: int, idx, wavelet):
 
 
 def wave_set_receivers(ctx: Context, field: int, idx, traces=None, capacity_steps=0):
-    """idx: sequence of (i, j[, k]); traces: device tensor of capacity_steps*nrec floats."""
+    """idx: sequence of (i, j[, k]); traces: float32 CUDA tensor of at least
+    capacity_steps * nrec elements (checked here)."""
     idx = np.asarray(idx, dtype=np.int64).reshape(len(idx), -1) if len(idx) else np.zeros((0, 3), np.int64)
     full = np.zeros((idx.shape[0], 3), np.int64)
     full[:, : idx.shape[1]] = idx
     full = np.ascontiguousarray(full)
-    ptr = None if traces is None else C.c_void_p(traces.data_ptr())
+    ptr = None
+    if traces is not None:
+        need = 4 * max(int(capacity_steps), 0) * full.shape[0]
+        ptr = _device_buffer(traces, "traces", need, _torch().float32)
     _check(lib().wave_set_receivers(ctx.ptr, field, full.ctypes.data_as(C.POINTER(C.c_int64)),
                                     full.shape[0], ptr, capacity_steps))
+    ctx.nrec = full.shape[0]
 
 
 def wave_step(ctx: Context, n: int):
@@ -258,15 +286,28 @@ def wave_half_step(ctx: Context, which: int):
 
 
 def wave_set_z_ghosts(ctx: Context, p_lo=None, p_hi=None, vz_lo=None, vz_hi=None):
-    """Ghost-plane buffers (device tensors of two planes each, laid out as
-    wave_get_layout says) of the cut faces; None for a face of the grid."""
-    ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
-    _check(lib().wave_set_z_ghosts(ctx.ptr, ptr(p_lo), ptr(p_hi), ptr(vz_lo), ptr(vz_hi)))
+    """Ghost-plane buffers (CUDA tensors of at least two planes each, laid out
+    as wave_get_layout says; checked here) of the cut faces; None for a face
+    of the grid."""
+    bufs = list(zip(("p_lo", "p_hi", "vz_lo", "vz_hi"), (p_lo, p_hi, vz_lo, vz_hi)))
+    for nm, t in bufs:
+        if t is not None:
+            _device_buffer(t, nm, 0)
+    need = 0
+    if any(t is not None for _, t in bufs):
+        _, plane, eb = wave_get_layout(ctx)
+        need = 2 * plane * eb
+    ptrs = [None if t is None else _device_buffer(t, nm, need) for nm, t in bufs]
+    _check(lib().wave_set_z_ghosts(ctx.ptr, *ptrs))
 
 
 def wave_copy_planes(ctx: Context, field: int, z_first: int, nplanes: int, dst):
-    """Copy planes z_first .. z_first + nplanes - 1 of a field into the device tensor dst."""
-    _check(lib().wave_copy_planes(ctx.ptr, field, int(z_first), int(nplanes), C.c_void_p(dst.data_ptr())))
+    """Copy planes z_first .. z_first + nplanes - 1 of a field into the CUDA
+    tensor dst (at least nplanes planes of the layout; checked here)."""
+    _device_buffer(dst, "dst", 0)
+    _, plane, eb = wave_get_layout(ctx)
+    ptr = _device_buffer(dst, "dst", max(int(nplanes), 0) * plane * eb)
+    _check(lib().wave_copy_planes(ctx.ptr, field, int(z_first), int(nplanes), ptr))
 
 
 def wave_get_layout(ctx: Context):
@@ -277,7 +318,10 @@ def wave_get_layout(ctx: Context):
 
 
 def wave_set_energy_trace(ctx: Context, device_energy=None, capacity=0):
-    ptr = None if device_energy is None else C.c_void_p(device_energy.data_ptr())
+    """device_energy: float64 CUDA tensor of at least capacity elements (checked here)."""
+    ptr = None
+    if device_energy is not None:
+        ptr = _device_buffer(device_energy, "device_energy", 8 * max(int(capacity), 0), _torch().float64)
     _check(lib().wave_set_energy_trace(ctx.ptr, ptr, capacity))
 
 
@@ -352,15 +396,16 @@ def wave_reset(ctx: Context):
 def wave_record(ctx: Context, nsteps: int, ncheckpoints: int = 0):
     """Forward run of nsteps steps with checkpoints for the adjoint."""
     _check(lib().wave_record(ctx.ptr, int(nsteps), int(ncheckpoints)))
+    ctx.recorded_steps = int(nsteps)
 
 
 def wave_adjoint_step(ctx: Context, n: int, residual=None):
-    """n adjoint steps; residual: device float32 tensor [nsteps, nrec]."""
+    """n adjoint steps; residual: float32 CUDA tensor [nsteps, nrec] of the
+    recorded run (its size is checked here)."""
     ptr = None
     if residual is not None:
-        if residual.dtype != _torch().float32 or not residual.is_cuda or not residual.is_contiguous():
-            raise TypeError("residual must be a contiguous float32 CUDA tensor")
-        ptr = C.c_void_p(residual.data_ptr())
+        need = 4 * ctx.recorded_steps * ctx.nrec
+        ptr = _device_buffer(residual, "residual", need, _torch().float32)
     _check(lib().wave_adjoint_step(ctx.ptr, int(n), ptr))
 
 
@@ -370,8 +415,9 @@ def wave_get_gradient(ctx: Context, out=None):
     torch = _torch()
     if out is None:
         out = torch.empty(tuple(ctx.n[:ctx.ndim][::-1]), dtype=torch.float32, device="cuda")
+    ptr = _device_buffer(out, "out", 4 * ctx.npts, torch.float32)
     left = C.c_int64()
-    _check(lib().wave_get_gradient(ctx.ptr, C.c_void_p(out.data_ptr()), C.byref(left)))
+    _check(lib().wave_get_gradient(ctx.ptr, ptr, C.byref(left)))
     return out, left.value
 
 

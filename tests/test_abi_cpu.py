@@ -135,3 +135,40 @@ def test_static_energy_binding_rejects_bad_tensors(lib):
         with pytest.raises(ValueError) as e:
             call(**kw)
         assert word in str(e.value), (kw, str(e.value))
+
+
+def test_binding_checks_device_buffers_before_the_call():
+    """Receivers, the energy trace, the adjoint residual, the gradient output,
+    ghost planes and plane copies take caller device buffers that the library
+    cannot check; the binding refuses a tensor of the wrong element type, too
+    short, not contiguous, not a tensor, or on the host, before any call into
+    the library (the context here has no library object behind it)."""
+    import torch
+    ctx = W.Context(None, 2, (16, 12, 1), W.WAVE_FP16, W.WAVE_ACOUSTIC)
+    recs = [(1, 2), (3, 4), (5, 6)]
+    f32 = lambda n: torch.zeros(n, dtype=torch.float32)
+    cases = [
+        (lambda: W.wave_set_receivers(ctx, W.WAVE_F_P, recs, f32(3 * 10), 10), "CUDA"),
+        (lambda: W.wave_set_receivers(ctx, W.WAVE_F_P, recs, f32(3 * 10 - 1), 10), "bytes"),
+        (lambda: W.wave_set_receivers(ctx, W.WAVE_F_P, recs, torch.zeros(30, dtype=torch.float64), 10),
+         "float32"),
+        (lambda: W.wave_set_receivers(ctx, W.WAVE_F_P, recs, f32(60)[::2], 10), "contiguous"),
+        (lambda: W.wave_set_receivers(ctx, W.WAVE_F_P, recs, np.zeros(30, np.float32), 10), "torch tensor"),
+        (lambda: W.wave_set_energy_trace(ctx, torch.zeros(5, dtype=torch.float64), 6), "bytes"),
+        (lambda: W.wave_set_energy_trace(ctx, f32(6), 6), "float64"),
+        (lambda: W.wave_set_energy_trace(ctx, torch.zeros(6, dtype=torch.float64), 6), "CUDA"),
+        (lambda: W.wave_get_gradient(ctx, f32(16 * 12 - 1)), "bytes"),
+        (lambda: W.wave_get_gradient(ctx, torch.zeros(16 * 12, dtype=torch.float16)), "float32"),
+        (lambda: W.wave_copy_planes(ctx, W.WAVE_F_P, 0, 2, torch.zeros(64, dtype=torch.int16)), "CUDA"),
+        (lambda: W.wave_set_z_ghosts(ctx, None, torch.zeros(64, dtype=torch.int16)), "CUDA"),
+    ]
+    for call, word in cases:
+        with pytest.raises((ValueError, TypeError)) as e:
+            call()
+        assert word in str(e.value), (word, str(e.value))
+    # the residual of a recorded run of 7 steps at 3 receivers
+    ctx.nrec, ctx.recorded_steps = 3, 7
+    for res, word in [(f32(20), "bytes"), (torch.zeros(21, dtype=torch.float64), "float32"), (f32(21), "CUDA")]:
+        with pytest.raises(ValueError) as e:
+            W.wave_adjoint_step(ctx, 7, res)
+        assert word in str(e.value), (word, str(e.value))

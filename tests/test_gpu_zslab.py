@@ -101,6 +101,11 @@ def test_slab_call_order_and_ghost_checks():
         with pytest.raises(W.WaveError) as e:
             W.wave_set_z_ghosts(s.ctx, g, g, g, g)      # the z-lo face is the grid's wall
         assert e.value.status == W.WAVE_EINVAL
+        one_plane = g[: W.wave_get_layout(s.ctx)[1]]
+        with pytest.raises(ValueError):                 # refused by the binding, before the library
+            W.wave_set_z_ghosts(s.ctx, None, one_plane, None, one_plane)
+        with pytest.raises(ValueError):
+            W.wave_copy_planes(s.ctx, W.WAVE_F_P, 0, 2, one_plane)
         W.wave_half_step(s.ctx, 0)
         with pytest.raises(W.WaveError) as e:
             W.wave_half_step(s.ctx, 0)                  # the pressure half is due
